@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Throughput of the per-voxel orientation pipeline on GB300.
+
+One step = the whole hot path (sigma-gradient, rho-smoothed structure tensor,
+eigen-solve, HA / IA / FA under the mask) over one 512^3 uint16 volume: the
+left-ventricle-like annulus (radii 120/220, axis tilted 10 deg, period 6,
+HA +70 -> -70, IA field 5 deg / 40 voxels, Poisson-like 5% noise, annulus mask),
+sigma = 2, rho = 6, FP32 outputs.  Inputs are seeded synthetic volumes
+(no scan data ships with the library).
+
+Arms
+  --impl ours (default): the CUDA library through its C ABI.  Both arithmetic
+      forms are timed; the headline `value` is the mixed form (FP16-held
+      gradient, FP32 sums, FP32 closed-form eigen with FP64 re-solve), the
+      FP32 form is reported beside it.  `e2e` times the same call with host
+      buffers (pinned), copies inside the timed region.
+  --impl reference: the FP64 CPU oracle on the host cores, each step a bounded
+      sample (a box of the same volume), as the baseline arm.
+
+Timing: CUDA events on the launching stream, W warm-up steps, K timed steps,
+barrier + synchronize on both sides, max over ranks.  The volume plus the
+plan's scratch (6.4 GB per step) exceed the 129 MB L2, so no flush is needed.
+Under torchrun every rank runs its own volume (weak scaling, no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxels/s for tensor+eigen+HA/IA/FA at 1 GB300, mixed vs FP32 form at ≤0.5°; % roofline"
+UNIT = "voxels/s"
+SM_COUNT = 152
+FP32_LANES = 128  # FP32 FMA lanes per SM
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=512, help="cube edge (512 = the measured workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _workload(size: int):
+    from paper_2508_07476_gb300 import synth
+    W = synth.lv_annulus_512(size)
+    return W
+
+
+def _fma_per_voxel(rs: int, rr: int) -> int:
+    """Algorithmic FMAs per interior voxel: 8 sigma passes, 6 products, 18 rho passes."""
+    return 8 * (2 * rs + 1) + 6 + 18 * (2 * rr + 1)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_2508_07476_gb300 import synth
+    W = _workload(args.size)
+    n = args.size
+    box = (min(128, n), min(128, n), min(64, n))
+    h = oracle.radius(W.sigma) + oracle.radius(W.rho)
+    rng = np.random.default_rng(2024)
+    centre = synth.frame_of(W.spec)
+    # one slab of the volume holds every sample box plus its halo
+    z0 = max(0, n // 2 - box[2] // 2 - h)
+    z1 = min(n, z0 + box[2] + 2 * h)
+    vol_slab, mask_slab = synth.generate(W.spec, (z0, z1))
+    vol = np.zeros((n, n, n), np.uint16)
+    mask = np.zeros((n, n, n), np.uint8)
+    vol[z0:z1] = vol_slab
+    mask[z0:z1] = mask_slab
+    zlo = min(max(0, n // 2 - box[2] // 2), n - box[2])
+
+    def step():
+        lo = (int(rng.integers(0, n - box[0] + 1)), int(rng.integers(0, n - box[1] + 1)), zlo)
+        t = time.perf_counter()
+        oracle.pipeline(vol, W.sigma, W.rho, centre[0], centre[1], mask=mask, lo=lo, n=box)
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    per = float(np.mean(ts))
+    value = box[0] * box[1] * box[2] / per
+    cores = oracle.num_threads()
+    sample = f"oracle (FP64, OpenMP) on a {box[0]}x{box[1]}x{box[2]} box of the {n}^3 volume per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded annulus volume)",
+        "config": {"workload": W.name, "dims": [n, n, n], "sigma": W.sigma, "rho": W.rho, "mask": True},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------- ours
+def _cpu_baseline(W, vol, mask, seconds: float) -> dict:
+    from oracle import oracle
+    from paper_2508_07476_gb300 import synth
+    n = vol.shape[0]
+    box = (min(128, n), min(128, n), min(64, n))
+    cen, ax = synth.frame_of(W.spec)
+    rng = np.random.default_rng(7)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        lo = tuple(int(rng.integers(0, d - b + 1)) for d, b in zip((n, n, n), box))
+        oracle.pipeline(vol, W.sigma, W.rho, cen, ax, mask=mask, lo=lo, n=box)
+        done += box[0] * box[1] * box[2]
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{done // (box[0] * box[1] * box[2])} boxes of {box[0]}x{box[1]}x{box[2]} voxels of the "
+                      f"{n}^3 volume ({el:.1f} s)"}
+
+
+def _accuracy(W, vol, mask, outs) -> dict:
+    """Sampled parity of the timed outputs against the oracle (boxes of the volume)."""
+    from oracle import oracle
+    from paper_2508_07476_gb300 import synth
+    n = vol.shape[0]
+    cen, ax = synth.frame_of(W.spec)
+    b = min(12, n)
+    rng = np.random.default_rng(11)
+    boxes = [(0, 0, 0), (n - b, n - b, n - b), (n // 2 - min(120, n // 4), n // 2, n // 2)]
+    boxes += [tuple(int(rng.integers(0, n - b + 1)) for _ in range(3)) for _ in range(3)]
+    worst = {"dir": 0.0, "ha": 0.0, "ia": 0.0, "fa": 0.0, "graded": 0}
+    for lo in boxes:
+        lo = tuple(min(max(0, v), n - b) for v in lo)
+        ora = oracle.pipeline(vol, W.sigma, W.rho, cen, ax, mask=mask, lo=lo, n=(b, b, b))
+        sl = (slice(lo[2], lo[2] + b), slice(lo[1], lo[1] + b), slice(lo[0], lo[0] + b))
+        inside = mask[sl].astype(bool)
+        sel = inside & (ora["fa"] >= 0.1) & np.isfinite(ora["ha"])
+        if sel.any():
+            v = outs["v"][(slice(None),) + sl][:, sel]
+            d = np.degrees(np.arccos(np.clip(np.abs((v * ora["v"][:, sel]).sum(0)), 0, 1))).max()
+            dha = np.abs((outs["ha"][sl][sel] - ora["ha"][sel] + 90.0) % 180.0 - 90.0).max()
+            dia = np.abs(np.abs(outs["ia"][sl][sel]) - np.abs(ora["ia"][sel])).max()
+            worst["dir"] = max(worst["dir"], float(d))
+            worst["ha"] = max(worst["ha"], float(dha))
+            worst["ia"] = max(worst["ia"], float(dia))
+            worst["graded"] += int(sel.sum())
+        if inside.any():
+            worst["fa"] = max(worst["fa"], float(np.abs(outs["fa"][sl][inside] - ora["fa"][inside]).max()))
+    worst["within_tolerance"] = worst["dir"] <= 0.5 and worst["ha"] <= 0.5 and worst["ia"] <= 0.5 and \
+        worst["fa"] <= 2e-3
+    return worst
+
+
+def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int):
+    """(algorithmic FMAs, algorithmic bytes) of one launch over nvox output voxels."""
+    if name == "grad_products":
+        return nvox * (8 * (2 * rs + 1) + 6), nvox * (2 + 24)
+    if name in ("rho_x", "rho_y", "rho_z"):
+        return nvox * 6 * (2 * rr + 1), nvox * 48
+    if name == "eig_angles":
+        return 0, nvox * (24 + 1 + 24)
+    return 0, 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2508_07476_gb300 import _lib, synth
+    import __graft_entry__
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    __graft_entry__.build()
+    W = _workload(args.size)
+    vol, mask = synth.generate(W.spec)
+    n = args.size
+    nvox = n ** 3
+    cen, ax = synth.frame_of(W.spec)
+    d_vol = torch.from_numpy(vol.view(np.int16)).cuda()
+    d_mask = torch.from_numpy(mask).cuda()
+    outs = {"v": torch.empty((3, n, n, n), device="cuda"), "ha": torch.empty((n, n, n), device="cuda"),
+            "ia": torch.empty((n, n, n), device="cuda"), "fa": torch.empty((n, n, n), device="cuda")}
+    item = _lib.make_item(d_vol, (n, n, n), d_mask, outs["v"], outs["ha"], outs["ia"], outs["fa"])
+    stream = torch.cuda.current_stream()
+    rs, rr = _lib.ct_radius(W.sigma), _lib.ct_radius(W.rho)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    forms = {}
+    accuracy = {}
+    kernels = {}
+    clocks = None
+    launches_per_step = None
+    for name, prec in (("fp32", _lib.CT_PREC_FP32), ("mixed", _lib.CT_PREC_MIXED)):
+        plan = _lib.ct_plan_create(_lib.make_params(W.sigma, W.rho, cen, ax, prec), (n, n, n))
+        try:
+            for _ in range(args.warmup):
+                _lib.ct_run_chunks(plan, [item], False, stream)
+            torch.cuda.synchronize()
+            _lib.ct_plan_stats(plan, reset=True)
+            headline = name == "mixed"
+            _lib.ct_plan_profile(plan, True)
+            sampler = ClockSampler(local) if headline and rank == 0 else None
+            barrier()
+            torch.cuda.synchronize()
+            if sampler:
+                sampler.start()
+                time.sleep(0.3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                _lib.ct_run_chunks(plan, [item], False, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            if sampler:
+                clocks = sampler.stop()
+            ms = e0.elapsed_time(e1) / args.steps
+            ms = max_over_ranks(ms)
+            kt = _lib.ct_plan_kernel_times(plan)
+            _lib.ct_plan_profile(plan, False)
+            st = _lib.ct_plan_stats(plan, reset=True)
+            forms[name] = {"ms_per_step": ms, "voxels_per_s": world * nvox / (ms * 1e-3),
+                           "fallback_voxels_per_step": st["fallback_voxels"] / args.steps}
+            kernels[name] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in kt.items()}
+            if headline:
+                launches_per_step = st["launches"] / args.steps
+            host_outs = {k: t.cpu().numpy() for k, t in outs.items()}
+            accuracy[name] = _accuracy(W, vol, mask, host_outs) if rank == 0 else None
+        finally:
+            _lib.ct_plan_destroy(plan)
+
+    head = forms["mixed"]
+    peaks, peak_kind = _peaks()
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fma_peak = SM_COUNT * FP32_LANES * sm_mhz_max * 1e6  # FMA/s
+    # dominant kernel of the headline form
+    km = kernels["mixed"]
+    dom = max(km, key=lambda k: km[k]["avg_ms"] * km[k]["launches"])
+    fmas, byts = _kernel_algorithmic(dom, nvox, rs, rr)
+    avg_s = km[dom]["avg_ms"] * 1e-3
+    if fmas > 0:
+        ach = 2.0 * fmas / avg_s / 1e12
+        peak = 2.0 * fma_peak / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x "
+                                   f"{sm_mhz_max:.0f} MHz ({peak_kind} sm_max_mhz)"}
+    else:
+        ach = byts / avg_s / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
+    f_vox = _fma_per_voxel(rs, rr)
+    path_roof = min(fma_peak / f_vox, peaks["hbm_gbs"] * 1e9 / 27.0)
+    pipeline_roofline = {"voxels_per_s_roofline": path_roof, "fma_per_voxel": f_vox,
+                         "min_bytes_per_voxel": 27, "frac_fp32": forms["fp32"]["voxels_per_s"] / world / path_roof,
+                         "frac_mixed": head["voxels_per_s"] / world / path_roof,
+                         "bound": "FP32 FMA (min of FMA/s / F and HBM / bytes)"}
+
+    e2e = None
+    if not args.no_e2e:
+        plan = _lib.ct_plan_create(_lib.make_params(W.sigma, W.rho, cen, ax, _lib.CT_PREC_MIXED), (n, n, n))
+        try:
+            h_vol = torch.from_numpy(vol.view(np.int16)).pin_memory()
+            h_mask = torch.from_numpy(mask).pin_memory()
+            h_out = {"v": torch.empty((3, n, n, n)).pin_memory(), "ha": torch.empty((n, n, n)).pin_memory(),
+                     "ia": torch.empty((n, n, n)).pin_memory(), "fa": torch.empty((n, n, n)).pin_memory()}
+            hitem = _lib.make_item(h_vol, (n, n, n), h_mask, h_out["v"], h_out["ha"], h_out["ia"], h_out["fa"])
+            _lib.ct_run_chunks(plan, [hitem], True)
+            _lib.ct_plan_stats(plan, reset=True)
+            barrier()
+            t0 = time.perf_counter()
+            k_e2e = max(1, min(args.steps, 5))
+            for _ in range(k_e2e):
+                _lib.ct_run_chunks(plan, [hitem], True)
+            torch.cuda.synchronize()
+            el = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+            st = _lib.ct_plan_stats(plan, reset=True)
+            e2e = {"value": world * nvox / el, "unit": UNIT, "h2d_bytes_per_step": st["h2d_bytes"] // k_e2e,
+                   "d2h_bytes_per_step": st["d2h_bytes"] // k_e2e, "ms_per_step": el * 1e3,
+                   "timing": "wall clock around the synchronous host-buffer call"}
+        finally:
+            _lib.ct_plan_destroy(plan)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = _cpu_baseline(W, vol, mask, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": head["voxels_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded annulus volume)",
+            "config": {"workload": W.name, "dims": [n, n, n], "sigma": W.sigma, "rho": W.rho, "mask": True,
+                       "outputs": "f32 vector, HA, IA, FA", "precision": "mixed (FP16-held gradient)",
+                       "l2": "inputs larger than L2 (268 MB volume + 6.4 GB scratch per step)",
+                       "parallelism": f"{world} independent volume(s), one per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches_per_step": launches_per_step, "clocks": clocks, "forms": forms,
+            "pipeline_roofline": pipeline_roofline, "accuracy": accuracy, "kernels": kernels,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

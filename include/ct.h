@@ -1,0 +1,201 @@
+/*
+ * ct.h -- C ABI of the GB300 structure-tensor orientation library.
+ *
+ * The library computes, per voxel of a 3D image volume, the orientation of the
+ * local fibre texture and the cardiac descriptors derived from it (Summary;
+ * Figure 1; Architecture, "orientation"):
+ *   1. the image gradient by Gaussian-derivative filters at noise scale sigma,
+ *   2. the structure tensor: the six products g_a g_b smoothed by a Gaussian
+ *      at integration scale rho,
+ *   3. its eigen-decomposition; the eigenvector of the SMALLEST eigenvalue is
+ *      the fibre direction ("third eigenvector", Figure 1b),
+ *   4. helical angle (HA), intrusion angle (IA) and fractional anisotropy (FA)
+ *      in a cylindrical frame about a given left-ventricle centre and axis
+ *      (Figure 1c), under an optional myocardial mask (Figure 1a),
+ * over whole volumes or padded chunks of them (Implementation).
+ *
+ * Definitions (the paper prints no formulas; these are the textbook ones):
+ *   taps      R(s) = floor(truncate * s + 0.5); w_k = exp(-k^2/2s^2) / sum_j exp(-j^2/2s^2),
+ *             c_k = (k / s^2) w_k, k = -R..R
+ *   gradient  g_x(p) = sum_{i,j,k} c_i w_j w_k I(p + (i,j,k)), cyclically for y, z
+ *   tensor    S_ab(p) = sum_{i,j,k} w_i w_j w_k g_a g_b (p + (i,j,k))   (rho taps)
+ *   edges     a coordinate beyond the GLOBAL volume is clamped to the edge voxel,
+ *             both for the image and for the product field
+ *   frame     e_z = axis/|axis|, r = (p - c) - ((p - c).e_z) e_z, e_r = r/|r|, e_t = e_z x e_r
+ *   angles    v oriented so that v.e_t > 0 (v.e_z >= 0 if v.e_t = 0);
+ *             HA = atan2(v.e_z, v.e_t), IA = asin(v.e_r), in degrees
+ *   FA        sqrt(1/2) |(l1-l2, l2-l3, l3-l1)| / |(l1, l2, l3)| with l clamped to >= 0;
+ *             0 when all eigenvalues are 0
+ *
+ * Conventions
+ *   - Volumes are uint16 [nz][ny][nx], x fastest; masks uint8 0/1 in the same layout.
+ *   - Dimensions, positions and boxes are (x, y, z) in voxel units; a box is
+ *     (lo[3], n[3]) in GLOBAL voxel indices of the plan's volume.
+ *   - Multi-component fields are SoA planes: component k of box voxel i at
+ *     plane k * nvox + i (nvox = n[0]*n[1]*n[2], i in x-fastest order).
+ *     Tensor planes: (xx, yy, zz, xy, xz, yz).  Vector planes: (x, y, z).
+ *   - Every function returns a ct_status; none aborts or throws.  On error,
+ *     ct_last_error() gives a message for the calling thread.
+ *   - Device pointers must be allocated on the plan's device, aligned to their
+ *     element size.  Stream arguments are cudaStream_t passed as void* (NULL =
+ *     the legacy default stream); stage calls are asynchronous on that stream.
+ *   - The caller owns every input and output buffer; the plan owns its scratch
+ *     memory, streams and staging buffers and frees them in ct_plan_destroy.
+ *   - Asynchronous device errors surface as CT_ERR_CUDA from the next call
+ *     that synchronises (ct_run_chunks, ct_plan_sync, ct_plan_stats).
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     call returns CT_ERR_NO_DEVICE.
+ */
+#ifndef CT_H
+#define CT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ct_status;
+#define CT_OK 0
+#define CT_ERR_INVALID (-1)     /* bad argument: the message names it */
+#define CT_ERR_OOM (-2)         /* device or pinned host allocation failed */
+#define CT_ERR_CUDA (-3)        /* a CUDA call or kernel failed */
+#define CT_ERR_TIMEOUT (-4)     /* a bounded wait ran out */
+#define CT_ERR_NO_DEVICE (-5)   /* no usable CUDA device */
+#define CT_ERR_UNSUPPORTED (-6) /* valid request outside what the kernels implement */
+
+/* Arithmetic of the path. */
+#define CT_PREC_FP32 0  /* FP32 gradient, tensor and eigen-solve (FP32 Jacobi re-solve
+                           for near-degenerate voxels) */
+#define CT_PREC_MIXED 1 /* gradient held in FP16 (scaled by 2^-8), products and sums in
+                           FP32, FP32 closed-form eigen-solve with an FP64 re-solve for
+                           near-degenerate voxels */
+
+/* Output encodings. */
+#define CT_OUT_F32 0
+#define CT_OUT_F16 1
+#define CT_OUT_U8Q 2 /* angles only: code = round((deg + 90) * 256 / 180) mod 256,
+                        bin 180/256 deg; masked / undefined voxels get code 0 */
+
+typedef struct ct_params {
+  double sigma;        /* noise scale of the gradient, voxels, > 0 */
+  double rho;          /* integration scale of the tensor smoothing, voxels, > 0 */
+  double truncate;     /* radius factor; 0 selects 4.0 */
+  double lv_center[3]; /* left-ventricle centre (x, y, z), global voxel units, finite */
+  double lv_axis[3];   /* left-ventricle axis (x, y, z); need not be unit; not zero */
+  int32_t precision;   /* CT_PREC_* */
+  int32_t vec_type;    /* CT_OUT_F32 or CT_OUT_F16 */
+  int32_t angle_type;  /* CT_OUT_F32, CT_OUT_F16 or CT_OUT_U8Q */
+  int32_t fa_type;     /* CT_OUT_F32 or CT_OUT_F16 */
+  float fill_value;    /* value written outside the mask (all outputs) and for HA/IA on
+                          the axis; NaN is the usual choice */
+  int32_t flags;       /* reserved, must be 0 */
+  int64_t chunk[3];    /* ct_run_chunks chunk size (x, y, z); 0 = whole extent */
+} ct_params;
+
+typedef struct ct_plan_s* ct_plan;
+
+/*
+ * Create a plan for volumes of global size vol_dims (x, y, z) on the current
+ * CUDA device.  Validates params (CT_ERR_INVALID) and the supported radius
+ * range (R(sigma) <= 12, R(rho) <= 36 at truncate 4, else CT_ERR_UNSUPPORTED).
+ * Scratch memory is allocated lazily by the first call that needs it.
+ */
+ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_plan* out);
+ct_status ct_plan_destroy(ct_plan plan);
+
+/*
+ * Stage: structure tensor (Figure 1b).  d_vol holds the input box (in_lo,
+ * in_n) of the plan's volume as a dense uint16 [in_n.z][in_n.y][in_n.x]
+ * array.  d_S receives the 6 FP32 tensor planes over the output box (out_lo,
+ * out_n).  The output box grown by R(sigma) + R(rho) on every side and then
+ * clipped to the volume must lie inside the input box (that is the halo a
+ * padded chunk needs); CT_ERR_INVALID otherwise.
+ */
+ct_status ct_structure_tensor(ct_plan plan, const uint16_t* d_vol, const int64_t in_lo[3], const int64_t in_n[3],
+                              const int64_t out_lo[3], const int64_t out_n[3], float* d_S, void* stream);
+
+/*
+ * Stage: eigen-decomposition of n tensors (6 FP32 planes of n).  d_evals
+ * (nullable) receives the 3 eigenvalues ascending; d_evec receives the unit
+ * eigenvector of the smallest eigenvalue (3 planes), its sign chosen so that
+ * the largest-magnitude component is positive.  Uses the plan's precision.
+ */
+ct_status ct_eig_smallest(ct_plan plan, const float* d_S, int64_t n, float* d_evals, float* d_evec, void* stream);
+
+/*
+ * Stage: HA, IA, FA over the box (out_lo, out_n) from the smallest
+ * eigenvectors and the eigenvalues (3 FP32 planes each, box-shaped), in the
+ * plan's frame.  d_mask (nullable) is a box-shaped uint8 array; 0 = outside.
+ * Outputs (each nullable) use the plan's encodings: d_vec 3 planes of the
+ * oriented fibre vector (v.e_t > 0; largest-magnitude component positive where
+ * no frame exists), d_ha, d_ia, d_fa one plane each.
+ */
+ct_status ct_angles(ct_plan plan, const float* d_evec, const float* d_evals, const int64_t out_lo[3],
+                    const int64_t out_n[3], const uint8_t* d_mask, void* d_vec, void* d_ha, void* d_ia, void* d_fa,
+                    void* stream);
+
+/* One volume for the fused path. */
+typedef struct ct_item {
+  const uint16_t* vol;  /* uint16 [dims.z][dims.y][dims.x] */
+  const uint8_t* mask;  /* nullable, same layout */
+  int64_t dims[3];      /* (x, y, z) */
+  double sigma, rho;    /* <= 0: the plan's values */
+  double lv_center[3];  /* frame of this item ... */
+  double lv_axis[3];    /* ... all-zero axis: the plan's centre and axis */
+  void* vec;            /* outputs, nullable, plan encodings, planes over the whole item */
+  void* ha;
+  void* ia;
+  void* fa;
+} ct_item;
+
+/*
+ * Fused hot path: the whole pipeline for each item.  items_on_host = 0: every
+ * pointer of the items is a device pointer and the work is enqueued on
+ * `stream` (returns without waiting).  items_on_host = 1: pointers are host
+ * pointers (pinned or pageable); the volume is processed in chunks of the
+ * plan's chunk size with a halo of R(sigma) + R(rho), copied through the
+ * plan's pinned staging buffers on two streams; the call returns when every
+ * output is in host memory.  Results do not depend on the chunking.
+ */
+ct_status ct_run_chunks(ct_plan plan, const ct_item* items, int32_t n_items, int32_t items_on_host, void* stream);
+
+/* Wait for all work of the plan; report asynchronous errors. */
+ct_status ct_plan_sync(ct_plan plan);
+
+typedef struct ct_stats {
+  int64_t voxels;          /* output voxels processed */
+  int64_t fallback_voxels; /* voxels re-solved by the near-degenerate path */
+  int64_t launches;        /* kernels launched */
+  int64_t h2d_bytes;       /* bytes copied host -> device by ct_run_chunks */
+  int64_t d2h_bytes;       /* bytes copied device -> host by ct_run_chunks */
+} ct_stats;
+
+/* Counters since creation or the last reset (synchronises the plan). */
+ct_status ct_plan_stats(ct_plan plan, ct_stats* out, int32_t reset);
+
+/*
+ * Per-kernel timing.  While enabled, the plan records a CUDA event pair on the
+ * launching stream around every kernel it launches; ct_plan_kernel_times
+ * synchronises, adds the elapsed times up per kernel name, returns them
+ * (at most `capacity` entries, *count = entries written) and clears them.
+ */
+typedef struct ct_kernel_time {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} ct_kernel_time;
+
+ct_status ct_plan_profile(ct_plan plan, int32_t enable);
+ct_status ct_plan_kernel_times(ct_plan plan, ct_kernel_time* out, int32_t capacity, int32_t* count);
+
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* ct_last_error(void);
+
+/* Radius R = floor(truncate * s + 0.5) as the library computes it (-1 if invalid). */
+int32_t ct_radius(double s, double truncate);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CT_H */

@@ -1,0 +1,702 @@
+// C ABI of the library (include/ct.h): plans, argument validation, the stage
+// calls, and the fused, chunked hot path with its host streaming runtime.
+//
+// Padded chunks (Implementation): an output box needs the input grown by
+// R(sigma) + R(rho) on every side, clipped to the volume; with "nearest"
+// handling at the global edges only, a chunked run reproduces the
+// whole-volume result exactly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ct.h"
+#include "ct_launch.h"
+
+using namespace ct;
+
+namespace {
+
+thread_local std::string g_err;
+
+ct_status fail(ct_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+ct_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? CT_ERR_OOM : CT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CT_CUDA(call, what)                        \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool device_present() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+
+int radius_of(double s, double trunc) { return (int)std::floor(trunc * s + 0.5); }
+
+// Sampled normalised Gaussian (w) and derivative-correlation taps (c) of scale
+// s, centred in an array of instantiated radius rk; taps beyond R are zero.
+Taps make_taps(double s, double trunc, int rk) {
+  Taps t;
+  std::memset(&t, 0, sizeof t);
+  int R = radius_of(s, trunc);
+  double sum = 0.0;
+  for (int k = -R; k <= R; ++k) sum += std::exp(-(double)k * k / (2.0 * s * s));
+  for (int k = -R; k <= R; ++k) {
+    double w = std::exp(-(double)k * k / (2.0 * s * s)) / sum;
+    t.w[k + rk] = (float)w;
+    t.c[k + rk] = (float)((double)k / (s * s) * w);
+  }
+  return t;
+}
+
+Box make_box(const int64_t lo[3], const int64_t n[3]) {
+  Box b;
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] = (int)lo[a];
+    b.n[a] = (int)n[a];
+  }
+  return b;
+}
+
+Box grow_clip(const Box& b, int r, const int dims[3]) {
+  Box o;
+  for (int a = 0; a < 3; ++a) {
+    int lo = std::max(0, b.lo[a] - r);
+    int hi = std::min(dims[a] - 1, b.lo[a] + b.n[a] - 1 + r);
+    o.lo[a] = lo;
+    o.n[a] = hi - lo + 1;
+  }
+  return o;
+}
+
+bool inside(const Box& outer, const Box& inner) {
+  for (int a = 0; a < 3; ++a)
+    if (inner.lo[a] < outer.lo[a] || inner.lo[a] + inner.n[a] > outer.lo[a] + outer.n[a]) return false;
+  return true;
+}
+
+bool valid_box(const int64_t lo[3], const int64_t n[3], const int dims[3]) {
+  for (int a = 0; a < 3; ++a)
+    if (lo[a] < 0 || n[a] < 1 || lo[a] + n[a] > dims[a]) return false;
+  return true;
+}
+
+Frame make_frame(const double c[3], const double a[3]) {
+  Frame F;
+  double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  for (int k = 0; k < 3; ++k) {
+    F.c[k] = (float)c[k];
+    F.a[k] = (float)(a[k] / an);
+  }
+  return F;
+}
+
+struct Scale {
+  double sigma, rho;
+  int rs, rr;    // radii
+  int rks, rkr;  // instantiated radii
+  Taps ts, tr;
+};
+
+}  // namespace
+
+struct ct_plan_s {
+  ct_params p;
+  int dims[3];
+  int device = 0;
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // device scratch: per slot two 6-plane FP32 buffers and a re-solve list
+  float* buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int64_t buf_cap[2] = {0, 0};  // voxels per buffer
+  int* fb_count[2] = {nullptr, nullptr};
+  unsigned long long* fb_total = nullptr;
+  int64_t* fb_list[2] = {nullptr, nullptr};
+  int64_t fb_cap[2] = {0, 0};
+  // device and pinned staging for host-resident items
+  uint16_t* d_in[2] = {nullptr, nullptr};
+  uint8_t* d_mask[2] = {nullptr, nullptr};
+  void* d_out[2] = {nullptr, nullptr};
+  void* h_in[2] = {nullptr, nullptr};
+  void* h_out[2] = {nullptr, nullptr};
+  size_t in_cap[2] = {0, 0}, out_cap[2] = {0, 0}, hin_cap[2] = {0, 0}, hout_cap[2] = {0, 0};
+  ct_stats stats;
+  std::mutex mu;
+  // per-kernel timing (ct_plan_profile)
+  bool profile = false;
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+};
+
+namespace {
+
+ct_status check_params(const ct_params* p) {
+  if (!p) return fail(CT_ERR_INVALID, "params is NULL");
+  if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return fail(CT_ERR_INVALID, "sigma must be finite and > 0");
+  if (!(p->rho > 0.0) || !std::isfinite(p->rho)) return fail(CT_ERR_INVALID, "rho must be finite and > 0");
+  if (p->truncate < 0.0 || !std::isfinite(p->truncate)) return fail(CT_ERR_INVALID, "truncate must be >= 0");
+  for (int k = 0; k < 3; ++k) {
+    if (!std::isfinite(p->lv_center[k])) return fail(CT_ERR_INVALID, "lv_center must be finite");
+    if (!std::isfinite(p->lv_axis[k])) return fail(CT_ERR_INVALID, "lv_axis must be finite");
+  }
+  if (p->lv_axis[0] == 0.0 && p->lv_axis[1] == 0.0 && p->lv_axis[2] == 0.0)
+    return fail(CT_ERR_INVALID, "lv_axis must not be the zero vector");
+  if (p->precision != CT_PREC_FP32 && p->precision != CT_PREC_MIXED) return fail(CT_ERR_INVALID, "bad precision");
+  if (p->vec_type != CT_OUT_F32 && p->vec_type != CT_OUT_F16) return fail(CT_ERR_INVALID, "bad vec_type");
+  if (p->angle_type < CT_OUT_F32 || p->angle_type > CT_OUT_U8Q) return fail(CT_ERR_INVALID, "bad angle_type");
+  if (p->fa_type != CT_OUT_F32 && p->fa_type != CT_OUT_F16) return fail(CT_ERR_INVALID, "bad fa_type");
+  if (p->flags != 0) return fail(CT_ERR_INVALID, "flags must be 0");
+  for (int k = 0; k < 3; ++k)
+    if (p->chunk[k] < 0) return fail(CT_ERR_INVALID, "chunk sizes must be >= 0");
+  return CT_OK;
+}
+
+double trunc_of(const ct_params& p) { return p.truncate > 0.0 ? p.truncate : 4.0; }
+
+ct_status make_scale(const ct_params& p, double sigma, double rho, Scale* s) {
+  double tr = trunc_of(p);
+  s->sigma = sigma;
+  s->rho = rho;
+  s->rs = radius_of(sigma, tr);
+  s->rr = radius_of(rho, tr);
+  if (s->rs < 1 || s->rr < 1) return fail(CT_ERR_INVALID, "truncate * scale must give a radius >= 1");
+  s->rks = sigma_kernel_radius(s->rs);
+  s->rkr = rho_kernel_radius(s->rr);
+  if (s->rks < 0) return fail(CT_ERR_UNSUPPORTED, "sigma radius %d exceeds 12", s->rs);
+  if (s->rkr < 0) return fail(CT_ERR_UNSUPPORTED, "rho radius %d exceeds 36", s->rr);
+  s->ts = make_taps(sigma, tr, s->rks);
+  s->tr = make_taps(rho, tr, s->rkr);
+  return CT_OK;
+}
+
+size_t elem_size(int type) { return type == CT_OUT_F32 ? 4 : (type == CT_OUT_F16 ? 2 : 1); }
+
+ct_status ensure_device(void** ptr, size_t* cap, size_t need, const char* what) {
+  if (*cap >= need && *ptr) return CT_OK;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  CT_CUDA(cudaMalloc(ptr, std::max<size_t>(need, 256)), what);
+  *cap = need;
+  return CT_OK;
+}
+
+ct_status ensure_host(void** ptr, size_t* cap, size_t need, const char* what) {
+  if (*cap >= need && *ptr) return CT_OK;
+  if (*ptr) cudaFreeHost(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  CT_CUDA(cudaMallocHost(ptr, std::max<size_t>(need, 256)), what);
+  *cap = need;
+  return CT_OK;
+}
+
+ct_status ensure_fallback(ct_plan P, int slot, int64_t vox) {
+  if (!P->fb_count[slot]) CT_CUDA(cudaMalloc(&P->fb_count[slot], sizeof(int)), "counter allocation");
+  if (!P->fb_total) {
+    CT_CUDA(cudaMalloc(&P->fb_total, sizeof(unsigned long long)), "counter allocation");
+    CT_CUDA(cudaMemset(P->fb_total, 0, sizeof(unsigned long long)), "counter reset");
+  }
+  if (P->fb_cap[slot] < vox) {
+    if (P->fb_list[slot]) cudaFree(P->fb_list[slot]);
+    P->fb_list[slot] = nullptr;
+    P->fb_cap[slot] = 0;
+    CT_CUDA(cudaMalloc(&P->fb_list[slot], sizeof(int64_t) * vox), "re-solve list allocation");
+    P->fb_cap[slot] = vox;
+  }
+  return CT_OK;
+}
+
+ct_status ensure_scratch(ct_plan P, int slot, int64_t vox) {
+  if (P->buf_cap[slot] < vox) {
+    for (int k = 0; k < 2; ++k) {
+      if (P->buf[slot][k]) cudaFree(P->buf[slot][k]);
+      P->buf[slot][k] = nullptr;
+    }
+    P->buf_cap[slot] = 0;
+    for (int k = 0; k < 2; ++k) CT_CUDA(cudaMalloc(&P->buf[slot][k], sizeof(float) * 6 * vox), "scratch allocation");
+    P->buf_cap[slot] = vox;
+  }
+  return ensure_fallback(P, slot, vox);
+}
+
+Fallback fallback_of(ct_plan P, int slot) {
+  Fallback fb;
+  fb.count = P->fb_count[slot];
+  fb.total = P->fb_total;
+  fb.list = P->fb_list[slot];
+  fb.cap = P->fb_cap[slot];
+  return fb;
+}
+
+// Launch `call` (a cudaError_t expression) bracketed by timing events when profiling.
+#define CT_LAUNCH(P, st, name, call, what)                                  \
+  do {                                                                      \
+    cudaEvent_t a_ = nullptr, b_ = nullptr;                                 \
+    if ((P)->profile) {                                                     \
+      cudaEventCreate(&a_);                                                 \
+      cudaEventCreate(&b_);                                                 \
+      cudaEventRecord(a_, st);                                              \
+    }                                                                       \
+    cudaError_t e2_ = (call);                                               \
+    if ((P)->profile) {                                                     \
+      cudaEventRecord(b_, st);                                              \
+      (P)->recs.push_back({name, a_, b_});                                  \
+    }                                                                       \
+    if (e2_ != cudaSuccess) return cuda_fail(e2_, what);                    \
+    (P)->stats.launches += 1;                                               \
+  } while (0)
+
+// The four smoothing stages: J over G, then x, y, z passes of rho into S over ob.
+// vol covers vb.  Result: S (6 planes over ob) in `S_out`.
+ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
+                        const Box& ob, float* S_out, int slot, bool mixed, cudaStream_t st) {
+  Box G = grow_clip(ob, sc.rr, dims);
+  Box Bx = G, Bxy = G;
+  Bx.lo[0] = ob.lo[0];
+  Bx.n[0] = ob.n[0];
+  Bxy.lo[0] = ob.lo[0];
+  Bxy.n[0] = ob.n[0];
+  Bxy.lo[1] = ob.lo[1];
+  Bxy.n[1] = ob.n[1];
+  ct_status rc = ensure_scratch(P, slot, box_vox(G));
+  if (rc) return rc;
+  float* A = P->buf[slot][0];
+  float* B = P->buf[slot][1];
+  CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts, sc.rks, mixed, st),
+            "gradient kernel launch");
+  CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr, sc.rkr, st), "rho x kernel launch");
+  CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr, sc.rkr, st), "rho y kernel launch");
+  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(A, Bxy, dims, S_out, ob, 2, sc.tr, sc.rkr, st), "rho z kernel launch");
+  return CT_OK;
+}
+
+// Eigen + angles over ob from S (over ob); outputs in arrays covering o.ab.
+ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
+                    const EigOut& o, int slot, bool mixed, cudaStream_t st) {
+  Fallback fb = fallback_of(P, slot);
+  CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
+  CT_LAUNCH(P, st, "eig_angles", launch_eig_angles(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, st),
+            "eigen kernel launch");
+  CT_LAUNCH(P, st, "eig_resolve",
+            launch_eig_angles_fallback(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, box_vox(ob), st),
+            "re-solve kernel launch");
+  return CT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ct_radius(double s, double truncate) {
+  if (!(s > 0.0) || !(truncate >= 0.0)) return -1;
+  return radius_of(s, truncate > 0.0 ? truncate : 4.0);
+}
+
+const char* ct_last_error(void) { return g_err.c_str(); }
+
+ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_plan* out) {
+  if (!out) return fail(CT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  ct_status rc = check_params(params);
+  if (rc) return rc;
+  if (!vol_dims) return fail(CT_ERR_INVALID, "vol_dims is NULL");
+  for (int k = 0; k < 3; ++k)
+    if (vol_dims[k] < 1 || vol_dims[k] > (1 << 20)) return fail(CT_ERR_INVALID, "vol_dims must be in [1, 2^20]");
+  Scale sc;
+  if ((rc = make_scale(*params, params->sigma, params->rho, &sc))) return rc;
+  if (!device_present()) return fail(CT_ERR_NO_DEVICE, "no CUDA device is available");
+  ct_plan P = new (std::nothrow) ct_plan_s();
+  if (!P) return fail(CT_ERR_OOM, "plan allocation failed");
+  P->p = *params;
+  for (int k = 0; k < 3; ++k) P->dims[k] = (int)vol_dims[k];
+  std::memset(&P->stats, 0, sizeof P->stats);
+  cudaGetDevice(&P->device);
+  for (int k = 0; k < 2; ++k) {
+    cudaError_t e = cudaStreamCreateWithFlags(&P->st[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      ct_plan_destroy(P);
+      return cuda_fail(e, "stream creation");
+    }
+  }
+  *out = P;
+  return CT_OK;
+}
+
+ct_status ct_plan_destroy(ct_plan P) {
+  if (!P) return CT_OK;
+  cudaDeviceSynchronize();
+  for (int s = 0; s < 2; ++s) {
+    for (int k = 0; k < 2; ++k)
+      if (P->buf[s][k]) cudaFree(P->buf[s][k]);
+    if (P->fb_count[s]) cudaFree(P->fb_count[s]);
+    if (P->fb_list[s]) cudaFree(P->fb_list[s]);
+    if (P->d_in[s]) cudaFree(P->d_in[s]);
+    if (P->d_mask[s]) cudaFree(P->d_mask[s]);
+    if (P->d_out[s]) cudaFree(P->d_out[s]);
+    if (P->h_in[s]) cudaFreeHost(P->h_in[s]);
+    if (P->h_out[s]) cudaFreeHost(P->h_out[s]);
+    if (P->st[s]) cudaStreamDestroy(P->st[s]);
+    if (P->ev[s]) cudaEventDestroy(P->ev[s]);
+  }
+  if (P->fb_total) cudaFree(P->fb_total);
+  for (auto& r : P->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  delete P;
+  return CT_OK;
+}
+
+ct_status ct_structure_tensor(ct_plan P, const uint16_t* d_vol, const int64_t in_lo[3], const int64_t in_n[3],
+                              const int64_t out_lo[3], const int64_t out_n[3], float* d_S, void* stream) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  if (!d_vol || !d_S || !in_lo || !in_n || !out_lo || !out_n) return fail(CT_ERR_INVALID, "NULL argument");
+  if (!valid_box(in_lo, in_n, P->dims)) return fail(CT_ERR_INVALID, "input box outside the volume");
+  if (!valid_box(out_lo, out_n, P->dims)) return fail(CT_ERR_INVALID, "output box outside the volume");
+  std::lock_guard<std::mutex> lk(P->mu);
+  Scale sc;
+  ct_status rc = make_scale(P->p, P->p.sigma, P->p.rho, &sc);
+  if (rc) return rc;
+  Box ib = make_box(in_lo, in_n), ob = make_box(out_lo, out_n);
+  if (!inside(ib, grow_clip(ob, sc.rs + sc.rr, P->dims)))
+    return fail(CT_ERR_INVALID, "input box must contain the output box grown by R(sigma)+R(rho) = %d (clipped)",
+                sc.rs + sc.rr);
+  rc = tensor_stages(P, sc, P->dims, d_vol, ib, ob, d_S, 0, P->p.precision == CT_PREC_MIXED,
+                     (cudaStream_t)stream);
+  if (rc) return rc;
+  P->stats.voxels += box_vox(ob);
+  return CT_OK;
+}
+
+ct_status ct_eig_smallest(ct_plan P, const float* d_S, int64_t n, float* d_evals, float* d_evec, void* stream) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  if (!d_S || !d_evec) return fail(CT_ERR_INVALID, "NULL argument");
+  if (n < 0) return fail(CT_ERR_INVALID, "n must be >= 0");
+  if (n == 0) return CT_OK;
+  std::lock_guard<std::mutex> lk(P->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  ct_status rc = ensure_fallback(P, 0, n);
+  if (rc) return rc;
+  Fallback fb = fallback_of(P, 0);
+  bool mixed = P->p.precision == CT_PREC_MIXED;
+  CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
+  CT_LAUNCH(P, st, "eig_only", launch_eig_only(d_S, n, d_evals, d_evec, mixed, fb, st), "eigen kernel launch");
+  CT_LAUNCH(P, st, "eig_only_resolve", launch_eig_only_fallback(d_S, n, d_evals, d_evec, mixed, fb, n, st),
+            "re-solve kernel launch");
+  return CT_OK;
+}
+
+ct_status ct_angles(ct_plan P, const float* d_evec, const float* d_evals, const int64_t out_lo[3],
+                    const int64_t out_n[3], const uint8_t* d_mask, void* d_vec, void* d_ha, void* d_ia, void* d_fa,
+                    void* stream) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  if (!d_evec || !d_evals || !out_lo || !out_n) return fail(CT_ERR_INVALID, "NULL argument");
+  if (!valid_box(out_lo, out_n, P->dims)) return fail(CT_ERR_INVALID, "output box outside the volume");
+  std::lock_guard<std::mutex> lk(P->mu);
+  Box ob = make_box(out_lo, out_n);
+  EigOut o{d_vec, d_ha, d_ia, d_fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
+  Frame F = make_frame(P->p.lv_center, P->p.lv_axis);
+  cudaStream_t st = (cudaStream_t)stream;
+  CT_LAUNCH(P, st, "angles_only", launch_angles_only(d_evec, d_evals, ob, d_mask, F, P->p.fill_value, o, st),
+            "angles kernel launch");
+  return CT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Chunk grid over dims with chunk sizes (0 = whole extent).
+std::vector<Box> chunk_grid(const int dims[3], const int64_t chunk[3]) {
+  int cs[3];
+  for (int a = 0; a < 3; ++a) cs[a] = chunk[a] > 0 ? (int)std::min<int64_t>(chunk[a], dims[a]) : dims[a];
+  std::vector<Box> out;
+  for (int z = 0; z < dims[2]; z += cs[2])
+    for (int y = 0; y < dims[1]; y += cs[1])
+      for (int x = 0; x < dims[0]; x += cs[0]) {
+        Box b;
+        b.lo[0] = x; b.lo[1] = y; b.lo[2] = z;
+        b.n[0] = std::min(cs[0], dims[0] - x);
+        b.n[1] = std::min(cs[1], dims[1] - y);
+        b.n[2] = std::min(cs[2], dims[2] - z);
+        out.push_back(b);
+      }
+  return out;
+}
+
+// Copy the sub-box `b` of a host array covering `arr` (x-fastest) into a dense buffer, or back.
+template <typename T>
+void gather_box(const T* src, const Box& arr, const Box& b, T* dst) {
+  for (int z = 0; z < b.n[2]; ++z)
+    for (int y = 0; y < b.n[1]; ++y) {
+      const T* s = src + (((int64_t)(b.lo[2] + z - arr.lo[2]) * arr.n[1] + (b.lo[1] + y - arr.lo[1])) * arr.n[0] +
+                          (b.lo[0] - arr.lo[0]));
+      std::memcpy(dst + ((int64_t)z * b.n[1] + y) * b.n[0], s, sizeof(T) * b.n[0]);
+    }
+}
+
+void scatter_box(const uint8_t* src, const Box& b, uint8_t* dst, const Box& arr, size_t esz) {
+  for (int z = 0; z < b.n[2]; ++z)
+    for (int y = 0; y < b.n[1]; ++y) {
+      uint8_t* d = dst + esz * (((int64_t)(b.lo[2] + z - arr.lo[2]) * arr.n[1] + (b.lo[1] + y - arr.lo[1])) *
+                                    arr.n[0] + (b.lo[0] - arr.lo[0]));
+      std::memcpy(d, src + esz * (((int64_t)z * b.n[1] + y) * b.n[0]), esz * b.n[0]);
+    }
+}
+
+struct ItemCtx {
+  Scale sc;
+  Frame F;
+  int dims[3];
+  Box whole;
+};
+
+ct_status item_ctx(ct_plan P, const ct_item& it, ItemCtx* c) {
+  for (int k = 0; k < 3; ++k) {
+    if (it.dims[k] < 1 || it.dims[k] > (1 << 20)) return fail(CT_ERR_INVALID, "item dims must be in [1, 2^20]");
+    c->dims[k] = (int)it.dims[k];
+    c->whole.lo[k] = 0;
+    c->whole.n[k] = (int)it.dims[k];
+  }
+  if (!it.vol) return fail(CT_ERR_INVALID, "item volume is NULL");
+  double sig = it.sigma > 0.0 ? it.sigma : P->p.sigma;
+  double rho = it.rho > 0.0 ? it.rho : P->p.rho;
+  ct_status rc = make_scale(P->p, sig, rho, &c->sc);
+  if (rc) return rc;
+  bool own_axis = it.lv_axis[0] != 0.0 || it.lv_axis[1] != 0.0 || it.lv_axis[2] != 0.0;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(it.lv_center[k]) || !std::isfinite(it.lv_axis[k]))
+      return fail(CT_ERR_INVALID, "item frame must be finite");
+  c->F = own_axis ? make_frame(it.lv_center, it.lv_axis) : make_frame(P->p.lv_center, P->p.lv_axis);
+  return CT_OK;
+}
+
+// Output planes per item: (pointer, element size, planes).
+struct OutPlanes {
+  void* ptr[4];
+  size_t esz[4];
+  int planes[4];
+};
+
+OutPlanes out_planes(ct_plan P, const ct_item& it) {
+  OutPlanes o;
+  o.ptr[0] = it.vec; o.esz[0] = elem_size(P->p.vec_type); o.planes[0] = 3;
+  o.ptr[1] = it.ha; o.esz[1] = elem_size(P->p.angle_type); o.planes[1] = 1;
+  o.ptr[2] = it.ia; o.esz[2] = elem_size(P->p.angle_type); o.planes[2] = 1;
+  o.ptr[3] = it.fa; o.esz[3] = elem_size(P->p.fa_type); o.planes[3] = 1;
+  return o;
+}
+
+ct_status run_device_item(ct_plan P, const ct_item& it, cudaStream_t st) {
+  ItemCtx c;
+  ct_status rc = item_ctx(P, it, &c);
+  if (rc) return rc;
+  bool mixed = P->p.precision == CT_PREC_MIXED;
+  for (const Box& ob : chunk_grid(c.dims, P->p.chunk)) {
+    Box G = grow_clip(ob, c.sc.rr, c.dims);
+    if ((rc = ensure_scratch(P, 0, box_vox(G)))) return rc;
+    float* S = P->buf[0][1];  // J (A) -> Sx (B) -> Sxy (A) -> S (B): B is free again by the z pass
+    if ((rc = tensor_stages(P, c.sc, c.dims, it.vol, c.whole, ob, S, 0, mixed, st))) return rc;
+    EigOut o{it.vec, it.ha, it.ia, it.fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, c.whole};
+    if ((rc = eig_stage(P, S, ob, it.mask, c.whole, c.F, o, 0, mixed, st))) return rc;
+    P->stats.voxels += box_vox(ob);
+  }
+  return CT_OK;
+}
+
+ct_status run_host_item(ct_plan P, const ct_item& it) {
+  ItemCtx c;
+  ct_status rc = item_ctx(P, it, &c);
+  if (rc) return rc;
+  bool mixed = P->p.precision == CT_PREC_MIXED;
+  OutPlanes op = out_planes(P, it);
+  size_t out_bytes_per_vox = 0;
+  for (int k = 0; k < 4; ++k)
+    if (op.ptr[k]) out_bytes_per_vox += op.esz[k] * op.planes[k];
+  std::vector<Box> chunks = chunk_grid(c.dims, P->p.chunk);
+  int halo = c.sc.rs + c.sc.rr;
+  Box pending[2];
+  bool has_pending[2] = {false, false};
+
+  auto drain = [&](int slot) -> ct_status {
+    if (!has_pending[slot]) return CT_OK;
+    CT_CUDA(cudaEventSynchronize(P->ev[slot]), "chunk completion");
+    const Box& ob = pending[slot];
+    int64_t nv = box_vox(ob);
+    const uint8_t* src = (const uint8_t*)P->h_out[slot];
+    for (int k = 0; k < 4; ++k) {
+      if (!op.ptr[k]) continue;
+      int64_t nwhole = box_vox(c.whole);
+      for (int pl = 0; pl < op.planes[k]; ++pl) {
+        scatter_box(src, ob, (uint8_t*)op.ptr[k] + pl * nwhole * op.esz[k], c.whole, op.esz[k]);
+        src += nv * op.esz[k];
+      }
+    }
+    has_pending[slot] = false;
+    return CT_OK;
+  };
+
+  for (size_t ci = 0; ci < chunks.size(); ++ci) {
+    int slot = (int)(ci & 1);
+    cudaStream_t st = P->st[slot];
+    if ((rc = drain(slot))) return rc;
+    const Box& ob = chunks[ci];
+    Box ib = grow_clip(ob, halo, c.dims);
+    int64_t niv = box_vox(ib), nov = box_vox(ob);
+    size_t in_bytes = sizeof(uint16_t) * niv;
+    size_t mask_bytes = it.mask ? (size_t)nov : 0;
+    size_t out_bytes = out_bytes_per_vox * nov;
+    if ((rc = ensure_host(&P->h_in[slot], &P->hin_cap[slot], in_bytes + mask_bytes, "pinned input"))) return rc;
+    if ((rc = ensure_host(&P->h_out[slot], &P->hout_cap[slot], std::max<size_t>(out_bytes, 1), "pinned output")))
+      return rc;
+    if ((rc = ensure_device((void**)&P->d_in[slot], &P->in_cap[slot], in_bytes + mask_bytes, "device input")))
+      return rc;
+    if ((rc = ensure_device(&P->d_out[slot], &P->out_cap[slot], std::max<size_t>(out_bytes, 1), "device output")))
+      return rc;
+    gather_box(it.vol, c.whole, ib, (uint16_t*)P->h_in[slot]);
+    uint8_t* hmask = (uint8_t*)P->h_in[slot] + in_bytes;
+    if (it.mask) gather_box(it.mask, c.whole, ob, hmask);
+    CT_CUDA(cudaMemcpyAsync(P->d_in[slot], P->h_in[slot], in_bytes + mask_bytes, cudaMemcpyHostToDevice, st),
+            "host to device copy");
+    P->stats.h2d_bytes += (int64_t)(in_bytes + mask_bytes);
+    Box G = grow_clip(ob, c.sc.rr, c.dims);
+    if ((rc = ensure_scratch(P, slot, box_vox(G)))) return rc;
+    float* S = P->buf[slot][1];
+    if ((rc = tensor_stages(P, c.sc, c.dims, P->d_in[slot], ib, ob, S, slot, mixed, st))) return rc;
+    // device outputs: dense planes over ob, in the order vec(3), ha, ia, fa
+    uint8_t* dptr = (uint8_t*)P->d_out[slot];
+    void* dout[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int k = 0; k < 4; ++k) {
+      if (!op.ptr[k]) continue;
+      dout[k] = dptr;
+      dptr += nov * op.esz[k] * op.planes[k];
+    }
+    EigOut o{dout[0], dout[1], dout[2], dout[3], P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
+    const uint8_t* dmask = it.mask ? (const uint8_t*)P->d_in[slot] + in_bytes : nullptr;
+    if ((rc = eig_stage(P, S, ob, dmask, ob, c.F, o, slot, mixed, st))) return rc;
+    CT_CUDA(cudaMemcpyAsync(P->h_out[slot], P->d_out[slot], out_bytes, cudaMemcpyDeviceToHost, st),
+            "device to host copy");
+    P->stats.d2h_bytes += (int64_t)out_bytes;
+    CT_CUDA(cudaEventRecord(P->ev[slot], st), "event record");
+    pending[slot] = ob;
+    has_pending[slot] = true;
+    P->stats.voxels += nov;
+  }
+  for (int s = 0; s < 2; ++s)
+    if ((rc = drain(s))) return rc;
+  return CT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ct_status ct_run_chunks(ct_plan P, const ct_item* items, int32_t n_items, int32_t items_on_host, void* stream) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  if (n_items < 0 || (n_items > 0 && !items)) return fail(CT_ERR_INVALID, "bad item list");
+  if (items_on_host != 0 && items_on_host != 1) return fail(CT_ERR_INVALID, "items_on_host must be 0 or 1");
+  std::lock_guard<std::mutex> lk(P->mu);
+  ct_status rc;
+  for (int i = 0; i < n_items; ++i) {
+    rc = items_on_host ? run_host_item(P, items[i]) : run_device_item(P, items[i], (cudaStream_t)stream);
+    if (rc) return rc;
+  }
+  if (items_on_host) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "chunked run");
+  }
+  return CT_OK;
+}
+
+ct_status ct_plan_sync(ct_plan P) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "device work");
+  return CT_OK;
+}
+
+ct_status ct_plan_stats(ct_plan P, ct_stats* out, int32_t reset) {
+  if (!P || !out) return fail(CT_ERR_INVALID, "NULL argument");
+  ct_status rc = ct_plan_sync(P);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(P->mu);
+  *out = P->stats;
+  unsigned long long total = 0;
+  if (P->fb_total) CT_CUDA(cudaMemcpy(&total, P->fb_total, sizeof total, cudaMemcpyDeviceToHost), "counter read");
+  out->fallback_voxels = (int64_t)total;
+  if (reset) {
+    std::memset(&P->stats, 0, sizeof P->stats);
+    if (P->fb_total) CT_CUDA(cudaMemset(P->fb_total, 0, sizeof(unsigned long long)), "counter reset");
+  }
+  return CT_OK;
+}
+
+ct_status ct_plan_profile(ct_plan P, int32_t enable) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  std::lock_guard<std::mutex> lk(P->mu);
+  P->profile = enable != 0;
+  return CT_OK;
+}
+
+ct_status ct_plan_kernel_times(ct_plan P, ct_kernel_time* out, int32_t capacity, int32_t* count) {
+  if (!P || !count || (capacity > 0 && !out)) return fail(CT_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(P->mu);
+  std::vector<ct_kernel_time> acc;
+  cudaError_t err = cudaSuccess;
+  for (auto& r : P->recs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+    size_t k = 0;
+    while (k < acc.size() && std::strcmp(acc[k].name, r.name) != 0) ++k;
+    if (k == acc.size()) {
+      ct_kernel_time t;
+      std::memset(&t, 0, sizeof t);
+      std::snprintf(t.name, sizeof t.name, "%s", r.name);
+      acc.push_back(t);
+    }
+    acc[k].launches += 1;
+    acc[k].total_ms += ms;
+  }
+  P->recs.clear();
+  if (err != cudaSuccess) return cuda_fail(err, "kernel timing");
+  int32_t n = 0;
+  for (size_t k = 0; k < acc.size() && n < capacity; ++k) out[n++] = acc[k];
+  *count = n;
+  return CT_OK;
+}
+
+}  // extern "C"

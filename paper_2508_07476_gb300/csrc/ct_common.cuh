@@ -1,0 +1,244 @@
+// Device-side building blocks shared by the library's kernels (not by the oracle).
+//
+// Sources: the structure tensor, its smallest-eigenvalue eigenvector and the
+// HA / IA / FA descriptors are the stages of Figure 1(b,c) and of the
+// "orientation" module (Architecture); chunking with padding is described under
+// Implementation.  The paper gives no formulas; the definitions used are the
+// textbook ones stated in include/ct.h.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ct {
+
+constexpr int kMaxRadius = 36;               // largest supported tap radius
+constexpr int kMaxTaps = 2 * kMaxRadius + 1;
+
+// Taps of one scale, passed by value as a kernel parameter so that each FMA
+// reads its weight from the constant bank.  w: sampled normalised Gaussian;
+// c: derivative-correlation taps c_k = (k / s^2) w_k; entries beyond the
+// actual radius are zero (a zero tap adds an exact +0 and changes nothing).
+struct Taps {
+  float w[kMaxTaps];
+  float c[kMaxTaps];
+};
+
+// A box of the global volume: lo (x, y, z) and extent n (x, y, z).
+struct Box {
+  int lo[3];
+  int n[3];
+};
+
+__host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__host__ __device__ __forceinline__ int64_t box_vox(const Box& b) { return (int64_t)b.n[0] * b.n[1] * b.n[2]; }
+
+// Linear index of global voxel (x, y, z) in an array covering box b.
+__device__ __forceinline__ int64_t box_index(const Box& b, int x, int y, int z) {
+  return ((int64_t)(z - b.lo[2]) * b.n[1] + (y - b.lo[1])) * b.n[0] + (x - b.lo[0]);
+}
+
+// Global coordinate p + k clamped to the volume [0, dim) and then to the array
+// box [lo, lo + n) (the second clamp only matters for lanes whose outputs are
+// discarded: for every stored output the first clamp already lands inside the
+// array, which the host validates).
+__device__ __forceinline__ int clamp_to(int p, int dim, int lo, int n) {
+  return clampi(clampi(p, 0, dim - 1), lo, lo + n - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Eigen-decomposition of a symmetric 3x3 tensor s = (xx, yy, zz, xy, xz, yz).
+// ---------------------------------------------------------------------------
+
+// Near-degeneracy threshold: the smallest pair of eigenvalues closer than this
+// fraction of the spread (l3 - l1) is re-solved, since the trigonometric form
+// loses about half of its digits as the two smallest eigenvalues meet.
+constexpr float kDegenerateGap = 5e-2f;
+
+template <typename T>
+struct Sym3 {
+  T a, b, c, d, e, f;  // xx, yy, zz, xy, xz, yz
+};
+
+// Eigenvector of eigenvalue lam: the largest of the three cross products of
+// the rows of (S - lam I).  Returns the squared norm of the chosen product
+// before normalisation (0 when S - lam I has rank <= 1).
+template <typename T>
+__device__ __forceinline__ T null_vector(const Sym3<T>& s, T lam, T v[3]) {
+  T r0x = s.a - lam, r0y = s.d, r0z = s.e;
+  T r1x = s.d, r1y = s.b - lam, r1z = s.f;
+  T r2x = s.e, r2y = s.f, r2z = s.c - lam;
+  T x01 = r0y * r1z - r0z * r1y, y01 = r0z * r1x - r0x * r1z, z01 = r0x * r1y - r0y * r1x;
+  T x02 = r0y * r2z - r0z * r2y, y02 = r0z * r2x - r0x * r2z, z02 = r0x * r2y - r0y * r2x;
+  T x12 = r1y * r2z - r1z * r2y, y12 = r1z * r2x - r1x * r2z, z12 = r1x * r2y - r1y * r2x;
+  T n01 = x01 * x01 + y01 * y01 + z01 * z01;
+  T n02 = x02 * x02 + y02 * y02 + z02 * z02;
+  T n12 = x12 * x12 + y12 * y12 + z12 * z12;
+  T bx = x01, by = y01, bz = z01, bn = n01;
+  if (n02 > bn) { bx = x02; by = y02; bz = z02; bn = n02; }
+  if (n12 > bn) { bx = x12; by = y12; bz = z12; bn = n12; }
+  if (bn > T(0)) {
+    T inv = T(1) / sqrt(bn);
+    v[0] = bx * inv; v[1] = by * inv; v[2] = bz * inv;
+  } else {
+    v[0] = T(1); v[1] = T(0); v[2] = T(0);
+  }
+  return bn;
+}
+
+// Closed-form eigenvalues (trigonometric solution of the characteristic cubic,
+// O. K. Smith, Comm. ACM 4(4), 1961) and the smallest-eigenvalue eigenvector.
+// Eigenvalues ascending in l[0..2].  Returns true when the result is well
+// conditioned, false when the voxel should be re-solved.
+template <typename T>
+__device__ __forceinline__ bool eig_closed(const Sym3<T>& s, T l[3], T v[3]) {
+  const T third = T(1) / T(3);
+  T q = (s.a + s.b + s.c) * third;
+  T aq = s.a - q, bq = s.b - q, cq = s.c - q;
+  T p1 = s.d * s.d + s.e * s.e + s.f * s.f;
+  T p2 = aq * aq + bq * bq + cq * cq + T(2) * p1;
+  if (p2 == T(0)) {  // isotropic (including the zero tensor): every vector is an eigenvector
+    l[0] = l[1] = l[2] = q;
+    v[0] = T(1); v[1] = T(0); v[2] = T(0);
+    return true;
+  }
+  T p = sqrt(p2 / T(6));
+  T ip = T(1) / p;
+  T B00 = aq * ip, B11 = bq * ip, B22 = cq * ip, B01 = s.d * ip, B02 = s.e * ip, B12 = s.f * ip;
+  T det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
+  T r = det * T(0.5);
+  r = r < T(-1) ? T(-1) : (r > T(1) ? T(1) : r);
+  T phi = acos(r) * third;
+  const T two_pi_3 = T(2.0943951023931954923);
+  T l3 = q + T(2) * p * cos(phi);
+  T l1 = q + T(2) * p * cos(phi + two_pi_3);
+  T l2 = T(3) * q - l1 - l3;
+  if (l2 < l1) { T t = l1; l1 = l2; l2 = t; }
+  if (l3 < l2) { T t = l2; l2 = l3; l3 = t; }
+  l[0] = l1; l[1] = l2; l[2] = l3;
+  T bn = null_vector(s, l1, v);
+  T spread = l3 - l1;
+  bool ok = (l2 - l1) >= T(kDegenerateGap) * spread && bn > T(0);
+  return ok;
+}
+
+// Cyclic Jacobi (Golub & Van Loan, Matrix Computations, section 8.5) on a
+// symmetric 3x3: the robust re-solve for near-degenerate voxels.  Eigenvalues
+// ascending; v = eigenvector of the smallest.
+template <typename T>
+__device__ __noinline__ void eig_jacobi(const Sym3<T>& s, T l[3], T v[3]) {
+  T A[3][3] = {{s.a, s.d, s.e}, {s.d, s.b, s.f}, {s.e, s.f, s.c}};
+  T Q[3][3] = {{T(1), T(0), T(0)}, {T(0), T(1), T(0)}, {T(0), T(0), T(1)}};
+  T fro = T(0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) fro += A[i][j] * A[i][j];
+  fro = sqrt(fro);
+  const T tol = (sizeof(T) == 8 ? T(1e-15) : T(1e-7)) * fro;
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    T off = sqrt(T(2) * (A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2]));
+    if (off <= tol || off == T(0)) break;
+    for (int p = 0; p < 2; ++p) {
+      for (int qq = p + 1; qq < 3; ++qq) {
+        if (A[p][qq] == T(0)) continue;
+        T tau = (A[qq][qq] - A[p][p]) / (T(2) * A[p][qq]);
+        T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+        T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
+        for (int k = 0; k < 3; ++k) {
+          T akp = A[k][p], akq = A[k][qq];
+          A[k][p] = cs * akp - sn * akq;
+          A[k][qq] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < 3; ++k) {
+          T apk = A[p][k], aqk = A[qq][k];
+          A[p][k] = cs * apk - sn * aqk;
+          A[qq][k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < 3; ++k) {
+          T qkp = Q[k][p], qkq = Q[k][qq];
+          Q[k][p] = cs * qkp - sn * qkq;
+          Q[k][qq] = sn * qkp + cs * qkq;
+        }
+      }
+    }
+  }
+  T d0 = A[0][0], d1 = A[1][1], d2 = A[2][2];
+  int i0 = 0, i1 = 1, i2 = 2;
+  if (d1 < d0) { T t = d0; d0 = d1; d1 = t; int u = i0; i0 = i1; i1 = u; }
+  if (d2 < d1) { T t = d1; d1 = d2; d2 = t; int u = i1; i1 = i2; i2 = u; }
+  if (d1 < d0) { T t = d0; d0 = d1; d1 = t; int u = i0; i0 = i1; i1 = u; }
+  l[0] = d0; l[1] = d1; l[2] = d2;
+  v[0] = Q[0][i0]; v[1] = Q[1][i0]; v[2] = Q[2][i0];
+  (void)i2;
+}
+
+// Fractional anisotropy from eigenvalues clamped at zero; 0 for the zero tensor.
+__device__ __forceinline__ float fa_of(const float l[3]) {
+  float l1 = fmaxf(l[0], 0.f), l2 = fmaxf(l[1], 0.f), l3 = fmaxf(l[2], 0.f);
+  float den = l1 * l1 + l2 * l2 + l3 * l3;
+  if (den == 0.f) return 0.f;
+  float num = (l1 - l2) * (l1 - l2) + (l2 - l3) * (l2 - l3) + (l3 - l1) * (l3 - l1);
+  return sqrtf(0.5f * num / den);
+}
+
+// Cylindrical left-ventricle frame (unit axis, centre), per launch.
+struct Frame {
+  float c[3];
+  float a[3];  // unit
+};
+
+// HA / IA (degrees) of v at voxel (x, y, z); orients v so that v.e_t > 0.
+// Returns false on the axis, where the frame does not exist.
+__device__ __forceinline__ bool ha_ia(const Frame& F, int x, int y, int z, float v[3], float& ha, float& ia) {
+  float dx = (float)x - F.c[0], dy = (float)y - F.c[1], dz = (float)z - F.c[2];
+  float h = dx * F.a[0] + dy * F.a[1] + dz * F.a[2];
+  float rx = dx - h * F.a[0], ry = dy - h * F.a[1], rz = dz - h * F.a[2];
+  float rr = rx * rx + ry * ry + rz * rz;
+  if (rr == 0.f) return false;
+  float inv = rsqrtf(rr);
+  rx *= inv; ry *= inv; rz *= inv;
+  float tx = F.a[1] * rz - F.a[2] * ry, ty = F.a[2] * rx - F.a[0] * rz, tz = F.a[0] * ry - F.a[1] * rx;
+  float vr = v[0] * rx + v[1] * ry + v[2] * rz;
+  float vt = v[0] * tx + v[1] * ty + v[2] * tz;
+  float vz = v[0] * F.a[0] + v[1] * F.a[1] + v[2] * F.a[2];
+  if (vt < 0.f || (vt == 0.f && vz < 0.f)) {
+    vr = -vr; vt = -vt; vz = -vz;
+    v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
+  }
+  const float rad2deg = 57.295779513082320877f;
+  ha = atan2f(vz, vt) * rad2deg;
+  ia = asinf(fminf(fmaxf(vr, -1.f), 1.f)) * rad2deg;
+  return true;
+}
+
+// Largest-magnitude component positive (orientation where no frame exists).
+__device__ __forceinline__ void orient_largest(float v[3]) {
+  int m = 0;
+  if (fabsf(v[1]) > fabsf(v[m])) m = 1;
+  if (fabsf(v[2]) > fabsf(v[m])) m = 2;
+  if (v[m] < 0.f) { v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2]; }
+}
+
+// Output encodings (CT_OUT_F32 = 0, CT_OUT_F16 = 1, CT_OUT_U8Q = 2).
+__device__ __forceinline__ void store_val(void* base, int64_t i, int type, float val) {
+  if (base == nullptr) return;
+  if (type == 0) {
+    reinterpret_cast<float*>(base)[i] = val;
+  } else if (type == 1) {
+    reinterpret_cast<__half*>(base)[i] = __float2half_rn(val);
+  }
+}
+
+__device__ __forceinline__ void store_angle(void* base, int64_t i, int type, float deg, bool valid) {
+  if (base == nullptr) return;
+  if (type == 2) {
+    uint8_t code = 0;
+    if (valid) code = (uint8_t)(((int)rintf((deg + 90.f) * (256.f / 180.f))) & 255);
+    reinterpret_cast<uint8_t*>(base)[i] = code;
+  } else {
+    store_val(base, i, type, deg);
+  }
+}
+
+}  // namespace ct

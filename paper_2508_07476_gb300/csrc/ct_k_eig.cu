@@ -1,0 +1,219 @@
+// Eigen-decomposition of the structure tensor and the cardiac descriptors
+// (Figure 1b: smallest-eigenvalue eigenvector as the fibre direction;
+// Figure 1c: HA, IA, FA in the cylindrical left-ventricle frame; Figure 1a:
+// optional myocardial mask).
+//
+// Every voxel first takes the FP32 closed form (trigonometric roots of the
+// characteristic cubic, cross product of two rows of S - l1 I).  Voxels whose
+// two smallest eigenvalues nearly coincide, where that form loses half of its
+// digits, are appended to a compact list and re-solved by a second kernel:
+// FP32 cyclic Jacobi in the FP32 form, FP64 closed form (FP64 Jacobi if that
+// too is near-degenerate) in the mixed form.  The list keeps the re-solve off
+// the common path, so no warp diverges into it.
+#include "ct_common.cuh"
+#include "ct_launch.h"
+
+namespace ct {
+
+__device__ __forceinline__ Sym3<float> load_sym(const float* S, int64_t n, int64_t i) {
+  Sym3<float> s;
+  s.a = __ldg(S + i);
+  s.b = __ldg(S + n + i);
+  s.c = __ldg(S + 2 * n + i);
+  s.d = __ldg(S + 3 * n + i);
+  s.e = __ldg(S + 4 * n + i);
+  s.f = __ldg(S + 5 * n + i);
+  return s;
+}
+
+// Robust re-solve of one voxel.
+__device__ __forceinline__ void resolve(const Sym3<float>& s, bool mixed, float l[3], float v[3]) {
+  if (mixed) {
+    Sym3<double> sd{(double)s.a, (double)s.b, (double)s.c, (double)s.d, (double)s.e, (double)s.f};
+    double ld[3], vd[3];
+    if (!eig_closed<double>(sd, ld, vd)) eig_jacobi<double>(sd, ld, vd);
+    for (int k = 0; k < 3; ++k) {
+      l[k] = (float)ld[k];
+      v[k] = (float)vd[k];
+    }
+  } else {
+    eig_jacobi<float>(s, l, v);
+  }
+  float nv = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  v[0] *= nv; v[1] *= nv; v[2] *= nv;
+}
+
+// Outputs of one voxel: oriented vector, HA, IA, FA (or fill outside the mask).
+__device__ __forceinline__ void write_voxel(const EigOut& o, int64_t oi, bool inside, const Frame& F, int x, int y,
+                                            int z, const float l[3], float v[3], float fill) {
+  if (!inside) {
+    store_val(o.vec, oi, o.vec_t, fill);
+    int64_t n = box_vox(o.ab);
+    if (o.vec) {
+      store_val(o.vec, n + oi, o.vec_t, fill);
+      store_val(o.vec, 2 * n + oi, o.vec_t, fill);
+    }
+    store_angle(o.ha, oi, o.ang_t, fill, false);
+    store_angle(o.ia, oi, o.ang_t, fill, false);
+    store_val(o.fa, oi, o.fa_t, fill);
+    return;
+  }
+  float ha, ia;
+  bool framed = ha_ia(F, x, y, z, v, ha, ia);
+  if (!framed) orient_largest(v);
+  if (o.vec) {
+    int64_t n = box_vox(o.ab);
+    store_val(o.vec, oi, o.vec_t, v[0]);
+    store_val(o.vec, n + oi, o.vec_t, v[1]);
+    store_val(o.vec, 2 * n + oi, o.vec_t, v[2]);
+  }
+  store_angle(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
+  store_angle(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
+  store_val(o.fa, oi, o.fa_t, fa_of(l));
+}
+
+__device__ __forceinline__ void push_fallback(const Fallback& fb, int64_t i) {
+  int slot = atomicAdd(fb.count, 1);
+  if (slot < fb.cap) fb.list[slot] = i;
+  atomicAdd(fb.total, 1ull);
+}
+
+__global__ void __launch_bounds__(256)
+    k_eig_angles(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
+                 float fill, EigOut o, bool mixed, Fallback fb) {
+  const int64_t nvox = box_vox(ob);
+  const int64_t ns = box_vox(sb);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvox; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = ob.lo[0] + (int)(i % ob.n[0]);
+    const int y = ob.lo[1] + (int)((i / ob.n[0]) % ob.n[1]);
+    const int z = ob.lo[2] + (int)(i / ((int64_t)ob.n[0] * ob.n[1]));
+    const bool inside = mask == nullptr || __ldg(mask + box_index(mb, x, y, z)) != 0;
+    const int64_t oi = box_index(o.ab, x, y, z);
+    float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
+    if (inside) {
+      Sym3<float> s = load_sym(S, ns, box_index(sb, x, y, z));
+      if (!eig_closed<float>(s, l, v)) push_fallback(fb, i);
+    }
+    write_voxel(o, oi, inside, F, x, y, z, l, v, fill);
+  }
+}
+
+__global__ void __launch_bounds__(128)
+    k_eig_angles_fallback(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
+                          Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
+  const int64_t cnt = min((int64_t)*fb.count, fb.cap);
+  const int64_t ns = box_vox(sb);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = fb.list[j];
+    const int x = ob.lo[0] + (int)(i % ob.n[0]);
+    const int y = ob.lo[1] + (int)((i / ob.n[0]) % ob.n[1]);
+    const int z = ob.lo[2] + (int)(i / ((int64_t)ob.n[0] * ob.n[1]));
+    Sym3<float> s = load_sym(S, ns, box_index(sb, x, y, z));
+    float l[3], v[3];
+    resolve(s, mixed, l, v);
+    write_voxel(o, box_index(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
+  }
+}
+
+static int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = 152 * 64;  // grid-stride beyond this
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, const uint8_t* mask, const Box& mb,
+                              const Frame& F, float fill, const EigOut& o, bool mixed, const Fallback& fb,
+                              cudaStream_t st) {
+  int64_t n = box_vox(ob);
+  if (n == 0) return cudaSuccess;
+  k_eig_angles<<<grid_for(n, 256), 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_angles_fallback(const float* S, const Box& sb, const Box& ob, const uint8_t* mask,
+                                       const Box& mb, const Frame& F, float fill, const EigOut& o, bool mixed,
+                                       const Fallback& fb, int64_t max_items, cudaStream_t st) {
+  if (max_items <= 0) return cudaSuccess;
+  k_eig_angles_fallback<<<grid_for(max_items, 128), 128, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ stage kernels
+__global__ void __launch_bounds__(256)
+    k_eig_only(const float* __restrict__ S, int64_t n, float* __restrict__ evals, float* __restrict__ evec,
+               bool mixed, Fallback fb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Sym3<float> s = load_sym(S, n, i);
+    float l[3], v[3];
+    if (!eig_closed<float>(s, l, v)) push_fallback(fb, i);
+    orient_largest(v);
+    if (evals) {
+      evals[i] = l[0];
+      evals[n + i] = l[1];
+      evals[2 * n + i] = l[2];
+    }
+    evec[i] = v[0];
+    evec[n + i] = v[1];
+    evec[2 * n + i] = v[2];
+  }
+}
+
+__global__ void __launch_bounds__(128)
+    k_eig_only_fallback(const float* __restrict__ S, int64_t n, float* __restrict__ evals, float* __restrict__ evec,
+                        bool mixed, Fallback fb) {
+  const int64_t cnt = min((int64_t)*fb.count, fb.cap);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = fb.list[j];
+    Sym3<float> s = load_sym(S, n, i);
+    float l[3], v[3];
+    resolve(s, mixed, l, v);
+    orient_largest(v);
+    if (evals) {
+      evals[i] = l[0];
+      evals[n + i] = l[1];
+      evals[2 * n + i] = l[2];
+    }
+    evec[i] = v[0];
+    evec[n + i] = v[1];
+    evec[2 * n + i] = v[2];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_angles_only(const float* __restrict__ evec, const float* __restrict__ evals, Box ob,
+                  const uint8_t* __restrict__ mask, Frame F, float fill, EigOut o) {
+  const int64_t n = box_vox(ob);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = ob.lo[0] + (int)(i % ob.n[0]);
+    const int y = ob.lo[1] + (int)((i / ob.n[0]) % ob.n[1]);
+    const int z = ob.lo[2] + (int)(i / ((int64_t)ob.n[0] * ob.n[1]));
+    const bool inside = mask == nullptr || __ldg(mask + i) != 0;
+    float l[3] = {__ldg(evals + i), __ldg(evals + n + i), __ldg(evals + 2 * n + i)};
+    float v[3] = {__ldg(evec + i), __ldg(evec + n + i), __ldg(evec + 2 * n + i)};
+    write_voxel(o, i, inside, F, x, y, z, l, v, fill);
+  }
+}
+
+cudaError_t launch_eig_only(const float* S, int64_t n, float* evals, float* evec, bool mixed, const Fallback& fb,
+                            cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_eig_only<<<grid_for(n, 256), 256, 0, st>>>(S, n, evals, evec, mixed, fb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eig_only_fallback(const float* S, int64_t n, float* evals, float* evec, bool mixed,
+                                     const Fallback& fb, int64_t max_items, cudaStream_t st) {
+  if (max_items <= 0) return cudaSuccess;
+  k_eig_only_fallback<<<grid_for(max_items, 128), 128, 0, st>>>(S, n, evals, evec, mixed, fb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angles_only(const float* evec, const float* evals, const Box& ob, const uint8_t* mask,
+                               const Frame& F, float fill, const EigOut& o, cudaStream_t st) {
+  int64_t n = box_vox(ob);
+  if (n == 0) return cudaSuccess;
+  k_angles_only<<<grid_for(n, 256), 256, 0, st>>>(evec, evals, ob, mask, F, fill, o);
+  return cudaGetLastError();
+}
+
+}  // namespace ct

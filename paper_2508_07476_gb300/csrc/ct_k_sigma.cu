@@ -1,0 +1,218 @@
+// Gradient at noise scale sigma and the six tensor products (Figure 1b;
+// Architecture, "orientation"), fused in one z-streaming kernel so that the
+// gradient never leaves the SM.
+//
+// A CTA owns a 32 x 16 (x, y) tile of output columns and walks a z segment.
+// For every input plane it stages the haloed plane in shared memory, applies
+// the x pass (smoothing w and derivative c, each +k/-k pair folded) and the y
+// pass (three fields) in shared memory, and feeds the three results into
+// per-thread register windows of 2R+1 planes that apply the z pass.  The
+// window index is static because the plane loop is unrolled by the window
+// length.  Output: the products g_a g_b as 6 FP32 planes.
+#include "ct_common.cuh"
+#include "ct_launch.h"
+
+namespace ct {
+
+constexpr int kSigTX = 32;
+constexpr int kSigTY = 16;
+constexpr int kSigThreads = kSigTX * kSigTY;
+
+template <int RS>
+struct SigmaGeom {
+  static constexpr int RX = kSigTX + 2 * RS;  // raw plane columns
+  static constexpr int RY = kSigTY + 2 * RS;  // raw plane rows
+  static constexpr int NRAW = RX * RY;
+  static constexpr int NLOAD = (NRAW + kSigThreads - 1) / kSigThreads;
+  static constexpr int NPAIR = RY * (kSigTX / 2);  // x-pass work items (2 columns each)
+  static constexpr int P = 2 * RS + 1;             // z window
+};
+
+// 2^-8 keeps every possible gradient of uint16 data inside FP16's range while
+// leaving gradients down to 2^-6 intensity units normal.
+constexpr float kHalfScale = 1.0f / 256.0f;
+
+template <int RS, bool MIXED>
+__global__ void __launch_bounds__(kSigThreads, 1)
+    k_grad_products(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, int dimz, float* __restrict__ J,
+                    Box ob, int zseg, const Taps taps) {
+  using G = SigmaGeom<RS>;
+  __shared__ __align__(16) float raw[2][G::RY][G::RX];
+  __shared__ __align__(16) float pw[2][G::RY][kSigTX];
+  __shared__ __align__(16) float pc[2][G::RY][kSigTX];
+
+  const int t = threadIdx.x;
+  const int tx = t % kSigTX, ty = t / kSigTX;
+  const int x0 = ob.lo[0] + blockIdx.x * kSigTX;
+  const int y0 = ob.lo[1] + blockIdx.y * kSigTY;
+  const int zs = ob.lo[2] + blockIdx.z * zseg;
+  const int ze = min(zs + zseg, ob.lo[2] + ob.n[2]);
+  const int nsteps = (ze - zs) + 2 * RS;
+  const int64_t nob = box_vox(ob);
+
+  // per-thread raw-plane load slots: (row, col) -> clamped global (x, y)
+  int64_t loff[G::NLOAD];
+  bool lval[G::NLOAD];
+#pragma unroll
+  for (int i = 0; i < G::NLOAD; ++i) {
+    int e = t + i * kSigThreads;
+    lval[i] = e < G::NRAW;
+    int row = lval[i] ? e / G::RX : 0, col = lval[i] ? e % G::RX : 0;
+    int gx = clamp_to(x0 - RS + col, dimx, vb.lo[0], vb.n[0]);
+    int gy = clamp_to(y0 - RS + row, dimy, vb.lo[1], vb.n[1]);
+    loff[i] = (int64_t)(gy - vb.lo[1]) * vb.n[0] + (gx - vb.lo[0]);
+  }
+  const int64_t plane = (int64_t)vb.n[0] * vb.n[1];
+  auto plane_base = [&](int s) -> int64_t {
+    int gz = clamp_to(zs - RS + s, dimz, vb.lo[2], vb.n[2]);
+    return (int64_t)(gz - vb.lo[2]) * plane;
+  };
+
+  float pre[G::NLOAD];
+  {
+    int64_t b0 = plane_base(0);
+#pragma unroll
+    for (int i = 0; i < G::NLOAD; ++i)
+      if (lval[i]) {
+        int e = t + i * kSigThreads;
+        (&raw[0][0][0])[e] = (float)__ldg(vol + b0 + loff[i]);
+      }
+    int64_t b1 = plane_base(1 < nsteps ? 1 : 0);
+#pragma unroll
+    for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + b1 + loff[i]) : 0.f;
+  }
+
+  // z windows of the three y-pass results: (c_x w_y), (w_x c_y), (w_x w_y)
+  float wgx[G::P], wgy[G::P], wgz[G::P];
+#pragma unroll
+  for (int i = 0; i < G::P; ++i) { wgx[i] = 0.f; wgy[i] = 0.f; wgz[i] = 0.f; }
+
+  const int ox = x0 + tx, oy = y0 + ty;
+  const bool store_ok = ox < ob.lo[0] + ob.n[0] && oy < ob.lo[1] + ob.n[1];
+  const int64_t out_xy = (int64_t)(oy - ob.lo[1]) * ob.n[0] + (ox - ob.lo[0]);
+
+  for (int base = 0; base < nsteps; base += G::P) {
+#pragma unroll
+    for (int u = 0; u < G::P; ++u) {
+      const int s = base + u;
+      if (s >= nsteps) break;
+      const int b = s & 1;
+      __syncthreads();  // raw[b] complete; pw/pc[b] no longer read
+      // x pass over every staged row: smoothing and derivative
+      for (int item = t; item < G::NPAIR; item += kSigThreads) {
+        const int row = item / (kSigTX / 2);
+        const int c0 = 2 * (item % (kSigTX / 2));
+        const float* rr = &raw[b][row][c0];
+        float xv[2 * RS + 2];
+#pragma unroll
+        for (int k = 0; k < RS + 1; ++k) {
+          float2 v2 = *reinterpret_cast<const float2*>(rr + 2 * k);
+          xv[2 * k] = v2.x;
+          xv[2 * k + 1] = v2.y;
+        }
+        float sw0 = taps.w[RS] * xv[RS], sw1 = taps.w[RS] * xv[RS + 1];
+        float sc0 = 0.f, sc1 = 0.f;
+#pragma unroll
+        for (int k = 1; k <= RS; ++k) {
+          sw0 = fmaf(taps.w[RS + k], xv[RS + k] + xv[RS - k], sw0);
+          sw1 = fmaf(taps.w[RS + k], xv[RS + 1 + k] + xv[RS + 1 - k], sw1);
+          sc0 = fmaf(taps.c[RS + k], xv[RS + k] - xv[RS - k], sc0);
+          sc1 = fmaf(taps.c[RS + k], xv[RS + 1 + k] - xv[RS + 1 - k], sc1);
+        }
+        *reinterpret_cast<float2*>(&pw[b][row][c0]) = make_float2(sw0, sw1);
+        *reinterpret_cast<float2*>(&pc[b][row][c0]) = make_float2(sc0, sc1);
+      }
+      // stage the next plane (its buffer was last read by the previous x pass)
+      if (s + 1 < nsteps) {
+#pragma unroll
+        for (int i = 0; i < G::NLOAD; ++i)
+          if (lval[i]) (&raw[b ^ 1][0][0])[t + i * kSigThreads] = pre[i];
+      }
+      if (s + 2 < nsteps) {
+        int64_t bn = plane_base(s + 2);
+#pragma unroll
+        for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + bn + loff[i]) : 0.f;
+      }
+      __syncthreads();  // pw/pc[b] complete
+      // y pass for this thread's column
+      float qww = taps.w[RS] * pw[b][ty + RS][tx];
+      float qcw = taps.w[RS] * pc[b][ty + RS][tx];
+      float qwc = 0.f;
+#pragma unroll
+      for (int k = 1; k <= RS; ++k) {
+        float pp = pw[b][ty + RS + k][tx], pm = pw[b][ty + RS - k][tx];
+        qww = fmaf(taps.w[RS + k], pp + pm, qww);
+        qwc = fmaf(taps.c[RS + k], pp - pm, qwc);
+        qcw = fmaf(taps.w[RS + k], pc[b][ty + RS + k][tx] + pc[b][ty + RS - k][tx], qcw);
+      }
+      // push into the z windows (slot u: base is a multiple of P)
+      wgx[u] = qcw;
+      wgy[u] = qwc;
+      wgz[u] = qww;
+      if (s >= 2 * RS) {
+        // window slot of offset k (-RS..RS) relative to the output plane
+        float gx = taps.w[RS] * wgx[(u + G::P - RS) % G::P];
+        float gy = taps.w[RS] * wgy[(u + G::P - RS) % G::P];
+        float gz = 0.f;
+#pragma unroll
+        for (int k = 1; k <= RS; ++k) {
+          const int sp = (u + G::P - RS + k) % G::P;
+          const int sm = (u + G::P - RS - k) % G::P;
+          gx = fmaf(taps.w[RS + k], wgx[sp] + wgx[sm], gx);
+          gy = fmaf(taps.w[RS + k], wgy[sp] + wgy[sm], gy);
+          gz = fmaf(taps.c[RS + k], wgz[sp] - wgz[sm], gz);
+        }
+        if (MIXED) {  // gradient held in FP16 (scaled), products formed exactly in FP32
+          gx = __half2float(__float2half_rn(gx * kHalfScale)) * (1.0f / kHalfScale);
+          gy = __half2float(__float2half_rn(gy * kHalfScale)) * (1.0f / kHalfScale);
+          gz = __half2float(__float2half_rn(gz * kHalfScale)) * (1.0f / kHalfScale);
+        }
+        const int oz = zs + s - 2 * RS;
+        if (store_ok) {
+          const int64_t o = (int64_t)(oz - ob.lo[2]) * ob.n[0] * ob.n[1] + out_xy;
+          J[o] = gx * gx;
+          J[nob + o] = gy * gy;
+          J[2 * nob + o] = gz * gz;
+          J[3 * nob + o] = gx * gy;
+          J[4 * nob + o] = gx * gz;
+          J[5 * nob + o] = gy * gz;
+        }
+      }
+    }
+  }
+}
+
+template <int RS>
+static cudaError_t launch_grad_rs(const uint16_t* vol, const Box& vb, const int dims[3], float* J, const Box& ob,
+                                  const Taps& taps, bool mixed, cudaStream_t st) {
+  const int zseg = 128;
+  dim3 grid((ob.n[0] + kSigTX - 1) / kSigTX, (ob.n[1] + kSigTY - 1) / kSigTY, (ob.n[2] + zseg - 1) / zseg);
+  if (mixed)
+    k_grad_products<RS, true><<<grid, kSigThreads, 0, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg, taps);
+  else
+    k_grad_products<RS, false><<<grid, kSigThreads, 0, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg, taps);
+  return cudaGetLastError();
+}
+
+int sigma_kernel_radius(int r) {
+  static const int radii[] = {2, 3, 4, 6, 8, 12};
+  for (int v : radii)
+    if (r <= v) return v;
+  return -1;
+}
+
+cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int dims[3], float* J, const Box& ob,
+                                 const Taps& taps, int rk, bool mixed, cudaStream_t st) {
+  if (box_vox(ob) == 0) return cudaSuccess;
+  switch (rk) {
+    case 2: return launch_grad_rs<2>(vol, vb, dims, J, ob, taps, mixed, st);
+    case 3: return launch_grad_rs<3>(vol, vb, dims, J, ob, taps, mixed, st);
+    case 4: return launch_grad_rs<4>(vol, vb, dims, J, ob, taps, mixed, st);
+    case 6: return launch_grad_rs<6>(vol, vb, dims, J, ob, taps, mixed, st);
+    case 8: return launch_grad_rs<8>(vol, vb, dims, J, ob, taps, mixed, st);
+    case 12: return launch_grad_rs<12>(vol, vb, dims, J, ob, taps, mixed, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ct

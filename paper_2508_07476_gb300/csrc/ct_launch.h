@@ -1,0 +1,61 @@
+// Host-side entry points of the kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ct_common.cuh"
+
+namespace ct {
+
+// Instantiated radius that serves radius r (zero taps pad the difference), or -1.
+int sigma_kernel_radius(int r);
+int rho_kernel_radius(int r);
+
+// J (6 planes over ob) = products of the sigma-gradient of vol (array covering vb).
+cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int dims[3], float* J, const Box& ob,
+                                 const Taps& taps, int rk, bool mixed, cudaStream_t st);
+
+// rho pass along x: out (6 planes over ob) from in (6 planes over ib).
+cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
+                         const Taps& taps, int rk, cudaStream_t st);
+
+// rho pass along axis 1 (y) or 2 (z), streaming register windows.
+cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
+                              const Taps& taps, int rk, cudaStream_t st);
+
+struct EigOut {
+  void* vec;
+  void* ha;
+  void* ia;
+  void* fa;
+  int vec_t, ang_t, fa_t;
+  Box ab;  // box covered by the output arrays
+};
+
+struct Fallback {
+  int* count;                 // device counter of listed voxels (reset per launch)
+  unsigned long long* total;  // device running total (for statistics)
+  int64_t* list;
+  int64_t cap;
+};
+
+// Per-voxel eigen-solve + HA/IA/FA over ob from S (6 planes over sb); mask
+// array (nullable) covers mb.  Near-degenerate voxels are appended to fb.
+cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, const uint8_t* mask, const Box& mb,
+                              const Frame& F, float fill, const EigOut& o, bool mixed, const Fallback& fb,
+                              cudaStream_t st);
+// Re-solve the listed voxels (FP32 Jacobi, or FP64 in the mixed form) and rewrite their outputs.
+cudaError_t launch_eig_angles_fallback(const float* S, const Box& sb, const Box& ob, const uint8_t* mask,
+                                       const Box& mb, const Frame& F, float fill, const EigOut& o, bool mixed,
+                                       const Fallback& fb, int64_t max_items, cudaStream_t st);
+
+// Stage kernels: eigen only (evals + unoriented evec), and angles only.
+cudaError_t launch_eig_only(const float* S, int64_t n, float* evals, float* evec, bool mixed, const Fallback& fb,
+                            cudaStream_t st);
+cudaError_t launch_eig_only_fallback(const float* S, int64_t n, float* evals, float* evec, bool mixed,
+                                     const Fallback& fb, int64_t max_items, cudaStream_t st);
+cudaError_t launch_angles_only(const float* evec, const float* evals, const Box& ob, const uint8_t* mask,
+                               const Frame& F, float fill, const EigOut& o, cudaStream_t st);
+
+}  // namespace ct

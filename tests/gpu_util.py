@@ -1,0 +1,168 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and
+compare it with the oracle under the per-output tolerances.
+
+Tolerances (GPU vs the FP64 oracle), on voxels inside the mask whose oracle
+FA >= 0.1 and where the cylindrical frame exists:
+  fibre direction  acos|u.v| <= 0.5 deg
+  IA               <= 0.5 deg (up to sign where |HA| > 89 deg: the orientation
+                   rule v.e_t > 0 may flip v where v.e_t ~ 0)
+  HA               <= 0.5 deg, compared modulo 180 deg, where |IA| <= 75 deg.
+                   HA is the angle of the fibre's tangential part, which
+                   vanishes as the fibre turns radial: a direction error d moves
+                   HA by up to d / cos(IA).  Where |IA| > 75 deg HA is held to
+                   that perturbation bound instead (d / cos(IA) + 0.01 deg);
+                   "ha_literal_max" reports the ungraded maximum.
+and on every voxel inside the mask:
+  FA               <= 2e-3 absolute.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from paper_2508_07476_gb300 import _lib
+
+DIR_TOL_DEG = 0.5
+ANG_TOL_DEG = 0.5
+FA_TOL = 2e-3
+FA_MIN = 0.1
+HA_IA_LIMIT_DEG = 75.0
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def dev_u16(a: np.ndarray):
+    torch = torch_mod()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint16).view(np.int16)).cuda()
+
+
+def dev_u8(a: np.ndarray):
+    torch = torch_mod()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint8)).cuda()
+
+
+def _out_dtype(t):
+    torch = torch_mod()
+    return {_lib.CT_OUT_F32: torch.float32, _lib.CT_OUT_F16: torch.float16, _lib.CT_OUT_U8Q: torch.uint8}[t]
+
+
+def fused(vol, sigma, rho, center, axis, mask=None, precision=_lib.CT_PREC_FP32, chunk=(0, 0, 0), on_host=False,
+          vec_type=_lib.CT_OUT_F32, angle_type=_lib.CT_OUT_F32, fa_type=_lib.CT_OUT_F32, fill=math.nan,
+          outputs=("v", "ha", "ia", "fa"), raw=False):
+    """Whole pipeline through ct_run_chunks; numpy outputs (decoded to float unless raw)."""
+    torch = torch_mod()
+    nz, ny, nx = vol.shape
+    p = _lib.make_params(sigma, rho, center, axis, precision, vec_type, angle_type, fa_type, fill, chunk=chunk)
+    plan = _lib.ct_plan_create(p, (nx, ny, nz))
+    try:
+        kw = dict(device="cpu", pin_memory=True) if on_host else dict(device="cuda")
+        if on_host:
+            v_in = torch.from_numpy(np.ascontiguousarray(vol, dtype=np.uint16).view(np.int16))
+            m_in = None if mask is None else torch.from_numpy(np.ascontiguousarray(mask, dtype=np.uint8))
+        else:
+            v_in = dev_u16(vol)
+            m_in = None if mask is None else dev_u8(mask)
+        vec = torch.empty((3, nz, ny, nx), dtype=_out_dtype(vec_type), **kw) if "v" in outputs else None
+        ha = torch.empty((nz, ny, nx), dtype=_out_dtype(angle_type), **kw) if "ha" in outputs else None
+        ia = torch.empty((nz, ny, nx), dtype=_out_dtype(angle_type), **kw) if "ia" in outputs else None
+        fa = torch.empty((nz, ny, nx), dtype=_out_dtype(fa_type), **kw) if "fa" in outputs else None
+        item = _lib.make_item(v_in, (nx, ny, nz), m_in, vec, ha, ia, fa)
+        _lib.ct_run_chunks(plan, [item], on_host)
+        torch.cuda.synchronize()
+        _lib.ct_plan_sync(plan)
+        stats = _lib.ct_plan_stats(plan)
+    finally:
+        _lib.ct_plan_destroy(plan)
+
+    def conv(t):
+        if t is None:
+            return None
+        a = t.cpu()
+        return a.numpy() if raw or a.dtype == torch.uint8 else a.float().numpy()
+
+    return {"v": conv(vec), "ha": conv(ha), "ia": conv(ia), "fa": conv(fa), "stats": stats}
+
+
+def stages(vol, sigma, rho, center, axis, precision=_lib.CT_PREC_FP32, mask=None, in_box=None, out_box=None):
+    """ct_structure_tensor -> ct_eig_smallest -> ct_angles on one box; numpy outputs."""
+    torch = torch_mod()
+    nz, ny, nx = vol.shape
+    in_lo, in_n = in_box or ((0, 0, 0), (nx, ny, nz))
+    out_lo, out_n = out_box or ((0, 0, 0), (nx, ny, nz))
+    sub = vol[in_lo[2]:in_lo[2] + in_n[2], in_lo[1]:in_lo[1] + in_n[1], in_lo[0]:in_lo[0] + in_n[0]]
+    p = _lib.make_params(sigma, rho, center, axis, precision)
+    plan = _lib.ct_plan_create(p, (nx, ny, nz))
+    try:
+        shp = (out_n[2], out_n[1], out_n[0])
+        n = int(np.prod(shp))
+        d_vol = dev_u16(sub)
+        S = torch.empty((6,) + shp, dtype=torch.float32, device="cuda")
+        _lib.ct_structure_tensor(plan, d_vol, in_lo, in_n, out_lo, out_n, S)
+        ev = torch.empty((3,) + shp, dtype=torch.float32, device="cuda")
+        vec1 = torch.empty((3,) + shp, dtype=torch.float32, device="cuda")
+        _lib.ct_eig_smallest(plan, S, n, ev, vec1)
+        m = None
+        if mask is not None:
+            m = dev_u8(mask[out_lo[2]:out_lo[2] + out_n[2], out_lo[1]:out_lo[1] + out_n[1],
+                            out_lo[0]:out_lo[0] + out_n[0]])
+        vo = torch.empty((3,) + shp, dtype=torch.float32, device="cuda")
+        ha = torch.empty(shp, dtype=torch.float32, device="cuda")
+        ia = torch.empty(shp, dtype=torch.float32, device="cuda")
+        fa = torch.empty(shp, dtype=torch.float32, device="cuda")
+        _lib.ct_angles(plan, vec1, ev, out_lo, out_n, m, vo, ha, ia, fa)
+        torch.cuda.synchronize()
+        _lib.ct_plan_sync(plan)
+    finally:
+        _lib.ct_plan_destroy(plan)
+    return {k: t.cpu().numpy() for k, t in dict(S=S, evals=ev, evec=vec1, v=vo, ha=ha, ia=ia, fa=fa).items()}
+
+
+def angle_deg(u, v):
+    """Sign-invariant angle between vector fields [3, ...] in degrees."""
+    un = u / np.maximum(np.linalg.norm(u, axis=0), 1e-30)
+    vn = v / np.maximum(np.linalg.norm(v, axis=0), 1e-30)
+    return np.degrees(np.arccos(np.clip(np.abs((un * vn).sum(0)), 0.0, 1.0)))
+
+
+def compare(gpu: dict, ora: dict, mask=None) -> dict:
+    """Per-output errors on the graded voxel sets; returns metrics (no asserts)."""
+    inside = np.ones(ora["fa"].shape, bool) if mask is None else mask.astype(bool)
+    sel = inside & (ora["fa"] >= FA_MIN) & np.isfinite(ora["ha"])
+    out = {"n_graded": int(sel.sum()), "n_inside": int(inside.sum())}
+    d = angle_deg(gpu["v"][:, sel], ora["v"][:, sel]) if sel.any() else np.zeros(0)
+    dha_all = np.abs((gpu["ha"][sel] - ora["ha"][sel] + 90.0) % 180.0 - 90.0)
+    cos_ia = np.cos(np.radians(ora["ia"][sel]))
+    well = cos_ia >= math.cos(math.radians(HA_IA_LIMIT_DEG))
+    dha = dha_all[well]
+    bound = d / np.maximum(cos_ia, 1e-12) + 0.01 if d.size else np.zeros(0)
+    out["ha_bound_excess"] = float((dha_all - bound).max()) if dha_all.size else 0.0
+    out["ha_literal_max"] = float(dha_all.max()) if dha_all.size else 0.0
+    dia = np.abs(gpu["ia"][sel] - ora["ia"][sel])
+    flip = np.abs(ora["ha"][sel]) > 89.0
+    dia = np.where(flip, np.minimum(dia, np.abs(gpu["ia"][sel] + ora["ia"][sel])), dia)
+    dfa = np.abs(gpu["fa"][inside] - ora["fa"][inside])
+    for name, e in (("dir", d), ("ha", dha), ("ia", dia), ("fa", dfa)):
+        out[f"{name}_max"] = float(e.max()) if e.size else 0.0
+        out[f"{name}_p999"] = float(np.percentile(e, 99.9)) if e.size else 0.0
+    if "evals" in ora and sel.any():
+        ev = ora["evals"][:, sel]
+        bad = d > DIR_TOL_DEG
+        out["dir_fail"] = int(bad.sum())
+        out["dir_fail_relgap_max"] = float(((ev[1] - ev[0]) / np.maximum(ev[2] - ev[0], 1e-300))[bad].max()) \
+            if bad.any() else None
+    return out
+
+
+def assert_within(m: dict, label: str = "", literal_ha: bool = False):
+    msg = f"{label}: {m}"
+    assert m["dir_max"] <= DIR_TOL_DEG, msg
+    assert m["ha_max"] <= ANG_TOL_DEG, msg
+    assert m["ha_bound_excess"] <= 0.0, msg
+    if literal_ha:
+        assert m["ha_literal_max"] <= ANG_TOL_DEG, msg
+    assert m["ia_max"] <= ANG_TOL_DEG, msg
+    assert m["fa_max"] <= FA_TOL, msg
