@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -146,6 +147,7 @@ struct ct_plan_s {
   size_t in_cap[2] = {0, 0}, out_cap[2] = {0, 0}, hin_cap[2] = {0, 0}, hout_cap[2] = {0, 0};
   ct_stats stats;
   std::mutex mu;
+  int stream_block = 16;  // outputs per thread block of the y / z passes (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -293,8 +295,10 @@ ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uin
   CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts, sc.rks, mixed, st),
             "gradient kernel launch");
   CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr, sc.rkr, st), "rho x kernel launch");
-  CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr, sc.rkr, st), "rho y kernel launch");
-  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(A, Bxy, dims, S_out, ob, 2, sc.tr, sc.rkr, st), "rho z kernel launch");
+  CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr, sc.rkr, P->stream_block, st),
+            "rho y kernel launch");
+  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(A, Bxy, dims, S_out, ob, 2, sc.tr, sc.rkr, P->stream_block, st),
+            "rho z kernel launch");
   return CT_OK;
 }
 
@@ -338,6 +342,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   P->p = *params;
   for (int k = 0; k < 3; ++k) P->dims[k] = (int)vol_dims[k];
   std::memset(&P->stats, 0, sizeof P->stats);
+  if (const char* e = std::getenv("CT_TUNE_STREAM_BLOCK")) P->stream_block = std::atoi(e) == 8 ? 8 : 16;
   cudaGetDevice(&P->device);
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = cudaStreamCreateWithFlags(&P->st[k], cudaStreamNonBlocking);
@@ -453,24 +458,29 @@ std::vector<Box> chunk_grid(const int dims[3], const int64_t chunk[3]) {
   return out;
 }
 
-// Copy the sub-box `b` of a host array covering `arr` (x-fastest) into a dense buffer, or back.
-template <typename T>
-void gather_box(const T* src, const Box& arr, const Box& b, T* dst) {
-  for (int z = 0; z < b.n[2]; ++z)
-    for (int y = 0; y < b.n[1]; ++y) {
-      const T* s = src + (((int64_t)(b.lo[2] + z - arr.lo[2]) * arr.n[1] + (b.lo[1] + y - arr.lo[1])) * arr.n[0] +
-                          (b.lo[0] - arr.lo[0]));
-      std::memcpy(dst + ((int64_t)z * b.n[1] + y) * b.n[0], s, sizeof(T) * b.n[0]);
-    }
-}
-
-void scatter_box(const uint8_t* src, const Box& b, uint8_t* dst, const Box& arr, size_t esz) {
-  for (int z = 0; z < b.n[2]; ++z)
-    for (int y = 0; y < b.n[1]; ++y) {
-      uint8_t* d = dst + esz * (((int64_t)(b.lo[2] + z - arr.lo[2]) * arr.n[1] + (b.lo[1] + y - arr.lo[1])) *
-                                    arr.n[0] + (b.lo[0] - arr.lo[0]));
-      std::memcpy(d, src + esz * (((int64_t)z * b.n[1] + y) * b.n[0]), esz * b.n[0]);
-    }
+// 3D copy of box `b` between an array covering `arr` (x-fastest, element size
+// esz) and a dense array covering exactly `b`.
+cudaError_t copy_box(const void* src, void* dst, const Box& arr, const Box& b, size_t esz, bool to_device,
+                     cudaStream_t st) {
+  cudaMemcpy3DParms p;
+  std::memset(&p, 0, sizeof p);
+  cudaPitchedPtr whole = make_cudaPitchedPtr(const_cast<void*>(to_device ? src : dst), esz * arr.n[0], arr.n[0],
+                                             arr.n[1]);
+  cudaPitchedPtr dense = make_cudaPitchedPtr(const_cast<void*>(to_device ? dst : src), esz * b.n[0], b.n[0], b.n[1]);
+  cudaPos pos = make_cudaPos(esz * (b.lo[0] - arr.lo[0]), b.lo[1] - arr.lo[1], b.lo[2] - arr.lo[2]);
+  if (to_device) {
+    p.srcPtr = whole;
+    p.srcPos = pos;
+    p.dstPtr = dense;
+    p.kind = cudaMemcpyHostToDevice;
+  } else {
+    p.srcPtr = dense;
+    p.dstPtr = whole;
+    p.dstPos = pos;
+    p.kind = cudaMemcpyDeviceToHost;
+  }
+  p.extent = make_cudaExtent(esz * b.n[0], b.n[1], b.n[2]);
+  return cudaMemcpy3DAsync(&p, st);
 }
 
 struct ItemCtx {
@@ -533,6 +543,10 @@ ct_status run_device_item(ct_plan P, const ct_item& it, cudaStream_t st) {
   return CT_OK;
 }
 
+// Host-resident item: chunks alternate between the plan's two streams; each
+// chunk's haloed input box is copied straight from the caller's array, and its
+// outputs straight back into the caller's arrays, so copies of one chunk
+// overlap the kernels of the other.  Stream order protects each slot's buffers.
 ct_status run_host_item(ct_plan P, const ct_item& it) {
   ItemCtx c;
   ct_status rc = item_ctx(P, it, &c);
@@ -544,50 +558,27 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
     if (op.ptr[k]) out_bytes_per_vox += op.esz[k] * op.planes[k];
   std::vector<Box> chunks = chunk_grid(c.dims, P->p.chunk);
   int halo = c.sc.rs + c.sc.rr;
-  Box pending[2];
-  bool has_pending[2] = {false, false};
-
-  auto drain = [&](int slot) -> ct_status {
-    if (!has_pending[slot]) return CT_OK;
-    CT_CUDA(cudaEventSynchronize(P->ev[slot]), "chunk completion");
-    const Box& ob = pending[slot];
-    int64_t nv = box_vox(ob);
-    const uint8_t* src = (const uint8_t*)P->h_out[slot];
-    for (int k = 0; k < 4; ++k) {
-      if (!op.ptr[k]) continue;
-      int64_t nwhole = box_vox(c.whole);
-      for (int pl = 0; pl < op.planes[k]; ++pl) {
-        scatter_box(src, ob, (uint8_t*)op.ptr[k] + pl * nwhole * op.esz[k], c.whole, op.esz[k]);
-        src += nv * op.esz[k];
-      }
-    }
-    has_pending[slot] = false;
-    return CT_OK;
-  };
-
+  int64_t nwhole = box_vox(c.whole);
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
     int slot = (int)(ci & 1);
     cudaStream_t st = P->st[slot];
-    if ((rc = drain(slot))) return rc;
     const Box& ob = chunks[ci];
     Box ib = grow_clip(ob, halo, c.dims);
     int64_t niv = box_vox(ib), nov = box_vox(ob);
-    size_t in_bytes = sizeof(uint16_t) * niv;
+    size_t in_bytes = (sizeof(uint16_t) * niv + 255) / 256 * 256;
     size_t mask_bytes = it.mask ? (size_t)nov : 0;
     size_t out_bytes = out_bytes_per_vox * nov;
-    if ((rc = ensure_host(&P->h_in[slot], &P->hin_cap[slot], in_bytes + mask_bytes, "pinned input"))) return rc;
-    if ((rc = ensure_host(&P->h_out[slot], &P->hout_cap[slot], std::max<size_t>(out_bytes, 1), "pinned output")))
-      return rc;
     if ((rc = ensure_device((void**)&P->d_in[slot], &P->in_cap[slot], in_bytes + mask_bytes, "device input")))
       return rc;
     if ((rc = ensure_device(&P->d_out[slot], &P->out_cap[slot], std::max<size_t>(out_bytes, 1), "device output")))
       return rc;
-    gather_box(it.vol, c.whole, ib, (uint16_t*)P->h_in[slot]);
-    uint8_t* hmask = (uint8_t*)P->h_in[slot] + in_bytes;
-    if (it.mask) gather_box(it.mask, c.whole, ob, hmask);
-    CT_CUDA(cudaMemcpyAsync(P->d_in[slot], P->h_in[slot], in_bytes + mask_bytes, cudaMemcpyHostToDevice, st),
-            "host to device copy");
-    P->stats.h2d_bytes += (int64_t)(in_bytes + mask_bytes);
+    CT_CUDA(copy_box(it.vol, P->d_in[slot], c.whole, ib, sizeof(uint16_t), true, st), "host to device copy");
+    uint8_t* dmask = nullptr;
+    if (it.mask) {
+      dmask = (uint8_t*)P->d_in[slot] + in_bytes;
+      CT_CUDA(copy_box(it.mask, dmask, c.whole, ob, 1, true, st), "host to device copy");
+    }
+    P->stats.h2d_bytes += (int64_t)(sizeof(uint16_t) * niv + mask_bytes);
     Box G = grow_clip(ob, c.sc.rr, c.dims);
     if ((rc = ensure_scratch(P, slot, box_vox(G)))) return rc;
     float* S = P->buf[slot][1];
@@ -601,18 +592,19 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
       dptr += nov * op.esz[k] * op.planes[k];
     }
     EigOut o{dout[0], dout[1], dout[2], dout[3], P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
-    const uint8_t* dmask = it.mask ? (const uint8_t*)P->d_in[slot] + in_bytes : nullptr;
     if ((rc = eig_stage(P, S, ob, dmask, ob, c.F, o, slot, mixed, st))) return rc;
-    CT_CUDA(cudaMemcpyAsync(P->h_out[slot], P->d_out[slot], out_bytes, cudaMemcpyDeviceToHost, st),
-            "device to host copy");
+    for (int k = 0; k < 4; ++k) {
+      if (!op.ptr[k]) continue;
+      for (int pl = 0; pl < op.planes[k]; ++pl) {
+        const uint8_t* src = (const uint8_t*)dout[k] + (size_t)pl * nov * op.esz[k];
+        uint8_t* dst = (uint8_t*)op.ptr[k] + (size_t)pl * nwhole * op.esz[k];
+        CT_CUDA(copy_box(src, dst, c.whole, ob, op.esz[k], false, st), "device to host copy");
+      }
+    }
     P->stats.d2h_bytes += (int64_t)out_bytes;
-    CT_CUDA(cudaEventRecord(P->ev[slot], st), "event record");
-    pending[slot] = ob;
-    has_pending[slot] = true;
     P->stats.voxels += nov;
   }
-  for (int s = 0; s < 2; ++s)
-    if ((rc = drain(s))) return rc;
+  for (int s = 0; s < 2; ++s) CT_CUDA(cudaStreamSynchronize(P->st[s]), "chunked run");
   return CT_OK;
 }
 

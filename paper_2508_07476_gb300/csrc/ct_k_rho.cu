@@ -35,22 +35,44 @@ __global__ void __launch_bounds__(kRxThreads)
   static_assert(W % 4 == 0, "row stride must allow 16-byte loads");
   __shared__ __align__(16) float sin_[6][kRxRows][W];
   __shared__ __align__(16) float sout[6][kRxRows][kRxOut];
+  __shared__ int64_t rin[kRxRows], rout[kRxRows];  // row offsets (component 0) in the input / output arrays
+  __shared__ int rvalid[kRxRows];
 
   const int t = threadIdx.x;
   const int x0 = ob.lo[0] + blockIdx.y * kRxOut;
   const int nrows = ob.n[1] * ob.n[2];
   const int row0 = blockIdx.x * kRxRows;
   const int64_t nib = box_vox(ib), nob = box_vox(ob);
-
-  // stage: element e -> (comp, row, col)
-  for (int e = t; e < 6 * kRxRows * W; e += kRxThreads) {
-    const int col = e % W;
-    const int row = (e / W) % kRxRows;
-    const int comp = e / (W * kRxRows);
-    const int r = min(row0 + row, nrows - 1);
+  if (t < kRxRows) {
+    const int r = min(row0 + t, nrows - 1);
     const int y = ob.lo[1] + r % ob.n[1], z = ob.lo[2] + r / ob.n[1];
-    const int gx = clamp_to(x0 - RR + col, dimx, ib.lo[0], ib.n[0]);
-    sin_[comp][row][col] = __ldg(in + comp * nib + box_index(ib, gx, y, z));
+    rin[t] = box_index(ib, ib.lo[0], y, z);
+    rout[t] = box_index(ob, ob.lo[0], y, z);
+    rvalid[t] = row0 + t < nrows;
+  }
+  __syncthreads();
+
+  // stage in 16-byte chunks: q -> (comp, row, 4 columns).  A chunk that lies
+  // inside the volume and the input array, on a 16-byte boundary, is one
+  // vector load; a chunk that needs clamping takes four scalar loads.
+  constexpr int QW = W / 4;
+  const int xlo_ok = max(0, ib.lo[0]), xhi_ok = min(dimx, ib.lo[0] + ib.n[0]);  // [xlo_ok, xhi_ok) loadable as is
+  for (int q = t; q < 6 * kRxRows * QW; q += kRxThreads) {
+    const int cq = q % QW;
+    const int row = (q / QW) % kRxRows;
+    const int comp = q / (QW * kRxRows);
+    const int gx0 = x0 - RR + 4 * cq;
+    const float* rowp = in + comp * nib + rin[row] - ib.lo[0];
+    float4 v;
+    if (gx0 >= xlo_ok && gx0 + 3 < xhi_ok && ((reinterpret_cast<uintptr_t>(rowp + gx0) & 15) == 0)) {
+      v = __ldg(reinterpret_cast<const float4*>(rowp + gx0));
+    } else {
+      v.x = __ldg(rowp + clamp_to(gx0, dimx, ib.lo[0], ib.n[0]));
+      v.y = __ldg(rowp + clamp_to(gx0 + 1, dimx, ib.lo[0], ib.n[0]));
+      v.z = __ldg(rowp + clamp_to(gx0 + 2, dimx, ib.lo[0], ib.n[0]));
+      v.w = __ldg(rowp + clamp_to(gx0 + 3, dimx, ib.lo[0], ib.n[0]));
+    }
+    *reinterpret_cast<float4*>(&sin_[comp][row][4 * cq]) = v;
   }
   __syncthreads();
   {
@@ -82,82 +104,123 @@ __global__ void __launch_bounds__(kRxThreads)
     dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
   }
   __syncthreads();
-  for (int e = t; e < 6 * kRxRows * kRxOut; e += kRxThreads) {
-    const int col = e % kRxOut;
-    const int row = (e / kRxOut) % kRxRows;
-    const int comp = e / (kRxOut * kRxRows);
-    const int r = row0 + row;
-    const int x = x0 + col;
-    if (r < nrows && x < ob.lo[0] + ob.n[0]) {
-      const int y = ob.lo[1] + r % ob.n[1], z = ob.lo[2] + r / ob.n[1];
-      out[comp * nob + box_index(ob, x, y, z)] = sout[comp][row][col];
+  const int xend = ob.lo[0] + ob.n[0];
+  constexpr int QO = kRxOut / 4;
+  for (int q = t; q < 6 * kRxRows * QO; q += kRxThreads) {
+    const int cq = q % QO;
+    const int row = (q / QO) % kRxRows;
+    const int comp = q / (QO * kRxRows);
+    if (!rvalid[row]) continue;
+    const int x = x0 + 4 * cq;
+    float* dst = out + comp * nob + rout[row] + (x - ob.lo[0]);
+    const float4 v = *reinterpret_cast<const float4*>(&sout[comp][row][4 * cq]);
+    if (x + 3 < xend && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+      *reinterpret_cast<float4*>(dst) = v;
+    } else {
+      if (x < xend) dst[0] = v.x;
+      if (x + 1 < xend) dst[1] = v.y;
+      if (x + 2 < xend) dst[2] = v.z;
+      if (x + 3 < xend) dst[3] = v.w;
     }
   }
 }
 
 // ------------------------------------------------------ y / z streaming pass
-constexpr int kStreamD = 4;  // prefetch distance (steps)
+// One thread per (x, component, cross-row) column walks the pass axis in
+// blocks of kT outputs.  A block's outputs come from a register window of
+// kT + 2R inputs; between blocks the window slides by kT (2R register moves
+// per kT (2R+1) FMAs), so the code of one block is small and no halo is
+// re-read.  Inputs arrive through a per-thread shared-memory ring two blocks
+// deep, filled by cp.async one block ahead of use.  Offsets inside one
+// component plane are 32-bit (planes are limited to 2^31 voxels).
+constexpr int kStreamThreads = 256;
 
-template <int RR>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void cp_async4(uint32_t smem_dst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// A CTA spans blockDim.x consecutive x (a multiple of 32) and blockDim.y
+// (component, cross-row) pairs, so the accesses of one step form contiguous runs.
+template <int RR, int kT>
+__global__ void __launch_bounds__(kStreamThreads)
     k_rho_stream(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis,
                  int seg, const Taps taps) {
   constexpr int P = 2 * RR + 1;
-  constexpr int Q = P + kStreamD;
+  constexpr int WN = kT + 2 * RR;
+  __shared__ float ring[2 * kT][kStreamThreads];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int other = 3 - axis;  // the non-x cross axis
-  const int x = ob.lo[0] + blockIdx.x * 32 + threadIdx.x;
-  const int cross = blockIdx.y * blockDim.y + threadIdx.y;  // (comp, other) pair
-  const int n_other = ob.n[other];
-  if (cross >= 6 * n_other) return;
+  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_other = other == 1 ? ob.n[1] : ob.n[2];
+  const bool cok = blockIdx.y * blockDim.y + threadIdx.y < 6 * n_other;
+  const int cross = min(blockIdx.y * blockDim.y + threadIdx.y, 6 * n_other - 1);  // (comp, other) pair
   const int comp = cross / n_other;
-  const int o = ob.lo[other] + cross % n_other;
-  const int p0 = ob.lo[axis] + blockIdx.z * seg;  // first output position on the axis
-  const int L = min(seg, ob.lo[axis] + ob.n[axis] - p0);
+  const int o = (other == 1 ? ob.lo[1] : ob.lo[2]) + cross % n_other;
+  const int a_lo = axis == 1 ? ob.lo[1] : ob.lo[2], a_n = axis == 1 ? ob.n[1] : ob.n[2];
+  const int p0 = a_lo + blockIdx.z * seg;  // first output position on the axis
+  const int L = min(seg, a_lo + a_n - p0);
   if (L <= 0) return;
-  const bool xok = x < ob.lo[0] + ob.n[0];
-  const int xi = xok ? x : ob.lo[0] + ob.n[0] - 1;
+  const bool xok = x < ob.lo[0] + ob.n[0] && cok;
+  const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
 
-  // input: fixed (x, other), varying axis coordinate
-  const int64_t nib = box_vox(ib);
-  int ci[3];
-  ci[0] = xi;
-  ci[other] = o;
-  ci[axis] = ib.lo[axis];
-  const float* base = in + comp * nib + box_index(ib, ci[0], ci[1], ci[2]);
-  const int64_t istride = axis == 1 ? (int64_t)ib.n[0] : (int64_t)ib.n[0] * ib.n[1];
-  const int alo = ib.lo[axis], an = ib.n[axis];
-  auto ld = [&](int step) -> float {  // input step j <-> position p0 - RR + j
-    int p = clamp_to(p0 - RR + step, dim_axis, alo, an);
-    return __ldg(base + (int64_t)(p - alo) * istride);
-  };
+  // input column: fixed (x, other); element offset of axis position a is (a - alo) * istride
+  const int alo = axis == 1 ? ib.lo[1] : ib.lo[2], an = axis == 1 ? ib.n[1] : ib.n[2];
+  const int yb = axis == 1 ? ib.lo[1] : o;
+  const int zb = axis == 1 ? o : ib.lo[2];
+  const float* base = in + comp * box_vox(ib) + box_index(ib, xi, yb, zb);
+  const int istride = axis == 1 ? ib.n[0] : ib.n[0] * ib.n[1];
+  const int qlo = max(0, alo) - alo, qhi = min(dim_axis - 1, alo + an - 1) - alo;  // clamp range, relative
+  const int q0 = p0 - RR - alo;  // relative position of input step 0
+  auto src = [&](int step) -> const float* { return base + min(max(q0 + step, qlo), qhi) * istride; };
 
-  const int64_t nob = box_vox(ob);
-  int co[3];
-  co[0] = xi;
-  co[other] = o;
-  co[axis] = p0;
-  float* obase = out + comp * nob + box_index(ob, co[0], co[1], co[2]);
-  const int64_t ostride = axis == 1 ? (int64_t)ob.n[0] : (int64_t)ob.n[0] * ob.n[1];
+  const int yo = axis == 1 ? p0 : o;
+  const int zo = axis == 1 ? o : p0;
+  float* obase = out + comp * box_vox(ob) + box_index(ob, xi, yo, zo);
+  const int ostride = axis == 1 ? ob.n[0] : ob.n[0] * ob.n[1];
 
-  float win[Q];
-#pragma unroll
-  for (int j = 0; j < Q - 1; ++j) win[j] = ld(j);
-  win[Q - 1] = 0.f;
+  const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(&ring[0][tid]);
+  constexpr uint32_t kSlot = kStreamThreads * sizeof(float);
 
-  for (int b = 0; b < L; b += Q) {
+  float win[WN];
 #pragma unroll
-    for (int u = 0; u < Q; ++u) {
-      const int s = b + u;
-      if (s >= L) break;
-      win[(u + Q - 1) % Q] = ld(s + Q - 1);
-      float a0 = 0.f, a1 = 0.f;
+  for (int j = 0; j < 2 * RR; ++j) win[j] = __ldg(src(j));
+  // blocks 0 and 1: steps 2R + t, t < 2 kT, into ring slot t
 #pragma unroll
-      for (int k = 0; k < P; k += 2) a0 = fmaf(taps.w[k], win[(u + k) % Q], a0);
+  for (int h = 0; h < 2; ++h) {
 #pragma unroll
-      for (int k = 1; k < P; k += 2) a1 = fmaf(taps.w[k], win[(u + k) % Q], a1);
-      if (xok) obase[(int64_t)s * ostride] = a0 + a1;
-    }
+    for (int t = 0; t < kT; ++t) cp_async4(ring0 + (h * kT + t) * kSlot, src(2 * RR + h * kT + t));
+    cp_async_commit();
   }
+  const int nb = (L + kT - 1) / kT;
+  for (int bk = 0; bk < nb; ++bk) {
+    cp_async_wait<1>();  // block bk has landed (block bk + 1 may still be in flight)
+    const int half = (bk & 1) * kT;
+#pragma unroll
+    for (int t = 0; t < kT; ++t) win[2 * RR + t] = ring[half + t][tid];
+    const int s0 = bk * kT;
+#pragma unroll
+    for (int i = 0; i < kT; ++i) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < P; k += 4) {
+        a0 = fmaf(taps.w[k], win[i + k], a0);
+        if (k + 1 < P) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
+        if (k + 2 < P) a2 = fmaf(taps.w[k + 2], win[i + k + 2], a2);
+        if (k + 3 < P) a3 = fmaf(taps.w[k + 3], win[i + k + 3], a3);
+      }
+      if (xok && s0 + i < L) obase[(s0 + i) * ostride] = (a0 + a1) + (a2 + a3);
+    }
+    // refill the slots just consumed with block bk + 2 (their values are in registers)
+#pragma unroll
+    for (int t = 0; t < kT; ++t) cp_async4(ring0 + (half + t) * kSlot, src(2 * RR + (bk + 2) * kT + t));
+    cp_async_commit();
+#pragma unroll
+    for (int j = 0; j < 2 * RR; ++j) win[j] = win[j + kT];
+  }
+  cp_async_wait<0>();
 }
 
 template <int RR>
@@ -187,34 +250,40 @@ cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], floa
 
 template <int RR>
 static cudaError_t launch_stream_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
-                                   int axis, const Taps& taps, cudaStream_t st) {
+                                   int axis, const Taps& taps, int block_t, cudaStream_t st) {
   const int other = 3 - axis;
   const int n_axis = ob.n[axis];
+  if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   // segment the walk so that the grid has enough CTAs to fill the GPU
   int64_t cols = (int64_t)((ob.n[0] + 31) / 32) * 32 * 6 * ob.n[other];
   int nseg = 1;
-  while (nseg < 16 && cols * nseg < (int64_t)152 * 2048 * 4 && n_axis / (nseg * 2) >= 4 * (2 * RR + 1)) nseg *= 2;
+  while (nseg < 16 && cols * nseg < (int64_t)152 * 1024 * 8 && n_axis / (nseg * 2) >= 4 * (2 * RR + 1)) nseg *= 2;
   int seg = (n_axis + nseg - 1) / nseg;
-  dim3 block(32, 8);
-  dim3 grid((ob.n[0] + 31) / 32, (6 * ob.n[other] + 7) / 8, (n_axis + seg - 1) / seg);
+  int wx = 1;  // warps along x per CTA
+  while (wx < kStreamThreads / 32 && 32 * wx < ob.n[0]) wx *= 2;
+  dim3 block(32 * wx, kStreamThreads / (32 * wx));
+  dim3 grid((ob.n[0] + block.x - 1) / block.x, (6 * ob.n[other] + block.y - 1) / block.y, (n_axis + seg - 1) / seg);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
-  k_rho_stream<RR><<<grid, block, 0, st>>>(in, ib, dims[axis], out, ob, axis, seg, taps);
+  if (block_t == 8)
+    k_rho_stream<RR, 8><<<grid, block, 0, st>>>(in, ib, dims[axis], out, ob, axis, seg, taps);
+  else
+    k_rho_stream<RR, 16><<<grid, block, 0, st>>>(in, ib, dims[axis], out, ob, axis, seg, taps);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                              const Taps& taps, int rk, cudaStream_t st) {
+                              const Taps& taps, int rk, int block_t, cudaStream_t st) {
   if (box_vox(ob) == 0) return cudaSuccess;
   if (axis != 1 && axis != 2) return cudaErrorInvalidValue;
   switch (rk) {
-    case 4: return launch_stream_r<4>(in, ib, dims, out, ob, axis, taps, st);
-    case 6: return launch_stream_r<6>(in, ib, dims, out, ob, axis, taps, st);
-    case 8: return launch_stream_r<8>(in, ib, dims, out, ob, axis, taps, st);
-    case 12: return launch_stream_r<12>(in, ib, dims, out, ob, axis, taps, st);
-    case 16: return launch_stream_r<16>(in, ib, dims, out, ob, axis, taps, st);
-    case 24: return launch_stream_r<24>(in, ib, dims, out, ob, axis, taps, st);
-    case 32: return launch_stream_r<32>(in, ib, dims, out, ob, axis, taps, st);
-    case 36: return launch_stream_r<36>(in, ib, dims, out, ob, axis, taps, st);
+    case 4: return launch_stream_r<4>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 6: return launch_stream_r<6>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 8: return launch_stream_r<8>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 12: return launch_stream_r<12>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 16: return launch_stream_r<16>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 24: return launch_stream_r<24>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 32: return launch_stream_r<32>(in, ib, dims, out, ob, axis, taps, block_t, st);
+    case 36: return launch_stream_r<36>(in, ib, dims, out, ob, axis, taps, block_t, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -20,9 +20,9 @@ cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int d
 cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                          const Taps& taps, int rk, cudaStream_t st);
 
-// rho pass along axis 1 (y) or 2 (z), streaming register windows.
+// rho pass along axis 1 (y) or 2 (z), streaming register windows of block_t (8 or 16) outputs.
 cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                              const Taps& taps, int rk, cudaStream_t st);
+                              const Taps& taps, int rk, int block_t, cudaStream_t st);
 
 struct EigOut {
   void* vec;

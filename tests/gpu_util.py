@@ -122,10 +122,12 @@ def stages(vol, sigma, rho, center, axis, precision=_lib.CT_PREC_FP32, mask=None
 
 
 def angle_deg(u, v):
-    """Sign-invariant angle between vector fields [3, ...] in degrees."""
-    un = u / np.maximum(np.linalg.norm(u, axis=0), 1e-30)
-    vn = v / np.maximum(np.linalg.norm(v, axis=0), 1e-30)
-    return np.degrees(np.arccos(np.clip(np.abs((un * vn).sum(0)), 0.0, 1.0)))
+    """Sign-invariant angle between vector fields [3, ...] in degrees (float64,
+    atan2 of |u x v| and |u . v|, accurate for tiny angles)."""
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    cr = np.cross(u, v, axis=0)
+    return np.degrees(np.arctan2(np.linalg.norm(cr, axis=0), np.abs((u * v).sum(0))))
 
 
 def compare(gpu: dict, ora: dict, mask=None) -> dict:
