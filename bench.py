@@ -123,6 +123,22 @@ def _workload(size: int):
     return W
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Largest value over the ranks (the step time the job is charged with)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_voxels_per_s(voxels_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank processes its own volume (weak scaling)."""
+    return world * voxels_per_rank / (ms_max * 1e-3)
+
+
 def _fma_per_voxel(rs: int, rr: int) -> int:
     """Algorithmic FMAs per interior voxel: 8 sigma passes, 6 products, 18 rho passes."""
     return 8 * (2 * rs + 1) + 6 + 18 * (2 * rr + 1)
@@ -275,14 +291,6 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     forms = {}
     accuracy = {}
     kernels = {}
@@ -313,11 +321,11 @@ def run_ours(args):
             if sampler:
                 clocks = sampler.stop()
             ms = e0.elapsed_time(e1) / args.steps
-            ms = max_over_ranks(ms)
+            ms = max_over_ranks(ms, world)
             kt = _lib.ct_plan_kernel_times(plan)
             _lib.ct_plan_profile(plan, False)
             st = _lib.ct_plan_stats(plan, reset=True)
-            forms[name] = {"ms_per_step": ms, "voxels_per_s": world * nvox / (ms * 1e-3),
+            forms[name] = {"ms_per_step": ms, "voxels_per_s": job_voxels_per_s(nvox, world, ms),
                            "fallback_voxels_per_step": st["fallback_voxels"] / args.steps}
             kernels[name] = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in kt.items()}
             if headline:
@@ -371,7 +379,7 @@ def run_ours(args):
             for _ in range(k_e2e):
                 _lib.ct_run_chunks(plan, [hitem], True)
             torch.cuda.synchronize()
-            el = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+            el = max_over_ranks((time.perf_counter() - t0) / k_e2e, world)
             st = _lib.ct_plan_stats(plan, reset=True)
             e2e = {"value": world * nvox / el, "unit": UNIT, "h2d_bytes_per_step": st["h2d_bytes"] // k_e2e,
                    "d2h_bytes_per_step": st["d2h_bytes"] // k_e2e, "ms_per_step": el * 1e3,
