@@ -175,6 +175,24 @@ typedef struct ct_stats {
 ct_status ct_plan_stats(ct_plan plan, ct_stats* out, int32_t reset);
 
 /*
+ * Eigen stage for callers that cannot allocate device memory: frameworks that
+ * own all device memory through their own pools, services that forbid
+ * allocation once running (cudaMalloc may synchronise the device), code that
+ * must not fail for lack of memory half-way through.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ * Same arguments and results as ct_eig_smallest, without a plan: precision is
+ * CT_PREC_FP32 or CT_PREC_MIXED.  The re-solve list lives in a fixed 8 MiB
+ * array of the library's device image (resident on every device that loads
+ * the library, until exit), so at most 2^20 tensors per call; larger n is
+ * CT_ERR_INVALID.  No allocation of any kind is made.  The first call on a
+ * device looks the array's address up (make it before any stream capture).
+ * All calls share the array: each call clears its counters on `stream`, and
+ * calls that overlap on the GPU race on it.
+ */
+ct_status ct_eig_smallest_noalloc(const float* d_S, int64_t n, float* d_evals, float* d_evec, int32_t precision,
+                                  void* stream);
+
+/*
  * Per-kernel timing.  While enabled, the plan records a CUDA event pair on the
  * launching stream around every kernel it launches; ct_plan_kernel_times
  * synchronises, adds the elapsed times up per kernel name, returns them

@@ -83,6 +83,8 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.POINTER(ct_item), ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     ("ct_plan_sync", ctypes.c_int32, [ctypes.c_void_p]),
     ("ct_plan_stats", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ct_stats), ctypes.c_int32]),
+    ("ct_eig_smallest_noalloc", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("ct_plan_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("ct_plan_kernel_times", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_kernel_time), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -172,6 +174,10 @@ def ct_structure_tensor(plan, vol, in_lo, in_n, out_lo, out_n, S, stream=None) -
 
 def ct_eig_smallest(plan, S, n: int, evals, evec, stream=None) -> None:
     _check(load().ct_eig_smallest(plan, _ptr(S), int(n), _ptr(evals), _ptr(evec), _stream(stream)))
+
+
+def ct_eig_smallest_noalloc(S, n: int, evals, evec, precision: int = CT_PREC_FP32, stream=None) -> None:
+    _check(load().ct_eig_smallest_noalloc(_ptr(S), int(n), _ptr(evals), _ptr(evec), int(precision), _stream(stream)))
 
 
 def ct_angles(plan, evec, evals, out_lo, out_n, mask, vec, ha, ia, fa, stream=None) -> None:

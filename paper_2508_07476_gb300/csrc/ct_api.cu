@@ -692,3 +692,16 @@ ct_status ct_plan_kernel_times(ct_plan P, ct_kernel_time* out, int32_t capacity,
 }
 
 }  // extern "C"
+
+namespace ct {
+// Record a message for ct_last_error from another translation unit of the library.
+ct_status set_error(ct_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+}  // namespace ct
