@@ -41,7 +41,11 @@ def _needs(obj: str, src: str, headers) -> bool:
     return os.path.getmtime(src) > t or any(os.path.getmtime(h) > t for h in headers)
 
 
-def build(verbose: bool = False, jobs: int | None = None, extra_flags=()) -> str:
+def build(verbose: bool = False, jobs: int | None = None, extra_flags=(), out_dir: str | None = None) -> str:
+    """Compile and link; `out_dir` (default the in-tree _build) and `extra_flags`
+    allow side-by-side builds with other compile-time tunables."""
+    BUILD = out_dir or globals()["BUILD"]
+    LIB = os.path.join(BUILD, "libct_gb300.so")
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \

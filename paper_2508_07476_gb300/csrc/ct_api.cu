@@ -138,6 +138,10 @@ struct ct_plan_s {
   unsigned long long* fb_total = nullptr;
   int64_t* fb_list[2] = {nullptr, nullptr};
   int64_t fb_cap[2] = {0, 0};
+  // re-solve list of the fused z pass (index + tensor per entry)
+  int64_t* fs_idx[2] = {nullptr, nullptr};
+  float* fs_S[2] = {nullptr, nullptr};
+  int64_t fs_cap[2] = {0, 0};
   // device and pinned staging for host-resident items
   uint16_t* d_in[2] = {nullptr, nullptr};
   uint8_t* d_mask[2] = {nullptr, nullptr};
@@ -148,6 +152,8 @@ struct ct_plan_s {
   ct_stats stats;
   std::mutex mu;
   int stream_block = 16;  // outputs per thread block of the y / z passes (tuning choice)
+  bool fuse_z_eig = false;  // z pass fused with the eigen stage, or split (tuning choice)
+  bool fuse_xy = true;      // x and y passes in one kernel, or two (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -249,6 +255,38 @@ ct_status ensure_scratch(ct_plan P, int slot, int64_t vox) {
   return ensure_fallback(P, slot, vox);
 }
 
+// List for the fused z pass: 1/16 of the voxels (at least 64 Ki entries); the
+// kernel re-solves in place whatever does not fit.
+ct_status ensure_fused_fallback(ct_plan P, int slot, int64_t vox) {
+  int64_t cap = std::max<int64_t>(65536, vox / 16);
+  if (!P->fb_count[slot]) CT_CUDA(cudaMalloc(&P->fb_count[slot], sizeof(int)), "counter allocation");
+  if (!P->fb_total) {
+    CT_CUDA(cudaMalloc(&P->fb_total, sizeof(unsigned long long)), "counter allocation");
+    CT_CUDA(cudaMemset(P->fb_total, 0, sizeof(unsigned long long)), "counter reset");
+  }
+  if (P->fs_cap[slot] < cap) {
+    if (P->fs_idx[slot]) cudaFree(P->fs_idx[slot]);
+    if (P->fs_S[slot]) cudaFree(P->fs_S[slot]);
+    P->fs_idx[slot] = nullptr;
+    P->fs_S[slot] = nullptr;
+    P->fs_cap[slot] = 0;
+    CT_CUDA(cudaMalloc(&P->fs_idx[slot], sizeof(int64_t) * cap), "re-solve list allocation");
+    CT_CUDA(cudaMalloc(&P->fs_S[slot], sizeof(float) * 6 * cap), "re-solve list allocation");
+    P->fs_cap[slot] = cap;
+  }
+  return CT_OK;
+}
+
+FallbackS fused_fallback_of(ct_plan P, int slot) {
+  FallbackS fb;
+  fb.count = P->fb_count[slot];
+  fb.total = P->fb_total;
+  fb.idx = P->fs_idx[slot];
+  fb.S = P->fs_S[slot];
+  fb.cap = P->fs_cap[slot];
+  return fb;
+}
+
 Fallback fallback_of(ct_plan P, int slot) {
   Fallback fb;
   fb.count = P->fb_count[slot];
@@ -276,10 +314,11 @@ Fallback fallback_of(ct_plan P, int slot) {
     (P)->stats.launches += 1;                                               \
   } while (0)
 
-// The four smoothing stages: J over G, then x, y, z passes of rho into S over ob.
-// vol covers vb.  Result: S (6 planes over ob) in `S_out`.
-ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
-                        const Box& ob, float* S_out, int slot, bool mixed, cudaStream_t st) {
+// Gradient, products and the x, y passes of rho: J over G (first buffer), then
+// S_xy over Bxy (returned with its box; the second buffer when x and y are
+// fused, the first otherwise).  vol covers vb.
+ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb, const Box& ob,
+                    int slot, bool mixed, cudaStream_t st, float** Sxy, Box* Bxy_out) {
   Box G = grow_clip(ob, sc.rr, dims);
   Box Bx = G, Bxy = G;
   Bx.lo[0] = ob.lo[0];
@@ -294,11 +333,57 @@ ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uin
   float* B = P->buf[slot][1];
   CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts, sc.rks, mixed, st),
             "gradient kernel launch");
-  CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr, sc.rkr, st), "rho x kernel launch");
-  CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr, sc.rkr, P->stream_block, st),
-            "rho y kernel launch");
-  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(A, Bxy, dims, S_out, ob, 2, sc.tr, sc.rkr, P->stream_block, st),
+  if (P->fuse_xy) {
+    CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr, sc.rkr, st), "rho xy kernel launch");
+    *Sxy = B;
+  } else {
+    CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr, sc.rkr, st), "rho x kernel launch");
+    CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr, sc.rkr, P->stream_block, st),
+              "rho y kernel launch");
+    *Sxy = A;
+  }
+  *Bxy_out = Bxy;
+  return CT_OK;
+}
+
+// The whole smoothing chain into S (6 planes over ob): the stage API.
+ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
+                        const Box& ob, float* S_out, int slot, bool mixed, cudaStream_t st) {
+  float* Sxy = nullptr;
+  Box Bxy;
+  ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
+  if (rc) return rc;
+  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S_out, ob, 2, sc.tr, sc.rkr, P->stream_block, st),
             "rho z kernel launch");
+  return CT_OK;
+}
+
+ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
+                    const EigOut& o, int slot, bool mixed, cudaStream_t st);
+
+// The fused hot path: x, y passes, then the z pass fused with eigen + angles,
+// then the re-solve of the listed voxels.  Outputs in arrays covering o.ab.
+ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
+                       const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F, const EigOut& o, int slot,
+                       bool mixed, cudaStream_t st) {
+  float* Sxy = nullptr;
+  Box Bxy;
+  ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
+  if (rc) return rc;
+  if (!P->fuse_z_eig) {  // split: z pass into the free buffer, then the eigen stage
+    float* S = Sxy == P->buf[slot][0] ? P->buf[slot][1] : P->buf[slot][0];
+    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr, sc.rkr, P->stream_block, st),
+              "rho z kernel launch");
+    return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
+  }
+  if ((rc = ensure_fused_fallback(P, slot, box_vox(ob)))) return rc;
+  FallbackS fb = fused_fallback_of(P, slot);
+  CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
+  CT_LAUNCH(P, st, "rho_z_eig",
+            launch_rho_z_eig(Sxy, Bxy, dims, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, sc.tr, sc.rkr, st),
+            "rho z + eigen kernel launch");
+  CT_LAUNCH(P, st, "eig_resolve", launch_fallback_s(ob, F, P->p.fill_value, o, mixed, fb, fb.cap, st),
+            "re-solve kernel launch");
   return CT_OK;
 }
 
@@ -343,6 +428,8 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   for (int k = 0; k < 3; ++k) P->dims[k] = (int)vol_dims[k];
   std::memset(&P->stats, 0, sizeof P->stats);
   if (const char* e = std::getenv("CT_TUNE_STREAM_BLOCK")) P->stream_block = std::atoi(e) == 8 ? 8 : 16;
+  if (const char* e = std::getenv("CT_TUNE_FUSE_Z_EIG")) P->fuse_z_eig = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_FUSE_XY")) P->fuse_xy = std::atoi(e) != 0;
   cudaGetDevice(&P->device);
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = cudaStreamCreateWithFlags(&P->st[k], cudaStreamNonBlocking);
@@ -364,6 +451,8 @@ ct_status ct_plan_destroy(ct_plan P) {
       if (P->buf[s][k]) cudaFree(P->buf[s][k]);
     if (P->fb_count[s]) cudaFree(P->fb_count[s]);
     if (P->fb_list[s]) cudaFree(P->fb_list[s]);
+    if (P->fs_idx[s]) cudaFree(P->fs_idx[s]);
+    if (P->fs_S[s]) cudaFree(P->fs_S[s]);
     if (P->d_in[s]) cudaFree(P->d_in[s]);
     if (P->d_mask[s]) cudaFree(P->d_mask[s]);
     if (P->d_out[s]) cudaFree(P->d_out[s]);
@@ -532,12 +621,8 @@ ct_status run_device_item(ct_plan P, const ct_item& it, cudaStream_t st) {
   if (rc) return rc;
   bool mixed = P->p.precision == CT_PREC_MIXED;
   for (const Box& ob : chunk_grid(c.dims, P->p.chunk)) {
-    Box G = grow_clip(ob, c.sc.rr, c.dims);
-    if ((rc = ensure_scratch(P, 0, box_vox(G)))) return rc;
-    float* S = P->buf[0][1];  // J (A) -> Sx (B) -> Sxy (A) -> S (B): B is free again by the z pass
-    if ((rc = tensor_stages(P, c.sc, c.dims, it.vol, c.whole, ob, S, 0, mixed, st))) return rc;
     EigOut o{it.vec, it.ha, it.ia, it.fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, c.whole};
-    if ((rc = eig_stage(P, S, ob, it.mask, c.whole, c.F, o, 0, mixed, st))) return rc;
+    if ((rc = fused_stages(P, c.sc, c.dims, it.vol, c.whole, ob, it.mask, c.whole, c.F, o, 0, mixed, st))) return rc;
     P->stats.voxels += box_vox(ob);
   }
   return CT_OK;
@@ -579,10 +664,6 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
       CT_CUDA(copy_box(it.mask, dmask, c.whole, ob, 1, true, st), "host to device copy");
     }
     P->stats.h2d_bytes += (int64_t)(sizeof(uint16_t) * niv + mask_bytes);
-    Box G = grow_clip(ob, c.sc.rr, c.dims);
-    if ((rc = ensure_scratch(P, slot, box_vox(G)))) return rc;
-    float* S = P->buf[slot][1];
-    if ((rc = tensor_stages(P, c.sc, c.dims, P->d_in[slot], ib, ob, S, slot, mixed, st))) return rc;
     // device outputs: dense planes over ob, in the order vec(3), ha, ia, fa
     uint8_t* dptr = (uint8_t*)P->d_out[slot];
     void* dout[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -592,7 +673,7 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
       dptr += nov * op.esz[k] * op.planes[k];
     }
     EigOut o{dout[0], dout[1], dout[2], dout[3], P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
-    if ((rc = eig_stage(P, S, ob, dmask, ob, c.F, o, slot, mixed, st))) return rc;
+    if ((rc = fused_stages(P, c.sc, c.dims, P->d_in[slot], ib, ob, dmask, ob, c.F, o, slot, mixed, st))) return rc;
     for (int k = 0; k < 4; ++k) {
       if (!op.ptr[k]) continue;
       for (int pl = 0; pl < op.planes[k]; ++pl) {

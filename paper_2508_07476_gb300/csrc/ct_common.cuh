@@ -48,6 +48,14 @@ __device__ __forceinline__ int clamp_to(int p, int dim, int lo, int n) {
   return clampi(clampi(p, 0, dim - 1), lo, lo + n - 1);
 }
 
+// Asynchronous 4-byte global -> shared copies (cp.async), grouped per commit.
+__device__ __forceinline__ void cp_async4(uint32_t smem_dst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------------------
 // Eigen-decomposition of a symmetric 3x3 tensor s = (xx, yy, zz, xy, xz, yz).
 // ---------------------------------------------------------------------------
@@ -90,38 +98,91 @@ __device__ __forceinline__ T null_vector(const Sym3<T>& s, T lam, T v[3]) {
 
 // Closed-form eigenvalues (trigonometric solution of the characteristic cubic,
 // O. K. Smith, Comm. ACM 4(4), 1961) and the smallest-eigenvalue eigenvector.
+// With B = (S - qI)/p, q = tr/3, p^2 = |S - qI|_F^2 / 6 and phi = acos(det(B)/2)/3:
+//   l3 = q + 2p cos(phi),  l1 = q + 2p cos(phi + 2pi/3) = q - p (cos(phi) + sqrt(3) sin(phi)),
+//   l2 = 3q - l1 - l3.
 // Eigenvalues ascending in l[0..2].  Returns true when the result is well
-// conditioned, false when the voxel should be re-solved.
+// conditioned, false when the voxel should be re-solved.  The FP32 form takes
+// sin/cos of phi (in [0, pi/3]) from the hardware approximations and the
+// reciprocal square roots from rsqrt; the errors they add, a few 1e-7 of p,
+// are far below what the re-solve threshold leaves between l1 and l2.
 template <typename T>
-__device__ __forceinline__ bool eig_closed(const Sym3<T>& s, T l[3], T v[3]) {
-  const T third = T(1) / T(3);
-  T q = (s.a + s.b + s.c) * third;
-  T aq = s.a - q, bq = s.b - q, cq = s.c - q;
-  T p1 = s.d * s.d + s.e * s.e + s.f * s.f;
-  T p2 = aq * aq + bq * bq + cq * cq + T(2) * p1;
-  if (p2 == T(0)) {  // isotropic (including the zero tensor): every vector is an eigenvector
+__device__ __forceinline__ bool eig_closed(const Sym3<T>& s, T l[3], T v[3]);
+
+template <>
+__device__ __forceinline__ bool eig_closed<float>(const Sym3<float>& s, float l[3], float v[3]) {
+  const float q = (s.a + s.b + s.c) * (1.f / 3.f);
+  const float aq = s.a - q, bq = s.b - q, cq = s.c - q;
+  const float p1 = s.d * s.d + s.e * s.e + s.f * s.f;
+  const float p2 = aq * aq + bq * bq + cq * cq + 2.f * p1;
+  if (p2 == 0.f) {  // isotropic (including the zero tensor): every vector is an eigenvector
     l[0] = l[1] = l[2] = q;
-    v[0] = T(1); v[1] = T(0); v[2] = T(0);
+    v[0] = 1.f; v[1] = 0.f; v[2] = 0.f;
     return true;
   }
-  T p = sqrt(p2 / T(6));
-  T ip = T(1) / p;
-  T B00 = aq * ip, B11 = bq * ip, B22 = cq * ip, B01 = s.d * ip, B02 = s.e * ip, B12 = s.f * ip;
-  T det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
-  T r = det * T(0.5);
-  r = r < T(-1) ? T(-1) : (r > T(1) ? T(1) : r);
-  T phi = acos(r) * third;
-  const T two_pi_3 = T(2.0943951023931954923);
-  T l3 = q + T(2) * p * cos(phi);
-  T l1 = q + T(2) * p * cos(phi + two_pi_3);
-  T l2 = T(3) * q - l1 - l3;
-  if (l2 < l1) { T t = l1; l1 = l2; l2 = t; }
-  if (l3 < l2) { T t = l2; l2 = l3; l3 = t; }
+  const float p6 = p2 * (1.f / 6.f);
+  const float ip = rsqrtf(p6);
+  const float p = p6 * ip;
+  const float B00 = aq * ip, B11 = bq * ip, B22 = cq * ip, B01 = s.d * ip, B02 = s.e * ip, B12 = s.f * ip;
+  const float det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
+  const float r = fminf(fmaxf(0.5f * det, -1.f), 1.f);
+  const float phi = acosf(r) * (1.f / 3.f);
+  float sp, cp;
+  __sincosf(phi, &sp, &cp);
+  float l3 = q + 2.f * p * cp;
+  float l1 = q - p * (cp + 1.7320508075688772f * sp);
+  float l2 = 3.f * q - l1 - l3;
+  if (l2 < l1) { float t = l1; l1 = l2; l2 = t; }
+  if (l3 < l2) { float t = l2; l2 = l3; l3 = t; }
   l[0] = l1; l[1] = l2; l[2] = l3;
-  T bn = null_vector(s, l1, v);
-  T spread = l3 - l1;
-  bool ok = (l2 - l1) >= T(kDegenerateGap) * spread && bn > T(0);
-  return ok;
+  // null vector of S - l1 I: the largest cross product of two of its rows
+  const float r0x = s.a - l1, r0y = s.d, r0z = s.e;
+  const float r1x = s.d, r1y = s.b - l1, r1z = s.f;
+  const float r2x = s.e, r2y = s.f, r2z = s.c - l1;
+  const float x01 = r0y * r1z - r0z * r1y, y01 = r0z * r1x - r0x * r1z, z01 = r0x * r1y - r0y * r1x;
+  const float x02 = r0y * r2z - r0z * r2y, y02 = r0z * r2x - r0x * r2z, z02 = r0x * r2y - r0y * r2x;
+  const float x12 = r1y * r2z - r1z * r2y, y12 = r1z * r2x - r1x * r2z, z12 = r1x * r2y - r1y * r2x;
+  const float n01 = x01 * x01 + y01 * y01 + z01 * z01;
+  const float n02 = x02 * x02 + y02 * y02 + z02 * z02;
+  const float n12 = x12 * x12 + y12 * y12 + z12 * z12;
+  float bx = x01, by = y01, bz = z01, bn = n01;
+  if (n02 > bn) { bx = x02; by = y02; bz = z02; bn = n02; }
+  if (n12 > bn) { bx = x12; by = y12; bz = z12; bn = n12; }
+  if (bn > 0.f) {
+    const float inv = rsqrtf(bn);
+    v[0] = bx * inv; v[1] = by * inv; v[2] = bz * inv;
+  } else {
+    v[0] = 1.f; v[1] = 0.f; v[2] = 0.f;
+  }
+  return (l2 - l1) >= kDegenerateGap * (l3 - l1) && bn > 0.f;
+}
+
+// FP64 version (the re-solve of the mixed form): library acos / cos / sqrt.
+template <>
+__device__ __forceinline__ bool eig_closed<double>(const Sym3<double>& s, double l[3], double v[3]) {
+  const double q = (s.a + s.b + s.c) / 3.0;
+  const double aq = s.a - q, bq = s.b - q, cq = s.c - q;
+  const double p1 = s.d * s.d + s.e * s.e + s.f * s.f;
+  const double p2 = aq * aq + bq * bq + cq * cq + 2.0 * p1;
+  if (p2 == 0.0) {
+    l[0] = l[1] = l[2] = q;
+    v[0] = 1.0; v[1] = 0.0; v[2] = 0.0;
+    return true;
+  }
+  const double p = sqrt(p2 / 6.0);
+  const double ip = 1.0 / p;
+  const double B00 = aq * ip, B11 = bq * ip, B22 = cq * ip, B01 = s.d * ip, B02 = s.e * ip, B12 = s.f * ip;
+  const double det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
+  const double r = fmin(fmax(0.5 * det, -1.0), 1.0);
+  const double phi = acos(r) / 3.0;
+  double l3 = q + 2.0 * p * cos(phi);
+  double l1 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+  double l2 = 3.0 * q - l1 - l3;
+  if (l2 < l1) { double t = l1; l1 = l2; l2 = t; }
+  if (l3 < l2) { double t = l2; l2 = l3; l3 = t; }
+  l[0] = l1; l[1] = l2; l[2] = l3;
+  const double bn = null_vector(s, l1, v);
+  return (l2 - l1) >= (double)kDegenerateGap * (l3 - l1) && bn > 0.0;
 }
 
 // Cyclic Jacobi (Golub & Van Loan, Matrix Computations, section 8.5) on a
@@ -179,7 +240,7 @@ __device__ __forceinline__ float fa_of(const float l[3]) {
   float den = l1 * l1 + l2 * l2 + l3 * l3;
   if (den == 0.f) return 0.f;
   float num = (l1 - l2) * (l1 - l2) + (l2 - l3) * (l2 - l3) + (l3 - l1) * (l3 - l1);
-  return sqrtf(0.5f * num / den);
+  return sqrtf(__fdividef(0.5f * num, den));
 }
 
 // Cylindrical left-ventricle frame (unit axis, centre), per launch.

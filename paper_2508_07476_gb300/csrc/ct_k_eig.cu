@@ -78,39 +78,24 @@ __device__ __forceinline__ void push_fallback(const Fallback& fb, int64_t i) {
   atomicAdd(fb.total, 1ull);
 }
 
-// Each thread takes two voxels per iteration (i and i + stride) and issues the
-// mask and tensor loads of both before any arithmetic, for memory parallelism.
+// One thread per voxel on a 3D grid (x from the thread index, y and z from the
+// block index, rows beyond 65535 folded into blockIdx.z), so no index division.
 __global__ void __launch_bounds__(256)
     k_eig_angles(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
                  float fill, EigOut o, bool mixed, Fallback fb) {
-  const int64_t nvox = box_vox(ob);
-  const int64_t ns = box_vox(sb);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < nvox; i0 += 2 * stride) {
-    int x[2], y[2], z[2];
-    bool live[2], inside[2];
-    Sym3<float> s[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t i = i0 + h * stride;
-      live[h] = i < nvox;
-      const int64_t ii = live[h] ? i : i0;
-      x[h] = ob.lo[0] + (int)(ii % ob.n[0]);
-      y[h] = ob.lo[1] + (int)((ii / ob.n[0]) % ob.n[1]);
-      z[h] = ob.lo[2] + (int)(ii / ((int64_t)ob.n[0] * ob.n[1]));
-      inside[h] = mask == nullptr || __ldg(mask + box_index(mb, x[h], y[h], z[h])) != 0;
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      if (inside[h]) s[h] = load_sym(S, ns, box_index(sb, x[h], y[h], z[h]));
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (!live[h]) continue;
-      float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
-      if (inside[h] && !eig_closed<float>(s[h], l, v)) push_fallback(fb, i0 + h * stride);
-      write_voxel(o, box_index(o.ab, x[h], y[h], z[h]), inside[h], F, x[h], y[h], z[h], l, v, fill);
-    }
+  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= ob.lo[0] + ob.n[0]) return;
+  const int row = blockIdx.z * gridDim.y + blockIdx.y;  // y + ny * z within ob
+  if (row >= ob.n[1] * ob.n[2]) return;
+  const int yr = row % ob.n[1], zr = row / ob.n[1];  // one division per thread, 32-bit
+  const int y = ob.lo[1] + yr, z = ob.lo[2] + zr;
+  const bool inside = mask == nullptr || __ldg(mask + box_index(mb, x, y, z)) != 0;
+  float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
+  if (inside) {
+    const Sym3<float> s = load_sym(S, box_vox(sb), box_index(sb, x, y, z));
+    if (!eig_closed<float>(s, l, v)) push_fallback(fb, ((int64_t)zr * ob.n[1] + yr) * ob.n[0] + (x - ob.lo[0]));
   }
+  write_voxel(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
 
 __global__ void __launch_bounds__(128)
@@ -141,7 +126,10 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
                               cudaStream_t st) {
   int64_t n = box_vox(ob);
   if (n == 0) return cudaSuccess;
-  k_eig_angles<<<grid_for((n + 1) / 2, 256), 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  const int rows = ob.n[1] * ob.n[2];
+  const int gy = rows < 65535 ? rows : 65535;
+  dim3 grid((ob.n[0] + 255) / 256, gy, (rows + gy - 1) / gy);
+  k_eig_angles<<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   return cudaGetLastError();
 }
 

@@ -23,13 +23,26 @@ int rho_kernel_radius(int r) {
 }
 
 // ----------------------------------------------------------------- x pass
-constexpr int kRxOut = 128;  // outputs per row per CTA
-constexpr int kRxRows = 4;   // rows per CTA
-constexpr int kRxPer = 8;    // outputs per thread
-constexpr int kRxThreads = 6 * kRxRows * (kRxOut / kRxPer);  // 384
+// Tile shape (compile-time tunables): outputs per row, rows per CTA, outputs per thread.
+#ifndef CT_RX_OUT
+#define CT_RX_OUT 128
+#endif
+#ifndef CT_RX_ROWS
+#define CT_RX_ROWS 4
+#endif
+#ifndef CT_RX_PER
+#define CT_RX_PER 8
+#endif
+#ifndef CT_RX_MINB
+#define CT_RX_MINB 1
+#endif
+constexpr int kRxOut = CT_RX_OUT;
+constexpr int kRxRows = CT_RX_ROWS;
+constexpr int kRxPer = CT_RX_PER;
+constexpr int kRxThreads = 6 * kRxRows * (kRxOut / kRxPer);
 
 template <int RR>
-__global__ void __launch_bounds__(kRxThreads)
+__global__ void __launch_bounds__(kRxThreads, CT_RX_MINB)
     k_rho_x(const float* __restrict__ in, Box ib, int dimx, float* __restrict__ out, Box ob, const Taps taps) {
   constexpr int W = kRxOut + 2 * RR;  // staged row length (multiple of 4 for even RR)
   static_assert(W % 4 == 0, "row stride must allow 16-byte loads");
@@ -100,8 +113,8 @@ __global__ void __launch_bounds__(kRxThreads)
       acc[i] = a0 + a1;
     }
     float4* dst = reinterpret_cast<float4*>(&sout[comp][row][seg * kRxPer]);
-    dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+#pragma unroll
+    for (int i = 0; i < kRxPer / 4; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
   }
   __syncthreads();
   const int xend = ob.lo[0] + ob.n[0];
@@ -135,12 +148,6 @@ __global__ void __launch_bounds__(kRxThreads)
 // component plane are 32-bit (planes are limited to 2^31 voxels).
 constexpr int kStreamThreads = 256;
 
-__device__ __forceinline__ void cp_async4(uint32_t smem_dst, const float* gsrc) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // A CTA spans blockDim.x consecutive x (a multiple of 32) and blockDim.y
 // (component, cross-row) pairs, so the accesses of one step form contiguous runs.

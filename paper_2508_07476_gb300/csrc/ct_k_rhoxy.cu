@@ -1,0 +1,198 @@
+// The x and y passes of the integration-scale smoothing (Figure 1b) fused in
+// one y-streaming kernel, so the x-smoothed field never goes to HBM.
+//
+// A CTA owns kXT output columns (x) of one (z, component) row and walks y.
+// Input rows of the product field arrive kTB at a time through a cp.async
+// ring of kStages stages; all threads apply the x pass to those kTB rows
+// (each thread kTB consecutive outputs of one row, register-blocked from
+// 16-byte shared loads), the results go to shared memory, and each thread
+// appends its own column's kTB values to a register window of kTB + 2R rows
+// that applies the y pass.  Shared row strides are padded so that the eight
+// lanes of a 16-byte access phase hit distinct banks.
+#include "ct_common.cuh"
+#include "ct_launch.h"
+
+namespace ct {
+
+#ifndef CT_XY_TB
+#define CT_XY_TB 16
+#endif
+#ifndef CT_XY_MINB
+#define CT_XY_MINB 1
+#endif
+constexpr int kXT = 256;        // output columns per CTA (= threads)
+constexpr int kTB = CT_XY_TB;   // rows per block (8 or 16)
+constexpr int kStages = 3;      // cp.async ring depth (blocks)
+static_assert(kTB == 8 || kTB == 16, "rows per block");
+
+template <int RR>
+struct XYGeom {
+  static constexpr int XW = kXT + 2 * RR;                      // staged row width (x pass: 8 per thread)
+  static constexpr int XS = XW + ((4 - XW % 8) + 8) % 8;       // padded stride, = 4 (mod 8)
+  static constexpr int SXS = kXT + 4;                          // x-pass output row stride
+  static constexpr int QW = XW / 4;                            // 16-byte chunks per staged row
+  static constexpr int W = (2 * RR + kTB - 1) / kTB;           // warm-up blocks
+  static constexpr int PAD = W * kTB - 2 * RR;                 // extra leading rows
+  static constexpr int WN = kTB + 2 * RR;                      // y window
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
+}
+
+template <int RR>
+__global__ void __launch_bounds__(kXT, CT_XY_MINB)
+    k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
+             const Taps taps) {
+  using G = XYGeom<RR>;
+  extern __shared__ __align__(16) float smem[];
+  float* stage = smem;                              // [kStages][kTB][XS]
+  float* sx = smem + kStages * kTB * G::XS;         // [kTB][SXS]
+
+  const int t = threadIdx.x;
+  const int x0 = ob.lo[0] + blockIdx.x * kXT;
+  const int xend = ob.lo[0] + ob.n[0];
+  const int comp = blockIdx.y / ob.n[2];
+  const int z = ob.lo[2] + blockIdx.y % ob.n[2];
+  const int p0 = ob.lo[1] + blockIdx.z * seg;
+  const int L = min(seg, ob.lo[1] + ob.n[1] - p0);
+  if (L <= 0) return;
+
+  // input rows: row j of the walk is y = p0 - RR - PAD + j, clamped
+  const float* plane = in + comp * box_vox(ib) + (int64_t)(z - ib.lo[2]) * ib.n[0] * ib.n[1];
+  const int ylo = max(0, ib.lo[1]), yhi = min(dimy - 1, ib.lo[1] + ib.n[1] - 1);
+  const int xlo_ok = max(0, ib.lo[0]), xhi_ok = min(dimx, ib.lo[0] + ib.n[0]);
+  const int nblocks = G::W + (L + kTB - 1) / kTB;
+  const uint32_t stage0 = (uint32_t)__cvta_generic_to_shared(stage);
+
+  auto issue = [&](int b) {  // stage block b (kTB rows) into ring slot b % kStages
+    float* dst = stage + (b % kStages) * kTB * G::XS;
+    const uint32_t dst_s = stage0 + (uint32_t)((b % kStages) * kTB * G::XS) * 4u;
+    for (int q = t; q < kTB * G::QW; q += kXT) {
+      const int rr = q / G::QW, cq = q % G::QW;
+      const int y = min(max(p0 - RR - G::PAD + b * kTB + rr, ylo), yhi);
+      const float* row = plane + (int64_t)(y - ib.lo[1]) * ib.n[0] - ib.lo[0];
+      const int gx0 = x0 - RR + 4 * cq;
+      if (gx0 >= xlo_ok && gx0 + 3 < xhi_ok && ((reinterpret_cast<uintptr_t>(row + gx0) & 15) == 0)) {
+        cp_async16(dst_s + (uint32_t)(rr * G::XS + 4 * cq) * 4u, row + gx0);
+      } else {
+        float* d = dst + rr * G::XS + 4 * cq;
+        d[0] = __ldg(row + clamp_to(gx0, dimx, ib.lo[0], ib.n[0]));
+        d[1] = __ldg(row + clamp_to(gx0 + 1, dimx, ib.lo[0], ib.n[0]));
+        d[2] = __ldg(row + clamp_to(gx0 + 2, dimx, ib.lo[0], ib.n[0]));
+        d[3] = __ldg(row + clamp_to(gx0 + 3, dimx, ib.lo[0], ib.n[0]));
+      }
+    }
+  };
+
+  // y window of this thread's column
+  float win[G::WN];
+#pragma unroll
+  for (int j = 0; j < G::WN; ++j) win[j] = 0.f;
+  // x pass: each thread computes 8 consecutive outputs of one row per 256 outputs;
+  // with 16-row blocks it takes two rows (xr and xr + 8)
+  const int xr = t % 8;
+  const int xseg = t / 8;
+  const bool xok = x0 + t < xend;
+  float* obase = out + comp * box_vox(ob) + box_index(ob, min(x0 + t, xend - 1), p0, z);
+  const int ostride = ob.n[0];
+
+#pragma unroll
+  for (int b = 0; b < kStages - 1; ++b) {
+    if (b < nblocks) issue(b);
+    cp_async_commit();
+  }
+  for (int b = 0; b < nblocks; ++b) {
+    cp_async_wait<kStages - 2>();  // block b has landed (this thread's copies)
+    __syncthreads();               // ... and everyone's; slot (b-1) % kStages is free again
+    if (b + kStages - 1 < nblocks) issue(b + kStages - 1);
+    cp_async_commit();
+    // x pass: 8 outputs of row xr (+ 8 r), columns xseg*8 .. +7
+#pragma unroll
+    for (int r8 = 0; r8 < kTB / 8; ++r8) {
+      const int row = xr + 8 * r8;
+      const float* src = stage + (b % kStages) * kTB * G::XS + row * G::XS + xseg * 8;
+      float acc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+#pragma unroll
+      for (int j4 = 0; j4 < (8 + 2 * RR + 3) / 4; ++j4) {
+        const float4 v4 = *reinterpret_cast<const float4*>(src + 4 * j4);
+        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 4 * j4 + e;  // input index; contributes to outputs i with 0 <= j - i <= 2R
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (j - i >= 0 && j - i <= 2 * RR) acc[i] = fmaf(taps.w[j - i], vv[e], acc[i]);
+        }
+      }
+      float4* d = reinterpret_cast<float4*>(sx + row * G::SXS + xseg * 8);
+      d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      d[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+    __syncthreads();  // x-pass rows complete
+    // y pass: slide the window by kTB and append this column's new rows
+#pragma unroll
+    for (int j = 0; j < 2 * RR; ++j) win[j] = win[j + kTB];
+#pragma unroll
+    for (int r = 0; r < kTB; ++r) win[2 * RR + r] = sx[r * G::SXS + t];
+    if (b >= G::W) {
+      const int m = (b - G::W) * kTB;  // first output row of this block, relative to p0
+#pragma unroll
+      for (int i = 0; i < kTB; ++i) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * RR; k += 4) {
+          a0 = fmaf(taps.w[k], win[i + k], a0);
+          if (k + 1 <= 2 * RR) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
+          if (k + 2 <= 2 * RR) a2 = fmaf(taps.w[k + 2], win[i + k + 2], a2);
+          if (k + 3 <= 2 * RR) a3 = fmaf(taps.w[k + 3], win[i + k + 3], a3);
+        }
+        if (xok && m + i < L) obase[(m + i) * ostride] = (a0 + a1) + (a2 + a3);
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int RR>
+static cudaError_t launch_xy_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
+                               const Taps& taps, cudaStream_t st) {
+  using G = XYGeom<RR>;
+  if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_rho_xy<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int64_t rows = (int64_t)6 * ob.n[2];
+  if (rows > 65535) return cudaErrorInvalidValue;
+  const int64_t ctas = (int64_t)((ob.n[0] + kXT - 1) / kXT) * rows;
+  int nseg = 1;
+  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 && ob.n[1] / (nseg * 2) >= 8 * kTB) nseg *= 2;
+  const int seg = (ob.n[1] + nseg - 1) / nseg;
+  dim3 grid((ob.n[0] + kXT - 1) / kXT, (unsigned)rows, (ob.n[1] + seg - 1) / seg);
+  k_rho_xy<RR><<<grid, kXT, smem, st>>>(in, ib, dims[0], dims[1], out, ob, seg, taps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
+                          const Taps& taps, int rk, cudaStream_t st) {
+  if (box_vox(ob) == 0) return cudaSuccess;
+  switch (rk) {
+    case 4: return launch_xy_r<4>(in, ib, dims, out, ob, taps, st);
+    case 6: return launch_xy_r<6>(in, ib, dims, out, ob, taps, st);
+    case 8: return launch_xy_r<8>(in, ib, dims, out, ob, taps, st);
+    case 12: return launch_xy_r<12>(in, ib, dims, out, ob, taps, st);
+    case 16: return launch_xy_r<16>(in, ib, dims, out, ob, taps, st);
+    case 24: return launch_xy_r<24>(in, ib, dims, out, ob, taps, st);
+    case 32: return launch_xy_r<32>(in, ib, dims, out, ob, taps, st);
+    case 36: return launch_xy_r<36>(in, ib, dims, out, ob, taps, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ct

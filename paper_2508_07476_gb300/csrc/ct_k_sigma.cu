@@ -17,6 +17,10 @@ namespace ct {
 constexpr int kSigTX = 32;
 constexpr int kSigTY = 16;
 constexpr int kSigThreads = kSigTX * kSigTY;
+#ifndef CT_SIG_PREFETCH
+#define CT_SIG_PREFETCH 4
+#endif
+constexpr int kSigPrefetch = CT_SIG_PREFETCH;  // planes ahead for the L2 prefetch hint
 
 template <int RS>
 struct SigmaGeom {
@@ -38,8 +42,7 @@ __global__ void __launch_bounds__(kSigThreads, 1)
                     Box ob, int zseg, const Taps taps) {
   using G = SigmaGeom<RS>;
   __shared__ __align__(16) float raw[2][G::RY][G::RX];
-  __shared__ __align__(16) float pw[2][G::RY][kSigTX];
-  __shared__ __align__(16) float pc[2][G::RY][kSigTX];
+  __shared__ __align__(16) float2 pwc[2][G::RY][kSigTX];  // (smoothed, derivative) of the x pass
 
   const int t = threadIdx.x;
   const int tx = t % kSigTX, ty = t / kSigTX;
@@ -119,8 +122,7 @@ __global__ void __launch_bounds__(kSigThreads, 1)
           sc0 = fmaf(taps.c[RS + k], xv[RS + k] - xv[RS - k], sc0);
           sc1 = fmaf(taps.c[RS + k], xv[RS + 1 + k] - xv[RS + 1 - k], sc1);
         }
-        *reinterpret_cast<float2*>(&pw[b][row][c0]) = make_float2(sw0, sw1);
-        *reinterpret_cast<float2*>(&pc[b][row][c0]) = make_float2(sc0, sc1);
+        *reinterpret_cast<float4*>(&pwc[b][row][c0]) = make_float4(sw0, sc0, sw1, sc1);
       }
       // stage the next plane (its buffer was last read by the previous x pass)
       if (s + 1 < nsteps) {
@@ -133,17 +135,24 @@ __global__ void __launch_bounds__(kSigThreads, 1)
 #pragma unroll
         for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + bn + loff[i]) : 0.f;
       }
+      if (s + kSigPrefetch < nsteps) {  // warm L2 for a later plane (a hint: no registers held)
+        int64_t bp = plane_base(s + kSigPrefetch);
+#pragma unroll
+        for (int i = 0; i < G::NLOAD; ++i)
+          if (lval[i]) asm volatile("prefetch.global.L2 [%0];" ::"l"(vol + bp + loff[i]));
+      }
       __syncthreads();  // pw/pc[b] complete
       // y pass for this thread's column
-      float qww = taps.w[RS] * pw[b][ty + RS][tx];
-      float qcw = taps.w[RS] * pc[b][ty + RS][tx];
+      const float2 c0v = pwc[b][ty + RS][tx];
+      float qww = taps.w[RS] * c0v.x;
+      float qcw = taps.w[RS] * c0v.y;
       float qwc = 0.f;
 #pragma unroll
       for (int k = 1; k <= RS; ++k) {
-        float pp = pw[b][ty + RS + k][tx], pm = pw[b][ty + RS - k][tx];
-        qww = fmaf(taps.w[RS + k], pp + pm, qww);
-        qwc = fmaf(taps.c[RS + k], pp - pm, qwc);
-        qcw = fmaf(taps.w[RS + k], pc[b][ty + RS + k][tx] + pc[b][ty + RS - k][tx], qcw);
+        const float2 pp = pwc[b][ty + RS + k][tx], pm = pwc[b][ty + RS - k][tx];
+        qww = fmaf(taps.w[RS + k], pp.x + pm.x, qww);
+        qwc = fmaf(taps.c[RS + k], pp.x - pm.x, qwc);
+        qcw = fmaf(taps.w[RS + k], pp.y + pm.y, qcw);
       }
       // push into the z windows (slot u: base is a multiple of P)
       wgx[u] = qcw;

@@ -20,6 +20,10 @@ cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int d
 cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                          const Taps& taps, int rk, cudaStream_t st);
 
+// rho passes along x and y fused: out (6 planes over ob) from in (6 planes over ib).
+cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
+                          const Taps& taps, int rk, cudaStream_t st);
+
 // rho pass along axis 1 (y) or 2 (z), streaming register windows of block_t (8 or 16) outputs.
 cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
                               const Taps& taps, int rk, int block_t, cudaStream_t st);
@@ -39,6 +43,24 @@ struct Fallback {
   int64_t* list;
   int64_t cap;
 };
+
+// Near-degenerate voxels of the fused z pass: ob-linear index and the tensor
+// (6 floats per entry, AoS), since that tensor is stored nowhere else.
+struct FallbackS {
+  int* count;
+  unsigned long long* total;
+  int64_t* idx;
+  float* S;
+  int64_t cap;
+};
+
+// rho pass along z fused with eigen-solve + HA/IA/FA: S_xy (6 planes over ib) ->
+// outputs over ob (arrays covering o.ab); mask (nullable) covers mb.
+cudaError_t launch_rho_z_eig(const float* in, const Box& ib, const int dims[3], const Box& ob, const uint8_t* mask,
+                             const Box& mb, const Frame& F, float fill, const EigOut& o, bool mixed,
+                             const FallbackS& fb, const Taps& taps, int rk, cudaStream_t st);
+cudaError_t launch_fallback_s(const Box& ob, const Frame& F, float fill, const EigOut& o, bool mixed,
+                              const FallbackS& fb, int64_t max_items, cudaStream_t st);
 
 // Per-voxel eigen-solve + HA/IA/FA over ob from S (6 planes over sb); mask
 // array (nullable) covers mb.  Near-degenerate voxels are appended to fb.
