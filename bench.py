@@ -252,14 +252,25 @@ def _accuracy(W, vol, mask, outs) -> dict:
 
 
 def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int):
-    """(algorithmic FMAs, algorithmic bytes) of one launch over nvox output voxels."""
+    """(algorithmic FMAs, algorithmic HBM bytes) of one launch over nvox output voxels:
+    FMAs count taps unfolded; bytes count each input and output once."""
     if name == "grad_products":
         return nvox * (8 * (2 * rs + 1) + 6), nvox * (2 + 24)
     if name in ("rho_x", "rho_y", "rho_z"):
         return nvox * 6 * (2 * rr + 1), nvox * 48
+    if name == "rho_xy":
+        return nvox * 12 * (2 * rr + 1), nvox * 48
+    if name == "rho_z_eig":
+        return nvox * 6 * (2 * rr + 1), nvox * (24 + 1 + 24)
     if name == "eig_angles":
         return 0, nvox * (24 + 1 + 24)
     return 0, 0
+
+
+# DRAM bytes per output voxel of a kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over the launch / voxels of the
+# capture); valid only for the kernel version summarised in the named file.
+MEASURED_TRAFFIC = {"rho_xy": (45.0, "profiles/rho_xy_annulus256.md")}
 
 
 def run_ours(args):
@@ -347,8 +358,10 @@ def run_ours(args):
     if fmas > 0:
         ach = 2.0 * fmas / avg_s / 1e12
         peak = 2.0 * fma_peak / 1e12
+        tr = MEASURED_TRAFFIC.get(dom)
         roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
+                    "frac": ach / peak, "traffic": None if tr is None else tr[0] * nvox,
+                    "traffic_source": None if tr is None else tr[1],
                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x "
                                    f"{sm_mhz_max:.0f} MHz ({peak_kind} sm_max_mhz)"}
     else:
