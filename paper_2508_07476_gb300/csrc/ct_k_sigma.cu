@@ -30,6 +30,15 @@ struct SigmaGeom {
   static constexpr int NLOAD = (NRAW + kSigThreads - 1) / kSigThreads;
   static constexpr int NPAIR = RY * (kSigTX / 2);  // x-pass work items (2 columns each)
   static constexpr int P = 2 * RS + 1;             // z window
+  // cp.async staging of interior tiles: rows of CW uint16 from x0 - XA (16-byte chunks)
+  static constexpr int XA = (RS + 7) / 8 * 8;
+  static constexpr int CW = kSigTX + 2 * XA;
+  static constexpr int NCH = RY * (CW / 8);  // 16-byte chunks per plane
+  // dynamic shared memory: raw[2][RY][RX] f32 | pwc[2][RY][TX] f32x2 | ring[3][RY][CW] u16
+  static constexpr size_t RAW_B = sizeof(float) * 2 * RY * RX;
+  static constexpr size_t PWC_B = sizeof(float2) * 2 * RY * kSigTX;
+  static constexpr size_t RING_B = sizeof(uint16_t) * 3 * RY * CW;
+  static constexpr size_t SMEM = RAW_B + PWC_B + RING_B;
 };
 
 // 2^-8 keeps every possible gradient of uint16 data inside FP16's range while
@@ -41,8 +50,10 @@ __global__ void __launch_bounds__(kSigThreads, 1)
     k_grad_products(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, int dimz, float* __restrict__ J,
                     Box ob, int zseg, const Taps taps) {
   using G = SigmaGeom<RS>;
-  __shared__ __align__(16) float raw[2][G::RY][G::RX];
-  __shared__ __align__(16) float2 pwc[2][G::RY][kSigTX];  // (smoothed, derivative) of the x pass
+  extern __shared__ __align__(16) unsigned char sig_smem[];
+  auto raw = reinterpret_cast<float(*)[G::RY][G::RX]>(sig_smem);
+  auto pwc = reinterpret_cast<float2(*)[G::RY][kSigTX]>(sig_smem + G::RAW_B);  // x pass: (smoothed, derivative)
+  auto ring = reinterpret_cast<uint16_t(*)[G::RY][G::CW]>(sig_smem + G::RAW_B + G::PWC_B);  // cp.async landing
 
   const int t = threadIdx.x;
   const int tx = t % kSigTX, ty = t / kSigTX;
@@ -71,8 +82,42 @@ __global__ void __launch_bounds__(kSigThreads, 1)
     return (int64_t)(gz - vb.lo[2]) * plane;
   };
 
+  // Interior tiles (no clamping in x or y, 16-byte aligned rows) stream their
+  // raw planes with cp.async two planes ahead; edge tiles load through registers.
+  const bool interior = x0 - G::XA >= max(0, vb.lo[0]) && x0 + kSigTX + G::XA <= min(dimx, vb.lo[0] + vb.n[0]) &&
+                        y0 - RS >= max(0, vb.lo[1]) && y0 + kSigTY + RS <= min(dimy, vb.lo[1] + vb.n[1]) &&
+                        (vb.n[0] % 8) == 0 && ((x0 - G::XA - vb.lo[0]) % 8) == 0 &&
+                        ((reinterpret_cast<uintptr_t>(vol) & 15) == 0);
+  const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(&ring[0][0][0]);
+  auto issue_plane = [&](int s) {  // cp.async of plane s into ring slot s % 3
+    if (s < nsteps && t < G::NCH) {
+      const int row = t / (G::CW / 8), cq = t % (G::CW / 8);
+      const uint16_t* src = vol + plane_base(s) + (int64_t)(y0 - RS + row - vb.lo[1]) * vb.n[0] +
+                            (x0 - G::XA - vb.lo[0]) + 8 * cq;
+      const uint32_t dst = ring0 + (uint32_t)(((s % 3) * G::RY + row) * G::CW + 8 * cq) * 2u;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    }
+    cp_async_commit();
+  };
+  auto convert_plane = [&](int s, int slot_raw) {  // ring slot s % 3 -> raw[slot_raw] as float
+#pragma unroll
+    for (int i = 0; i < G::NLOAD; ++i)
+      if (lval[i]) {
+        const int e = t + i * kSigThreads;
+        const int row = e / G::RX, col = e % G::RX;
+        (&raw[slot_raw][0][0])[e] = (float)ring[s % 3][row][col + G::XA - RS];
+      }
+  };
+
   float pre[G::NLOAD];
-  {
+  if (interior) {
+    issue_plane(0);
+    issue_plane(1);
+    issue_plane(2);
+    cp_async_wait<2>();
+    __syncthreads();
+    convert_plane(0, 0);
+  } else {
     int64_t b0 = plane_base(0);
 #pragma unroll
     for (int i = 0; i < G::NLOAD; ++i)
@@ -100,7 +145,8 @@ __global__ void __launch_bounds__(kSigThreads, 1)
       const int s = base + u;
       if (s >= nsteps) break;
       const int b = s & 1;
-      __syncthreads();  // raw[b] complete; pw/pc[b] no longer read
+      if (interior) cp_async_wait<1>();  // plane s + 1 has landed (this thread's chunks)
+      __syncthreads();  // raw[b] complete; pw/pc[b] no longer read; ring slot of plane s + 1 complete
       // x pass over every staged row: smoothing and derivative
       for (int item = t; item < G::NPAIR; item += kSigThreads) {
         const int row = item / (kSigTX / 2);
@@ -125,15 +171,20 @@ __global__ void __launch_bounds__(kSigThreads, 1)
         *reinterpret_cast<float4*>(&pwc[b][row][c0]) = make_float4(sw0, sc0, sw1, sc1);
       }
       // stage the next plane (its buffer was last read by the previous x pass)
-      if (s + 1 < nsteps) {
+      if (interior) {
+        if (s + 1 < nsteps) convert_plane(s + 1, b ^ 1);
+        issue_plane(s + 3);  // into the slot of plane s, converted one step ago
+      } else {
+        if (s + 1 < nsteps) {
 #pragma unroll
-        for (int i = 0; i < G::NLOAD; ++i)
-          if (lval[i]) (&raw[b ^ 1][0][0])[t + i * kSigThreads] = pre[i];
-      }
-      if (s + 2 < nsteps) {
-        int64_t bn = plane_base(s + 2);
+          for (int i = 0; i < G::NLOAD; ++i)
+            if (lval[i]) (&raw[b ^ 1][0][0])[t + i * kSigThreads] = pre[i];
+        }
+        if (s + 2 < nsteps) {
+          int64_t bn = plane_base(s + 2);
 #pragma unroll
-        for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + bn + loff[i]) : 0.f;
+          for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + bn + loff[i]) : 0.f;
+        }
       }
       if (s + kSigPrefetch < nsteps) {  // warm L2 for a later plane (a hint: no registers held)
         int64_t bp = plane_base(s + kSigPrefetch);
@@ -189,17 +240,31 @@ __global__ void __launch_bounds__(kSigThreads, 1)
       }
     }
   }
+  cp_async_wait<0>();
 }
 
 template <int RS>
 static cudaError_t launch_grad_rs(const uint16_t* vol, const Box& vb, const int dims[3], float* J, const Box& ob,
                                   const Taps& taps, bool mixed, cudaStream_t st) {
+  using G = SigmaGeom<RS>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_grad_products<RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_grad_products<RS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)G::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   const int zseg = 128;
   dim3 grid((ob.n[0] + kSigTX - 1) / kSigTX, (ob.n[1] + kSigTY - 1) / kSigTY, (ob.n[2] + zseg - 1) / zseg);
   if (mixed)
-    k_grad_products<RS, true><<<grid, kSigThreads, 0, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg, taps);
+    k_grad_products<RS, true><<<grid, kSigThreads, G::SMEM, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg,
+                                                                   taps);
   else
-    k_grad_products<RS, false><<<grid, kSigThreads, 0, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg, taps);
+    k_grad_products<RS, false><<<grid, kSigThreads, G::SMEM, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg,
+                                                                    taps);
   return cudaGetLastError();
 }
 
