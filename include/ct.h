@@ -160,6 +160,20 @@ typedef struct ct_item {
  */
 ct_status ct_run_chunks(ct_plan plan, const ct_item* items, int32_t n_items, int32_t items_on_host, void* stream);
 
+/*
+ * Fused hot path for one padded chunk of the plan's volume (Implementation:
+ * chunks with padding): d_vol holds the input box (in_lo, in_n) as a dense
+ * uint16 array; every output is written for the output box (out_lo, out_n)
+ * into dense box-shaped arrays (plan encodings; each nullable); d_mask
+ * (nullable) is a box-shaped uint8 array over the output box.  The output box
+ * grown by R(sigma) + R(rho) and clipped to the volume must lie inside the
+ * input box.  Asynchronous on `stream`; results equal those of the
+ * whole-volume run.
+ */
+ct_status ct_run_box(ct_plan plan, const uint16_t* d_vol, const int64_t in_lo[3], const int64_t in_n[3],
+                     const int64_t out_lo[3], const int64_t out_n[3], const uint8_t* d_mask, void* d_vec, void* d_ha,
+                     void* d_ia, void* d_fa, void* stream);
+
 /* Wait for all work of the plan; report asynchronous errors. */
 ct_status ct_plan_sync(ct_plan plan);
 
@@ -191,6 +205,32 @@ ct_status ct_plan_stats(ct_plan plan, ct_stats* out, int32_t reset);
  */
 ct_status ct_eig_smallest_noalloc(const float* d_S, int64_t n, float* d_evals, float* d_evec, int32_t precision,
                                   void* stream);
+
+/*
+ * Seeded synthetic volume on the device (test and benchmark input; not part of
+ * the method).  Same definition, voxel for voxel, as the host generator of
+ * the Python package: an annulus about `center` / `axis` with rods along the
+ * local helix direction (HA linear from ha_in_deg at r_in to ha_out_deg at
+ * r_out, stripe period `period`), optional smooth out-of-plane tilt
+ * (ia_std_deg, ia_corr), noise (noise_kind 0: Gaussian of std noise_level;
+ * 1: std = noise_level * sqrt(background * clean)), SplitMix64 keyed by `seed`
+ * and the global voxel index.  Writes the box (lo, n) of a volume of size
+ * vol_dims as dense uint16 (and the annulus mask, nullable) on `stream`.
+ */
+typedef struct ct_synth_spec {
+  double center[3];
+  double axis[3];
+  double r_in, r_out, period, ha_in_deg, ha_out_deg;
+  double background, amplitude;
+  int32_t noise_kind;
+  int32_t reserved;
+  double noise_level;
+  double ia_std_deg, ia_corr;
+  uint64_t seed;
+} ct_synth_spec;
+
+ct_status ct_synth_annulus(const ct_synth_spec* spec, const int64_t vol_dims[3], const int64_t lo[3],
+                           const int64_t n[3], uint16_t* d_vol, uint8_t* d_mask, void* stream);
 
 /*
  * Per-kernel timing.  While enabled, the plan records a CUDA event pair on the

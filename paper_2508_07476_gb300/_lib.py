@@ -60,6 +60,14 @@ class ct_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class ct_synth_spec(ctypes.Structure):
+    _fields_ = [("center", _D3), ("axis", _D3), ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+                ("period", ctypes.c_double), ("ha_in_deg", ctypes.c_double), ("ha_out_deg", ctypes.c_double),
+                ("background", ctypes.c_double), ("amplitude", ctypes.c_double), ("noise_kind", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("noise_level", ctypes.c_double), ("ia_std_deg", ctypes.c_double),
+                ("ia_corr", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class CTError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"ct status {status}: {message}")
@@ -81,10 +89,15 @@ _SIGNATURES = [
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ct_run_chunks", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_item), ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    ("ct_run_box", ctypes.c_int32,
+     [ctypes.c_void_p, ctypes.c_void_p, _I64x3, _I64x3, _I64x3, _I64x3, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ct_plan_sync", ctypes.c_int32, [ctypes.c_void_p]),
     ("ct_plan_stats", ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ct_stats), ctypes.c_int32]),
     ("ct_eig_smallest_noalloc", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("ct_synth_annulus", ctypes.c_int32,
+     [ctypes.POINTER(ct_synth_spec), _I64x3, _I64x3, _I64x3, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ct_plan_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("ct_plan_kernel_times", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_kernel_time), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -201,6 +214,33 @@ def ct_run_chunks(plan, items: Sequence[ct_item], items_on_host: bool, stream=No
     arr = (ct_item * len(items))(*items)
     _check(load().ct_run_chunks(plan, arr, len(items), 1 if items_on_host else 0,
                                 None if items_on_host else _stream(stream)))
+
+
+def ct_run_box(plan, vol, in_lo, in_n, out_lo, out_n, mask, vec, ha, ia, fa, stream=None) -> None:
+    _check(load().ct_run_box(plan, _ptr(vol), _i64x3(in_lo), _i64x3(in_n), _i64x3(out_lo), _i64x3(out_n), _ptr(mask),
+                             _ptr(vec), _ptr(ha), _ptr(ia), _ptr(fa), _stream(stream)))
+
+
+def make_synth_spec(spec) -> ct_synth_spec:
+    """C description of a synth.AnnulusSpec."""
+    c = ct_synth_spec()
+    c.center = _D3(*spec.centre_xyz())
+    c.axis = _D3(*[float(v) for v in spec.axis])
+    c.r_in, c.r_out, c.period = spec.r_in, spec.r_out, spec.period
+    c.ha_in_deg, c.ha_out_deg = spec.ha_in_deg, spec.ha_out_deg
+    c.background, c.amplitude = spec.background, spec.amplitude
+    kind, level = spec.noise
+    c.noise_kind = {"gauss": 0, "poisson_like": 1}[kind]
+    c.noise_level = level
+    c.ia_std_deg, c.ia_corr = spec.ia_std_deg, spec.ia_corr
+    c.seed = spec.seed
+    return c
+
+
+def ct_synth_annulus(spec, vol_dims, lo, n, vol, mask=None, stream=None) -> None:
+    cs = make_synth_spec(spec)
+    _check(load().ct_synth_annulus(ctypes.byref(cs), _i64x3(vol_dims), _i64x3(lo), _i64x3(n), _ptr(vol), _ptr(mask),
+                                   _stream(stream)))
 
 
 def ct_plan_sync(plan) -> None:

@@ -129,26 +129,38 @@ struct ct_plan_s {
   ct_params p;
   int dims[3];
   int device = 0;
-  cudaStream_t st[2] = {nullptr, nullptr};
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  // device scratch: per slot two 6-plane FP32 buffers and a re-solve list
-  float* buf[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  int64_t buf_cap[2] = {0, 0};  // voxels per buffer
-  int* fb_count[2] = {nullptr, nullptr};
-  unsigned long long* fb_total = nullptr;
-  int64_t* fb_list[2] = {nullptr, nullptr};
-  int64_t fb_cap[2] = {0, 0};
+  // Scratch slots: slots 0 and 1 serve the two streams of host streaming;
+  // batches of device items use up to kSlots streams, one slot each.
+  static constexpr int kSlots = 8;
+  cudaStream_t st[kSlots] = {};
+  cudaEvent_t ev[kSlots] = {};
+  float* buf[kSlots][2] = {};
+  int64_t buf_cap[kSlots] = {};  // voxels per buffer
+  int* fb_count[kSlots] = {};
+  unsigned long long* fb_total = nullptr;  // running count of re-solved voxels
+  int64_t* fb_list[kSlots] = {};
+  int64_t fb_cap[kSlots] = {};
   // re-solve list of the fused z pass (index + tensor per entry)
-  int64_t* fs_idx[2] = {nullptr, nullptr};
-  float* fs_S[2] = {nullptr, nullptr};
-  int64_t fs_cap[2] = {0, 0};
-  // device and pinned staging for host-resident items
+  int64_t* fs_idx[kSlots] = {};
+  float* fs_S[kSlots] = {};
+  int64_t fs_cap[kSlots] = {};
+  // device staging for host-resident items
   uint16_t* d_in[2] = {nullptr, nullptr};
   uint8_t* d_mask[2] = {nullptr, nullptr};
   void* d_out[2] = {nullptr, nullptr};
   void* h_in[2] = {nullptr, nullptr};
   void* h_out[2] = {nullptr, nullptr};
   size_t in_cap[2] = {0, 0}, out_cap[2] = {0, 0}, hin_cap[2] = {0, 0}, hout_cap[2] = {0, 0};
+  // batches: graph of the multi-stream launch sequence, keyed by the item list
+  int batch_streams = 4;
+  bool batch_graph = true;
+  cudaStream_t gst = nullptr;   // origin stream of the captured graph
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_key = 0;
+  int64_t graph_launches = 0, graph_voxels = 0;
+  bool capturing = false;
   ct_stats stats;
   std::mutex mu;
   int stream_block = 16;  // outputs per thread block of the y / z passes (tuning choice)
@@ -300,13 +312,14 @@ Fallback fallback_of(ct_plan P, int slot) {
 #define CT_LAUNCH(P, st, name, call, what)                                  \
   do {                                                                      \
     cudaEvent_t a_ = nullptr, b_ = nullptr;                                 \
-    if ((P)->profile) {                                                     \
+    const bool prof_ = (P)->profile && !(P)->capturing;                     \
+    if (prof_) {                                                            \
       cudaEventCreate(&a_);                                                 \
       cudaEventCreate(&b_);                                                 \
       cudaEventRecord(a_, st);                                              \
     }                                                                       \
     cudaError_t e2_ = (call);                                               \
-    if ((P)->profile) {                                                     \
+    if (prof_) {                                                            \
       cudaEventRecord(b_, st);                                              \
       (P)->recs.push_back({name, a_, b_});                                  \
     }                                                                       \
@@ -422,6 +435,11 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   Scale sc;
   if ((rc = make_scale(*params, params->sigma, params->rho, &sc))) return rc;
   if (!device_present()) return fail(CT_ERR_NO_DEVICE, "no CUDA device is available");
+  {
+    cudaError_t e = prepare_sigma_kernels();
+    if (e == cudaSuccess) e = prepare_rho_xy_kernels();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attribute set-up");
+  }
   ct_plan P = new (std::nothrow) ct_plan_s();
   if (!P) return fail(CT_ERR_OOM, "plan allocation failed");
   P->p = *params;
@@ -430,6 +448,9 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_STREAM_BLOCK")) P->stream_block = std::atoi(e) == 8 ? 8 : 16;
   if (const char* e = std::getenv("CT_TUNE_FUSE_Z_EIG")) P->fuse_z_eig = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_FUSE_XY")) P->fuse_xy = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
+    P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
+  if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;
   cudaGetDevice(&P->device);
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = cudaStreamCreateWithFlags(&P->st[k], cudaStreamNonBlocking);
@@ -446,18 +467,25 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
 ct_status ct_plan_destroy(ct_plan P) {
   if (!P) return CT_OK;
   cudaDeviceSynchronize();
-  for (int s = 0; s < 2; ++s) {
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->gst) cudaStreamDestroy(P->gst);
+  for (int k = 0; k < 2; ++k)
+    if (P->gev[k]) cudaEventDestroy(P->gev[k]);
+  for (int s = 0; s < ct_plan_s::kSlots; ++s) {
     for (int k = 0; k < 2; ++k)
       if (P->buf[s][k]) cudaFree(P->buf[s][k]);
     if (P->fb_count[s]) cudaFree(P->fb_count[s]);
     if (P->fb_list[s]) cudaFree(P->fb_list[s]);
     if (P->fs_idx[s]) cudaFree(P->fs_idx[s]);
     if (P->fs_S[s]) cudaFree(P->fs_S[s]);
-    if (P->d_in[s]) cudaFree(P->d_in[s]);
-    if (P->d_mask[s]) cudaFree(P->d_mask[s]);
-    if (P->d_out[s]) cudaFree(P->d_out[s]);
-    if (P->h_in[s]) cudaFreeHost(P->h_in[s]);
-    if (P->h_out[s]) cudaFreeHost(P->h_out[s]);
+    if (s < 2) {
+      if (P->d_in[s]) cudaFree(P->d_in[s]);
+      if (P->d_mask[s]) cudaFree(P->d_mask[s]);
+      if (P->d_out[s]) cudaFree(P->d_out[s]);
+      if (P->h_in[s]) cudaFreeHost(P->h_in[s]);
+      if (P->h_out[s]) cudaFreeHost(P->h_out[s]);
+    }
     if (P->st[s]) cudaStreamDestroy(P->st[s]);
     if (P->ev[s]) cudaEventDestroy(P->ev[s]);
   }
@@ -628,6 +656,128 @@ ct_status run_device_item(ct_plan P, const ct_item& it, cudaStream_t st) {
   return CT_OK;
 }
 
+ct_status ensure_stream(ct_plan P, int k) {
+  if (!P->st[k]) {
+    CT_CUDA(cudaStreamCreateWithFlags(&P->st[k], cudaStreamNonBlocking), "stream creation");
+    CT_CUDA(cudaEventCreateWithFlags(&P->ev[k], cudaEventDisableTiming), "event creation");
+  }
+  return CT_OK;
+}
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// A batch of device-resident volumes (uneven sizes, per-item scales and
+// frames): items go round-robin onto up to kSlots streams, each with its own
+// scratch slot, so that small volumes run side by side.  The whole
+// multi-stream launch sequence is captured once into a CUDA graph (cached
+// under a hash of the item list and the plan's settings) and replayed with a
+// single graph launch; with graphs off, every item is launched in turn on the
+// caller's stream.
+ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t user) {
+  bool mixed = P->p.precision == CT_PREC_MIXED;
+  std::vector<ItemCtx> ctx(n);
+  ct_status rc;
+  for (int i = 0; i < n; ++i)
+    if ((rc = item_ctx(P, items[i], &ctx[i]))) return rc;
+  if (!P->batch_graph) {
+    for (int i = 0; i < n; ++i) {
+      const ItemCtx& c = ctx[i];
+      EigOut o{items[i].vec, items[i].ha, items[i].ia, items[i].fa, P->p.vec_type, P->p.angle_type, P->p.fa_type,
+               c.whole};
+      if ((rc = fused_stages(P, c.sc, c.dims, items[i].vol, c.whole, c.whole, items[i].mask, c.whole, c.F, o, 0,
+                             mixed, user)))
+        return rc;
+      P->stats.voxels += box_vox(c.whole);
+    }
+    return CT_OK;
+  }
+  const int K = std::max(1, std::min(std::min(P->batch_streams, ct_plan_s::kSlots), n));
+  // scratch of every slot sized for its largest item, before any capture
+  std::vector<int64_t> gmax(K, 0), omax(K, 0);
+  int64_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    const int k = i % K;
+    gmax[k] = std::max(gmax[k], box_vox(grow_clip(ctx[i].whole, ctx[i].sc.rr, ctx[i].dims)));
+    omax[k] = std::max(omax[k], box_vox(ctx[i].whole));
+    total += box_vox(ctx[i].whole);
+  }
+  for (int k = 0; k < K; ++k) {
+    if ((rc = ensure_stream(P, k))) return rc;
+    if ((rc = ensure_scratch(P, k, gmax[k]))) return rc;
+    if ((rc = ensure_fused_fallback(P, k, omax[k]))) return rc;
+  }
+  if (!P->gst) {
+    CT_CUDA(cudaStreamCreateWithFlags(&P->gst, cudaStreamNonBlocking), "stream creation");
+    for (int k = 0; k < 2; ++k) CT_CUDA(cudaEventCreateWithFlags(&P->gev[k], cudaEventDisableTiming), "event creation");
+  }
+  uint64_t key = 1469598103934665603ull;
+  key = fnv1a(key, items, sizeof(ct_item) * (size_t)n);
+  key = fnv1a(key, &P->p, sizeof(ct_params));
+  key = fnv1a(key, &K, sizeof K);
+  if (!P->graph_exec || P->graph_key != key) {
+    if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    P->graph_exec = nullptr;
+    P->graph = nullptr;
+    const int64_t launches0 = P->stats.launches;
+    CT_CUDA(cudaStreamBeginCapture(P->gst, cudaStreamCaptureModeRelaxed), "graph capture");
+    P->capturing = true;
+    cudaError_t e = cudaEventRecord(P->gev[0], P->gst);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(P->st[k], P->gev[0], 0);
+    rc = CT_OK;
+    for (int i = 0; i < n && e == cudaSuccess && rc == CT_OK; ++i) {
+      const int k = i % K;
+      const ItemCtx& c = ctx[i];
+      EigOut o{items[i].vec, items[i].ha, items[i].ia, items[i].fa, P->p.vec_type, P->p.angle_type, P->p.fa_type,
+               c.whole};
+      rc = fused_stages(P, c.sc, c.dims, items[i].vol, c.whole, c.whole, items[i].mask, c.whole, c.F, o, k, mixed,
+                        P->st[k]);
+    }
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(P->ev[k], P->st[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(P->gst, P->ev[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(P->gst, &g);
+    P->capturing = false;
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      P->graph_exec = nullptr;
+      return cuda_fail(e, "graph instantiation");
+    }
+    P->graph = g;
+    P->graph_key = key;
+    P->graph_launches = P->stats.launches - launches0;
+    P->stats.launches = launches0;
+    P->graph_voxels = total;
+  }
+  CT_CUDA(cudaEventRecord(P->gev[1], user), "event record");
+  CT_CUDA(cudaStreamWaitEvent(P->gst, P->gev[1], 0), "stream wait");
+  CT_CUDA(cudaGraphLaunch(P->graph_exec, P->gst), "graph launch");
+  CT_CUDA(cudaEventRecord(P->gev[1], P->gst), "event record");
+  CT_CUDA(cudaStreamWaitEvent(user, P->gev[1], 0), "stream wait");
+  P->stats.launches += P->graph_launches;
+  P->stats.voxels += P->graph_voxels;
+  return CT_OK;
+}
+
 // Host-resident item: chunks alternate between the plan's two streams; each
 // chunk's haloed input box is copied straight from the caller's array, and its
 // outputs straight back into the caller's arrays, so copies of one chunk
@@ -699,14 +849,43 @@ ct_status ct_run_chunks(ct_plan P, const ct_item* items, int32_t n_items, int32_
   if (items_on_host != 0 && items_on_host != 1) return fail(CT_ERR_INVALID, "items_on_host must be 0 or 1");
   std::lock_guard<std::mutex> lk(P->mu);
   ct_status rc;
-  for (int i = 0; i < n_items; ++i) {
-    rc = items_on_host ? run_host_item(P, items[i]) : run_device_item(P, items[i], (cudaStream_t)stream);
+  if (!items_on_host && n_items > 1) {
+    rc = run_device_batch(P, items, n_items, (cudaStream_t)stream);
     if (rc) return rc;
+  } else {
+    for (int i = 0; i < n_items; ++i) {
+      rc = items_on_host ? run_host_item(P, items[i]) : run_device_item(P, items[i], (cudaStream_t)stream);
+      if (rc) return rc;
+    }
   }
   if (items_on_host) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "chunked run");
   }
+  return CT_OK;
+}
+
+ct_status ct_run_box(ct_plan P, const uint16_t* d_vol, const int64_t in_lo[3], const int64_t in_n[3],
+                     const int64_t out_lo[3], const int64_t out_n[3], const uint8_t* d_mask, void* d_vec, void* d_ha,
+                     void* d_ia, void* d_fa, void* stream) {
+  if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
+  if (!d_vol || !in_lo || !in_n || !out_lo || !out_n) return fail(CT_ERR_INVALID, "NULL argument");
+  if (!valid_box(in_lo, in_n, P->dims)) return fail(CT_ERR_INVALID, "input box outside the volume");
+  if (!valid_box(out_lo, out_n, P->dims)) return fail(CT_ERR_INVALID, "output box outside the volume");
+  std::lock_guard<std::mutex> lk(P->mu);
+  Scale sc;
+  ct_status rc = make_scale(P->p, P->p.sigma, P->p.rho, &sc);
+  if (rc) return rc;
+  Box ib = make_box(in_lo, in_n), ob = make_box(out_lo, out_n);
+  if (!inside(ib, grow_clip(ob, sc.rs + sc.rr, P->dims)))
+    return fail(CT_ERR_INVALID, "input box must contain the output box grown by R(sigma)+R(rho) = %d (clipped)",
+                sc.rs + sc.rr);
+  Frame F = make_frame(P->p.lv_center, P->p.lv_axis);
+  EigOut o{d_vec, d_ha, d_ia, d_fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
+  rc = fused_stages(P, sc, P->dims, d_vol, ib, ob, d_mask, ob, F, o, 0, P->p.precision == CT_PREC_MIXED,
+                    (cudaStream_t)stream);
+  if (rc) return rc;
+  P->stats.voxels += box_vox(ob);
   return CT_OK;
 }
 

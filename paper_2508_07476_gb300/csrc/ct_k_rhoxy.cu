@@ -179,6 +179,25 @@ static cudaError_t launch_xy_r(const float* in, const Box& ib, const int dims[3]
   return cudaGetLastError();
 }
 
+template <int RR>
+static cudaError_t prepare_xy_r() {
+  using G = XYGeom<RR>;
+  const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
+  return cudaFuncSetAttribute(k_rho_xy<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_rho_xy_kernels() {
+  cudaError_t e = prepare_xy_r<4>();
+  if (e == cudaSuccess) e = prepare_xy_r<6>();
+  if (e == cudaSuccess) e = prepare_xy_r<8>();
+  if (e == cudaSuccess) e = prepare_xy_r<12>();
+  if (e == cudaSuccess) e = prepare_xy_r<16>();
+  if (e == cudaSuccess) e = prepare_xy_r<24>();
+  if (e == cudaSuccess) e = prepare_xy_r<32>();
+  if (e == cudaSuccess) e = prepare_xy_r<36>();
+  return e;
+}
+
 cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                           const Taps& taps, int rk, cudaStream_t st) {
   if (box_vox(ob) == 0) return cudaSuccess;

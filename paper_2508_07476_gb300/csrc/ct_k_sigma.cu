@@ -268,6 +268,26 @@ static cudaError_t launch_grad_rs(const uint16_t* vol, const Box& vb, const int 
   return cudaGetLastError();
 }
 
+template <int RS>
+static cudaError_t prepare_rs() {
+  using G = SigmaGeom<RS>;
+  cudaError_t e = cudaFuncSetAttribute(k_grad_products<RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)G::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grad_products<RS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+  return e;
+}
+
+cudaError_t prepare_sigma_kernels() {
+  cudaError_t e = prepare_rs<2>();
+  if (e == cudaSuccess) e = prepare_rs<3>();
+  if (e == cudaSuccess) e = prepare_rs<4>();
+  if (e == cudaSuccess) e = prepare_rs<6>();
+  if (e == cudaSuccess) e = prepare_rs<8>();
+  if (e == cudaSuccess) e = prepare_rs<12>();
+  return e;
+}
+
 int sigma_kernel_radius(int r) {
   static const int radii[] = {2, 3, 4, 6, 8, 12};
   for (int v : radii)

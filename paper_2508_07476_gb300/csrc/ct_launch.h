@@ -8,6 +8,11 @@
 
 namespace ct {
 
+// Set the shared-memory attributes of every kernel instantiation (once per process,
+// before any launch may be captured into a graph).
+cudaError_t prepare_sigma_kernels();
+cudaError_t prepare_rho_xy_kernels();
+
 // Instantiated radius that serves radius r (zero taps pad the difference), or -1.
 int sigma_kernel_radius(int r);
 int rho_kernel_radius(int r);

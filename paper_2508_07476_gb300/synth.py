@@ -293,6 +293,36 @@ def lv_annulus_512(n: int = 512) -> Workload:
     return Workload(f"lv_annulus{n}_s2_r6", spec, 2.0, 6.0, True)
 
 
+def crop_batch(count: int = 200, seed: int = 4, size_range: Tuple[int, int] = (64, 384),
+               sigmas: Sequence[float] = (1.0, 1.5, 2.0, 3.0), rhos: Sequence[float] = (2.0, 4.0, 6.0, 8.0)):
+    """Uneven crops, each its own small heart-wall volume: every axis uniform in
+    size_range, its own sigma and rho, a random LV centre (middle half of the
+    crop) and axis (within 20 deg of z), radii 0.2 / 0.42 of the smallest side,
+    HA range +-(30..80) deg, Gaussian noise of 2-10% of the background.  All
+    draws come from the counter-based generator (seed, stream 11), crop j using
+    counters 32 j .. 32 j + 31."""
+    out = []
+    lo, hi = size_range
+    for j in range(count):
+        u = uniform01(seed, 11, np.arange(32 * j, 32 * j + 32, dtype=np.uint64))
+        nx, ny, nz = (int(lo + min(hi - lo, np.floor(u[k] * (hi - lo + 1)))) for k in range(3))
+        sigma = float(sigmas[min(len(sigmas) - 1, int(u[3] * len(sigmas)))])
+        rho = float(rhos[min(len(rhos) - 1, int(u[4] * len(rhos)))])
+        cx = (0.25 + 0.5 * u[5]) * (nx - 1)
+        cy = (0.25 + 0.5 * u[6]) * (ny - 1)
+        cz = (0.25 + 0.5 * u[7]) * (nz - 1)
+        tilt = math.radians(20.0 * u[8])
+        az = 2.0 * math.pi * u[9]
+        axis = (math.sin(tilt) * math.cos(az), math.sin(tilt) * math.sin(az), math.cos(tilt))
+        m = min(nx, ny, nz)
+        ha = 30.0 + 50.0 * u[10]
+        spec = AnnulusSpec(shape=(nz, ny, nx), r_in=0.2 * m, r_out=0.42 * m, period=6.0, ha_in_deg=ha,
+                           ha_out_deg=-ha, center=(cx, cy, cz), axis=axis,
+                           noise=("gauss", (0.02 + 0.08 * u[11]) * 1000.0), seed=1000 + j)
+        out.append(Workload(f"crop{j}_{nx}x{ny}x{nz}_s{sigma}_r{rho}", spec, sigma, rho, False))
+    return out
+
+
 def frame_of(spec: AnnulusSpec) -> Tuple[Sequence[float], Sequence[float]]:
     """(lv_center, lv_axis) in (x, y, z) voxel units, as the pipeline takes them."""
     return spec.centre_xyz(), tuple(float(v) for v in spec.axis)

@@ -1,0 +1,114 @@
+"""Batches of uneven volumes and caller-chunked boxes through the C ABI.
+
+A batch (ct_run_chunks with several device items) runs its items side by side
+on several streams inside one captured CUDA graph; each item's outputs must
+equal, bit for bit, those of running the item alone, and match the oracle.
+ct_run_box on padded chunks must reproduce the whole-volume run bit for bit.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2508_07476_gb300 import _lib, build, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import gpu_util as G  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    _lib.load()
+
+
+def _alloc(shape):
+    nz, ny, nx = shape
+    return (torch.empty((3, nz, ny, nx), device="cuda"), torch.empty((nz, ny, nx), device="cuda"),
+            torch.empty((nz, ny, nx), device="cuda"), torch.empty((nz, ny, nx), device="cuda"))
+
+
+def _run_batch(crops, vols, precision, graph: bool):
+    os.environ["CT_TUNE_BATCH_GRAPH"] = "1" if graph else "0"
+    try:
+        plan = _lib.ct_plan_create(_lib.make_params(1.0, 2.0, (0, 0, 0), (0, 0, 1), precision), (1, 1, 1))
+    finally:
+        del os.environ["CT_TUNE_BATCH_GRAPH"]
+    outs, items = [], []
+    for w, v in zip(crops, vols):
+        nz, ny, nx = w.spec.shape
+        o = _alloc(w.spec.shape)
+        outs.append(o)
+        cen, ax = synth.frame_of(w.spec)
+        items.append(_lib.make_item(v, (nx, ny, nz), None, *o, sigma=w.sigma, rho=w.rho, lv_center=cen, lv_axis=ax))
+    try:
+        _lib.ct_run_chunks(plan, items, False)
+        torch.cuda.synchronize()
+        s1 = _lib.ct_plan_stats(plan, reset=True)
+        _lib.ct_run_chunks(plan, items, False)  # same item list: the cached graph replays
+        torch.cuda.synchronize()
+        s2 = _lib.ct_plan_stats(plan, reset=True)
+    finally:
+        _lib.ct_plan_destroy(plan)
+    res = [{k: t.cpu().numpy() for k, t in zip(("v", "ha", "ia", "fa"), o)} for o in outs]
+    return res, s1, s2
+
+
+@pytest.mark.parametrize("prec", [_lib.CT_PREC_FP32, _lib.CT_PREC_MIXED])
+def test_batch_graph_equals_items_alone_and_oracle(prec):
+    crops = synth.crop_batch(count=6, seed=9, size_range=(20, 56), sigmas=(1.0, 1.5), rhos=(2.0, 3.0, 4.0))
+    host = [synth.generate(w.spec)[0] for w in crops]
+    vols = [G.dev_u16(h) for h in host]
+    batched, s1, s2 = _run_batch(crops, vols, prec, graph=True)
+    seq, _, _ = _run_batch(crops, vols, prec, graph=False)
+    assert s1["voxels"] == s2["voxels"] == sum(h.size for h in host)
+    assert s2["launches"] == s1["launches"] > 0
+    for w, h, b, q in zip(crops, host, batched, seq):
+        for k in ("v", "ha", "ia", "fa"):
+            np.testing.assert_array_equal(b[k], q[k], err_msg=f"{w.name} {k}")
+        cen, ax = synth.frame_of(w.spec)
+        alone = G.fused(h, w.sigma, w.rho, cen, ax, precision=prec)
+        for k in ("v", "ha", "ia", "fa"):
+            np.testing.assert_array_equal(b[k], alone[k], err_msg=f"{w.name} {k} (alone)")
+        ora = O.pipeline(h, w.sigma, w.rho, cen, ax)
+        G.assert_within(G.compare(b, ora, precision=prec), w.name)
+
+
+def test_run_box_chunks_equal_whole():
+    W = synth.single_chunk_64()
+    vol, mask = synth.generate(W.spec)
+    cen, ax = synth.frame_of(W.spec)
+    whole = G.fused(vol, W.sigma, W.rho, cen, ax, mask=mask)
+    nz, ny, nx = vol.shape
+    h = O.radius(W.sigma) + O.radius(W.rho)
+    plan = _lib.ct_plan_create(_lib.make_params(W.sigma, W.rho, cen, ax), (nx, ny, nz))
+    got = {k: np.full_like(whole[k], -1.0) for k in ("v", "ha", "ia", "fa")}
+    try:
+        for z0 in range(0, nz, 24):
+            for x0 in range(0, nx, 40):
+                lo = (x0, 0, z0)
+                n = (min(40, nx - x0), ny, min(24, nz - z0))
+                ilo = tuple(max(0, a - h) for a in lo)
+                ihi = tuple(min(d, a + b + h) for a, b, d in zip(lo, n, (nx, ny, nz)))
+                ino = tuple(b - a for a, b in zip(ilo, ihi))
+                sub = vol[ilo[2]:ihi[2], ilo[1]:ihi[1], ilo[0]:ihi[0]]
+                msub = mask[lo[2]:lo[2] + n[2], lo[1]:lo[1] + n[1], lo[0]:lo[0] + n[0]]
+                o = _alloc((n[2], n[1], n[0]))
+                _lib.ct_run_box(plan, G.dev_u16(sub), ilo, ino, lo, n, G.dev_u8(msub), *o)
+                torch.cuda.synchronize()
+                sl = (slice(lo[2], lo[2] + n[2]), slice(lo[1], lo[1] + n[1]), slice(lo[0], lo[0] + n[0]))
+                for k, t in zip(("v", "ha", "ia", "fa"), o):
+                    a = t.cpu().numpy()
+                    if k == "v":
+                        got[k][(slice(None),) + sl] = a
+                    else:
+                        got[k][sl] = a
+    finally:
+        _lib.ct_plan_destroy(plan)
+    for k in ("v", "ha", "ia", "fa"):
+        np.testing.assert_array_equal(got[k], whole[k], err_msg=k)

@@ -166,7 +166,7 @@ def test_fused_helix64_matches_oracle(prec):
     W, vol, _, cen, ax = _helix64()
     ora = O.pipeline(vol, W.sigma, W.rho, cen, ax)
     gpu = G.fused(vol, W.sigma, W.rho, cen, ax, precision=prec)
-    m = G.compare(gpu, ora)
+    m = G.compare(gpu, ora, precision=prec)
     print("helix64", prec, m)
     # the FP32 form meets the HA bound literally on every graded voxel
     G.assert_within(m, f"helix64 prec={prec}", literal_ha=(prec == FP32))
@@ -182,7 +182,7 @@ def test_fused_ragged_masked(shape, sigma, rho, prec):
     ax = (0.2, -0.1, 1.0)
     ora = O.pipeline(vol, sigma, rho, cen, ax, mask=mask)
     gpu = G.fused(vol, sigma, rho, cen, ax, mask=mask, precision=prec)
-    G.assert_within(G.compare(gpu, ora, mask), f"ragged {shape}", literal_ha=(prec == FP32))
+    G.assert_within(G.compare(gpu, ora, mask, precision=prec), f"ragged {shape}", literal_ha=(prec == FP32))
     out = ~mask.astype(bool)
     assert np.all(np.isnan(gpu["fa"][out])) and np.all(np.isnan(gpu["ha"][out])) and np.all(np.isnan(gpu["v"][:, out]))
 
@@ -289,5 +289,5 @@ def test_full_size_annulus512_sampled(annulus512, prec):
         ora = O.pipeline(vol, W.sigma, W.rho, cen, ax, mask=mask, lo=lo, n=n)
         sl = (slice(lo[2], lo[2] + n[2]), slice(lo[1], lo[1] + n[1]), slice(lo[0], lo[0] + n[0]))
         sub = {k: (gpu[k][(slice(None),) + sl] if k == "v" else gpu[k][sl]) for k in ("v", "ha", "ia", "fa")}
-        m = G.compare(sub, ora, mask[sl])
+        m = G.compare(sub, ora, mask[sl], precision=prec)
         G.assert_within(m, f"box {lo} {n} prec={prec}")
