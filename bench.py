@@ -56,6 +56,10 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["annulus512", "crops200", "stream2048", "tera4096"], default="annulus512",
+                    help="annulus512 (default, the headline line) or one of the other workload shapes")
+    ap.add_argument("--crops", type=int, default=200)
+    ap.add_argument("--zplanes", type=int, default=0, help="stream2048/tera4096: limit the z extent (0 = full)")
     return ap.parse_args()
 
 
@@ -423,10 +427,231 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _line(metric, value, unit, args, ms, config, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded, generated on the device)", "config": config}
+    line.update(extra)
+    print(json.dumps(line))
+
+
+def run_crops(args):
+    """Uneven crops: one graph-batched call for all crops vs one launch sequence per crop."""
+    import torch
+    from paper_2508_07476_gb300 import _lib, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    crops = synth.crop_batch(args.crops)
+    vols, outs, items = [], [], []
+    total = 0
+    for w in crops:
+        nz, ny, nx = w.spec.shape
+        v = torch.empty((nz, ny, nx), dtype=torch.int16, device="cuda")
+        _lib.ct_synth_annulus(w.spec, (nx, ny, nz), (0, 0, 0), (nx, ny, nz), v, flags=_lib.CT_SYNTH_FP32)
+        o = [torch.empty((3, nz, ny, nx), dtype=torch.float16, device="cuda")] + \
+            [torch.empty((nz, ny, nx), dtype=torch.float16, device="cuda") for _ in range(3)]
+        cen, ax = synth.frame_of(w.spec)
+        items.append(_lib.make_item(v, (nx, ny, nz), None, *o, sigma=w.sigma, rho=w.rho, lv_center=cen,
+                                    lv_axis=ax))
+        vols.append(v)
+        outs.append(o)
+        total += nx * ny * nz
+    torch.cuda.synchronize()
+    res = {}
+    for mode in ("graph", "per_crop"):
+        os.environ["CT_TUNE_BATCH_GRAPH"] = "1" if mode == "graph" else "0"
+        plan = _lib.ct_plan_create(_lib.make_params(2.0, 6.0, (0, 0, 0), (0, 0, 1), _lib.CT_PREC_MIXED,
+                                                    _lib.CT_OUT_F16, _lib.CT_OUT_F16, _lib.CT_OUT_F16), (1, 1, 1))
+        del os.environ["CT_TUNE_BATCH_GRAPH"]
+        try:
+            for _ in range(args.warmup):
+                _lib.ct_run_chunks(plan, items, False)
+            torch.cuda.synchronize()
+            _lib.ct_plan_stats(plan, reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                _lib.ct_run_chunks(plan, items, False)
+            e1.record()
+            torch.cuda.synchronize()
+            st = _lib.ct_plan_stats(plan, reset=True)
+            ms = e0.elapsed_time(e1) / args.steps
+            res[mode] = {"ms_per_step": ms, "voxels_per_s": total / (ms * 1e-3),
+                         "launches_per_step": st["launches"] / args.steps}
+        finally:
+            _lib.ct_plan_destroy(plan)
+    _line("voxels/s, 200 uneven crops, one graph-batched call", res["graph"]["voxels_per_s"], UNIT, args,
+          res["graph"]["ms_per_step"],
+          {"workload": f"crops{args.crops}", "voxels": total, "sizes": "each axis U[64,384]",
+           "sigma": "per crop from {1,1.5,2,3}", "rho": "per crop from {2,4,6,8}", "outputs": "f16 v, HA, IA, FA",
+           "precision": "mixed"},
+          {"modes": res, "gpu_launches": res["graph"]["launches_per_step"] * args.steps})
+
+
+def run_stream(args):
+    """Host-resident volume streamed through the device in padded chunks on two streams."""
+    import torch
+    from paper_2508_07476_gb300 import _lib, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    W = synth.lv_annulus_512(512)
+    # the 4x-scaled annulus of the 2048 x 2048 x 1024 stream
+    spec = synth.AnnulusSpec(shape=(1024, 2048, 2048), r_in=480.0, r_out=880.0, period=8.0, ha_in_deg=70.0,
+                             ha_out_deg=-70.0, axis=W.spec.axis, noise=("poisson_like", 0.05), ia_std_deg=5.0,
+                             ia_corr=40.0, seed=3)
+    nz = args.zplanes or 1024
+    ny = nx = 2048
+    h_vol = torch.empty((nz, ny, nx), dtype=torch.int16, pin_memory=True)
+    h_mask = torch.empty((nz, ny, nx), dtype=torch.uint8, pin_memory=True)
+    slab = 64
+    dv = torch.empty((slab, ny, nx), dtype=torch.int16, device="cuda")
+    dm = torch.empty((slab, ny, nx), dtype=torch.uint8, device="cuda")
+    for z0 in range(0, nz, slab):
+        k = min(slab, nz - z0)
+        _lib.ct_synth_annulus(spec, (nx, ny, 1024), (0, 0, z0), (nx, ny, k), dv, dm, flags=_lib.CT_SYNTH_FP32)
+        h_vol[z0:z0 + k].copy_(dv[:k])
+        h_mask[z0:z0 + k].copy_(dm[:k])
+    del dv, dm
+    torch.cuda.synchronize()
+    outs = [torch.empty((3, nz, ny, nx), dtype=torch.float16, pin_memory=True)] + \
+        [torch.empty((nz, ny, nx), dtype=torch.float16, pin_memory=True) for _ in range(3)]
+    cen, ax = synth.frame_of(spec)
+    plan = _lib.ct_plan_create(_lib.make_params(2.0, 8.0, cen, ax, _lib.CT_PREC_MIXED, _lib.CT_OUT_F16,
+                                                _lib.CT_OUT_F16, _lib.CT_OUT_F16, chunk=(256, 256, 256)),
+                               (nx, ny, nz))
+    try:
+        item = _lib.make_item(h_vol, (nx, ny, nz), h_mask, *outs)
+        for _ in range(args.warmup):
+            _lib.ct_run_chunks(plan, [item], True)
+        _lib.ct_plan_stats(plan, reset=True)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _lib.ct_run_chunks(plan, [item], True)
+        el = (time.perf_counter() - t0) / args.steps
+        st = _lib.ct_plan_stats(plan, reset=True)
+    finally:
+        _lib.ct_plan_destroy(plan)
+    vox = nx * ny * nz
+    h2d, d2h = st["h2d_bytes"] / args.steps, st["d2h_bytes"] / args.steps
+    _line("voxels/s, host-resident 2048x2048x1024 volume streamed in 256^3 chunks", vox / el, UNIT, args, el * 1e3,
+          {"workload": f"stream2048x2048x{nz}", "chunk": [256, 256, 256], "halo": 40, "sigma": 2.0, "rho": 8.0,
+           "mask": True, "outputs": "f16 v, HA, IA, FA", "precision": "mixed", "host_buffers": "pinned"},
+          {"e2e": {"value": vox / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+           "host_link_gbs": (h2d + d2h) / el / 1e9, "gpu_launches": st["launches"]})
+
+
+def run_tera(args):
+    """Teravoxel-shaped stream: each padded chunk generated on the device, processed, and its u8 / f16
+    outputs copied into a pinned ring that a host sink checksums; two chunks resident at a time."""
+    import torch
+    from paper_2508_07476_gb300 import _lib, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    nx = ny = 4096
+    nzf = 2048
+    nz = args.zplanes or nzf
+    spec = synth.AnnulusSpec(shape=(nzf, ny, nx), r_in=1000.0, r_out=1800.0, period=10.0, ha_in_deg=70.0,
+                             ha_out_deg=-70.0, axis=(math.sin(math.radians(10.0)), 0.0, math.cos(math.radians(10.0))),
+                             noise=("poisson_like", 0.05), ia_std_deg=5.0, ia_corr=40.0, seed=5)
+    cen, ax = synth.frame_of(spec)
+    sigma, rho, C = 3.0, 9.0, 384
+    halo = _lib.ct_radius(sigma) + _lib.ct_radius(rho)
+    chunks = [(x, y, z) for z in range(0, nz, C) for y in range(0, ny, C) for x in range(0, nx, C)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    plans = [_lib.ct_plan_create(_lib.make_params(sigma, rho, cen, ax, _lib.CT_PREC_MIXED, _lib.CT_OUT_F32,
+                                                  _lib.CT_OUT_U8Q, _lib.CT_OUT_F16), (nx, ny, nzf)) for _ in range(2)]
+    cin = C + 2 * halo
+    slots = []
+    for _ in range(2):
+        slots.append({
+            "vol": torch.empty(cin ** 3, dtype=torch.int16, device="cuda"),
+            "mask": torch.empty(C ** 3, dtype=torch.uint8, device="cuda"),
+            "ha": torch.empty(C ** 3, dtype=torch.uint8, device="cuda"),
+            "ia": torch.empty(C ** 3, dtype=torch.uint8, device="cuda"),
+            "fa": torch.empty(C ** 3, dtype=torch.float16, device="cuda"),
+            "h": torch.empty(C ** 3 * 4, dtype=torch.uint8, pin_memory=True),
+            "ev": torch.cuda.Event(), "n": 0, "pending": False})
+    sink = {"sum": 0, "voxels": 0, "wait_s": 0.0, "read_s": 0.0}
+    F32 = _lib.CT_SYNTH_FP32
+
+    def drain(sl):
+        # The host consumer: waits for the slot's copies, then reads every byte
+        # (a wrapping 64-bit sum), as a writer to storage would.
+        if not sl["pending"]:
+            return
+        t0 = time.perf_counter()
+        sl["ev"].synchronize()
+        t1 = time.perf_counter()
+        n = sl["n"]
+        sink["sum"] = (sink["sum"] + int(sl["h"][:4 * n].view(torch.int64).sum())) & ((1 << 64) - 1)
+        sink["voxels"] += n
+        sink["wait_s"] += t1 - t0
+        sink["read_s"] += time.perf_counter() - t1
+        sl["pending"] = False
+
+    def run_chunks(todo):
+        for i, (x0, y0, z0) in enumerate(todo):
+            sl, st, plan = slots[i & 1], streams[i & 1], plans[i & 1]
+            drain(sl)
+            lo = (x0, y0, z0)
+            n = (min(C, nx - x0), min(C, ny - y0), min(C, nz - z0))
+            ilo = tuple(max(0, a - halo) for a in lo)
+            ihi = tuple(min(d, a + b + halo) for a, b, d in zip(lo, n, (nx, ny, nzf)))
+            ino = tuple(b - a for a, b in zip(ilo, ihi))
+            nv = n[0] * n[1] * n[2]
+            assert nv % 2 == 0
+            with torch.cuda.stream(st):
+                _lib.ct_synth_annulus(spec, (nx, ny, nzf), ilo, ino, sl["vol"], None, st, flags=F32)
+                _lib.ct_synth_annulus(spec, (nx, ny, nzf), lo, n, None, sl["mask"], st, flags=F32)
+                _lib.ct_run_box(plan, sl["vol"], ilo, ino, lo, n, sl["mask"], None, sl["ha"], sl["ia"], sl["fa"], st)
+                h = sl["h"]
+                h[:nv].copy_(sl["ha"][:nv], non_blocking=True)
+                h[nv:2 * nv].copy_(sl["ia"][:nv], non_blocking=True)
+                h[2 * nv:4 * nv].copy_(sl["fa"][:nv].view(torch.uint8), non_blocking=True)
+                sl["ev"].record(st)
+            sl["n"] = nv
+            sl["pending"] = True
+        for sl in slots:
+            drain(sl)
+
+    try:
+        # warm-up: the first chunks (plans size their buffers, streams spin up)
+        run_chunks(chunks[:max(3, args.warmup)])
+        sink.update({"sum": 0, "voxels": 0, "wait_s": 0.0, "read_s": 0.0})
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run_chunks(chunks)
+        torch.cuda.synchronize()
+        el = (time.perf_counter() - t0) / args.steps
+    finally:
+        for p in plans:
+            _lib.ct_plan_destroy(p)
+    vox = nx * ny * nz
+    _line("voxels/s, device-generated 4096x4096x2048 stream in 384^3 chunks (generation included)", vox / el, UNIT,
+          args, el * 1e3,
+          {"workload": f"tera4096x4096x{nz}", "chunk": [C, C, C], "halo": halo, "sigma": sigma, "rho": rho,
+           "mask": True, "outputs": "u8 HA, u8 IA (180/256 deg bins), f16 FA", "precision": "mixed",
+           "resident_chunks": 2, "generator": "device, FP32 form, padded chunk + output-box mask per chunk",
+           "sink": "two pinned host slots, every byte read by a 64-bit host checksum", "warmup": "first chunks"},
+          {"sink_voxels": sink["voxels"], "sink_checksum": sink["sum"],
+           "host_s_per_step": {"waiting_for_gpu": sink["wait_s"] / args.steps, "sink_read": sink["read_s"] / args.steps},
+           "e2e": {"value": vox / el, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * vox}})
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "crops200":
+        run_crops(args)
+    elif args.workload == "stream2048":
+        run_stream(args)
+    elif args.workload == "tera4096":
+        run_tera(args)
     else:
         run_ours(args)
 

@@ -215,15 +215,22 @@ ct_status ct_eig_smallest_noalloc(const float* d_S, int64_t n, float* d_evals, f
  * (ia_std_deg, ia_corr), noise (noise_kind 0: Gaussian of std noise_level;
  * 1: std = noise_level * sqrt(background * clean)), SplitMix64 keyed by `seed`
  * and the global voxel index.  Writes the box (lo, n) of a volume of size
- * vol_dims as dense uint16 (and the annulus mask, nullable) on `stream`.
+ * vol_dims as dense uint16 (and the annulus mask, nullable) on `stream`;
+ * with d_vol NULL only the mask is written (it needs no arithmetic beyond the
+ * radius).  flags: 0 = FP64 arithmetic (the definition); CT_SYNTH_FP32 = the same
+ * construction in FP32 with 24-bit uniforms (about one intensity unit from
+ * the FP64 form, far faster on this GPU's FP32 pipes).  Other bits, a zero
+ * axis, r_out <= r_in, period <= 0 or ia_corr <= 0 with ia_std_deg > 0 are
+ * CT_ERR_INVALID.
  */
+#define CT_SYNTH_FP32 1
 typedef struct ct_synth_spec {
   double center[3];
   double axis[3];
   double r_in, r_out, period, ha_in_deg, ha_out_deg;
   double background, amplitude;
   int32_t noise_kind;
-  int32_t reserved;
+  int32_t flags;
   double noise_level;
   double ia_std_deg, ia_corr;
   uint64_t seed;

@@ -64,7 +64,7 @@ class ct_synth_spec(ctypes.Structure):
     _fields_ = [("center", _D3), ("axis", _D3), ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
                 ("period", ctypes.c_double), ("ha_in_deg", ctypes.c_double), ("ha_out_deg", ctypes.c_double),
                 ("background", ctypes.c_double), ("amplitude", ctypes.c_double), ("noise_kind", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("noise_level", ctypes.c_double), ("ia_std_deg", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("noise_level", ctypes.c_double), ("ia_std_deg", ctypes.c_double),
                 ("ia_corr", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
@@ -221,9 +221,13 @@ def ct_run_box(plan, vol, in_lo, in_n, out_lo, out_n, mask, vec, ha, ia, fa, str
                              _ptr(vec), _ptr(ha), _ptr(ia), _ptr(fa), _stream(stream)))
 
 
-def make_synth_spec(spec) -> ct_synth_spec:
+CT_SYNTH_FP32 = 1
+
+
+def make_synth_spec(spec, flags: int = 0) -> ct_synth_spec:
     """C description of a synth.AnnulusSpec."""
     c = ct_synth_spec()
+    c.flags = flags
     c.center = _D3(*spec.centre_xyz())
     c.axis = _D3(*[float(v) for v in spec.axis])
     c.r_in, c.r_out, c.period = spec.r_in, spec.r_out, spec.period
@@ -237,8 +241,8 @@ def make_synth_spec(spec) -> ct_synth_spec:
     return c
 
 
-def ct_synth_annulus(spec, vol_dims, lo, n, vol, mask=None, stream=None) -> None:
-    cs = make_synth_spec(spec)
+def ct_synth_annulus(spec, vol_dims, lo, n, vol, mask=None, stream=None, flags: int = 0) -> None:
+    cs = make_synth_spec(spec, flags)
     _check(load().ct_synth_annulus(ctypes.byref(cs), _i64x3(vol_dims), _i64x3(lo), _i64x3(n), _ptr(vol), _ptr(mask),
                                    _stream(stream)))
 

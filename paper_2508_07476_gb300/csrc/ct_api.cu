@@ -228,16 +228,6 @@ ct_status ensure_device(void** ptr, size_t* cap, size_t need, const char* what) 
   return CT_OK;
 }
 
-ct_status ensure_host(void** ptr, size_t* cap, size_t need, const char* what) {
-  if (*cap >= need && *ptr) return CT_OK;
-  if (*ptr) cudaFreeHost(*ptr);
-  *ptr = nullptr;
-  *cap = 0;
-  CT_CUDA(cudaMallocHost(ptr, std::max<size_t>(need, 256)), what);
-  *cap = need;
-  return CT_OK;
-}
-
 ct_status ensure_fallback(ct_plan P, int slot, int64_t vox) {
   if (!P->fb_count[slot]) CT_CUDA(cudaMalloc(&P->fb_count[slot], sizeof(int)), "counter allocation");
   if (!P->fb_total) {

@@ -47,3 +47,63 @@ def test_device_generator_matches_host(wl):
     sl = (slice(lo[2], lo[2] + n[2]), slice(lo[1], lo[1] + n[1]), slice(lo[0], lo[0] + n[0]))
     np.testing.assert_array_equal(box, full[sl])
     np.testing.assert_array_equal(mbox, mfull[sl])
+
+
+def _device_full(spec, flags, with_mask=True):
+    nz, ny, nx = spec.shape
+    v = torch.empty((nz, ny, nx), dtype=torch.int16, device="cuda")
+    m = torch.empty((nz, ny, nx), dtype=torch.uint8, device="cuda") if with_mask else None
+    _lib.ct_synth_annulus(spec, (nx, ny, nz), (0, 0, 0), (nx, ny, nz), v, m, flags=flags)
+    torch.cuda.synchronize()
+    return v.cpu().numpy().view(np.uint16), (m.cpu().numpy() if with_mask else None)
+
+
+def test_fp32_form_close_to_definition():
+    """The FP32 form differs from the FP64 definition by rounding only: about
+    one intensity unit, a few units where a 24-bit uniform moves a noise tail."""
+    spec = synth.lv_annulus_512(96).spec
+    v64, m64 = _device_full(spec, 0)
+    v32, m32 = _device_full(spec, _lib.CT_SYNTH_FP32)
+    d = np.abs(v64.astype(np.int64) - v32.astype(np.int64))
+    assert (d <= 1).mean() > 0.995 and d.max() <= 40, ((d <= 1).mean(), d.max())
+    assert (m64 != m32).mean() < 1e-3
+
+
+def test_fp32_form_large_coordinates():
+    """Radii of a few thousand voxels: FP32 phases still hold."""
+    import math
+    spec = synth.AnnulusSpec(shape=(2048, 4096, 4096), r_in=1000.0, r_out=1800.0, period=10.0, ha_in_deg=70.0,
+                             ha_out_deg=-70.0, axis=(math.sin(math.radians(10.0)), 0.0, math.cos(math.radians(10.0))),
+                             noise=("poisson_like", 0.05), ia_std_deg=5.0, ia_corr=40.0, seed=5)
+    dims = (4096, 4096, 2048)
+    lo, n = (2047 + 1300, 2047 - 40, 1500), (96, 80, 24)
+    out = []
+    for flags in (0, _lib.CT_SYNTH_FP32):
+        v = torch.empty((n[2], n[1], n[0]), dtype=torch.int16, device="cuda")
+        _lib.ct_synth_annulus(spec, dims, lo, n, v, None, flags=flags)
+        torch.cuda.synchronize()
+        out.append(v.cpu().numpy().view(np.uint16).astype(np.int64))
+    d = np.abs(out[0] - out[1])
+    assert out[0].std() > 100  # the box crosses the wall
+    assert (d <= 1).mean() > 0.99 and d.max() <= 40, ((d <= 1).mean(), d.max())
+
+
+def test_mask_only_and_direct_lattice():
+    """Mask-only calls write the same mask; an IA field finer than a block row
+    (lattice values drawn per voxel, not from the block table) still matches
+    the host definition."""
+    spec = synth.AnnulusSpec(shape=(12, 20, 150), r_in=3.0, r_out=9.0, period=4.0, ha_in_deg=50.0,
+                             ha_out_deg=-50.0, noise=("gauss", 40.0), ia_std_deg=8.0, ia_corr=3.0, seed=9)
+    ref, mref = synth.generate(spec)
+    full, mfull = _device_full(spec, 0)
+    d = np.abs(full.astype(np.int64) - ref.astype(np.int64))
+    assert d.max() <= 1 and (d > 0).mean() < 1e-3
+    nz, ny, nx = spec.shape
+    m = torch.empty((nz, ny, nx), dtype=torch.uint8, device="cuda")
+    _lib.ct_synth_annulus(spec, (nx, ny, nz), (0, 0, 0), (nx, ny, nz), None, m)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(m.cpu().numpy(), mfull)
+    with pytest.raises(_lib.CTError):
+        _lib.ct_synth_annulus(spec, (nx, ny, nz), (0, 0, 0), (nx, ny, nz), None, None)
+    with pytest.raises(_lib.CTError):
+        _lib.ct_synth_annulus(spec, (nx, ny, nz), (0, 0, 0), (nx, ny, nz), m.view(torch.int16)[:1], None, flags=6)
