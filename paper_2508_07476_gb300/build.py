@@ -41,10 +41,12 @@ def _needs(obj: str, src: str, headers) -> bool:
     return os.path.getmtime(src) > t or any(os.path.getmtime(h) > t for h in headers)
 
 
-def build(verbose: bool = False, jobs: int | None = None, extra_flags=(), out_dir: str | None = None) -> str:
-    """Compile and link; `out_dir` (default the in-tree _build) and `extra_flags`
-    allow side-by-side builds with other compile-time tunables."""
+def build(verbose: bool = False, jobs: int | None = None, extra_flags=(), out_dir: str | None = None,
+          csrc: str | None = None) -> str:
+    """Compile and link; `out_dir` (default the in-tree _build), `extra_flags`
+    and `csrc` (another source tree) allow side-by-side builds of variants."""
     BUILD = out_dir or globals()["BUILD"]
+    CSRC = csrc or globals()["CSRC"]
     LIB = os.path.join(BUILD, "libct_gb300.so")
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))

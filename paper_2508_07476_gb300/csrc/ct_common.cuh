@@ -56,6 +56,31 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// atan2(y, x) on the closed right half-plane (x >= 0), in radians.  The ratio
+// a = min(|y|, x) / max(|y|, x) is reduced by the addition formula
+// atan(a) = pi/6 + atan((sqrt3 a - 1) / (sqrt3 + a)) when a > 2 - sqrt3, so the
+// argument u of Gregory's series u - u^3/3 + u^5/5 - u^7/7 + u^9/9 stays within
+// |u| <= 2 - sqrt3, where the first omitted term is below 5e-8; |y| > x uses
+// atan(a) = pi/2 - atan(1/a).  One division; the result is within a few 1e-7
+// rad of atan2 (angles are reported to far coarser than that).
+__device__ __forceinline__ float atan2_right(float y, float x) {
+  const float ay = fabsf(y);
+  const bool swap = ay > x;
+  const float n = swap ? x : ay, d = swap ? ay : x;  // 0 <= n <= d
+  const bool red = n > 0.26794919243112270f * d;
+  const float nn = red ? fmaf(1.7320508075688772f, n, -d) : n;
+  const float dd = red ? fmaf(1.7320508075688772f, d, n) : d;
+  const float u = d > 0.f ? __fdividef(nn, dd) : 0.f;
+  const float t = u * u;
+  float p = fmaf(t, 1.f / 9.f, -1.f / 7.f);
+  p = fmaf(t, p, 1.f / 5.f);
+  p = fmaf(t, p, -1.f / 3.f);
+  p = fmaf(t, p, 1.f);
+  float r = fmaf(u, p, red ? 0.52359877559829887f : 0.f);
+  r = swap ? 1.5707963267948966f - r : r;
+  return copysignf(r, y);
+}
+
 // ---------------------------------------------------------------------------
 // Eigen-decomposition of a symmetric 3x3 tensor s = (xx, yy, zz, xy, xz, yz).
 // ---------------------------------------------------------------------------
@@ -268,8 +293,9 @@ __device__ __forceinline__ bool ha_ia(const Frame& F, int x, int y, int z, float
     v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
   }
   const float rad2deg = 57.295779513082320877f;
-  ha = atan2f(vz, vt) * rad2deg;
-  ia = asinf(fminf(fmaxf(vr, -1.f), 1.f)) * rad2deg;
+  ha = atan2_right(vz, vt) * rad2deg;
+  const float pp = vt * vt + vz * vz;  // IA = asin(vr) as the angle of v out of the (e_t, e_z) plane
+  ia = atan2_right(vr, pp > 0.f ? pp * rsqrtf(pp) : 0.f) * rad2deg;
   return true;
 }
 
@@ -281,24 +307,29 @@ __device__ __forceinline__ void orient_largest(float v[3]) {
   if (v[m] < 0.f) { v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2]; }
 }
 
-// Output encodings (CT_OUT_F32 = 0, CT_OUT_F16 = 1, CT_OUT_U8Q = 2).
+// Output encodings (CT_OUT_F32 = 0, CT_OUT_F16 = 1, CT_OUT_U8Q = 2).  TYPE is a
+// compile-time encoding, or -1 for the run-time one in `type`.
+template <int TYPE = -1>
 __device__ __forceinline__ void store_val(void* base, int64_t i, int type, float val) {
   if (base == nullptr) return;
-  if (type == 0) {
+  const int ty = TYPE >= 0 ? TYPE : type;
+  if (ty == 0) {
     reinterpret_cast<float*>(base)[i] = val;
-  } else if (type == 1) {
+  } else if (ty == 1) {
     reinterpret_cast<__half*>(base)[i] = __float2half_rn(val);
   }
 }
 
+template <int TYPE = -1>
 __device__ __forceinline__ void store_angle(void* base, int64_t i, int type, float deg, bool valid) {
   if (base == nullptr) return;
-  if (type == 2) {
+  const int ty = TYPE >= 0 ? TYPE : type;
+  if (ty == 2) {
     uint8_t code = 0;
     if (valid) code = (uint8_t)(((int)rintf((deg + 90.f) * (256.f / 180.f))) & 255);
     reinterpret_cast<uint8_t*>(base)[i] = code;
   } else {
-    store_val(base, i, type, deg);
+    store_val<TYPE>(base, i, ty, deg);
   }
 }
 

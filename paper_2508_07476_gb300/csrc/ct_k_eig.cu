@@ -10,6 +10,7 @@
 // FP32 cyclic Jacobi in the FP32 form, FP64 closed form (FP64 Jacobi if that
 // too is near-degenerate) in the mixed form.  The list keeps the re-solve off
 // the common path, so no warp diverges into it.
+#include "ct.h"
 #include "ct_common.cuh"
 #include "ct_launch.h"
 
@@ -44,18 +45,21 @@ __device__ __forceinline__ void resolve(const Sym3<float>& s, bool mixed, float 
 }
 
 // Outputs of one voxel: oriented vector, HA, IA, FA (or fill outside the mask).
+// VT / AT / FT: compile-time encodings of the vector / angle / FA outputs, or
+// -1 to take them from `o` at run time.
+template <int VT = -1, int AT = -1, int FT = -1>
 __device__ __forceinline__ void write_voxel(const EigOut& o, int64_t oi, bool inside, const Frame& F, int x, int y,
                                             int z, const float l[3], float v[3], float fill) {
   if (!inside) {
-    store_val(o.vec, oi, o.vec_t, fill);
+    store_val<VT>(o.vec, oi, o.vec_t, fill);
     int64_t n = box_vox(o.ab);
     if (o.vec) {
-      store_val(o.vec, n + oi, o.vec_t, fill);
-      store_val(o.vec, 2 * n + oi, o.vec_t, fill);
+      store_val<VT>(o.vec, n + oi, o.vec_t, fill);
+      store_val<VT>(o.vec, 2 * n + oi, o.vec_t, fill);
     }
-    store_angle(o.ha, oi, o.ang_t, fill, false);
-    store_angle(o.ia, oi, o.ang_t, fill, false);
-    store_val(o.fa, oi, o.fa_t, fill);
+    store_angle<AT>(o.ha, oi, o.ang_t, fill, false);
+    store_angle<AT>(o.ia, oi, o.ang_t, fill, false);
+    store_val<FT>(o.fa, oi, o.fa_t, fill);
     return;
   }
   float ha, ia;
@@ -63,13 +67,13 @@ __device__ __forceinline__ void write_voxel(const EigOut& o, int64_t oi, bool in
   if (!framed) orient_largest(v);
   if (o.vec) {
     int64_t n = box_vox(o.ab);
-    store_val(o.vec, oi, o.vec_t, v[0]);
-    store_val(o.vec, n + oi, o.vec_t, v[1]);
-    store_val(o.vec, 2 * n + oi, o.vec_t, v[2]);
+    store_val<VT>(o.vec, oi, o.vec_t, v[0]);
+    store_val<VT>(o.vec, n + oi, o.vec_t, v[1]);
+    store_val<VT>(o.vec, 2 * n + oi, o.vec_t, v[2]);
   }
-  store_angle(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
-  store_angle(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
-  store_val(o.fa, oi, o.fa_t, fa_of(l));
+  store_angle<AT>(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
+  store_angle<AT>(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
+  store_val<FT>(o.fa, oi, o.fa_t, fa_of(l));
 }
 
 __device__ __forceinline__ void push_fallback(const Fallback& fb, int64_t i) {
@@ -80,7 +84,13 @@ __device__ __forceinline__ void push_fallback(const Fallback& fb, int64_t i) {
 
 // One thread per voxel on a 3D grid (x from the thread index, y and z from the
 // block index, rows beyond 65535 folded into blockIdx.z), so no index division.
-__global__ void __launch_bounds__(256)
+// 8 CTAs of 256 threads per SM (32 registers): the kernel streams HBM and
+// needs every resident warp to cover its latency.
+#ifndef CT_EIG_MINB
+#define CT_EIG_MINB 8
+#endif
+template <int VT, int AT, int FT>
+__global__ void __launch_bounds__(256, CT_EIG_MINB)
     k_eig_angles(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
                  float fill, EigOut o, bool mixed, Fallback fb) {
   const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,7 +105,7 @@ __global__ void __launch_bounds__(256)
     const Sym3<float> s = load_sym(S, box_vox(sb), box_index(sb, x, y, z));
     if (!eig_closed<float>(s, l, v)) push_fallback(fb, ((int64_t)zr * ob.n[1] + yr) * ob.n[0] + (x - ob.lo[0]));
   }
-  write_voxel(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
+  write_voxel<VT, AT, FT>(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
 
 __global__ void __launch_bounds__(128)
@@ -129,7 +139,15 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
   const int rows = ob.n[1] * ob.n[2];
   const int gy = rows < 65535 ? rows : 65535;
   dim3 grid((ob.n[0] + 255) / 256, gy, (rows + gy - 1) / gy);
-  k_eig_angles<<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  // the encodings of the common configurations are compiled in; others are read at run time
+  if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32)
+    k_eig_angles<0, 0, 0><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16)
+    k_eig_angles<1, 1, 1><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16)
+    k_eig_angles<-1, 2, 1><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  else
+    k_eig_angles<-1, -1, -1><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   return cudaGetLastError();
 }
 

@@ -151,8 +151,14 @@ constexpr int kStreamThreads = 256;
 
 // A CTA spans blockDim.x consecutive x (a multiple of 32) and blockDim.y
 // (component, cross-row) pairs, so the accesses of one step form contiguous runs.
+#ifndef CT_RZ_CHAINS
+#define CT_RZ_CHAINS 1
+#endif
+#ifndef CT_RZ_MINB
+#define CT_RZ_MINB 1
+#endif
 template <int RR, int kT>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
     k_rho_stream(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis,
                  int seg, const Taps taps) {
   constexpr int P = 2 * RR + 1;
@@ -208,6 +214,16 @@ __global__ void __launch_bounds__(kStreamThreads)
 #pragma unroll
     for (int t = 0; t < kT; ++t) win[2 * RR + t] = ring[half + t][tid];
     const int s0 = bk * kT;
+#if CT_RZ_CHAINS == 1
+    // one chain per output: the kT outputs of the block are the independent work
+#pragma unroll
+    for (int i = 0; i < kT; ++i) {
+      float a = taps.w[0] * win[i];
+#pragma unroll
+      for (int k = 1; k < P; ++k) a = fmaf(taps.w[k], win[i + k], a);
+      if (xok && s0 + i < L) obase[(s0 + i) * ostride] = a;
+    }
+#else
 #pragma unroll
     for (int i = 0; i < kT; ++i) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -220,6 +236,7 @@ __global__ void __launch_bounds__(kStreamThreads)
       }
       if (xok && s0 + i < L) obase[(s0 + i) * ostride] = (a0 + a1) + (a2 + a3);
     }
+#endif
     // refill the slots just consumed with block bk + 2 (their values are in registers)
 #pragma unroll
     for (int t = 0; t < kT; ++t) cp_async4(ring0 + (half + t) * kSlot, src(2 * RR + (bk + 2) * kT + t));

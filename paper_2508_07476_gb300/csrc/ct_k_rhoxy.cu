@@ -18,15 +18,21 @@ namespace ct {
 #define CT_XY_TB 16
 #endif
 #ifndef CT_XY_MINB
-#define CT_XY_MINB 1
+#define CT_XY_MINB 2
+#endif
+#ifndef CT_XY_CHAINS
+#define CT_XY_CHAINS 4
 #endif
 constexpr int kXT = 256;        // output columns per CTA (= threads)
-constexpr int kTB = CT_XY_TB;   // rows per block (8 or 16)
 constexpr int kStages = 3;      // cp.async ring depth (blocks)
-static_assert(kTB == 8 || kTB == 16, "rows per block");
+static_assert(CT_XY_TB == 8 || CT_XY_TB == 16, "rows per block");
 
 template <int RR>
 struct XYGeom {
+  // rows per block: 8 for the widest kernels, whose y window would not fit
+  // the register budget of two CTAs per SM with 16
+  static constexpr int TB = RR >= 32 ? 8 : CT_XY_TB;
+  static constexpr int kTB = TB;
   static constexpr int XW = kXT + 2 * RR;                      // staged row width (x pass: 8 per thread)
   static constexpr int XS = XW + ((4 - XW % 8) + 8) % 8;       // padded stride, = 4 (mod 8)
   static constexpr int SXS = kXT + 4;                          // x-pass output row stride
@@ -45,6 +51,7 @@ __global__ void __launch_bounds__(kXT, CT_XY_MINB)
     k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
              const Taps taps) {
   using G = XYGeom<RR>;
+  constexpr int kTB = G::TB;
   extern __shared__ __align__(16) float smem[];
   float* stage = smem;                              // [kStages][kTB][XS]
   float* sx = smem + kStages * kTB * G::XS;         // [kTB][SXS]
@@ -65,18 +72,36 @@ __global__ void __launch_bounds__(kXT, CT_XY_MINB)
   const int nblocks = G::W + (L + kTB - 1) / kTB;
   const uint32_t stage0 = (uint32_t)__cvta_generic_to_shared(stage);
 
+  // This thread's 16-byte chunks of a staged block: chunk q = t + kXT i is row
+  // q / QW, columns 4 (q % QW) .. +3.  Column-dependent parts are fixed for the
+  // walk; a chunk is copied by cp.async when it lies inside the input box and
+  // rows are 16-byte aligned, else element by element with clamping.
+  constexpr int NQ = (kTB * G::QW + kXT - 1) / kXT;
+  int q_row[NQ], q_col[NQ];
+  bool q_fast[NQ];
+  const bool rows_aligned = (ib.n[0] % 4) == 0 && ((reinterpret_cast<uintptr_t>(plane) & 15) == 0);
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int q = t + kXT * i;
+    q_row[i] = q < kTB * G::QW ? q / G::QW : -1;
+    const int gx0 = x0 - RR + 4 * (q % G::QW);
+    q_col[i] = gx0;
+    q_fast[i] = rows_aligned && gx0 >= xlo_ok && gx0 + 3 < xhi_ok && ((gx0 - ib.lo[0]) % 4) == 0;
+  }
   auto issue = [&](int b) {  // stage block b (kTB rows) into ring slot b % kStages
-    float* dst = stage + (b % kStages) * kTB * G::XS;
-    const uint32_t dst_s = stage0 + (uint32_t)((b % kStages) * kTB * G::XS) * 4u;
-    for (int q = t; q < kTB * G::QW; q += kXT) {
-      const int rr = q / G::QW, cq = q % G::QW;
+    const int slot = (b % kStages) * kTB * G::XS;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      if (q_row[i] < 0) continue;
+      const int rr = q_row[i];
       const int y = min(max(p0 - RR - G::PAD + b * kTB + rr, ylo), yhi);
-      const float* row = plane + (int64_t)(y - ib.lo[1]) * ib.n[0] - ib.lo[0];
-      const int gx0 = x0 - RR + 4 * cq;
-      if (gx0 >= xlo_ok && gx0 + 3 < xhi_ok && ((reinterpret_cast<uintptr_t>(row + gx0) & 15) == 0)) {
-        cp_async16(dst_s + (uint32_t)(rr * G::XS + 4 * cq) * 4u, row + gx0);
+      const float* row = plane + (y - ib.lo[1]) * ib.n[0] - ib.lo[0];
+      const int so = slot + rr * G::XS + (q_col[i] - (x0 - RR));
+      if (q_fast[i]) {
+        cp_async16(stage0 + (uint32_t)so * 4u, row + q_col[i]);
       } else {
-        float* d = dst + rr * G::XS + 4 * cq;
+        float* d = stage + so;
+        const int gx0 = q_col[i];
         d[0] = __ldg(row + clamp_to(gx0, dimx, ib.lo[0], ib.n[0]));
         d[1] = __ldg(row + clamp_to(gx0 + 1, dimx, ib.lo[0], ib.n[0]));
         d[2] = __ldg(row + clamp_to(gx0 + 2, dimx, ib.lo[0], ib.n[0]));
@@ -139,6 +164,15 @@ __global__ void __launch_bounds__(kXT, CT_XY_MINB)
     for (int r = 0; r < kTB; ++r) win[2 * RR + r] = sx[r * G::SXS + t];
     if (b >= G::W) {
       const int m = (b - G::W) * kTB;  // first output row of this block, relative to p0
+#if CT_XY_CHAINS == 1
+#pragma unroll
+      for (int i = 0; i < kTB; ++i) {
+        float a = taps.w[0] * win[i];
+#pragma unroll
+        for (int k = 1; k <= 2 * RR; ++k) a = fmaf(taps.w[k], win[i + k], a);
+        if (xok && m + i < L) obase[(m + i) * ostride] = a;
+      }
+#else
 #pragma unroll
       for (int i = 0; i < kTB; ++i) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -151,6 +185,7 @@ __global__ void __launch_bounds__(kXT, CT_XY_MINB)
         }
         if (xok && m + i < L) obase[(m + i) * ostride] = (a0 + a1) + (a2 + a3);
       }
+#endif
     }
   }
   cp_async_wait<0>();
@@ -160,6 +195,7 @@ template <int RR>
 static cudaError_t launch_xy_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                                const Taps& taps, cudaStream_t st) {
   using G = XYGeom<RR>;
+  constexpr int kTB = G::TB;
   if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
   static bool attr_set = false;
@@ -182,7 +218,7 @@ static cudaError_t launch_xy_r(const float* in, const Box& ib, const int dims[3]
 template <int RR>
 static cudaError_t prepare_xy_r() {
   using G = XYGeom<RR>;
-  const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
+  const size_t smem = sizeof(float) * (kStages * G::TB * G::XS + G::TB * G::SXS);
   return cudaFuncSetAttribute(k_rho_xy<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

@@ -38,35 +38,41 @@ __device__ __noinline__ void resolve_voxel(const Sym3<float>& s, bool mixed, flo
   v[0] *= nv; v[1] *= nv; v[2] *= nv;
 }
 
+// TY: compile-time encoding of all outputs (CT_OUT_F32 = 0), or -1 for the
+// run-time encodings in `o`.
+template <int TY = -1>
 __device__ __forceinline__ void emit(const EigOut& o, int64_t oi, bool inside, const Frame& F, int x, int y, int z,
                                      const float l[3], float v[3], float fill) {
   const int64_t n = box_vox(o.ab);
   if (!inside) {
     if (o.vec) {
-      store_val(o.vec, oi, o.vec_t, fill);
-      store_val(o.vec, n + oi, o.vec_t, fill);
-      store_val(o.vec, 2 * n + oi, o.vec_t, fill);
+      store_val<TY>(o.vec, oi, o.vec_t, fill);
+      store_val<TY>(o.vec, n + oi, o.vec_t, fill);
+      store_val<TY>(o.vec, 2 * n + oi, o.vec_t, fill);
     }
-    store_angle(o.ha, oi, o.ang_t, fill, false);
-    store_angle(o.ia, oi, o.ang_t, fill, false);
-    store_val(o.fa, oi, o.fa_t, fill);
+    store_angle<TY>(o.ha, oi, o.ang_t, fill, false);
+    store_angle<TY>(o.ia, oi, o.ang_t, fill, false);
+    store_val<TY>(o.fa, oi, o.fa_t, fill);
     return;
   }
   float ha, ia;
   const bool framed = ha_ia(F, x, y, z, v, ha, ia);
   if (!framed) orient_largest(v);
   if (o.vec) {
-    store_val(o.vec, oi, o.vec_t, v[0]);
-    store_val(o.vec, n + oi, o.vec_t, v[1]);
-    store_val(o.vec, 2 * n + oi, o.vec_t, v[2]);
+    store_val<TY>(o.vec, oi, o.vec_t, v[0]);
+    store_val<TY>(o.vec, n + oi, o.vec_t, v[1]);
+    store_val<TY>(o.vec, 2 * n + oi, o.vec_t, v[2]);
   }
-  store_angle(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
-  store_angle(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
-  store_val(o.fa, oi, o.fa_t, fa_of(l));
+  store_angle<TY>(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
+  store_angle<TY>(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
+  store_val<TY>(o.fa, oi, o.fa_t, fa_of(l));
 }
 
-template <int RR>
-__global__ void __launch_bounds__(kZThreads)
+#ifndef CT_ZE_MINB
+#define CT_ZE_MINB 1
+#endif
+template <int RR, int TY>
+__global__ void __launch_bounds__(kZThreads, CT_ZE_MINB)
     k_rho_z_eig(const float* __restrict__ in, Box ib, int dimz, Box ob, const uint8_t* __restrict__ mask, Box mb,
                 Frame F, float fill, EigOut o, bool mixed, FallbackS fb, int seg, const Taps taps) {
   constexpr int P = 2 * RR + 1;
@@ -109,15 +115,10 @@ __global__ void __launch_bounds__(kZThreads)
     float (*dst)[6][kZX] = sS[bk & 1];
 #pragma unroll
     for (int i = 0; i < kZT; ++i) {
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      float acc = taps.w[0] * win[i];
 #pragma unroll
-      for (int k = 0; k < P; k += 4) {
-        a0 = fmaf(taps.w[k], win[i + k], a0);
-        if (k + 1 < P) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
-        if (k + 2 < P) a2 = fmaf(taps.w[k + 2], win[i + k + 2], a2);
-        if (k + 3 < P) a3 = fmaf(taps.w[k + 3], win[i + k + 3], a3);
-      }
-      dst[i][comp][xl] = (a0 + a1) + (a2 + a3);
+      for (int k = 1; k < P; ++k) acc = fmaf(taps.w[k], win[i + k], acc);
+      dst[i][comp][xl] = acc;
     }
 #pragma unroll
     for (int t = 0; t < kZT; ++t) cp_async4(ring0 + (half + t) * kSlot, src(2 * RR + (bk + 2) * kZT + t));
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(kZThreads)
 #pragma unroll
     for (int j = 0; j < 2 * RR; ++j) win[j] = win[j + kZT];
     __syncthreads();  // the block's tensors are complete
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < kZVox; ++h) {
       const int vi = tid + h * kZThreads;
       const int t = vi / kZX, xv = vi % kZX;
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kZThreads)
           }
         }
       }
-      emit(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
+      emit<TY>(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
     }
   }
   cp_async_wait<0>();
@@ -180,7 +181,10 @@ static cudaError_t launch_rzeig_r(const float* in, const Box& ib, const int dims
   const int seg = (ob.n[2] + nseg - 1) / nseg;
   dim3 grid((ob.n[0] + kZX - 1) / kZX, ob.n[1], (ob.n[2] + seg - 1) / seg);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
-  k_rho_z_eig<RR><<<grid, kZThreads, 0, st>>>(in, ib, dims[2], ob, mask, mb, F, fill, o, mixed, fb, seg, taps);
+  if (o.vec_t == 0 && o.ang_t == 0 && o.fa_t == 0)
+    k_rho_z_eig<RR, 0><<<grid, kZThreads, 0, st>>>(in, ib, dims[2], ob, mask, mb, F, fill, o, mixed, fb, seg, taps);
+  else
+    k_rho_z_eig<RR, -1><<<grid, kZThreads, 0, st>>>(in, ib, dims[2], ob, mask, mb, F, fill, o, mixed, fb, seg, taps);
   return cudaGetLastError();
 }
 

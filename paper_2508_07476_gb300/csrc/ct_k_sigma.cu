@@ -21,6 +21,9 @@ constexpr int kSigThreads = kSigTX * kSigTY;
 #define CT_SIG_PREFETCH 4
 #endif
 constexpr int kSigPrefetch = CT_SIG_PREFETCH;  // planes ahead for the L2 prefetch hint
+#ifndef CT_SIG_ZSEG
+#define CT_SIG_ZSEG 256
+#endif
 
 template <int RS>
 struct SigmaGeom {
@@ -89,45 +92,113 @@ __global__ void __launch_bounds__(kSigThreads, 1)
                         (vb.n[0] % 8) == 0 && ((x0 - G::XA - vb.lo[0]) % 8) == 0 &&
                         ((reinterpret_cast<uintptr_t>(vol) & 15) == 0);
   const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(&ring[0][0][0]);
+  // Fixed per-thread parts of the per-plane work: this thread's 16-byte chunk
+  // of a staged plane (source offset within a plane, landing offset within a
+  // ring slot), the ring elements it converts, and the line it prefetches.
+  const int ich_row = t / (G::CW / 8), ich_cq = t % (G::CW / 8);
+  const int64_t ich_src = (int64_t)(y0 - RS + ich_row - vb.lo[1]) * vb.n[0] + (x0 - G::XA - vb.lo[0]) + 8 * ich_cq;
+  const uint32_t ich_dst = (uint32_t)(ich_row * G::CW + 8 * ich_cq) * 2u;
+  int cv_src[G::NLOAD];  // element of a ring slot converted into raw element t + i * threads (-1: none)
+#pragma unroll
+  for (int i = 0; i < G::NLOAD; ++i) {
+    const int e = t + i * kSigThreads;
+    cv_src[i] = lval[i] ? (e / G::RX) * G::CW + (e % G::RX) + G::XA - RS : -1;
+  }
+  int64_t pf_off = -1;  // first or last column of one staged row
+  if (t < 2 * G::RY) {
+    const int gx = clamp_to(x0 - RS + ((t & 1) ? G::RX - 1 : 0), dimx, vb.lo[0], vb.n[0]);
+    const int gy = clamp_to(y0 - RS + (t >> 1), dimy, vb.lo[1], vb.n[1]);
+    pf_off = (int64_t)(gy - vb.lo[1]) * vb.n[0] + (gx - vb.lo[0]);
+  }
   auto issue_plane = [&](int s) {  // cp.async of plane s into ring slot s % 3
     if (s < nsteps && t < G::NCH) {
-      const int row = t / (G::CW / 8), cq = t % (G::CW / 8);
-      const uint16_t* src = vol + plane_base(s) + (int64_t)(y0 - RS + row - vb.lo[1]) * vb.n[0] +
-                            (x0 - G::XA - vb.lo[0]) + 8 * cq;
-      const uint32_t dst = ring0 + (uint32_t)(((s % 3) * G::RY + row) * G::CW + 8 * cq) * 2u;
+      const uint16_t* src = vol + plane_base(s) + ich_src;
+      const uint32_t dst = ring0 + (uint32_t)((s % 3) * G::RY * G::CW) * 2u + ich_dst;
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
     }
     cp_async_commit();
   };
   auto convert_plane = [&](int s, int slot_raw) {  // ring slot s % 3 -> raw[slot_raw] as float
+    const uint16_t* rs = &ring[s % 3][0][0];
+    float* rd = &raw[slot_raw][0][0];
 #pragma unroll
     for (int i = 0; i < G::NLOAD; ++i)
-      if (lval[i]) {
-        const int e = t + i * kSigThreads;
-        const int row = e / G::RX, col = e % G::RX;
-        (&raw[slot_raw][0][0])[e] = (float)ring[s % 3][row][col + G::XA - RS];
-      }
+      if (cv_src[i] >= 0) rd[t + i * kSigThreads] = (float)rs[cv_src[i]];
   };
 
+  // x pass of the staged plane in raw[rb] into pwc[rb]: smoothing and derivative
+  auto xpass_item = [&](int rb, int item) {
+    {
+      const int row = item / (kSigTX / 2);
+      const int c0 = 2 * (item % (kSigTX / 2));
+      const float* rr = &raw[rb][row][c0];
+      float xv[2 * RS + 2];
+#pragma unroll
+      for (int k = 0; k < RS + 1; ++k) {
+        float2 v2 = *reinterpret_cast<const float2*>(rr + 2 * k);
+        xv[2 * k] = v2.x;
+        xv[2 * k + 1] = v2.y;
+      }
+      float sw0 = taps.w[RS] * xv[RS], sw1 = taps.w[RS] * xv[RS + 1];
+      float sc0 = 0.f, sc1 = 0.f;
+#pragma unroll
+      for (int k = 1; k <= RS; ++k) {
+        sw0 = fmaf(taps.w[RS + k], xv[RS + k] + xv[RS - k], sw0);
+        sw1 = fmaf(taps.w[RS + k], xv[RS + 1 + k] + xv[RS + 1 - k], sw1);
+        sc0 = fmaf(taps.c[RS + k], xv[RS + k] - xv[RS - k], sc0);
+        sc1 = fmaf(taps.c[RS + k], xv[RS + 1 + k] - xv[RS + 1 - k], sc1);
+      }
+      *reinterpret_cast<float4*>(&pwc[rb][row][c0]) = make_float4(sw0, sc0, sw1, sc1);
+    }
+  };
+  // One item per thread when the items match the threads exactly (straight-line
+  // code the compiler can interleave with the y and z passes), else a loop.
+  auto xpass = [&](int rb) {
+    if constexpr (G::NPAIR == kSigThreads) {
+      xpass_item(rb, t);
+    } else {
+      for (int item = t; item < G::NPAIR; item += kSigThreads) xpass_item(rb, item);
+    }
+  };
   float pre[G::NLOAD];
+  auto load_pre = [&](int s) {  // edge tiles: plane s into registers
+    const int64_t bs = plane_base(s);
+#pragma unroll
+    for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + bs + loff[i]) : 0.f;
+  };
+  auto store_pre = [&](int rb) {
+#pragma unroll
+    for (int i = 0; i < G::NLOAD; ++i)
+      if (lval[i]) (&raw[rb][0][0])[t + i * kSigThreads] = pre[i];
+  };
+
+  // Software pipeline, one barrier per plane: step s runs the x pass of plane
+  // s + 1 and the y and z passes of plane s (independent work), stages plane
+  // s + 2 and issues the copy of plane s + 4.
   if (interior) {
     issue_plane(0);
     issue_plane(1);
     issue_plane(2);
-    cp_async_wait<2>();
+    cp_async_wait<1>();
     __syncthreads();
     convert_plane(0, 0);
+    if (1 < nsteps) convert_plane(1, 1);
+    __syncthreads();
+    xpass(0);
+    issue_plane(3);  // into the slot of plane 0
+    cp_async_wait<1>();
+    __syncthreads();
   } else {
-    int64_t b0 = plane_base(0);
-#pragma unroll
-    for (int i = 0; i < G::NLOAD; ++i)
-      if (lval[i]) {
-        int e = t + i * kSigThreads;
-        (&raw[0][0][0])[e] = (float)__ldg(vol + b0 + loff[i]);
-      }
-    int64_t b1 = plane_base(1 < nsteps ? 1 : 0);
-#pragma unroll
-    for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + b1 + loff[i]) : 0.f;
+    load_pre(0);
+    store_pre(0);
+    if (1 < nsteps) {
+      load_pre(1);
+      store_pre(1);
+    }
+    if (2 < nsteps) load_pre(2);
+    __syncthreads();
+    xpass(0);
+    __syncthreads();
   }
 
   // z windows of the three y-pass results: (c_x w_y), (w_x c_y), (w_x w_y)
@@ -143,57 +214,10 @@ __global__ void __launch_bounds__(kSigThreads, 1)
 #pragma unroll
     for (int u = 0; u < G::P; ++u) {
       const int s = base + u;
-      if (s >= nsteps) break;
+      if (s >= nsteps) continue;
       const int b = s & 1;
-      if (interior) cp_async_wait<1>();  // plane s + 1 has landed (this thread's chunks)
-      __syncthreads();  // raw[b] complete; pw/pc[b] no longer read; ring slot of plane s + 1 complete
-      // x pass over every staged row: smoothing and derivative
-      for (int item = t; item < G::NPAIR; item += kSigThreads) {
-        const int row = item / (kSigTX / 2);
-        const int c0 = 2 * (item % (kSigTX / 2));
-        const float* rr = &raw[b][row][c0];
-        float xv[2 * RS + 2];
-#pragma unroll
-        for (int k = 0; k < RS + 1; ++k) {
-          float2 v2 = *reinterpret_cast<const float2*>(rr + 2 * k);
-          xv[2 * k] = v2.x;
-          xv[2 * k + 1] = v2.y;
-        }
-        float sw0 = taps.w[RS] * xv[RS], sw1 = taps.w[RS] * xv[RS + 1];
-        float sc0 = 0.f, sc1 = 0.f;
-#pragma unroll
-        for (int k = 1; k <= RS; ++k) {
-          sw0 = fmaf(taps.w[RS + k], xv[RS + k] + xv[RS - k], sw0);
-          sw1 = fmaf(taps.w[RS + k], xv[RS + 1 + k] + xv[RS + 1 - k], sw1);
-          sc0 = fmaf(taps.c[RS + k], xv[RS + k] - xv[RS - k], sc0);
-          sc1 = fmaf(taps.c[RS + k], xv[RS + 1 + k] - xv[RS + 1 - k], sc1);
-        }
-        *reinterpret_cast<float4*>(&pwc[b][row][c0]) = make_float4(sw0, sc0, sw1, sc1);
-      }
-      // stage the next plane (its buffer was last read by the previous x pass)
-      if (interior) {
-        if (s + 1 < nsteps) convert_plane(s + 1, b ^ 1);
-        issue_plane(s + 3);  // into the slot of plane s, converted one step ago
-      } else {
-        if (s + 1 < nsteps) {
-#pragma unroll
-          for (int i = 0; i < G::NLOAD; ++i)
-            if (lval[i]) (&raw[b ^ 1][0][0])[t + i * kSigThreads] = pre[i];
-        }
-        if (s + 2 < nsteps) {
-          int64_t bn = plane_base(s + 2);
-#pragma unroll
-          for (int i = 0; i < G::NLOAD; ++i) pre[i] = lval[i] ? (float)__ldg(vol + bn + loff[i]) : 0.f;
-        }
-      }
-      if (s + kSigPrefetch < nsteps) {  // warm L2 for a later plane (a hint: no registers held)
-        int64_t bp = plane_base(s + kSigPrefetch);
-#pragma unroll
-        for (int i = 0; i < G::NLOAD; ++i)
-          if (lval[i]) asm volatile("prefetch.global.L2 [%0];" ::"l"(vol + bp + loff[i]));
-      }
-      __syncthreads();  // pw/pc[b] complete
-      // y pass for this thread's column
+      if (s + 1 < nsteps) xpass(b ^ 1);
+      // y pass of plane s for this thread's column
       const float2 c0v = pwc[b][ty + RS][tx];
       float qww = taps.w[RS] * c0v.x;
       float qcw = taps.w[RS] * c0v.y;
@@ -238,6 +262,18 @@ __global__ void __launch_bounds__(kSigThreads, 1)
           J[5 * nob + o] = gy * gz;
         }
       }
+      // stage plane s + 2 into raw[b] (last read by the x pass of plane s)
+      if (interior) {
+        if (s + 2 < nsteps) convert_plane(s + 2, b);
+        issue_plane(s + 4);  // into the slot of plane s + 1, converted one step ago
+      } else {
+        if (s + 2 < nsteps) store_pre(b);
+        if (s + 3 < nsteps) load_pre(s + 3);
+      }
+      if (kSigPrefetch > 0 && s + kSigPrefetch < nsteps && pf_off >= 0)  // warm L2 for a later plane (a hint)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(vol + plane_base(s + kSigPrefetch) + pf_off));
+      if (interior) cp_async_wait<1>();  // plane s + 3 landed (this thread's chunks)
+      __syncthreads();
     }
   }
   cp_async_wait<0>();
@@ -257,7 +293,7 @@ static cudaError_t launch_grad_rs(const uint16_t* vol, const Box& vb, const int 
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int zseg = 128;
+  const int zseg = CT_SIG_ZSEG;
   dim3 grid((ob.n[0] + kSigTX - 1) / kSigTX, (ob.n[1] + kSigTY - 1) / kSigTY, (ob.n[2] + zseg - 1) / zseg);
   if (mixed)
     k_grad_products<RS, true><<<grid, kSigThreads, G::SMEM, st>>>(vol, vb, dims[0], dims[1], dims[2], J, ob, zseg,
