@@ -138,16 +138,18 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
   if (n == 0) return cudaSuccess;
   const int rows = ob.n[1] * ob.n[2];
   const int gy = rows < 65535 ? rows : 65535;
-  dim3 grid((ob.n[0] + 255) / 256, gy, (rows + gy - 1) / gy);
+  // 128-thread rows where 256 would leave more columns idle (e.g. width 384)
+  const int nt = ((ob.n[0] + 127) / 128 * 128 - ob.n[0]) < ((ob.n[0] + 255) / 256 * 256 - ob.n[0]) ? 128 : 256;
+  dim3 grid((ob.n[0] + nt - 1) / nt, gy, (rows + gy - 1) / gy);
   // the encodings of the common configurations are compiled in; others are read at run time
   if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32)
-    k_eig_angles<0, 0, 0><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    k_eig_angles<0, 0, 0><<<grid, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16)
-    k_eig_angles<1, 1, 1><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    k_eig_angles<1, 1, 1><<<grid, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16)
-    k_eig_angles<-1, 2, 1><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    k_eig_angles<-1, 2, 1><<<grid, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   else
-    k_eig_angles<-1, -1, -1><<<grid, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    k_eig_angles<-1, -1, -1><<<grid, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   return cudaGetLastError();
 }
 

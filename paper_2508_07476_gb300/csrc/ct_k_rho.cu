@@ -283,8 +283,13 @@ static cudaError_t launch_stream_r(const float* in, const Box& ib, const int dim
   int nseg = 1;
   while (nseg < 16 && cols * nseg < (int64_t)152 * 1024 * 8 && n_axis / (nseg * 2) >= 4 * (2 * RR + 1)) nseg *= 2;
   int seg = (n_axis + nseg - 1) / nseg;
-  int wx = 1;  // warps along x per CTA
-  while (wx < kStreamThreads / 32 && 32 * wx < ob.n[0]) wx *= 2;
+  // warps along x per CTA: the widest that leaves the fewest idle columns
+  int wx = 1;
+  for (int w = 2; w <= kStreamThreads / 32; w *= 2) {
+    const int span = 32 * w, best = 32 * wx;
+    if (32 * (w / 2) >= ob.n[0]) break;  // a narrower CTA already covers the row
+    if ((ob.n[0] + span - 1) / span * span <= (ob.n[0] + best - 1) / best * best) wx = w;
+  }
   dim3 block(32 * wx, kStreamThreads / (32 * wx));
   dim3 grid((ob.n[0] + block.x - 1) / block.x, (6 * ob.n[other] + block.y - 1) / block.y, (n_axis + seg - 1) / seg);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;

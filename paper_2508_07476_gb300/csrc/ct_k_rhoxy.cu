@@ -23,16 +23,18 @@ namespace ct {
 #ifndef CT_XY_CHAINS
 #define CT_XY_CHAINS 4
 #endif
-constexpr int kXT = 256;        // output columns per CTA (= threads)
 constexpr int kStages = 3;      // cp.async ring depth (blocks)
 static_assert(CT_XY_TB == 8 || CT_XY_TB == 16, "rows per block");
 
-template <int RR>
+// XT output columns per CTA (= threads): 256, or 128 for widths that 256
+// would cover with a mostly idle last CTA.
+template <int RR, int XT>
 struct XYGeom {
   // rows per block: 8 for the widest kernels, whose y window would not fit
-  // the register budget of two CTAs per SM with 16
+  // the register budget of 16 warps per SM with 16
   static constexpr int TB = RR >= 32 ? 8 : CT_XY_TB;
   static constexpr int kTB = TB;
+  static constexpr int kXT = XT;
   static constexpr int XW = kXT + 2 * RR;                      // staged row width (x pass: 8 per thread)
   static constexpr int XS = XW + ((4 - XW % 8) + 8) % 8;       // padded stride, = 4 (mod 8)
   static constexpr int SXS = kXT + 4;                          // x-pass output row stride
@@ -46,12 +48,13 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
 }
 
-template <int RR>
-__global__ void __launch_bounds__(kXT, CT_XY_MINB)
+template <int RR, int XT>
+__global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
     k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
              const Taps taps) {
-  using G = XYGeom<RR>;
+  using G = XYGeom<RR, XT>;
   constexpr int kTB = G::TB;
+  constexpr int kXT = XT;
   extern __shared__ __align__(16) float smem[];
   float* stage = smem;                              // [kStages][kTB][XS]
   float* sx = smem + kStages * kTB * G::XS;         // [kTB][SXS]
@@ -191,35 +194,47 @@ __global__ void __launch_bounds__(kXT, CT_XY_MINB)
   cp_async_wait<0>();
 }
 
+template <int RR, int XT>
+static cudaError_t launch_xy_rt(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
+                                const Taps& taps, cudaStream_t st) {
+  using G = XYGeom<RR, XT>;
+  constexpr int kTB = G::TB;
+  const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
+  const int64_t rows = (int64_t)6 * ob.n[2];
+  if (rows > 65535) return cudaErrorInvalidValue;
+  const int64_t ctas = (int64_t)((ob.n[0] + XT - 1) / XT) * rows;
+  int nseg = 1;
+  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ob.n[1] / (nseg * 2) >= 8 * kTB) nseg *= 2;
+  const int seg = (ob.n[1] + nseg - 1) / nseg;
+  dim3 grid((ob.n[0] + XT - 1) / XT, (unsigned)rows, (ob.n[1] + seg - 1) / seg);
+  k_rho_xy<RR, XT><<<grid, XT, smem, st>>>(in, ib, dims[0], dims[1], out, ob, seg, taps);
+  return cudaGetLastError();
+}
+
+// 128-column CTAs when they leave fewer idle columns than 256-column ones.
+static bool narrow_xy(int n0) {
+  const int w256 = (n0 + 255) / 256 * 256 - n0, w128 = (n0 + 127) / 128 * 128 - n0;
+  return w128 < w256;
+}
+
 template <int RR>
 static cudaError_t launch_xy_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                                const Taps& taps, cudaStream_t st) {
-  using G = XYGeom<RR>;
-  constexpr int kTB = G::TB;
   if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_rho_xy<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const int64_t rows = (int64_t)6 * ob.n[2];
-  if (rows > 65535) return cudaErrorInvalidValue;
-  const int64_t ctas = (int64_t)((ob.n[0] + kXT - 1) / kXT) * rows;
-  int nseg = 1;
-  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 && ob.n[1] / (nseg * 2) >= 8 * kTB) nseg *= 2;
-  const int seg = (ob.n[1] + nseg - 1) / nseg;
-  dim3 grid((ob.n[0] + kXT - 1) / kXT, (unsigned)rows, (ob.n[1] + seg - 1) / seg);
-  k_rho_xy<RR><<<grid, kXT, smem, st>>>(in, ib, dims[0], dims[1], out, ob, seg, taps);
-  return cudaGetLastError();
+  return narrow_xy(ob.n[0]) ? launch_xy_rt<RR, 128>(in, ib, dims, out, ob, taps, st)
+                            : launch_xy_rt<RR, 256>(in, ib, dims, out, ob, taps, st);
 }
 
 template <int RR>
 static cudaError_t prepare_xy_r() {
-  using G = XYGeom<RR>;
-  const size_t smem = sizeof(float) * (kStages * G::TB * G::XS + G::TB * G::SXS);
-  return cudaFuncSetAttribute(k_rho_xy<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  using G2 = XYGeom<RR, 256>;
+  using G1 = XYGeom<RR, 128>;
+  cudaError_t e = cudaFuncSetAttribute(k_rho_xy<RR, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * (kStages * G2::TB * G2::XS + G2::TB * G2::SXS)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rho_xy<RR, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(float) * (kStages * G1::TB * G1::XS + G1::TB * G1::SXS)));
+  return e;
 }
 
 cudaError_t prepare_rho_xy_kernels() {
