@@ -152,7 +152,7 @@ constexpr int kStreamThreads = 256;
 // A CTA spans blockDim.x consecutive x (a multiple of 32) and blockDim.y
 // (component, cross-row) pairs, so the accesses of one step form contiguous runs.
 #ifndef CT_RZ_CHAINS
-#define CT_RZ_CHAINS 1
+#define CT_RZ_CHAINS 2
 #endif
 #ifndef CT_RZ_MINB
 #define CT_RZ_MINB 1
@@ -222,6 +222,17 @@ __global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
 #pragma unroll
       for (int k = 1; k < P; ++k) a = fmaf(taps.w[k], win[i + k], a);
       if (xok && s0 + i < L) obase[(s0 + i) * ostride] = a;
+    }
+#elif CT_RZ_CHAINS == 2
+#pragma unroll
+    for (int i = 0; i < kT; ++i) {
+      float a0 = taps.w[0] * win[i], a1 = taps.w[1] * win[i + 1];
+#pragma unroll
+      for (int k = 2; k < P; k += 2) {
+        a0 = fmaf(taps.w[k], win[i + k], a0);
+        if (k + 1 < P) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
+      }
+      if (xok && s0 + i < L) obase[(s0 + i) * ostride] = a0 + a1;
     }
 #else
 #pragma unroll

@@ -21,7 +21,7 @@ namespace ct {
 #define CT_XY_MINB 2
 #endif
 #ifndef CT_XY_CHAINS
-#define CT_XY_CHAINS 4
+#define CT_XY_CHAINS 2
 #endif
 constexpr int kStages = 3;      // cp.async ring depth (blocks)
 static_assert(CT_XY_TB == 8 || CT_XY_TB == 16, "rows per block");
@@ -174,6 +174,17 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
 #pragma unroll
         for (int k = 1; k <= 2 * RR; ++k) a = fmaf(taps.w[k], win[i + k], a);
         if (xok && m + i < L) obase[(m + i) * ostride] = a;
+      }
+#elif CT_XY_CHAINS == 2
+#pragma unroll
+      for (int i = 0; i < kTB; ++i) {
+        float a0 = taps.w[0] * win[i], a1 = taps.w[1] * win[i + 1];
+#pragma unroll
+        for (int k = 2; k <= 2 * RR; k += 2) {
+          a0 = fmaf(taps.w[k], win[i + k], a0);
+          if (k + 1 <= 2 * RR) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
+        }
+        if (xok && m + i < L) obase[(m + i) * ostride] = a0 + a1;
       }
 #else
 #pragma unroll
