@@ -351,6 +351,25 @@ def run_ours(args):
         finally:
             _lib.ct_plan_destroy(plan)
 
+    # transmural HA profile of the mixed form's HA output (a reduction after the step, timed apart)
+    nd_p, nh_p = 20, 180
+    pspec = _lib.make_profile_spec(cen, ax, W.spec.r_in, W.spec.r_out, nd_p, nh_p, _lib.CT_OUT_F32)
+    hist = torch.zeros(nd_p * nh_p, dtype=torch.int64, device="cuda")
+    _lib.ct_transmural_profile(pspec, (n, n, n), (0, 0, 0), (n, n, n), outs["ha"], d_mask, hist, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        _lib.ct_transmural_profile(pspec, (n, n, n), (0, 0, 0), (n, n, n), outs["ha"], d_mask, hist, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy().reshape(nd_p, nh_p) // (reps + 1)
+    centres = (np.arange(nh_p) + 0.5) * 180.0 / nh_p - 90.0
+    prof_ms = e0.elapsed_time(e1) / reps
+    transmural = {"ms": prof_ms, "bins": [nd_p, nh_p], "voxels_counted": int(h.sum()),
+                  "gb_per_s": nvox * 5 / (prof_ms * 1e-3) / 1e9,
+                  "mean_ha_by_depth": [round(float((r * centres).sum() / max(r.sum(), 1)), 2) for r in h]}
+
     head = forms["mixed"]
     peaks, peak_kind = _peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -425,6 +444,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "gpu_launches_per_step": launches_per_step, "clocks": clocks, "forms": forms,
             "pipeline_roofline": pipeline_roofline, "accuracy": accuracy, "kernels": kernels,
+            "transmural_profile": transmural,
         }
         print(json.dumps(line))
     if world > 1:
@@ -632,6 +652,19 @@ def run_tera(args):
             run_chunks(chunks)
         torch.cuda.synchronize()
         el = (time.perf_counter() - t0) / args.steps
+        # the generator alone over the same chunks (timed apart, as the stream's input cost)
+        t0 = time.perf_counter()
+        for i, (x0, y0, z0) in enumerate(chunks):
+            sl, st = slots[i & 1], streams[i & 1]
+            lo = (x0, y0, z0)
+            n = (min(C, nx - x0), min(C, ny - y0), min(C, nz - z0))
+            ilo = tuple(max(0, a - halo) for a in lo)
+            ihi = tuple(min(d, a + b + halo) for a, b, d in zip(lo, n, (nx, ny, nzf)))
+            ino = tuple(b - a for a, b in zip(ilo, ihi))
+            _lib.ct_synth_annulus(spec, (nx, ny, nzf), ilo, ino, sl["vol"], None, st, flags=F32)
+            _lib.ct_synth_annulus(spec, (nx, ny, nzf), lo, n, None, sl["mask"], st, flags=F32)
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
     finally:
         for p in plans:
             _lib.ct_plan_destroy(p)
@@ -643,6 +676,10 @@ def run_tera(args):
            "resident_chunks": 2, "generator": "device, FP32 form, padded chunk + output-box mask per chunk",
            "sink": "two pinned host slots, every byte read by a 64-bit host checksum", "warmup": "first chunks"},
           {"sink_voxels": sink["voxels"], "sink_checksum": sink["sum"],
+           "generator_only": {"s_per_step": gen_s, "voxels_per_s": vox / gen_s,
+                              "note": "padded chunks + output-box masks generated alone, same streams"},
+           "pipeline_estimate": {"voxels_per_s": vox / max(el - gen_s, 1e-9),
+                                 "note": "stream time less the generator-only time"},
            "host_s_per_step": {"waiting_for_gpu": sink["wait_s"] / args.steps, "sink_read": sink["read_s"] / args.steps},
            "e2e": {"value": vox / el, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * vox}})
 

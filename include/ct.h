@@ -254,6 +254,39 @@ typedef struct ct_kernel_time {
 ct_status ct_plan_profile(ct_plan plan, int32_t enable);
 ct_status ct_plan_kernel_times(ct_plan plan, ct_kernel_time* out, int32_t capacity, int32_t* count);
 
+/*
+ * Transmural HA profile: the histogram of helical angle against normalised
+ * wall depth, the regional statistic the paper's analysis module plots
+ * (Architecture: "analysis", transmural profile of Figure 1(c)'s HA map).
+ * It reads the HA output of the pipeline, so it runs after ct_run_chunks /
+ * ct_angles on the same box; it is a reduction, not part of the per-voxel path.
+ *
+ * For every voxel of the box (lo, n) of a volume of size vol_dims (x, y, z):
+ *   depth d = (r - r_in) / (r_out - r_in), r = distance of the voxel centre
+ *   from the axis line through lv_center along lv_axis (voxel units, FP32);
+ *   the voxel counts when the mask (nullable, uint8 over the box) is non-zero,
+ *   HA is valid (finite; for CT_OUT_U8Q a code other than 0) and 0 <= d < 1;
+ *   then d_hist[kd * n_ha + kh] += 1 with kd = floor(d * n_depth) and
+ *   kh = floor((HA + 90) * n_ha / 180) clamped to [0, n_ha - 1].
+ * d_ha: dense over the box, encoding ha_type (CT_OUT_F32, CT_OUT_F16,
+ * CT_OUT_U8Q: code c decodes to c * 180/256 - 90).  d_hist: device
+ * uint64 [n_depth][n_ha], accumulated into (the caller zeroes it).
+ * n_depth * n_ha must be in [1, 16384]; r_out > r_in; non-zero axis;
+ * reserved 0.  Asynchronous on `stream`.
+ */
+typedef struct ct_profile_spec {
+  double lv_center[3];
+  double lv_axis[3];
+  double r_in, r_out;
+  int32_t n_depth, n_ha;
+  int32_t ha_type;
+  int32_t reserved;
+} ct_profile_spec;
+
+ct_status ct_transmural_profile(const ct_profile_spec* spec, const int64_t vol_dims[3], const int64_t lo[3],
+                                const int64_t n[3], const void* d_ha, const uint8_t* d_mask, uint64_t* d_hist,
+                                void* stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* ct_last_error(void);
 

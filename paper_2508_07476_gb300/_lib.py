@@ -68,6 +68,12 @@ class ct_synth_spec(ctypes.Structure):
                 ("ia_corr", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+class ct_profile_spec(ctypes.Structure):
+    _fields_ = [("lv_center", _D3), ("lv_axis", _D3), ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+                ("n_depth", ctypes.c_int32), ("n_ha", ctypes.c_int32), ("ha_type", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class CTError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"ct status {status}: {message}")
@@ -98,6 +104,9 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("ct_synth_annulus", ctypes.c_int32,
      [ctypes.POINTER(ct_synth_spec), _I64x3, _I64x3, _I64x3, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ct_transmural_profile", ctypes.c_int32,
+     [ctypes.POINTER(ct_profile_spec), _I64x3, _I64x3, _I64x3, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_void_p]),
     ("ct_plan_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("ct_plan_kernel_times", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_kernel_time), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -245,6 +254,21 @@ def ct_synth_annulus(spec, vol_dims, lo, n, vol, mask=None, stream=None, flags: 
     cs = make_synth_spec(spec, flags)
     _check(load().ct_synth_annulus(ctypes.byref(cs), _i64x3(vol_dims), _i64x3(lo), _i64x3(n), _ptr(vol), _ptr(mask),
                                    _stream(stream)))
+
+
+def make_profile_spec(lv_center, lv_axis, r_in: float, r_out: float, n_depth: int, n_ha: int,
+                      ha_type: int = CT_OUT_F32) -> ct_profile_spec:
+    p = ct_profile_spec()
+    p.lv_center = _D3(*lv_center)
+    p.lv_axis = _D3(*lv_axis)
+    p.r_in, p.r_out = r_in, r_out
+    p.n_depth, p.n_ha, p.ha_type, p.reserved = n_depth, n_ha, ha_type, 0
+    return p
+
+
+def ct_transmural_profile(spec: ct_profile_spec, vol_dims, lo, n, ha, mask, hist, stream=None) -> None:
+    _check(load().ct_transmural_profile(ctypes.byref(spec), _i64x3(vol_dims), _i64x3(lo), _i64x3(n), _ptr(ha),
+                                        _ptr(mask), _ptr(hist), _stream(stream)))
 
 
 def ct_plan_sync(plan) -> None:

@@ -15,7 +15,10 @@
 namespace ct {
 
 constexpr int kSigTX = 32;
-constexpr int kSigTY = 16;
+#ifndef CT_SIG_TY
+#define CT_SIG_TY 16
+#endif
+constexpr int kSigTY = CT_SIG_TY;
 constexpr int kSigThreads = kSigTX * kSigTY;
 #ifndef CT_SIG_PREFETCH
 #define CT_SIG_PREFETCH 4
@@ -49,7 +52,7 @@ struct SigmaGeom {
 constexpr float kHalfScale = 1.0f / 256.0f;
 
 template <int RS, bool MIXED>
-__global__ void __launch_bounds__(kSigThreads, 1)
+__global__ void __launch_bounds__(kSigThreads, 512 / kSigThreads)
     k_grad_products(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, int dimz, float* __restrict__ J,
                     Box ob, int zseg, const Taps taps) {
   using G = SigmaGeom<RS>;
