@@ -166,6 +166,7 @@ struct ct_plan_s {
   int stream_block = 16;  // outputs per thread block of the y / z passes (tuning choice)
   bool fuse_z_eig = false;  // z pass fused with the eigen stage, or split (tuning choice)
   bool fuse_xy = true;      // x and y passes in one kernel, or two (tuning choice)
+  bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -330,12 +331,20 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
   Bxy.n[0] = ob.n[0];
   Bxy.lo[1] = ob.lo[1];
   Bxy.n[1] = ob.n[1];
-  ct_status rc = ensure_scratch(P, slot, box_vox(G));
+  // the split gradient keeps its 3 partial planes (over G grown in z) in B
+  const Box Ab = grad_partial_box(G, vb, sc.rks, dims[2]);
+  const int64_t need = P->split_grad ? std::max<int64_t>(box_vox(G), (box_vox(Ab) + 1) / 2) : box_vox(G);
+  ct_status rc = ensure_scratch(P, slot, need);
   if (rc) return rc;
   float* A = P->buf[slot][0];
   float* B = P->buf[slot][1];
-  CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts, sc.rks, mixed, st),
-            "gradient kernel launch");
+  if (P->split_grad) {
+    CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts, sc.rks, st), "gradient x/y kernel launch");
+    CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts, sc.rks, mixed, st), "gradient z kernel launch");
+  } else {
+    CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts, sc.rks, mixed, st),
+              "gradient kernel launch");
+  }
   if (P->fuse_xy) {
     CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr, sc.rkr, st), "rho xy kernel launch");
     *Sxy = B;
@@ -428,6 +437,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   {
     cudaError_t e = prepare_sigma_kernels();
     if (e == cudaSuccess) e = prepare_rho_xy_kernels();
+    if (e == cudaSuccess) e = prepare_grad_split_kernels();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attribute set-up");
   }
   ct_plan P = new (std::nothrow) ct_plan_s();
@@ -438,6 +448,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_STREAM_BLOCK")) P->stream_block = std::atoi(e) == 8 ? 8 : 16;
   if (const char* e = std::getenv("CT_TUNE_FUSE_Z_EIG")) P->fuse_z_eig = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_FUSE_XY")) P->fuse_xy = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_SPLIT_GRAD")) P->split_grad = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;

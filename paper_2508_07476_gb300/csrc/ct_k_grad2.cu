@@ -1,0 +1,412 @@
+// Gradient at noise scale sigma and the six tensor products (Figure 1b;
+// Architecture, "orientation") as two streaming kernels:
+//
+//   k_grad_xy  the x and y passes of the three gradient components, per
+//              z-plane: F0 = w_y c_x I, F1 = c_y w_x I, F2 = w_y w_x I;
+//   k_grad_z   the z pass (g_x = w_z F0, g_y = w_z F1, g_z = c_z F2), the
+//              FP16 rounding of the mixed form and the six products g_a g_b.
+//
+// Both walk an axis with per-thread register windows (y in the first, z in
+// the second), so neither computes the halo rows of a 2-D tile.  The three
+// partial fields cross HBM once (12 B written and read per voxel); the
+// gradient itself never does.
+//
+// Every pass folds the +k / -k taps (sums for the smoothing taps w,
+// differences for the derivative taps c), so a constant volume gives an
+// exactly zero gradient.
+#include "ct_common.cuh"
+#include "ct_launch.h"
+
+namespace ct {
+
+// ---------------------------------------------------------------- x and y
+template <int RS, int XT>
+struct GXYGeom {
+  static constexpr int TB = 16;                           // rows per block
+  static constexpr int XA = (RS + 7) / 8 * 8;              // staged columns left of the first output
+  static constexpr int CW = XT + 2 * XA;                   // staged row width (a multiple of 8)
+  static constexpr int QW = CW / 8;                        // 8-column chunks per staged row
+  static constexpr int NQ = (TB * QW + XT - 1) / XT;       // chunks per thread per block
+  static constexpr int XS = CW + 4;                        // staged row stride (floats), = 4 (mod 8)
+  static constexpr int SXS = XT + 4;                       // x-pass output row stride
+  static constexpr int W = (2 * RS + TB - 1) / TB;         // warm-up blocks
+  static constexpr int PAD = W * TB - 2 * RS;              // extra leading rows
+  static constexpr int WN = TB + 2 * RS;                   // y window
+  static constexpr int OFF = XA - RS;                      // first needed staged column of output 0
+  static constexpr int B4 = OFF / 4 * 4, O4 = OFF % 4;     // 16-byte aligned start, remainder
+  static constexpr int NV = (8 + 2 * RS + O4 + 3) / 4;     // float4 loads per x-pass row
+  static constexpr size_t SMEM = sizeof(float) * (TB * XS + 2 * TB * SXS);
+};
+
+// 8 uint16 (one 16-byte chunk) -> 8 floats, exact.
+__device__ __forceinline__ void u16x8_to_f32(const uint4 q, float* f) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    f[2 * k] = (float)(w[k] & 0xffffu);
+    f[2 * k + 1] = (float)(w[k] >> 16);
+  }
+}
+
+template <int RS, int XT>
+__global__ void __launch_bounds__(XT, 512 / XT)
+    k_grad_xy(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, float* __restrict__ F, Box ab, int seg,
+              const Taps taps) {
+  using G = GXYGeom<RS, XT>;
+  constexpr int TB = G::TB;
+  extern __shared__ __align__(16) float gsm[];
+  float* stage = gsm;                  // [TB][XS] staged rows as float
+  float* sx = gsm + TB * G::XS;        // [2][TB][SXS]: w_x and c_x rows
+
+  const int t = threadIdx.x;
+  const int x0 = ab.lo[0] + blockIdx.x * XT;
+  const int xend = ab.lo[0] + ab.n[0];
+  const int z = ab.lo[2] + blockIdx.y;
+  const int p0 = ab.lo[1] + blockIdx.z * seg;
+  const int L = min(seg, ab.lo[1] + ab.n[1] - p0);
+  if (L <= 0) return;
+
+  const uint16_t* plane = vol + (int64_t)(z - vb.lo[2]) * vb.n[0] * vb.n[1];
+  const int ylo = max(0, vb.lo[1]), yhi = min(dimy - 1, vb.lo[1] + vb.n[1] - 1);
+  const int xlo_ok = max(0, vb.lo[0]), xhi_ok = min(dimx, vb.lo[0] + vb.n[0]);
+  const int nblocks = G::W + (L + TB - 1) / TB;
+  const bool aligned = (vb.n[0] % 8) == 0 && ((reinterpret_cast<uintptr_t>(vol) & 15) == 0);
+
+  // this thread's 16-byte chunks of a block: chunk q = t + XT i is row q / QW,
+  // columns x0 - XA + 8 (q % QW) .. +7 (loaded whole when inside the box and
+  // aligned, else element by element with clamping)
+  int q_row[G::NQ], q_col[G::NQ];
+  bool q_fast[G::NQ];
+#pragma unroll
+  for (int i = 0; i < G::NQ; ++i) {
+    const int q = t + XT * i;
+    q_row[i] = q < TB * G::QW ? q / G::QW : -1;
+    q_col[i] = x0 - G::XA + 8 * (q % G::QW);
+    q_fast[i] = aligned && q_col[i] >= xlo_ok && q_col[i] + 7 < xhi_ok && ((q_col[i] - vb.lo[0]) % 8) == 0;
+  }
+  uint4 pre[G::NQ];
+  auto load_block = [&](int b) {  // block b's chunks into registers
+#pragma unroll
+    for (int i = 0; i < G::NQ; ++i) {
+      if (q_row[i] < 0) continue;
+      const int y = min(max(p0 - RS - G::PAD + b * TB + q_row[i], ylo), yhi);
+      const uint16_t* row = plane + (int64_t)(y - vb.lo[1]) * vb.n[0] - vb.lo[0];
+      if (q_fast[i]) {
+        pre[i] = __ldg(reinterpret_cast<const uint4*>(row + q_col[i]));
+      } else {
+        uint32_t h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) h[e] = __ldg(row + clamp_to(q_col[i] + e, dimx, vb.lo[0], vb.n[0]));
+        pre[i] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+      }
+    }
+  };
+  auto store_block = [&]() {  // registers -> staged float rows
+#pragma unroll
+    for (int i = 0; i < G::NQ; ++i) {
+      if (q_row[i] < 0) continue;
+      float f[8];
+      u16x8_to_f32(pre[i], f);
+      float4* d = reinterpret_cast<float4*>(stage + q_row[i] * G::XS + (q_col[i] - (x0 - G::XA)));
+      d[0] = make_float4(f[0], f[1], f[2], f[3]);
+      d[1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
+  };
+
+  // y windows of this thread's column: c_x rows and w_x rows
+  float wc[G::WN], ww[G::WN];
+#pragma unroll
+  for (int j = 0; j < G::WN; ++j) { wc[j] = 0.f; ww[j] = 0.f; }
+  const int xr = t % 8;
+  const int xseg = t / 8;
+  const bool xok = x0 + t < xend;
+  const int64_t nab = box_vox(ab);
+  float* obase = F + box_index(ab, min(x0 + t, xend - 1), p0, z);
+  const int ostride = ab.n[0];
+
+  load_block(0);
+  for (int b = 0; b < nblocks; ++b) {
+    store_block();                           // the staged rows were last read before the previous barrier
+    if (b + 1 < nblocks) load_block(b + 1);  // in flight during this block's passes
+    __syncthreads();                         // staged rows complete; x-pass rows free
+    // x pass: 8 outputs of row xr (+ 8 r), columns xseg*8 .. +7, smoothing and derivative
+#pragma unroll
+    for (int r8 = 0; r8 < TB / 8; ++r8) {
+      const int row = xr + 8 * r8;
+      const float* src = stage + row * G::XS + 8 * xseg + G::B4;
+      float v[4 * G::NV];
+#pragma unroll
+      for (int j4 = 0; j4 < G::NV; ++j4) {
+        const float4 q = *reinterpret_cast<const float4*>(src + 4 * j4);
+        v[4 * j4] = q.x; v[4 * j4 + 1] = q.y; v[4 * j4 + 2] = q.z; v[4 * j4 + 3] = q.w;
+      }
+      float sw[8], sc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int m = G::O4 + i + RS;  // centre of output i in v
+        sw[i] = taps.w[RS] * v[m];
+        sc[i] = 0.f;
+#pragma unroll
+        for (int k = 1; k <= RS; ++k) {
+          sw[i] = fmaf(taps.w[RS + k], v[m + k] + v[m - k], sw[i]);
+          sc[i] = fmaf(taps.c[RS + k], v[m + k] - v[m - k], sc[i]);
+        }
+      }
+      float4* dw = reinterpret_cast<float4*>(sx + row * G::SXS + 8 * xseg);
+      float4* dc = reinterpret_cast<float4*>(sx + (TB + row) * G::SXS + 8 * xseg);
+      dw[0] = make_float4(sw[0], sw[1], sw[2], sw[3]);
+      dw[1] = make_float4(sw[4], sw[5], sw[6], sw[7]);
+      dc[0] = make_float4(sc[0], sc[1], sc[2], sc[3]);
+      dc[1] = make_float4(sc[4], sc[5], sc[6], sc[7]);
+    }
+    __syncthreads();  // x-pass rows complete
+    // y pass: slide the windows by TB, append this column's rows
+#pragma unroll
+    for (int j = 0; j < 2 * RS; ++j) { ww[j] = ww[j + TB]; wc[j] = wc[j + TB]; }
+#pragma unroll
+    for (int r = 0; r < TB; ++r) {
+      ww[2 * RS + r] = sx[r * G::SXS + t];
+      wc[2 * RS + r] = sx[(TB + r) * G::SXS + t];
+    }
+    if (b >= G::W) {
+      const int m0 = (b - G::W) * TB;  // first output row of this block, relative to p0
+#pragma unroll
+      for (int i = 0; i < TB; ++i) {
+        const int m = i + RS;
+        float f0 = taps.w[RS] * wc[m], f2 = taps.w[RS] * ww[m], f1 = 0.f;
+#pragma unroll
+        for (int k = 1; k <= RS; ++k) {
+          f0 = fmaf(taps.w[RS + k], wc[m + k] + wc[m - k], f0);
+          f1 = fmaf(taps.c[RS + k], ww[m + k] - ww[m - k], f1);
+          f2 = fmaf(taps.w[RS + k], ww[m + k] + ww[m - k], f2);
+        }
+        if (xok && m0 + i < L) {
+          float* o = obase + (int64_t)(m0 + i) * ostride;
+          o[0] = f0;
+          o[nab] = f1;
+          o[2 * nab] = f2;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- z pass
+// One thread per (x, y) column of the output box walks z.  The three partial
+// fields arrive by 4-byte cp.async into a shared ring of P = 2R+1 steps
+// (dynamic shared memory, P * 3 KB), issued kGzAhead steps ahead; ring slots
+// and register windows are indexed statically because the step loop is
+// unrolled by P.
+constexpr int kGzThreads = 256;
+constexpr int kGzAhead = 8;
+
+// 2^-8 keeps every possible gradient of uint16 data inside FP16's range while
+// leaving gradients down to 2^-6 intensity units normal.
+constexpr float kGzHalfScale = 1.0f / 256.0f;
+
+template <int RS, bool MIXED>
+__global__ void __launch_bounds__(kGzThreads, 2)
+    k_grad_z(const float* __restrict__ F, Box ab, float* __restrict__ J, Box ob, int seg, const Taps taps) {
+  constexpr int P = 2 * RS + 1;
+  constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
+  extern __shared__ __align__(16) float gz_ring[];  // [P][3][kGzThreads]
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  const int yr = blockIdx.y * blockDim.y + threadIdx.y;
+  const bool ok = x < ob.lo[0] + ob.n[0] && yr < ob.n[1];
+  const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
+  const int y = ob.lo[1] + min(yr, ob.n[1] - 1);
+  const int p0 = ob.lo[2] + blockIdx.z * seg;  // first output plane
+  const int L = min(seg, ob.lo[2] + ob.n[2] - p0);
+  if (L <= 0) return;
+  const int nsteps = L + 2 * RS;
+
+  // input column (xi, y) of the partial fields; step s reads plane p0 - RS + s,
+  // clamped to the planes the fields cover (the volume's edges, or the halo)
+  const int64_t nab = box_vox(ab);
+  const float* base = F + box_index(ab, xi, y, ab.lo[2]);
+  const int plane = ab.n[0] * ab.n[1];
+  const int q0 = p0 - RS - ab.lo[2];
+  auto src = [&](int s) -> const float* { return base + (int64_t)min(max(q0 + s, 0), ab.n[2] - 1) * plane; };
+  const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(gz_ring + tid);
+  constexpr uint32_t kField = kGzThreads * sizeof(float), kStep = 3 * kField;
+  auto issue = [&](int s, int slot) {
+    if (s < nsteps) {
+      const float* p = src(s);
+      cp_async4(ring0 + slot * kStep, p);
+      cp_async4(ring0 + slot * kStep + kField, p + nab);
+      cp_async4(ring0 + slot * kStep + 2 * kField, p + 2 * nab);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < AH; ++s) issue(s, s);
+
+  const int64_t nob = box_vox(ob);
+  float* obase = J + box_index(ob, xi, y, p0);
+  const int ostride = ob.n[0] * ob.n[1];
+  float w0[P], w1[P], w2[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) { w0[i] = 0.f; w1[i] = 0.f; w2[i] = 0.f; }
+
+  for (int base_s = 0; base_s < nsteps; base_s += P) {
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int s = base_s + u;
+      if (s >= nsteps) continue;
+      cp_async_wait<AH - 1>();  // step s has landed (this thread's own copies)
+      w0[u] = gz_ring[(3 * u) * kGzThreads + tid];
+      w1[u] = gz_ring[(3 * u + 1) * kGzThreads + tid];
+      w2[u] = gz_ring[(3 * u + 2) * kGzThreads + tid];
+      issue(s + AH, (u + AH) % P);  // into the slot of step s + AH - P, consumed already
+      if (s >= 2 * RS) {
+        const int c = (u + P - RS) % P;  // window slot of the output plane
+        float gx = taps.w[RS] * w0[c], gy = taps.w[RS] * w1[c], gz = 0.f;
+#pragma unroll
+        for (int k = 1; k <= RS; ++k) {
+          const int sp = (u + P - RS + k) % P, sm = (u + P - RS - k) % P;
+          gx = fmaf(taps.w[RS + k], w0[sp] + w0[sm], gx);
+          gy = fmaf(taps.w[RS + k], w1[sp] + w1[sm], gy);
+          gz = fmaf(taps.c[RS + k], w2[sp] - w2[sm], gz);
+        }
+        if (MIXED) {  // gradient held in FP16 (scaled), products formed exactly in FP32
+          gx = __half2float(__float2half_rn(gx * kGzHalfScale)) * (1.0f / kGzHalfScale);
+          gy = __half2float(__float2half_rn(gy * kGzHalfScale)) * (1.0f / kGzHalfScale);
+          gz = __half2float(__float2half_rn(gz * kGzHalfScale)) * (1.0f / kGzHalfScale);
+        }
+        if (ok) {
+          float* o = obase + (int64_t)(s - 2 * RS) * ostride;
+          o[0] = gx * gx;
+          o[nob] = gy * gy;
+          o[2 * nob] = gz * gz;
+          o[3 * nob] = gx * gy;
+          o[4 * nob] = gx * gz;
+          o[5 * nob] = gy * gz;
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------- launch
+template <int RS, int XT>
+static cudaError_t set_xy_attr() {
+  return cudaFuncSetAttribute(k_grad_xy<RS, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)GXYGeom<RS, XT>::SMEM);
+}
+
+template <int RS>
+static size_t gz_smem() {
+  return sizeof(float) * (2 * RS + 1) * 3 * kGzThreads;
+}
+
+template <int RS>
+static cudaError_t prepare_gs() {
+  cudaError_t e = set_xy_attr<RS, 256>();
+  if (e == cudaSuccess) e = set_xy_attr<RS, 128>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grad_z<RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gz_smem<RS>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grad_z<RS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gz_smem<RS>());
+  return e;
+}
+
+cudaError_t prepare_grad_split_kernels() {
+  cudaError_t e = prepare_gs<2>();
+  if (e == cudaSuccess) e = prepare_gs<3>();
+  if (e == cudaSuccess) e = prepare_gs<4>();
+  if (e == cudaSuccess) e = prepare_gs<6>();
+  if (e == cudaSuccess) e = prepare_gs<8>();
+  if (e == cudaSuccess) e = prepare_gs<12>();
+  return e;
+}
+
+// The box of the partial fields for gradient outputs over ob: ob grown by RS
+// in z and clipped to the volume and to the input box.
+Box grad_partial_box(const Box& ob, const Box& vb, int rs, int dimz) {
+  Box a = ob;
+  const int lo = max(max(0, vb.lo[2]), ob.lo[2] - rs);
+  const int hi = min(min(dimz, vb.lo[2] + vb.n[2]), ob.lo[2] + ob.n[2] + rs);
+  a.lo[2] = lo;
+  a.n[2] = hi - lo;
+  return a;
+}
+
+template <int RS, int XT>
+static cudaError_t launch_gxy_t(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
+                                const Taps& taps, cudaStream_t st) {
+  using G = GXYGeom<RS, XT>;
+  if (ab.n[2] > 65535) return cudaErrorInvalidValue;
+  const int64_t ctas = (int64_t)((ab.n[0] + XT - 1) / XT) * ab.n[2];
+  int nseg = 1;
+  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ab.n[1] / (nseg * 2) >= 8 * G::TB) nseg *= 2;
+  const int seg = (ab.n[1] + nseg - 1) / nseg;
+  dim3 grid((ab.n[0] + XT - 1) / XT, ab.n[2], (ab.n[1] + seg - 1) / seg);
+  k_grad_xy<RS, XT><<<grid, XT, G::SMEM, st>>>(vol, vb, dims[0], dims[1], F, ab, seg, taps);
+  return cudaGetLastError();
+}
+
+template <int RS>
+static cudaError_t launch_gxy_r(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
+                                const Taps& taps, cudaStream_t st) {
+  const int w256 = (ab.n[0] + 255) / 256 * 256 - ab.n[0], w128 = (ab.n[0] + 127) / 128 * 128 - ab.n[0];
+  return w128 < w256 ? launch_gxy_t<RS, 128>(vol, vb, dims, F, ab, taps, st)
+                     : launch_gxy_t<RS, 256>(vol, vb, dims, F, ab, taps, st);
+}
+
+template <int RS>
+static cudaError_t launch_gz_r(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps, bool mixed,
+                               cudaStream_t st) {
+  // warps along x: the widest that leaves the fewest idle columns
+  int wx = 1;
+  for (int w = 2; w <= kGzThreads / 32; w *= 2) {
+    const int span = 32 * w, best = 32 * wx;
+    if (32 * (w / 2) >= ob.n[0]) break;
+    if ((ob.n[0] + span - 1) / span * span <= (ob.n[0] + best - 1) / best * best) wx = w;
+  }
+  dim3 block(32 * wx, kGzThreads / (32 * wx));
+  const int64_t cols = (int64_t)((ob.n[0] + block.x - 1) / block.x) * ((ob.n[1] + block.y - 1) / block.y);
+  int nseg = 1;
+  while (nseg < 16 && cols * nseg < (int64_t)152 * 2 * 4 && ob.n[2] / (nseg * 2) >= 4 * (2 * RS + 1)) nseg *= 2;
+  const int seg = (ob.n[2] + nseg - 1) / nseg;
+  dim3 grid((ob.n[0] + block.x - 1) / block.x, (ob.n[1] + block.y - 1) / block.y, (ob.n[2] + seg - 1) / seg);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+  if (mixed)
+    k_grad_z<RS, true><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps);
+  else
+    k_grad_z<RS, false><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
+                           const Taps& taps, int rk, cudaStream_t st) {
+  if (box_vox(ab) == 0) return cudaSuccess;
+  if (box_vox(ab) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  switch (rk) {
+    case 2: return launch_gxy_r<2>(vol, vb, dims, F, ab, taps, st);
+    case 3: return launch_gxy_r<3>(vol, vb, dims, F, ab, taps, st);
+    case 4: return launch_gxy_r<4>(vol, vb, dims, F, ab, taps, st);
+    case 6: return launch_gxy_r<6>(vol, vb, dims, F, ab, taps, st);
+    case 8: return launch_gxy_r<8>(vol, vb, dims, F, ab, taps, st);
+    case 12: return launch_gxy_r<12>(vol, vb, dims, F, ab, taps, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps, int rk, bool mixed,
+                          cudaStream_t st) {
+  if (box_vox(ob) == 0) return cudaSuccess;
+  if (box_vox(ab) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  switch (rk) {
+    case 2: return launch_gz_r<2>(F, ab, J, ob, taps, mixed, st);
+    case 3: return launch_gz_r<3>(F, ab, J, ob, taps, mixed, st);
+    case 4: return launch_gz_r<4>(F, ab, J, ob, taps, mixed, st);
+    case 6: return launch_gz_r<6>(F, ab, J, ob, taps, mixed, st);
+    case 8: return launch_gz_r<8>(F, ab, J, ob, taps, mixed, st);
+    case 12: return launch_gz_r<12>(F, ab, J, ob, taps, mixed, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ct

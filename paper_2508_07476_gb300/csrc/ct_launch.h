@@ -12,6 +12,7 @@ namespace ct {
 // before any launch may be captured into a graph).
 cudaError_t prepare_sigma_kernels();
 cudaError_t prepare_rho_xy_kernels();
+cudaError_t prepare_grad_split_kernels();
 
 // Instantiated radius that serves radius r (zero taps pad the difference), or -1.
 int sigma_kernel_radius(int r);
@@ -20,6 +21,15 @@ int rho_kernel_radius(int r);
 // J (6 planes over ob) = products of the sigma-gradient of vol (array covering vb).
 cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int dims[3], float* J, const Box& ob,
                                  const Taps& taps, int rk, bool mixed, cudaStream_t st);
+
+// The split gradient: launch_grad_xy writes the x/y-filtered partial fields
+// (3 planes over ab = grad_partial_box(ob, vb, R, dims[2])) of vol; launch_grad_z
+// takes their z pass and writes J (6 planes over ob), as launch_grad_products does.
+Box grad_partial_box(const Box& ob, const Box& vb, int rs, int dimz);
+cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
+                           const Taps& taps, int rk, cudaStream_t st);
+cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps, int rk, bool mixed,
+                          cudaStream_t st);
 
 // rho pass along x: out (6 planes over ob) from in (6 planes over ib).
 cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
