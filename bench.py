@@ -370,6 +370,30 @@ def run_ours(args):
                   "gb_per_s": nvox * 5 / (prof_ms * 1e-3) / 1e9,
                   "mean_ha_by_depth": [round(float((r * centres).sum() / max(r.sum(), 1)), 2) for r in h]}
 
+    # streamline tractography through the mixed form's fibre field (timed apart from the step)
+    rng_t = np.random.default_rng(9)
+    zz, yy, xx = np.nonzero(mask)
+    pick = rng_t.choice(len(xx), min(100000, len(xx)), replace=False)
+    seeds = np.column_stack([xx[pick], yy[pick], zz[pick]]).astype(np.float32) + \
+        rng_t.uniform(-0.4, 0.4, (len(pick), 3)).astype(np.float32)
+    d_seeds = torch.from_numpy(seeds).cuda()
+    t_steps = 200
+    tp = _lib.make_track_params(0.5, t_steps, 0.1, 45.0)
+    pts = torch.empty((len(seeds), 2, t_steps + 1, 3), dtype=torch.float32, device="cuda")
+    tcnt = torch.empty((len(seeds), 2), dtype=torch.int32, device="cuda")
+    _lib.ct_track(tp, (n, n, n), outs["v"], outs["fa"], d_mask, d_seeds, len(seeds), pts, tcnt, stream)
+    e0.record(stream)
+    _lib.ct_track(tp, (n, n, n), outs["v"], outs["fa"], d_mask, d_seeds, len(seeds), pts, tcnt, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    track_ms = e0.elapsed_time(e1)
+    nsteps = int(tcnt.sum().item()) - int((tcnt > 0).sum().item())
+    tractography = {"ms": track_ms, "seeds": len(seeds), "tracks": 2 * len(seeds), "steps": nsteps,
+                    "steps_per_s": nsteps / (track_ms * 1e-3), "mean_points_per_track": float(tcnt.float().mean()),
+                    "params": {"step": 0.5, "max_steps": t_steps, "fa_min": 0.1, "max_turn_deg": 45.0,
+                               "scheme": "RK4, sign-aligned trilinear field"}}
+    del pts
+
     head = forms["mixed"]
     peaks, peak_kind = _peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -444,7 +468,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "gpu_launches_per_step": launches_per_step, "clocks": clocks, "forms": forms,
             "pipeline_roofline": pipeline_roofline, "accuracy": accuracy, "kernels": kernels,
-            "transmural_profile": transmural,
+            "transmural_profile": transmural, "tractography": tractography,
         }
         print(json.dumps(line))
     if world > 1:

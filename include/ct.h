@@ -287,6 +287,48 @@ ct_status ct_transmural_profile(const ct_profile_spec* spec, const int64_t vol_d
                                 const int64_t n[3], const void* d_ha, const uint8_t* d_mask, uint64_t* d_hist,
                                 void* stream);
 
+/*
+ * Streamline tractography through the fibre field (Figure 1(d); Architecture,
+ * "tractography").  The paper gives no integration scheme or stopping rule;
+ * this is the textbook one:
+ *   - direction at a point q: the 8 voxel vectors of q's interpolation cell
+ *     (corner i0 = min(floor(q), n - 2) per axis, weights trilinear), each
+ *     negated when it points against a reference direction r (the field is an
+ *     orientation: +v and -v are the same fibre), summed and normalised;
+ *     invalid when q lies outside [0, n-1] on an axis, a corner vector is not
+ *     finite, or the sum vanishes;
+ *   - one step from p along the current direction d: classical RK4 with
+ *     k1 = dir(p; d), k2 = dir(p + h/2 k1; k1), k3 = dir(p + h/2 k2; k2),
+ *     k4 = dir(p + h k3; k3), p' = p + h (k1 + 2 k2 + 2 k3 + k4) / 6 and the
+ *     new direction d' = normalise(k1 + 2 k2 + 2 k3 + k4);
+ *   - the track stops before p' when a direction is invalid, when d' turns
+ *     from d by more than max_turn_deg, when p' is outside the volume, when
+ *     the mask (nullable) is 0 at p's nearest voxel floor(p' + 1/2), or when
+ *     FA (nullable; trilinear, not aligned) at p' is below fa_min;
+ *   - from each seed two tracks: the forward one starts along
+ *     dir(seed; v at the seed's nearest voxel), the backward one along its
+ *     negation (neither starts when that voxel's vector is zero or not
+ *     finite, or dir is invalid); max_steps steps at most.
+ * d_vec: 3 FP32 planes [z][y][x] over the volume (the pipeline's vector
+ * output; NaN fill stops tracks), d_fa: 1 FP32 plane or NULL, d_mask: uint8
+ * or NULL, d_seeds: n_seeds x (x, y, z) FP32 voxel coordinates.
+ * Outputs: d_points: FP32 [n_seeds][2][max_steps + 1][3] (point 0 is the
+ * seed), d_count: int32 [n_seeds][2] points written per track (0 when the
+ * seed is outside the volume, 1 when it cannot start).  Every dims >= 2;
+ * step > 0; max_steps >= 1; reserved 0.  Asynchronous on `stream`.
+ */
+typedef struct ct_track_params {
+  double step;
+  double fa_min;
+  double max_turn_deg;
+  int32_t max_steps;
+  int32_t reserved;
+} ct_track_params;
+
+ct_status ct_track(const ct_track_params* params, const int64_t vol_dims[3], const float* d_vec, const float* d_fa,
+                   const uint8_t* d_mask, const float* d_seeds, int64_t n_seeds, float* d_points, int32_t* d_count,
+                   void* stream);
+
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* ct_last_error(void);
 

@@ -74,6 +74,11 @@ class ct_profile_spec(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class ct_track_params(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_double), ("fa_min", ctypes.c_double), ("max_turn_deg", ctypes.c_double),
+                ("max_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class CTError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"ct status {status}: {message}")
@@ -107,6 +112,9 @@ _SIGNATURES = [
     ("ct_transmural_profile", ctypes.c_int32,
      [ctypes.POINTER(ct_profile_spec), _I64x3, _I64x3, _I64x3, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_void_p]),
+    ("ct_track", ctypes.c_int32,
+     [ctypes.POINTER(ct_track_params), _I64x3, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("ct_plan_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("ct_plan_kernel_times", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_kernel_time), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -269,6 +277,18 @@ def make_profile_spec(lv_center, lv_axis, r_in: float, r_out: float, n_depth: in
 def ct_transmural_profile(spec: ct_profile_spec, vol_dims, lo, n, ha, mask, hist, stream=None) -> None:
     _check(load().ct_transmural_profile(ctypes.byref(spec), _i64x3(vol_dims), _i64x3(lo), _i64x3(n), _ptr(ha),
                                         _ptr(mask), _ptr(hist), _stream(stream)))
+
+
+def make_track_params(step: float, max_steps: int, fa_min: float = 0.0, max_turn_deg: float = 90.0) -> ct_track_params:
+    p = ct_track_params()
+    p.step, p.fa_min, p.max_turn_deg, p.max_steps, p.reserved = step, fa_min, max_turn_deg, max_steps, 0
+    return p
+
+
+def ct_track(params: ct_track_params, vol_dims, vec, fa, mask, seeds, n_seeds: int, points, count,
+             stream=None) -> None:
+    _check(load().ct_track(ctypes.byref(params), _i64x3(vol_dims), _ptr(vec), _ptr(fa), _ptr(mask), _ptr(seeds),
+                           int(n_seeds), _ptr(points), _ptr(count), _stream(stream)))
 
 
 def ct_plan_sync(plan) -> None:

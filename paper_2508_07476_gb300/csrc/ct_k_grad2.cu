@@ -198,14 +198,20 @@ __global__ void __launch_bounds__(XT, 512 / XT)
 // and register windows are indexed statically because the step loop is
 // unrolled by P.
 constexpr int kGzThreads = 256;
-constexpr int kGzAhead = 8;
+#ifndef CT_GZ_AHEAD
+#define CT_GZ_AHEAD 8
+#endif
+#ifndef CT_GZ_MINB
+#define CT_GZ_MINB 2
+#endif
+constexpr int kGzAhead = CT_GZ_AHEAD;
 
 // 2^-8 keeps every possible gradient of uint16 data inside FP16's range while
 // leaving gradients down to 2^-6 intensity units normal.
 constexpr float kGzHalfScale = 1.0f / 256.0f;
 
 template <int RS, bool MIXED>
-__global__ void __launch_bounds__(kGzThreads, 2)
+__global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
     k_grad_z(const float* __restrict__ F, Box ab, float* __restrict__ J, Box ob, int seg, const Taps taps) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)

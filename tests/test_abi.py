@@ -58,16 +58,18 @@ def test_struct_layout_matches_c(tmp_path):
         'printf("%zu %zu %zu\\n", offsetof(ct_item, dims), offsetof(ct_item, vec), sizeof(ct_stats));\n'
         'printf("%zu %zu %zu %zu %zu\\n", sizeof(ct_synth_spec), offsetof(ct_synth_spec, flags),'
         " offsetof(ct_synth_spec, seed), sizeof(ct_profile_spec), offsetof(ct_profile_spec, n_depth));\n"
+        'printf("%zu %zu\\n", sizeof(ct_track_params), offsetof(ct_track_params, max_steps));\n'
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
-    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
-    c_vals = [int(v) for v in (a.split() + b.split() + c.split())]
+    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
+    c_vals = [int(v) for v in (a.split() + b.split() + c.split() + d.split())]
     py_vals = [ctypes.sizeof(_lib.ct_params), _lib.ct_params.precision.offset, _lib.ct_params.fill_value.offset,
                _lib.ct_params.chunk.offset, ctypes.sizeof(_lib.ct_item), _lib.ct_item.dims.offset,
                _lib.ct_item.vec.offset, ctypes.sizeof(_lib.ct_stats), ctypes.sizeof(_lib.ct_synth_spec),
                _lib.ct_synth_spec.flags.offset, _lib.ct_synth_spec.seed.offset, ctypes.sizeof(_lib.ct_profile_spec),
-               _lib.ct_profile_spec.n_depth.offset]
+               _lib.ct_profile_spec.n_depth.offset, ctypes.sizeof(_lib.ct_track_params),
+               _lib.ct_track_params.max_steps.offset]
     assert c_vals == py_vals
 
 
