@@ -275,7 +275,7 @@ def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int):
 # DRAM bytes per output voxel of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch / voxels of the
 # capture); valid only for the kernel version summarised in the named file.
-MEASURED_TRAFFIC = {"rho_xy": (45.0, "profiles/rho_xy_annulus256.md")}
+MEASURED_TRAFFIC = {"rho_xy": (45.0, "profiles/kernels_annulus256.md")}
 
 
 def run_ours(args):
