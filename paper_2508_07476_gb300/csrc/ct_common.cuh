@@ -309,8 +309,8 @@ __device__ __forceinline__ void orient_largest(float v[3]) {
 
 // Output encodings (CT_OUT_F32 = 0, CT_OUT_F16 = 1, CT_OUT_U8Q = 2).  TYPE is a
 // compile-time encoding, or -1 for the run-time one in `type`.
-template <int TYPE = -1>
-__device__ __forceinline__ void store_val(void* base, int64_t i, int type, float val) {
+template <int TYPE = -1, typename IT = int64_t>
+__device__ __forceinline__ void store_val(void* base, IT i, int type, float val) {
   if (base == nullptr) return;
   const int ty = TYPE >= 0 ? TYPE : type;
   if (ty == 0) {
@@ -320,8 +320,8 @@ __device__ __forceinline__ void store_val(void* base, int64_t i, int type, float
   }
 }
 
-template <int TYPE = -1>
-__device__ __forceinline__ void store_angle(void* base, int64_t i, int type, float deg, bool valid) {
+template <int TYPE = -1, typename IT = int64_t>
+__device__ __forceinline__ void store_angle(void* base, IT i, int type, float deg, bool valid) {
   if (base == nullptr) return;
   const int ty = TYPE >= 0 ? TYPE : type;
   if (ty == 2) {
@@ -329,7 +329,7 @@ __device__ __forceinline__ void store_angle(void* base, int64_t i, int type, flo
     if (valid) code = (uint8_t)(((int)rintf((deg + 90.f) * (256.f / 180.f))) & 255);
     reinterpret_cast<uint8_t*>(base)[i] = code;
   } else {
-    store_val<TYPE>(base, i, ty, deg);
+    store_val<TYPE, IT>(base, i, ty, deg);
   }
 }
 

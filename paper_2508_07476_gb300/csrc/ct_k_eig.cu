@@ -47,33 +47,32 @@ __device__ __forceinline__ void resolve(const Sym3<float>& s, bool mixed, float 
 // Outputs of one voxel: oriented vector, HA, IA, FA (or fill outside the mask).
 // VT / AT / FT: compile-time encodings of the vector / angle / FA outputs, or
 // -1 to take them from `o` at run time.
-template <int VT = -1, int AT = -1, int FT = -1>
-__device__ __forceinline__ void write_voxel(const EigOut& o, int64_t oi, bool inside, const Frame& F, int x, int y,
+template <int VT = -1, int AT = -1, int FT = -1, typename IT = int64_t>
+__device__ __forceinline__ void write_voxel(const EigOut& o, IT oi, bool inside, const Frame& F, int x, int y,
                                             int z, const float l[3], float v[3], float fill) {
+  const IT n = (IT)box_vox(o.ab);
   if (!inside) {
-    store_val<VT>(o.vec, oi, o.vec_t, fill);
-    int64_t n = box_vox(o.ab);
+    store_val<VT, IT>(o.vec, oi, o.vec_t, fill);
     if (o.vec) {
-      store_val<VT>(o.vec, n + oi, o.vec_t, fill);
-      store_val<VT>(o.vec, 2 * n + oi, o.vec_t, fill);
+      store_val<VT, IT>(o.vec, n + oi, o.vec_t, fill);
+      store_val<VT, IT>(o.vec, 2 * n + oi, o.vec_t, fill);
     }
-    store_angle<AT>(o.ha, oi, o.ang_t, fill, false);
-    store_angle<AT>(o.ia, oi, o.ang_t, fill, false);
-    store_val<FT>(o.fa, oi, o.fa_t, fill);
+    store_angle<AT, IT>(o.ha, oi, o.ang_t, fill, false);
+    store_angle<AT, IT>(o.ia, oi, o.ang_t, fill, false);
+    store_val<FT, IT>(o.fa, oi, o.fa_t, fill);
     return;
   }
   float ha, ia;
   bool framed = ha_ia(F, x, y, z, v, ha, ia);
   if (!framed) orient_largest(v);
   if (o.vec) {
-    int64_t n = box_vox(o.ab);
-    store_val<VT>(o.vec, oi, o.vec_t, v[0]);
-    store_val<VT>(o.vec, n + oi, o.vec_t, v[1]);
-    store_val<VT>(o.vec, 2 * n + oi, o.vec_t, v[2]);
+    store_val<VT, IT>(o.vec, oi, o.vec_t, v[0]);
+    store_val<VT, IT>(o.vec, n + oi, o.vec_t, v[1]);
+    store_val<VT, IT>(o.vec, 2 * n + oi, o.vec_t, v[2]);
   }
-  store_angle<AT>(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
-  store_angle<AT>(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
-  store_val<FT>(o.fa, oi, o.fa_t, fa_of(l));
+  store_angle<AT, IT>(o.ha, oi, o.ang_t, framed ? ha : fill, framed);
+  store_angle<AT, IT>(o.ia, oi, o.ang_t, framed ? ia : fill, framed);
+  store_val<FT, IT>(o.fa, oi, o.fa_t, fa_of(l));
 }
 
 __device__ __forceinline__ void push_fallback(const Fallback& fb, int64_t i) {
@@ -106,6 +105,37 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
     if (!eig_closed<float>(s, l, v)) push_fallback(fb, ((int64_t)zr * ob.n[1] + yr) * ob.n[0] + (x - ob.lo[0]));
   }
   write_voxel<VT, AT, FT>(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
+}
+
+// The same for boxes whose planes fit 32-bit indices and whose rows fit the
+// grid's y and z: (y, z) from the block index, every index in 32 bits.
+__device__ __forceinline__ int box_index32(const Box& b, int x, int y, int z) {
+  return ((z - b.lo[2]) * b.n[1] + (y - b.lo[1])) * b.n[0] + (x - b.lo[0]);
+}
+
+template <int VT, int AT, int FT>
+__global__ void __launch_bounds__(256, CT_EIG_MINB)
+    k_eig_angles32(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
+                   float fill, EigOut o, bool mixed, Fallback fb) {
+  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= ob.lo[0] + ob.n[0]) return;
+  const int y = ob.lo[1] + blockIdx.y, z = ob.lo[2] + blockIdx.z;
+  const bool inside = mask == nullptr || __ldg(mask + box_index32(mb, x, y, z)) != 0;
+  float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
+  if (inside) {
+    const int ns = sb.n[0] * sb.n[1] * sb.n[2];
+    const int si = box_index32(sb, x, y, z);
+    Sym3<float> s;
+    s.a = __ldg(S + si);
+    s.b = __ldg(S + ns + si);
+    s.c = __ldg(S + 2 * ns + si);
+    s.d = __ldg(S + 3 * ns + si);
+    s.e = __ldg(S + 4 * ns + si);
+    s.f = __ldg(S + 5 * ns + si);
+    if (!eig_closed<float>(s, l, v))
+      push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
+  }
+  write_voxel<VT, AT, FT, int>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
 
 __global__ void __launch_bounds__(128)
@@ -141,6 +171,21 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
   // 128-thread rows where 256 would leave more columns idle (e.g. width 384)
   const int nt = ((ob.n[0] + 127) / 128 * 128 - ob.n[0]) < ((ob.n[0] + 255) / 256 * 256 - ob.n[0]) ? 128 : 256;
   dim3 grid((ob.n[0] + nt - 1) / nt, gy, (rows + gy - 1) / gy);
+  // 32-bit indices and a (x, y, z) grid when every plane set fits
+  const int64_t lim = ((int64_t)1 << 31) - 1;
+  if (ob.n[1] <= 65535 && ob.n[2] <= 65535 && 6 * box_vox(sb) <= lim && 3 * box_vox(o.ab) <= lim &&
+      box_vox(mb) <= lim) {
+    dim3 g3((ob.n[0] + nt - 1) / nt, ob.n[1], ob.n[2]);
+    if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32)
+      k_eig_angles32<0, 0, 0><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16)
+      k_eig_angles32<1, 1, 1><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16)
+      k_eig_angles32<-1, 2, 1><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    else
+      k_eig_angles32<-1, -1, -1><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    return cudaGetLastError();
+  }
   // the encodings of the common configurations are compiled in; others are read at run time
   if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32)
     k_eig_angles<0, 0, 0><<<grid, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
