@@ -19,6 +19,13 @@
  * (identical in exact arithmetic to the triple sum; the tests check the two
  * against each other on small volumes).
  *
+ * Anisotropic voxels (spacing (sx, sy, sz); reading stated where the paper is
+ * silent): sigma, rho, the LV centre and axis are in the units of the
+ * spacing; scale s along axis a becomes s / s_a voxels, gradient component a
+ * is divided by s_a (the gradient in physical units), and positions are
+ * (x sx, y sy, z sz).  An optional centreline gives slice z its own LV centre
+ * (cx, cy, z sz).  Unit spacing without a centreline is the isotropic case.
+ *
  * Conventions
  *   volume  vol[z][y][x], x fastest, uint16; dims = (nx, ny, nz)
  *   boxes   lo = (x0, y0, z0), n = (nx, ny, nz) in global voxel indices
@@ -68,12 +75,13 @@ typedef struct {
 static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
 static int64_t box_vox(const box_t* b) { return b->n[0] * b->n[1] * b->n[2]; }
 
-/* b grown by r on every side, then clipped to the volume [0, dims). */
-static box_t grow_clip(const box_t* b, int r, const int64_t dims[3]) {
-  box_t o;
+/* b grown by r[a] along each axis a, then clipped to the volume [0, dims). */
+static box_t grow_clip3(const box_t* b, const int r[3], const int64_t dims[3]) {
+  box_t o = *b;
   for (int a = 0; a < 3; ++a) {
-    int64_t lo = clampi(b->lo[a] - r, 0, dims[a] - 1);
-    int64_t hi = clampi(b->lo[a] + b->n[a] - 1 + r, 0, dims[a] - 1);
+    int64_t lo = b->lo[a] - r[a], hi = b->lo[a] + b->n[a] - 1 + r[a];
+    if (lo < 0) lo = 0;
+    if (hi > dims[a] - 1) hi = dims[a] - 1;
     o.lo[a] = lo;
     o.n[a] = hi - lo + 1;
   }
@@ -150,16 +158,23 @@ static int check_box(const int64_t dims[3], const int64_t lo[3], const int64_t n
 /*
  * Gradient at noise scale sigma (Figure 1b; Architecture, "orientation"):
  *   g_x = c_x * w_y * w_z * I,  g_y = w_x * c_y * w_z * I,  g_z = w_x * w_y * c_z * I
- * each a separable filter applied z, then y, then x.  Output: 3 planes over box.
+ * each a separable filter applied z, then y, then x, with the kernels of
+ * sig[a] (voxel units) along axis a (anisotropic voxels give a different
+ * scale per axis).  Output: 3 planes over box, in voxel units.
  */
-int cto_gradient(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3], double sigma,
-                 double truncate, double* g) {
-  if (!vol || !g || check_box(dims, lo, n) || !(sigma > 0.0)) return CTO_ERR_ARG;
-  int R = cto_radius(sigma, truncate);
-  double* w = malloc(sizeof(double) * (2 * R + 1));
-  double* c = malloc(sizeof(double) * (2 * R + 1));
+int cto_gradient3(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3],
+                  const double sig[3], double truncate, double* g) {
+  if (!vol || !g || check_box(dims, lo, n) || !(sig[0] > 0.0) || !(sig[1] > 0.0) || !(sig[2] > 0.0))
+    return CTO_ERR_ARG;
+  int R[3];
+  double *w[3] = {NULL, NULL, NULL}, *c[3] = {NULL, NULL, NULL};
+  for (int a = 0; a < 3; ++a) {
+    R[a] = cto_radius(sig[a], truncate);
+    w[a] = malloc(sizeof(double) * (2 * R[a] + 1));
+    c[a] = malloc(sizeof(double) * (2 * R[a] + 1));
+  }
   box_t ob = {{lo[0], lo[1], lo[2]}, {n[0], n[1], n[2]}};
-  box_t ib = grow_clip(&ob, R, dims);
+  box_t ib = grow_clip3(&ob, R, dims);
   box_t bz = ib; /* after the z pass: x, y still padded, z = output range */
   bz.lo[2] = ob.lo[2];
   bz.n[2] = ob.n[2];
@@ -170,11 +185,11 @@ int cto_gradient(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3]
   double* t1 = malloc(sizeof(double) * box_vox(&bz));
   double* t2 = malloc(sizeof(double) * box_vox(&by));
   int rc = CTO_OK;
-  if (!w || !c || !I || !t1 || !t2) {
+  if (!w[0] || !w[1] || !w[2] || !c[0] || !c[1] || !c[2] || !I || !t1 || !t2) {
     rc = CTO_ERR_OOM;
     goto done;
   }
-  cto_kernels(sigma, truncate, w, c);
+  for (int a = 0; a < 3; ++a) cto_kernels(sig[a], truncate, w[a], c[a]);
   for (int64_t z = 0; z < ib.n[2]; ++z)
     for (int64_t y = 0; y < ib.n[1]; ++y)
       for (int64_t x = 0; x < ib.n[0]; ++x)
@@ -183,20 +198,28 @@ int cto_gradient(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3]
   int64_t nv = box_vox(&ob);
   for (int comp = 0; comp < 3; ++comp) {
     /* derivative along axis `comp`, smoothing along the other two */
-    const double* tz = comp == 2 ? c : w;
-    const double* ty = comp == 1 ? c : w;
-    const double* tx = comp == 0 ? c : w;
-    if ((rc = pass1d(I, &ib, t1, &bz, 2, tz, R, comp == 2, dims))) goto done;
-    if ((rc = pass1d(t1, &bz, t2, &by, 1, ty, R, comp == 1, dims))) goto done;
-    if ((rc = pass1d(t2, &by, g + comp * nv, &ob, 0, tx, R, comp == 0, dims))) goto done;
+    const double* tz = comp == 2 ? c[2] : w[2];
+    const double* ty = comp == 1 ? c[1] : w[1];
+    const double* tx = comp == 0 ? c[0] : w[0];
+    if ((rc = pass1d(I, &ib, t1, &bz, 2, tz, R[2], comp == 2, dims))) goto done;
+    if ((rc = pass1d(t1, &bz, t2, &by, 1, ty, R[1], comp == 1, dims))) goto done;
+    if ((rc = pass1d(t2, &by, g + comp * nv, &ob, 0, tx, R[0], comp == 0, dims))) goto done;
   }
 done:
-  free(w);
-  free(c);
+  for (int a = 0; a < 3; ++a) {
+    free(w[a]);
+    free(c[a]);
+  }
   free(I);
   free(t1);
   free(t2);
   return rc;
+}
+
+int cto_gradient(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3], double sigma,
+                 double truncate, double* g) {
+  const double sig[3] = {sigma, sigma, sigma};
+  return cto_gradient3(vol, dims, lo, n, sig, truncate, g);
 }
 
 /*
@@ -206,13 +229,25 @@ done:
  * PRODUCT field at the global edges.  Output: 6 planes (xx,yy,zz,xy,xz,yz) over
  * the box (lo, n).  The gradient is evaluated only where it is needed: on the
  * box grown by R_rho and clipped to the volume.
+ * Per-axis form: sig[a] and rho3[a] are the scales along axis a in voxel
+ * units, and gscale[a] multiplies gradient component a before the products
+ * (1 / spacing[a] gives the gradient in physical units).
  */
-int cto_structure_tensor(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3],
-                         double sigma, double rho, double truncate, double* S) {
-  if (!vol || !S || check_box(dims, lo, n) || !(sigma > 0.0) || !(rho > 0.0)) return CTO_ERR_ARG;
-  int Rr = cto_radius(rho, truncate);
+int cto_structure_tensor3(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3],
+                          const double sig[3], const double rho3[3], const double gscale[3], double truncate,
+                          double* S) {
+  if (!vol || !S || check_box(dims, lo, n)) return CTO_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!(sig[a] > 0.0) || !(rho3[a] > 0.0)) return CTO_ERR_ARG;
+  int Rr[3];
+  double *w[3] = {NULL, NULL, NULL}, *c[3] = {NULL, NULL, NULL};
+  for (int a = 0; a < 3; ++a) {
+    Rr[a] = cto_radius(rho3[a], truncate);
+    w[a] = malloc(sizeof(double) * (2 * Rr[a] + 1));
+    c[a] = malloc(sizeof(double) * (2 * Rr[a] + 1));
+  }
   box_t ob = {{lo[0], lo[1], lo[2]}, {n[0], n[1], n[2]}};
-  box_t gb = grow_clip(&ob, Rr, dims);
+  box_t gb = grow_clip3(&ob, Rr, dims);
   box_t bz = gb;
   bz.lo[2] = ob.lo[2];
   bz.n[2] = ob.n[2];
@@ -224,33 +259,40 @@ int cto_structure_tensor(const uint16_t* vol, const int64_t dims[3], const int64
   double* J = malloc(sizeof(double) * ng);
   double* t1 = malloc(sizeof(double) * box_vox(&bz));
   double* t2 = malloc(sizeof(double) * box_vox(&by));
-  double* w = malloc(sizeof(double) * (2 * Rr + 1));
-  double* c = malloc(sizeof(double) * (2 * Rr + 1));
   int rc = CTO_OK;
-  if (!g || !J || !t1 || !t2 || !w || !c) {
+  if (!g || !J || !t1 || !t2 || !w[0] || !w[1] || !w[2] || !c[0] || !c[1] || !c[2]) {
     rc = CTO_ERR_OOM;
     goto done;
   }
-  if ((rc = cto_gradient(vol, dims, gb.lo, gb.n, sigma, truncate, g))) goto done;
-  cto_kernels(rho, truncate, w, c);
+  if ((rc = cto_gradient3(vol, dims, gb.lo, gb.n, sig, truncate, g))) goto done;
+  for (int a = 0; a < 3; ++a) cto_kernels(rho3[a], truncate, w[a], c[a]);
   static const int ca[6] = {0, 1, 2, 0, 0, 1};
   static const int cb[6] = {0, 1, 2, 1, 2, 2};
   for (int comp = 0; comp < 6; ++comp) {
     const double* ga = g + ca[comp] * ng;
     const double* gbb = g + cb[comp] * ng;
-    for (int64_t i = 0; i < ng; ++i) J[i] = ga[i] * gbb[i];
-    if ((rc = pass1d(J, &gb, t1, &bz, 2, w, Rr, 0, dims))) goto done;
-    if ((rc = pass1d(t1, &bz, t2, &by, 1, w, Rr, 0, dims))) goto done;
-    if ((rc = pass1d(t2, &by, S + comp * nv, &ob, 0, w, Rr, 0, dims))) goto done;
+    const double sa = gscale[ca[comp]], sb = gscale[cb[comp]];
+    for (int64_t i = 0; i < ng; ++i) J[i] = (sa * ga[i]) * (sb * gbb[i]);
+    if ((rc = pass1d(J, &gb, t1, &bz, 2, w[2], Rr[2], 0, dims))) goto done;
+    if ((rc = pass1d(t1, &bz, t2, &by, 1, w[1], Rr[1], 0, dims))) goto done;
+    if ((rc = pass1d(t2, &by, S + comp * nv, &ob, 0, w[0], Rr[0], 0, dims))) goto done;
   }
 done:
   free(g);
   free(J);
   free(t1);
   free(t2);
-  free(w);
-  free(c);
+  for (int a = 0; a < 3; ++a) {
+    free(w[a]);
+    free(c[a]);
+  }
   return rc;
+}
+
+int cto_structure_tensor(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3],
+                         double sigma, double rho, double truncate, double* S) {
+  const double sig[3] = {sigma, sigma, sigma}, rho3[3] = {rho, rho, rho}, one[3] = {1.0, 1.0, 1.0};
+  return cto_structure_tensor3(vol, dims, lo, n, sig, rho3, one, truncate, S);
 }
 
 /*
@@ -385,9 +427,10 @@ int cto_ha_ia(const double p[3], const double c[3], const double a[3], const dou
  * every output; on the axis HA and IA get `fill`.  Where no frame exists the
  * vector is oriented with its largest-magnitude component positive.
  */
-int cto_angles_field(const double* v1, const double* evals, const int64_t dims[3], const int64_t lo[3],
-                     const int64_t n[3], const double center[3], const double axis[3], const uint8_t* mask,
-                     double fill, double* vout, double* ha, double* ia, double* fa) {
+int cto_angles_field3(const double* v1, const double* evals, const int64_t dims[3], const int64_t lo[3],
+                      const int64_t n[3], const double center[3], const double axis[3], const double spacing[3],
+                      const double* centres, const uint8_t* mask, double fill, double* vout, double* ha, double* ia,
+                      double* fa) {
   if (!v1 || !evals || check_box(dims, lo, n)) return CTO_ERR_ARG;
   if (axis[0] == 0.0 && axis[1] == 0.0 && axis[2] == 0.0) return CTO_ERR_ARG;
   int64_t nv = n[0] * n[1] * n[2];
@@ -399,9 +442,16 @@ int cto_angles_field(const double* v1, const double* evals, const int64_t dims[3
         int64_t gx = lo[0] + x, gy = lo[1] + y, gz = lo[2] + z;
         double v[3] = {v1[i], v1[nv + i], v1[2 * nv + i]};
         double ev[3] = {evals[i], evals[nv + i], evals[2 * nv + i]};
-        double p[3] = {(double)gx, (double)gy, (double)gz};
+        /* physical position; the LV centre of this slice when a centreline is given */
+        double p[3] = {(double)gx * spacing[0], (double)gy * spacing[1], (double)gz * spacing[2]};
+        double cs[3] = {center[0], center[1], center[2]};
+        if (centres) {
+          cs[0] = centres[2 * gz];
+          cs[1] = centres[2 * gz + 1];
+          cs[2] = p[2];
+        }
         double h = fill, a = fill, vo[3];
-        if (!cto_ha_ia(p, center, axis, v, &h, &a, vo)) {
+        if (!cto_ha_ia(p, cs, axis, v, &h, &a, vo)) {
           int m = 0;
           for (int k = 1; k < 3; ++k)
             if (fabs(v[k]) > fabs(v[m])) m = k;
@@ -429,15 +479,30 @@ int cto_angles_field(const double* v1, const double* evals, const int64_t dims[3
   return CTO_OK;
 }
 
+int cto_angles_field(const double* v1, const double* evals, const int64_t dims[3], const int64_t lo[3],
+                     const int64_t n[3], const double center[3], const double axis[3], const uint8_t* mask,
+                     double fill, double* vout, double* ha, double* ia, double* fa) {
+  const double one[3] = {1.0, 1.0, 1.0};
+  return cto_angles_field3(v1, evals, dims, lo, n, center, axis, one, NULL, mask, fill, vout, ha, ia, fa);
+}
+
 /*
  * The whole per-voxel pipeline over the box (lo, n) of a volume: structure
  * tensor (6 planes), eigenvalues (3), oriented fibre vector (3), HA, IA, FA.
  * Any output pointer may be NULL except S.
  */
-int cto_pipeline(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3], double sigma,
-                 double rho, double truncate, const double center[3], const double axis[3], const uint8_t* mask,
-                 double fill, double* S, double* evals, double* vout, double* ha, double* ia, double* fa) {
-  int rc = cto_structure_tensor(vol, dims, lo, n, sigma, rho, truncate, S);
+int cto_pipeline3(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3], double sigma,
+                  double rho, double truncate, const double spacing[3], const double center[3], const double axis[3],
+                  const double* centres, const uint8_t* mask, double fill, double* S, double* evals, double* vout,
+                  double* ha, double* ia, double* fa) {
+  double sig[3], rho3[3], gs[3];
+  for (int a = 0; a < 3; ++a) {
+    if (!(spacing[a] > 0.0)) return CTO_ERR_ARG;
+    sig[a] = sigma / spacing[a];
+    rho3[a] = rho / spacing[a];
+    gs[a] = 1.0 / spacing[a];
+  }
+  int rc = cto_structure_tensor3(vol, dims, lo, n, sig, rho3, gs, truncate, S);
   if (rc) return rc;
   int64_t nv = n[0] * n[1] * n[2];
   double* ev = evals ? evals : malloc(sizeof(double) * 3 * nv);
@@ -448,10 +513,18 @@ int cto_pipeline(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3]
     return CTO_ERR_OOM;
   }
   cto_eig_field(S, nv, ev, v1);
-  rc = cto_angles_field(v1, ev, dims, lo, n, center, axis, mask, fill, vout, ha, ia, fa);
+  rc = cto_angles_field3(v1, ev, dims, lo, n, center, axis, spacing, centres, mask, fill, vout, ha, ia, fa);
   if (!evals) free(ev);
   free(v1);
   return rc;
+}
+
+int cto_pipeline(const uint16_t* vol, const int64_t dims[3], const int64_t lo[3], const int64_t n[3], double sigma,
+                 double rho, double truncate, const double center[3], const double axis[3], const uint8_t* mask,
+                 double fill, double* S, double* evals, double* vout, double* ha, double* ia, double* fa) {
+  const double one[3] = {1.0, 1.0, 1.0};
+  return cto_pipeline3(vol, dims, lo, n, sigma, rho, truncate, one, center, axis, NULL, mask, fill, S, evals, vout,
+                       ha, ia, fa);
 }
 
 /* Threads OpenMP will use (1 when built without OpenMP). */

@@ -51,7 +51,9 @@ def _bind(path: str):
     lib.cto_fa.restype = D
     lib.cto_ha_ia.argtypes = [P, P, P, P, P, P, P]
     lib.cto_angles_field.argtypes = [P, P, P, P, P, P, P, P, D, P, P, P, P]
+    lib.cto_angles_field3.argtypes = [P, P, P, P, P, P, P, P, P, P, D, P, P, P, P]
     lib.cto_pipeline.argtypes = [P, P, P, P, D, D, D, P, P, P, D, P, P, P, P, P, P]
+    lib.cto_pipeline3.argtypes = [P, P, P, P, D, D, D, P, P, P, P, P, D, P, P, P, P, P, P]
     lib.cto_num_threads.restype = ctypes.c_int
     return lib
 
@@ -195,8 +197,10 @@ def ha_ia(p, center, axis, v):
     return float(ha[0]), float(ia[0]), vo
 
 
-def angles_field(v1, evals, dims_xyz, lo, n, center, axis, mask=None, fill=float("nan")):
-    """(v oriented [3,...], HA, IA, FA) for a box, from smallest eigenvectors and eigenvalues."""
+def angles_field(v1, evals, dims_xyz, lo, n, center, axis, mask=None, fill=float("nan"), spacing=None,
+                 centres=None):
+    """(v oriented [3,...], HA, IA, FA) for a box, from smallest eigenvectors and eigenvalues
+    (``spacing`` / ``centres`` as in ``pipeline``)."""
     v1 = np.ascontiguousarray(v1, dtype=np.float64)
     evals = np.ascontiguousarray(evals, dtype=np.float64)
     shp = v1.shape[1:]
@@ -207,14 +211,25 @@ def angles_field(v1, evals, dims_xyz, lo, n, center, axis, mask=None, fill=float
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     c = np.ascontiguousarray(np.asarray(center, dtype=np.float64))
     a = np.ascontiguousarray(np.asarray(axis, dtype=np.float64))
-    _check(_load().cto_angles_field(_p(v1), _p(evals), _p(_i64(dims_xyz)), _p(_i64(lo)), _p(_i64(n)), _p(c), _p(a),
-                                     _p(m), fill, _p(vout), _p(ha), _p(ia), _p(fa_)), "angles_field")
+    if spacing is None and centres is None:
+        _check(_load().cto_angles_field(_p(v1), _p(evals), _p(_i64(dims_xyz)), _p(_i64(lo)), _p(_i64(n)), _p(c),
+                                         _p(a), _p(m), fill, _p(vout), _p(ha), _p(ia), _p(fa_)), "angles_field")
+        return vout, ha, ia, fa_
+    sp = np.ascontiguousarray(np.asarray((1.0, 1.0, 1.0) if spacing is None else spacing, dtype=np.float64))
+    ce = None if centres is None else np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1, 2))
+    _check(_load().cto_angles_field3(_p(v1), _p(evals), _p(_i64(dims_xyz)), _p(_i64(lo)), _p(_i64(n)), _p(c), _p(a),
+                                      _p(sp), _p(ce), _p(m), fill, _p(vout), _p(ha), _p(ia), _p(fa_)), "angles_field")
     return vout, ha, ia, fa_
 
 
 def pipeline(vol: np.ndarray, sigma: float, rho: float, center, axis, mask: Optional[np.ndarray] = None,
-             lo=None, n=None, truncate: float = 4.0, fill: float = float("nan")) -> dict:
-    """All per-voxel outputs over the box (lo, n): S, evals, v (oriented), ha, ia, fa."""
+             lo=None, n=None, truncate: float = 4.0, fill: float = float("nan"), spacing=None,
+             centres: Optional[np.ndarray] = None) -> dict:
+    """All per-voxel outputs over the box (lo, n): S, evals, v (oriented), ha, ia, fa.
+
+    ``spacing`` (x, y, z voxel size; sigma, rho, center and axis then in its
+    units) and ``centres`` (per-slice LV centre, [nz, 2] as (cx, cy)) select
+    the anisotropic form; S is then in physical units."""
     vol = np.ascontiguousarray(vol, dtype=np.uint16)
     lo, n = _box(vol, lo, n)
     shp = (int(n[2]), int(n[1]), int(n[0]))
@@ -225,7 +240,16 @@ def pipeline(vol: np.ndarray, sigma: float, rho: float, center, axis, mask: Opti
     m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     c = np.ascontiguousarray(np.asarray(center, dtype=np.float64))
     a = np.ascontiguousarray(np.asarray(axis, dtype=np.float64))
-    _check(_load().cto_pipeline(_p(vol), _p(_dims(vol)), _p(lo), _p(n), sigma, rho, truncate, _p(c), _p(a), _p(m),
-                                fill, _p(out["S"]), _p(out["evals"]), _p(out["v"]), _p(out["ha"]), _p(out["ia"]),
-                                _p(out["fa"])), "pipeline")
+    if spacing is None and centres is None:
+        _check(_load().cto_pipeline(_p(vol), _p(_dims(vol)), _p(lo), _p(n), sigma, rho, truncate, _p(c), _p(a),
+                                    _p(m), fill, _p(out["S"]), _p(out["evals"]), _p(out["v"]), _p(out["ha"]),
+                                    _p(out["ia"]), _p(out["fa"])), "pipeline")
+        return out
+    sp = np.ascontiguousarray(np.asarray((1.0, 1.0, 1.0) if spacing is None else spacing, dtype=np.float64))
+    ce = None if centres is None else np.ascontiguousarray(np.asarray(centres, dtype=np.float64).reshape(-1, 2))
+    if ce is not None and ce.shape[0] != vol.shape[0]:
+        raise ValueError("centres needs one (cx, cy) per z slice")
+    _check(_load().cto_pipeline3(_p(vol), _p(_dims(vol)), _p(lo), _p(n), sigma, rho, truncate, _p(sp), _p(c), _p(a),
+                                 _p(ce), _p(m), fill, _p(out["S"]), _p(out["evals"]), _p(out["v"]), _p(out["ha"]),
+                                 _p(out["ia"]), _p(out["fa"])), "pipeline")
     return out

@@ -15,8 +15,8 @@ MUTATIONS = {
     "transposed_product": ("static const int cb[6] = {0, 1, 2, 1, 2, 2};", "static const int cb[6] = {0, 1, 2, 2, 1, 2};"),
     "clamp_off_by_one": ("int64_t q = clampi(pa + k, 0, dims[axis] - 1)", "int64_t q = clampi(pa + k, 0, dims[axis] - 2)"),
     "dropped_outer_tap": ("for (int k = 1; k <= R; ++k) {", "for (int k = 1; k < R; ++k) {"),
-    "wrong_pass_axis": ("if ((rc = pass1d(t1, &bz, t2, &by, 1, w, Rr, 0, dims))) goto done;",
-                        "if ((rc = pass1d(t1, &bz, t2, &by, 1, w, Rr - 1, 0, dims))) goto done;"),
+    "wrong_pass_axis": ("if ((rc = pass1d(t1, &bz, t2, &by, 1, w[1], Rr[1], 0, dims))) goto done;",
+                        "if ((rc = pass1d(t1, &bz, t2, &by, 1, w[1], Rr[1] - 1, 0, dims))) goto done;"),
     "theta_cross_reversed": ("double et[3] = {ez[1] * er[2] - ez[2] * er[1],",
                              "double et[3] = {-ez[1] * er[2] + ez[2] * er[1],"),
     "ia_from_wrong_component": ("double s = vr > 1.0 ? 1.0 : (vr < -1.0 ? -1.0 : vr);",
