@@ -78,10 +78,10 @@ typedef int32_t ct_status;
                         bin 180/256 deg; masked / undefined voxels get code 0 */
 
 typedef struct ct_params {
-  double sigma;        /* noise scale of the gradient, voxels, > 0 */
-  double rho;          /* integration scale of the tensor smoothing, voxels, > 0 */
+  double sigma;        /* noise scale of the gradient, > 0 (units of `spacing`) */
+  double rho;          /* integration scale of the tensor smoothing, > 0 (units of `spacing`) */
   double truncate;     /* radius factor; 0 selects 4.0 */
-  double lv_center[3]; /* left-ventricle centre (x, y, z), global voxel units, finite */
+  double lv_center[3]; /* left-ventricle centre (x, y, z) in the units of `spacing`, finite */
   double lv_axis[3];   /* left-ventricle axis (x, y, z); need not be unit; not zero */
   int32_t precision;   /* CT_PREC_* */
   int32_t vec_type;    /* CT_OUT_F32 or CT_OUT_F16 */
@@ -91,6 +91,20 @@ typedef struct ct_params {
                           the axis; NaN is the usual choice */
   int32_t flags;       /* reserved, must be 0 */
   int64_t chunk[3];    /* ct_run_chunks chunk size (x, y, z); 0 = whole extent */
+  /*
+   * Anisotropic voxels (the paper is silent; the textbook reading): voxel size
+   * (x, y, z), each >= 0 and finite, 0 meaning 1 (all zero = voxel units).
+   * Scale s along axis a is s / spacing[a] voxels (its own radius), the
+   * gradient and so S are in physical units (component a divided by
+   * spacing[a]) and positions are (x spacing[0], y spacing[1], z spacing[2]).
+   */
+  double spacing[3];
+  /*
+   * Optional LV centreline (NULL = the fixed lv_center): vol_dims[2] pairs
+   * (cx, cy), slice z's centre being (cx, cy, z spacing[2]); copied by
+   * ct_plan_create.  Frames then vary along the axis.
+   */
+  const double* lv_centres;
 } ct_params;
 
 typedef struct ct_plan_s* ct_plan;
@@ -108,9 +122,11 @@ ct_status ct_plan_destroy(ct_plan plan);
  * Stage: structure tensor (Figure 1b).  d_vol holds the input box (in_lo,
  * in_n) of the plan's volume as a dense uint16 [in_n.z][in_n.y][in_n.x]
  * array.  d_S receives the 6 FP32 tensor planes over the output box (out_lo,
- * out_n).  The output box grown by R(sigma) + R(rho) on every side and then
- * clipped to the volume must lie inside the input box (that is the halo a
- * padded chunk needs); CT_ERR_INVALID otherwise.
+ * out_n).  The output box grown by R(sigma) + R(rho) on every side (per axis
+ * with anisotropic voxels: the radii of sigma / spacing[a] and rho /
+ * spacing[a]) and then clipped to the volume must lie inside the input box
+ * (that is the halo a padded chunk needs); CT_ERR_INVALID otherwise.  S is in
+ * the units of the spacing (voxel units by default).
  */
 ct_status ct_structure_tensor(ct_plan plan, const uint16_t* d_vol, const int64_t in_lo[3], const int64_t in_n[3],
                               const int64_t out_lo[3], const int64_t out_n[3], float* d_S, void* stream);

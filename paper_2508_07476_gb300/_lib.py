@@ -39,7 +39,7 @@ class ct_params(ctypes.Structure):
         ("lv_center", _D3), ("lv_axis", _D3),
         ("precision", ctypes.c_int32), ("vec_type", ctypes.c_int32), ("angle_type", ctypes.c_int32),
         ("fa_type", ctypes.c_int32), ("fill_value", ctypes.c_float), ("flags", ctypes.c_int32),
-        ("chunk", _I64x3),
+        ("chunk", _I64x3), ("spacing", _D3), ("lv_centres", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -175,8 +175,17 @@ def _stream(stream) -> Optional[int]:
 
 def make_params(sigma: float, rho: float, lv_center, lv_axis, precision: int = CT_PREC_FP32,
                 vec_type: int = CT_OUT_F32, angle_type: int = CT_OUT_F32, fa_type: int = CT_OUT_F32,
-                fill_value: float = math.nan, truncate: float = 4.0, chunk=(0, 0, 0), flags: int = 0) -> ct_params:
+                fill_value: float = math.nan, truncate: float = 4.0, chunk=(0, 0, 0), flags: int = 0,
+                spacing=(0.0, 0.0, 0.0), lv_centres=None) -> ct_params:
+    """ct_params; ``lv_centres`` (a sequence of (cx, cy) per z slice) is kept alive on the
+    returned object until the plan has copied it."""
     p = ct_params()
+    p.spacing = _D3(*spacing)
+    if lv_centres is not None:
+        flat = [float(v) for pair in lv_centres for v in pair]
+        buf = (ctypes.c_double * len(flat))(*flat)
+        p._centres_keep = buf
+        p.lv_centres = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))
     p.sigma, p.rho, p.truncate = sigma, rho, truncate
     p.lv_center = _D3(*lv_center)
     p.lv_axis = _D3(*lv_axis)

@@ -94,6 +94,18 @@ Box grow_clip(const Box& b, int r, const int dims[3]) {
   return o;
 }
 
+// grown by r[a] along axis a (anisotropic voxels give each axis its radius)
+Box grow_clip3(const Box& b, const int r[3], const int dims[3]) {
+  Box o;
+  for (int a = 0; a < 3; ++a) {
+    int lo = std::max(0, b.lo[a] - r[a]);
+    int hi = std::min(dims[a] - 1, b.lo[a] + b.n[a] - 1 + r[a]);
+    o.lo[a] = lo;
+    o.n[a] = hi - lo + 1;
+  }
+  return o;
+}
+
 bool inside(const Box& outer, const Box& inner) {
   for (int a = 0; a < 3; ++a)
     if (inner.lo[a] < outer.lo[a] || inner.lo[a] + inner.n[a] > outer.lo[a] + outer.n[a]) return false;
@@ -106,21 +118,33 @@ bool valid_box(const int64_t lo[3], const int64_t n[3], const int dims[3]) {
   return true;
 }
 
-Frame make_frame(const double c[3], const double a[3]) {
+// Voxel size with 0 meaning 1.
+void spacing_of(const ct_params& p, double sp[3]) {
+  for (int a = 0; a < 3; ++a) sp[a] = p.spacing[a] > 0.0 ? p.spacing[a] : 1.0;
+}
+
+Frame make_frame(const double c[3], const double a[3], const double sp[3], const float* centres) {
   Frame F;
   double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
   for (int k = 0; k < 3; ++k) {
     F.c[k] = (float)c[k];
     F.a[k] = (float)(a[k] / an);
+    F.sp[k] = (float)sp[k];
   }
+  F.centres = centres;
   return F;
 }
 
+// Per-axis scales: s / spacing[a] voxels along axis a.  The kernels of a pass
+// are instantiated at the largest radius over the axes they filter; shorter
+// tap sets are zero-padded to it.
 struct Scale {
   double sigma, rho;
-  int rs, rr;    // radii
-  int rks, rkr;  // instantiated radii
-  Taps ts, tr;
+  int rs[3], rr[3];  // radii per axis
+  int rks, rkr;      // instantiated radii
+  Taps ts[3], tr[3];
+  float ss[6];       // 1 / (spacing_a spacing_b) per tensor component: S in physical units
+  int halo[3];       // rs + rr per axis
 };
 
 }  // namespace
@@ -128,6 +152,8 @@ struct Scale {
 struct ct_plan_s {
   ct_params p;
   int dims[3];
+  double sp[3] = {1.0, 1.0, 1.0};  // voxel size (0 in the params means 1)
+  float* d_centres = nullptr;      // LV centreline on the device (dims[2] pairs), or none
   int device = 0;
   // Scratch slots: slots 0 and 1 serve the two streams of host streaming;
   // batches of device items use up to kSlots streams, one slot each.
@@ -196,24 +222,38 @@ ct_status check_params(const ct_params* p) {
   if (p->flags != 0) return fail(CT_ERR_INVALID, "flags must be 0");
   for (int k = 0; k < 3; ++k)
     if (p->chunk[k] < 0) return fail(CT_ERR_INVALID, "chunk sizes must be >= 0");
+  for (int k = 0; k < 3; ++k)
+    if (!(p->spacing[k] >= 0.0) || !std::isfinite(p->spacing[k]))
+      return fail(CT_ERR_INVALID, "spacing must be finite and >= 0 (0 = 1)");
   return CT_OK;
 }
 
 double trunc_of(const ct_params& p) { return p.truncate > 0.0 ? p.truncate : 4.0; }
 
 ct_status make_scale(const ct_params& p, double sigma, double rho, Scale* s) {
-  double tr = trunc_of(p);
+  double tr = trunc_of(p), sp[3];
+  spacing_of(p, sp);
   s->sigma = sigma;
   s->rho = rho;
-  s->rs = radius_of(sigma, tr);
-  s->rr = radius_of(rho, tr);
-  if (s->rs < 1 || s->rr < 1) return fail(CT_ERR_INVALID, "truncate * scale must give a radius >= 1");
-  s->rks = sigma_kernel_radius(s->rs);
-  s->rkr = rho_kernel_radius(s->rr);
-  if (s->rks < 0) return fail(CT_ERR_UNSUPPORTED, "sigma radius %d exceeds 12", s->rs);
-  if (s->rkr < 0) return fail(CT_ERR_UNSUPPORTED, "rho radius %d exceeds 36", s->rr);
-  s->ts = make_taps(sigma, tr, s->rks);
-  s->tr = make_taps(rho, tr, s->rkr);
+  int ms = 0, mr = 0;
+  for (int a = 0; a < 3; ++a) {
+    s->rs[a] = radius_of(sigma / sp[a], tr);
+    s->rr[a] = radius_of(rho / sp[a], tr);
+    if (s->rs[a] < 1 || s->rr[a] < 1) return fail(CT_ERR_INVALID, "truncate * scale must give a radius >= 1");
+    ms = std::max(ms, s->rs[a]);
+    mr = std::max(mr, s->rr[a]);
+    s->halo[a] = s->rs[a] + s->rr[a];
+  }
+  s->rks = sigma_kernel_radius(ms);
+  s->rkr = rho_kernel_radius(mr);
+  if (s->rks < 0) return fail(CT_ERR_UNSUPPORTED, "sigma radius %d exceeds 12", ms);
+  if (s->rkr < 0) return fail(CT_ERR_UNSUPPORTED, "rho radius %d exceeds 36", mr);
+  for (int a = 0; a < 3; ++a) {
+    s->ts[a] = make_taps(sigma / sp[a], tr, s->rks);
+    s->tr[a] = make_taps(rho / sp[a], tr, s->rkr);
+  }
+  static const int ca[6] = {0, 1, 2, 0, 0, 1}, cb[6] = {0, 1, 2, 1, 2, 2};
+  for (int k = 0; k < 6; ++k) s->ss[k] = (float)(1.0 / (sp[ca[k]] * sp[cb[k]]));
   return CT_OK;
 }
 
@@ -323,7 +363,7 @@ Fallback fallback_of(ct_plan P, int slot) {
 // fused, the first otherwise).  vol covers vb.
 ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb, const Box& ob,
                     int slot, bool mixed, cudaStream_t st, float** Sxy, Box* Bxy_out) {
-  Box G = grow_clip(ob, sc.rr, dims);
+  Box G = grow_clip3(ob, sc.rr, dims);
   Box Bx = G, Bxy = G;
   Bx.lo[0] = ob.lo[0];
   Bx.n[0] = ob.n[0];
@@ -339,18 +379,22 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
   float* A = P->buf[slot][0];
   float* B = P->buf[slot][1];
   if (P->split_grad) {
-    CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts, sc.rks, st), "gradient x/y kernel launch");
-    CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts, sc.rks, mixed, st), "gradient z kernel launch");
+    CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts[0], sc.ts[1], sc.rks, st),
+              "gradient x/y kernel launch");
+    CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts[2], sc.ss, sc.rks, mixed, st),
+              "gradient z kernel launch");
   } else {
-    CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts, sc.rks, mixed, st),
+    if (sc.rs[0] != sc.rs[1] || sc.rs[0] != sc.rs[2] || sc.ss[0] != 1.f || sc.ss[1] != 1.f || sc.ss[2] != 1.f)
+      return fail(CT_ERR_UNSUPPORTED, "the one-kernel gradient takes unit voxels only (CT_TUNE_SPLIT_GRAD=0)");
+    CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts[0], sc.rks, mixed, st),
               "gradient kernel launch");
   }
   if (P->fuse_xy) {
-    CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr, sc.rkr, st), "rho xy kernel launch");
+    CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr[0], sc.tr[1], sc.rkr, st), "rho xy kernel launch");
     *Sxy = B;
   } else {
-    CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr, sc.rkr, st), "rho x kernel launch");
-    CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr, sc.rkr, P->stream_block, st),
+    CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr[0], sc.rkr, st), "rho x kernel launch");
+    CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
               "rho y kernel launch");
     *Sxy = A;
   }
@@ -365,7 +409,7 @@ ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uin
   Box Bxy;
   ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
   if (rc) return rc;
-  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S_out, ob, 2, sc.tr, sc.rkr, P->stream_block, st),
+  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S_out, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
             "rho z kernel launch");
   return CT_OK;
 }
@@ -384,7 +428,7 @@ ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint
   if (rc) return rc;
   if (!P->fuse_z_eig) {  // split: z pass into the free buffer, then the eigen stage
     float* S = Sxy == P->buf[slot][0] ? P->buf[slot][1] : P->buf[slot][0];
-    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr, sc.rkr, P->stream_block, st),
+    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
               "rho z kernel launch");
     return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
   }
@@ -392,7 +436,7 @@ ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint
   FallbackS fb = fused_fallback_of(P, slot);
   CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
   CT_LAUNCH(P, st, "rho_z_eig",
-            launch_rho_z_eig(Sxy, Bxy, dims, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, sc.tr, sc.rkr, st),
+            launch_rho_z_eig(Sxy, Bxy, dims, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, sc.tr[2], sc.rkr, st),
             "rho z + eigen kernel launch");
   CT_LAUNCH(P, st, "eig_resolve", launch_fallback_s(ob, F, P->p.fill_value, o, mixed, fb, fb.cap, st),
             "re-solve kernel launch");
@@ -443,7 +487,26 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   ct_plan P = new (std::nothrow) ct_plan_s();
   if (!P) return fail(CT_ERR_OOM, "plan allocation failed");
   P->p = *params;
+  P->p.lv_centres = nullptr;  // the caller's array is copied below, not kept
   for (int k = 0; k < 3; ++k) P->dims[k] = (int)vol_dims[k];
+  spacing_of(*params, P->sp);
+  if (params->lv_centres) {
+    std::vector<float> c((size_t)2 * P->dims[2]);
+    for (size_t i = 0; i < c.size(); ++i) {
+      if (!std::isfinite(params->lv_centres[i])) {
+        delete P;
+        return fail(CT_ERR_INVALID, "lv_centres must be finite");
+      }
+      c[i] = (float)params->lv_centres[i];
+    }
+    cudaError_t e = cudaMalloc(&P->d_centres, sizeof(float) * c.size());
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_centres, c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      if (P->d_centres) cudaFree(P->d_centres);
+      delete P;
+      return cuda_fail(e, "centreline copy");
+    }
+  }
   std::memset(&P->stats, 0, sizeof P->stats);
   if (const char* e = std::getenv("CT_TUNE_STREAM_BLOCK")) P->stream_block = std::atoi(e) == 8 ? 8 : 16;
   if (const char* e = std::getenv("CT_TUNE_FUSE_Z_EIG")) P->fuse_z_eig = std::atoi(e) != 0;
@@ -468,6 +531,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
 ct_status ct_plan_destroy(ct_plan P) {
   if (!P) return CT_OK;
   cudaDeviceSynchronize();
+  if (P->d_centres) cudaFree(P->d_centres);
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->gst) cudaStreamDestroy(P->gst);
@@ -510,9 +574,9 @@ ct_status ct_structure_tensor(ct_plan P, const uint16_t* d_vol, const int64_t in
   ct_status rc = make_scale(P->p, P->p.sigma, P->p.rho, &sc);
   if (rc) return rc;
   Box ib = make_box(in_lo, in_n), ob = make_box(out_lo, out_n);
-  if (!inside(ib, grow_clip(ob, sc.rs + sc.rr, P->dims)))
-    return fail(CT_ERR_INVALID, "input box must contain the output box grown by R(sigma)+R(rho) = %d (clipped)",
-                sc.rs + sc.rr);
+  if (!inside(ib, grow_clip3(ob, sc.halo, P->dims)))
+    return fail(CT_ERR_INVALID, "input box must contain the output box grown by R(sigma)+R(rho) = (%d, %d, %d) (clipped)",
+                sc.halo[0], sc.halo[1], sc.halo[2]);
   rc = tensor_stages(P, sc, P->dims, d_vol, ib, ob, d_S, 0, P->p.precision == CT_PREC_MIXED,
                      (cudaStream_t)stream);
   if (rc) return rc;
@@ -547,7 +611,7 @@ ct_status ct_angles(ct_plan P, const float* d_evec, const float* d_evals, const 
   std::lock_guard<std::mutex> lk(P->mu);
   Box ob = make_box(out_lo, out_n);
   EigOut o{d_vec, d_ha, d_ia, d_fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
-  Frame F = make_frame(P->p.lv_center, P->p.lv_axis);
+  Frame F = make_frame(P->p.lv_center, P->p.lv_axis, P->sp, P->d_centres);
   cudaStream_t st = (cudaStream_t)stream;
   CT_LAUNCH(P, st, "angles_only", launch_angles_only(d_evec, d_evals, ob, d_mask, F, P->p.fill_value, o, st),
             "angles kernel launch");
@@ -624,7 +688,9 @@ ct_status item_ctx(ct_plan P, const ct_item& it, ItemCtx* c) {
   for (int k = 0; k < 3; ++k)
     if (!std::isfinite(it.lv_center[k]) || !std::isfinite(it.lv_axis[k]))
       return fail(CT_ERR_INVALID, "item frame must be finite");
-  c->F = own_axis ? make_frame(it.lv_center, it.lv_axis) : make_frame(P->p.lv_center, P->p.lv_axis);
+  // an item with its own frame has no centreline (the plan's belongs to the plan's volume)
+  c->F = own_axis ? make_frame(it.lv_center, it.lv_axis, P->sp, nullptr)
+                  : make_frame(P->p.lv_center, P->p.lv_axis, P->sp, P->d_centres);
   return CT_OK;
 }
 
@@ -705,7 +771,7 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
   int64_t total = 0;
   for (int i = 0; i < n; ++i) {
     const int k = i % K;
-    gmax[k] = std::max(gmax[k], box_vox(grow_clip(ctx[i].whole, ctx[i].sc.rr, ctx[i].dims)));
+    gmax[k] = std::max(gmax[k], box_vox(grow_clip3(ctx[i].whole, ctx[i].sc.rr, ctx[i].dims)));
     omax[k] = std::max(omax[k], box_vox(ctx[i].whole));
     total += box_vox(ctx[i].whole);
   }
@@ -793,13 +859,12 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
   for (int k = 0; k < 4; ++k)
     if (op.ptr[k]) out_bytes_per_vox += op.esz[k] * op.planes[k];
   std::vector<Box> chunks = chunk_grid(c.dims, P->p.chunk);
-  int halo = c.sc.rs + c.sc.rr;
   int64_t nwhole = box_vox(c.whole);
   for (size_t ci = 0; ci < chunks.size(); ++ci) {
     int slot = (int)(ci & 1);
     cudaStream_t st = P->st[slot];
     const Box& ob = chunks[ci];
-    Box ib = grow_clip(ob, halo, c.dims);
+    Box ib = grow_clip3(ob, c.sc.halo, c.dims);
     int64_t niv = box_vox(ib), nov = box_vox(ob);
     size_t in_bytes = (sizeof(uint16_t) * niv + 255) / 256 * 256;
     size_t mask_bytes = it.mask ? (size_t)nov : 0;
@@ -878,10 +943,10 @@ ct_status ct_run_box(ct_plan P, const uint16_t* d_vol, const int64_t in_lo[3], c
   ct_status rc = make_scale(P->p, P->p.sigma, P->p.rho, &sc);
   if (rc) return rc;
   Box ib = make_box(in_lo, in_n), ob = make_box(out_lo, out_n);
-  if (!inside(ib, grow_clip(ob, sc.rs + sc.rr, P->dims)))
-    return fail(CT_ERR_INVALID, "input box must contain the output box grown by R(sigma)+R(rho) = %d (clipped)",
-                sc.rs + sc.rr);
-  Frame F = make_frame(P->p.lv_center, P->p.lv_axis);
+  if (!inside(ib, grow_clip3(ob, sc.halo, P->dims)))
+    return fail(CT_ERR_INVALID, "input box must contain the output box grown by R(sigma)+R(rho) = (%d, %d, %d) (clipped)",
+                sc.halo[0], sc.halo[1], sc.halo[2]);
+  Frame F = make_frame(P->p.lv_center, P->p.lv_axis, P->sp, P->d_centres);
   EigOut o{d_vec, d_ha, d_ia, d_fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
   rc = fused_stages(P, sc, P->dims, d_vol, ib, ob, d_mask, ob, F, o, 0, P->p.precision == CT_PREC_MIXED,
                     (cudaStream_t)stream);

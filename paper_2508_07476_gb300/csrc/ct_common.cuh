@@ -271,13 +271,28 @@ __device__ __forceinline__ float fa_of(const float l[3]) {
 // Cylindrical left-ventricle frame (unit axis, centre), per launch.
 struct Frame {
   float c[3];
-  float a[3];  // unit
+  float a[3];                      // unit
+  float sp[3];                     // voxel size: position = (x sp0, y sp1, z sp2)
+  const float* centres = nullptr;  // per-slice LV centre (cx, cy) on the device, or none
 };
 
-// HA / IA (degrees) of v at voxel (x, y, z); orients v so that v.e_t > 0.
+// HA / IA (degrees) of v at voxel (x, y, z) (global indices; the frame is in
+// the units of the voxel size); orients v so that v.e_t > 0.
 // Returns false on the axis, where the frame does not exist.
+// PLAIN: unit voxels and a fixed centre, known at compile time (the same
+// arithmetic as the general form with spacing 1, without its work).
+template <bool PLAIN = false>
 __device__ __forceinline__ bool ha_ia(const Frame& F, int x, int y, int z, float v[3], float& ha, float& ia) {
-  float dx = (float)x - F.c[0], dy = (float)y - F.c[1], dz = (float)z - F.c[2];
+  const float px = PLAIN ? (float)x : (float)x * F.sp[0];
+  const float py = PLAIN ? (float)y : (float)y * F.sp[1];
+  const float pz = PLAIN ? (float)z : (float)z * F.sp[2];
+  float cx = F.c[0], cy = F.c[1], cz = F.c[2];
+  if (!PLAIN && F.centres) {  // this slice's centre on the centreline
+    cx = __ldg(F.centres + 2 * z);
+    cy = __ldg(F.centres + 2 * z + 1);
+    cz = pz;
+  }
+  float dx = px - cx, dy = py - cy, dz = pz - cz;
   float h = dx * F.a[0] + dy * F.a[1] + dz * F.a[2];
   float rx = dx - h * F.a[0], ry = dy - h * F.a[1], rz = dz - h * F.a[2];
   float rr = rx * rx + ry * ry + rz * rz;

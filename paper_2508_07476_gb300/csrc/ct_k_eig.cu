@@ -47,7 +47,7 @@ __device__ __forceinline__ void resolve(const Sym3<float>& s, bool mixed, float 
 // Outputs of one voxel: oriented vector, HA, IA, FA (or fill outside the mask).
 // VT / AT / FT: compile-time encodings of the vector / angle / FA outputs, or
 // -1 to take them from `o` at run time.
-template <int VT = -1, int AT = -1, int FT = -1, typename IT = int64_t>
+template <int VT = -1, int AT = -1, int FT = -1, typename IT = int64_t, bool PLAIN = false>
 __device__ __forceinline__ void write_voxel(const EigOut& o, IT oi, bool inside, const Frame& F, int x, int y,
                                             int z, const float l[3], float v[3], float fill) {
   const IT n = (IT)box_vox(o.ab);
@@ -63,7 +63,7 @@ __device__ __forceinline__ void write_voxel(const EigOut& o, IT oi, bool inside,
     return;
   }
   float ha, ia;
-  bool framed = ha_ia(F, x, y, z, v, ha, ia);
+  bool framed = ha_ia<PLAIN>(F, x, y, z, v, ha, ia);
   if (!framed) orient_largest(v);
   if (o.vec) {
     store_val<VT, IT>(o.vec, oi, o.vec_t, v[0]);
@@ -113,7 +113,7 @@ __device__ __forceinline__ int box_index32(const Box& b, int x, int y, int z) {
   return ((z - b.lo[2]) * b.n[1] + (y - b.lo[1])) * b.n[0] + (x - b.lo[0]);
 }
 
-template <int VT, int AT, int FT>
+template <int VT, int AT, int FT, bool PLAIN>
 __global__ void __launch_bounds__(256, CT_EIG_MINB)
     k_eig_angles32(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
                    float fill, EigOut o, bool mixed, Fallback fb) {
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
     if (!eig_closed<float>(s, l, v))
       push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
   }
-  write_voxel<VT, AT, FT, int>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
+  write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
 
 __global__ void __launch_bounds__(128)
@@ -176,14 +176,23 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
   if (ob.n[1] <= 65535 && ob.n[2] <= 65535 && 6 * box_vox(sb) <= lim && 3 * box_vox(o.ab) <= lim &&
       box_vox(mb) <= lim) {
     dim3 g3((ob.n[0] + nt - 1) / nt, ob.n[1], ob.n[2]);
-    if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32)
-      k_eig_angles32<0, 0, 0><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
-    else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16)
-      k_eig_angles32<1, 1, 1><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
-    else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16)
-      k_eig_angles32<-1, 2, 1><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
-    else
-      k_eig_angles32<-1, -1, -1><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    // unit voxels and a fixed centre take the plain frame
+    const bool plain = F.sp[0] == 1.f && F.sp[1] == 1.f && F.sp[2] == 1.f && F.centres == nullptr;
+    if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32) {
+      if (plain)
+        k_eig_angles32<0, 0, 0, true><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+      else
+        k_eig_angles32<0, 0, 0, false><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    } else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16) {
+      if (plain)
+        k_eig_angles32<1, 1, 1, true><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+      else
+        k_eig_angles32<1, 1, 1, false><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    } else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16) {
+      k_eig_angles32<-1, 2, 1, false><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    } else {
+      k_eig_angles32<-1, -1, -1, false><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+    }
     return cudaGetLastError();
   }
   // the encodings of the common configurations are compiled in; others are read at run time

@@ -51,7 +51,7 @@ __device__ __forceinline__ void u16x8_to_f32(const uint4 q, float* f) {
 template <int RS, int XT>
 __global__ void __launch_bounds__(XT, 512 / XT)
     k_grad_xy(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, float* __restrict__ F, Box ab, int seg,
-              const Taps taps) {
+              const Taps tx, const Taps ty) {
   using G = GXYGeom<RS, XT>;
   constexpr int TB = G::TB;
   extern __shared__ __align__(16) float gsm[];
@@ -144,12 +144,12 @@ __global__ void __launch_bounds__(XT, 512 / XT)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int m = G::O4 + i + RS;  // centre of output i in v
-        sw[i] = taps.w[RS] * v[m];
+        sw[i] = tx.w[RS] * v[m];
         sc[i] = 0.f;
 #pragma unroll
         for (int k = 1; k <= RS; ++k) {
-          sw[i] = fmaf(taps.w[RS + k], v[m + k] + v[m - k], sw[i]);
-          sc[i] = fmaf(taps.c[RS + k], v[m + k] - v[m - k], sc[i]);
+          sw[i] = fmaf(tx.w[RS + k], v[m + k] + v[m - k], sw[i]);
+          sc[i] = fmaf(tx.c[RS + k], v[m + k] - v[m - k], sc[i]);
         }
       }
       float4* dw = reinterpret_cast<float4*>(sx + row * G::SXS + 8 * xseg);
@@ -173,12 +173,12 @@ __global__ void __launch_bounds__(XT, 512 / XT)
 #pragma unroll
       for (int i = 0; i < TB; ++i) {
         const int m = i + RS;
-        float f0 = taps.w[RS] * wc[m], f2 = taps.w[RS] * ww[m], f1 = 0.f;
+        float f0 = ty.w[RS] * wc[m], f2 = ty.w[RS] * ww[m], f1 = 0.f;
 #pragma unroll
         for (int k = 1; k <= RS; ++k) {
-          f0 = fmaf(taps.w[RS + k], wc[m + k] + wc[m - k], f0);
-          f1 = fmaf(taps.c[RS + k], ww[m + k] - ww[m - k], f1);
-          f2 = fmaf(taps.w[RS + k], ww[m + k] + ww[m - k], f2);
+          f0 = fmaf(ty.w[RS + k], wc[m + k] + wc[m - k], f0);
+          f1 = fmaf(ty.c[RS + k], ww[m + k] - ww[m - k], f1);
+          f2 = fmaf(ty.w[RS + k], ww[m + k] + ww[m - k], f2);
         }
         if (xok && m0 + i < L) {
           float* o = obase + (int64_t)(m0 + i) * ostride;
@@ -198,6 +198,12 @@ __global__ void __launch_bounds__(XT, 512 / XT)
 // and register windows are indexed statically because the step loop is
 // unrolled by P.
 constexpr int kGzThreads = 256;
+
+// Scale of each product g_a g_b (1 / (spacing_a spacing_b)); `unit` when all are 1.
+struct ProdScale {
+  float s[6];
+  int unit;
+};
 #ifndef CT_GZ_AHEAD
 #define CT_GZ_AHEAD 8
 #endif
@@ -212,7 +218,8 @@ constexpr float kGzHalfScale = 1.0f / 256.0f;
 
 template <int RS, bool MIXED>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
-    k_grad_z(const float* __restrict__ F, Box ab, float* __restrict__ J, Box ob, int seg, const Taps taps) {
+    k_grad_z(const float* __restrict__ F, Box ab, float* __restrict__ J, Box ob, int seg, const Taps taps,
+             const ProdScale ps) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
   extern __shared__ __align__(16) float gz_ring[];  // [P][3][kGzThreads]
@@ -282,12 +289,21 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
         }
         if (ok) {
           float* o = obase + (int64_t)(s - 2 * RS) * ostride;
-          o[0] = gx * gx;
-          o[nob] = gy * gy;
-          o[2 * nob] = gz * gz;
-          o[3 * nob] = gx * gy;
-          o[4 * nob] = gx * gz;
-          o[5 * nob] = gy * gz;
+          if (ps.unit) {
+            o[0] = gx * gx;
+            o[nob] = gy * gy;
+            o[2 * nob] = gz * gz;
+            o[3 * nob] = gx * gy;
+            o[4 * nob] = gx * gz;
+            o[5 * nob] = gy * gz;
+          } else {  // physical units: component ab divided by spacing_a spacing_b
+            o[0] = (gx * gx) * ps.s[0];
+            o[nob] = (gy * gy) * ps.s[1];
+            o[2 * nob] = (gz * gz) * ps.s[2];
+            o[3 * nob] = (gx * gy) * ps.s[3];
+            o[4 * nob] = (gx * gz) * ps.s[4];
+            o[5 * nob] = (gy * gz) * ps.s[5];
+          }
         }
       }
     }
@@ -341,7 +357,7 @@ Box grad_partial_box(const Box& ob, const Box& vb, int rs, int dimz) {
 
 template <int RS, int XT>
 static cudaError_t launch_gxy_t(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
-                                const Taps& taps, cudaStream_t st) {
+                                const Taps& tx, const Taps& ty, cudaStream_t st) {
   using G = GXYGeom<RS, XT>;
   if (ab.n[2] > 65535) return cudaErrorInvalidValue;
   const int64_t ctas = (int64_t)((ab.n[0] + XT - 1) / XT) * ab.n[2];
@@ -349,21 +365,21 @@ static cudaError_t launch_gxy_t(const uint16_t* vol, const Box& vb, const int di
   while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ab.n[1] / (nseg * 2) >= 8 * G::TB) nseg *= 2;
   const int seg = (ab.n[1] + nseg - 1) / nseg;
   dim3 grid((ab.n[0] + XT - 1) / XT, ab.n[2], (ab.n[1] + seg - 1) / seg);
-  k_grad_xy<RS, XT><<<grid, XT, G::SMEM, st>>>(vol, vb, dims[0], dims[1], F, ab, seg, taps);
+  k_grad_xy<RS, XT><<<grid, XT, G::SMEM, st>>>(vol, vb, dims[0], dims[1], F, ab, seg, tx, ty);
   return cudaGetLastError();
 }
 
 template <int RS>
 static cudaError_t launch_gxy_r(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
-                                const Taps& taps, cudaStream_t st) {
+                                const Taps& tx, const Taps& ty, cudaStream_t st) {
   const int w256 = (ab.n[0] + 255) / 256 * 256 - ab.n[0], w128 = (ab.n[0] + 127) / 128 * 128 - ab.n[0];
-  return w128 < w256 ? launch_gxy_t<RS, 128>(vol, vb, dims, F, ab, taps, st)
-                     : launch_gxy_t<RS, 256>(vol, vb, dims, F, ab, taps, st);
+  return w128 < w256 ? launch_gxy_t<RS, 128>(vol, vb, dims, F, ab, tx, ty, st)
+                     : launch_gxy_t<RS, 256>(vol, vb, dims, F, ab, tx, ty, st);
 }
 
 template <int RS>
-static cudaError_t launch_gz_r(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps, bool mixed,
-                               cudaStream_t st) {
+static cudaError_t launch_gz_r(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps,
+                               const ProdScale& ps, bool mixed, cudaStream_t st) {
   // warps along x: the widest that leaves the fewest idle columns
   int wx = 1;
   for (int w = 2; w <= kGzThreads / 32; w *= 2) {
@@ -379,38 +395,44 @@ static cudaError_t launch_gz_r(const float* F, const Box& ab, float* J, const Bo
   dim3 grid((ob.n[0] + block.x - 1) / block.x, (ob.n[1] + block.y - 1) / block.y, (ob.n[2] + seg - 1) / seg);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   if (mixed)
-    k_grad_z<RS, true><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps);
+    k_grad_z<RS, true><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
   else
-    k_grad_z<RS, false><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps);
+    k_grad_z<RS, false><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
-                           const Taps& taps, int rk, cudaStream_t st) {
+                           const Taps& tx, const Taps& ty, int rk, cudaStream_t st) {
   if (box_vox(ab) == 0) return cudaSuccess;
   if (box_vox(ab) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   switch (rk) {
-    case 2: return launch_gxy_r<2>(vol, vb, dims, F, ab, taps, st);
-    case 3: return launch_gxy_r<3>(vol, vb, dims, F, ab, taps, st);
-    case 4: return launch_gxy_r<4>(vol, vb, dims, F, ab, taps, st);
-    case 6: return launch_gxy_r<6>(vol, vb, dims, F, ab, taps, st);
-    case 8: return launch_gxy_r<8>(vol, vb, dims, F, ab, taps, st);
-    case 12: return launch_gxy_r<12>(vol, vb, dims, F, ab, taps, st);
+    case 2: return launch_gxy_r<2>(vol, vb, dims, F, ab, tx, ty, st);
+    case 3: return launch_gxy_r<3>(vol, vb, dims, F, ab, tx, ty, st);
+    case 4: return launch_gxy_r<4>(vol, vb, dims, F, ab, tx, ty, st);
+    case 6: return launch_gxy_r<6>(vol, vb, dims, F, ab, tx, ty, st);
+    case 8: return launch_gxy_r<8>(vol, vb, dims, F, ab, tx, ty, st);
+    case 12: return launch_gxy_r<12>(vol, vb, dims, F, ab, tx, ty, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps, int rk, bool mixed,
-                          cudaStream_t st) {
+cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& tz,
+                          const float scale[6], int rk, bool mixed, cudaStream_t st) {
   if (box_vox(ob) == 0) return cudaSuccess;
   if (box_vox(ab) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  ProdScale ps;
+  ps.unit = 1;
+  for (int k = 0; k < 6; ++k) {
+    ps.s[k] = scale[k];
+    ps.unit = ps.unit && scale[k] == 1.f;
+  }
   switch (rk) {
-    case 2: return launch_gz_r<2>(F, ab, J, ob, taps, mixed, st);
-    case 3: return launch_gz_r<3>(F, ab, J, ob, taps, mixed, st);
-    case 4: return launch_gz_r<4>(F, ab, J, ob, taps, mixed, st);
-    case 6: return launch_gz_r<6>(F, ab, J, ob, taps, mixed, st);
-    case 8: return launch_gz_r<8>(F, ab, J, ob, taps, mixed, st);
-    case 12: return launch_gz_r<12>(F, ab, J, ob, taps, mixed, st);
+    case 2: return launch_gz_r<2>(F, ab, J, ob, tz, ps, mixed, st);
+    case 3: return launch_gz_r<3>(F, ab, J, ob, tz, ps, mixed, st);
+    case 4: return launch_gz_r<4>(F, ab, J, ob, tz, ps, mixed, st);
+    case 6: return launch_gz_r<6>(F, ab, J, ob, tz, ps, mixed, st);
+    case 8: return launch_gz_r<8>(F, ab, J, ob, tz, ps, mixed, st);
+    case 12: return launch_gz_r<12>(F, ab, J, ob, tz, ps, mixed, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -9,6 +9,8 @@
 // appends its own column's kTB values to a register window of kTB + 2R rows
 // that applies the y pass.  Shared row strides are padded so that the eight
 // lanes of a 16-byte access phase hit distinct banks.
+#include <cstring>
+
 #include "ct_common.cuh"
 #include "ct_launch.h"
 
@@ -48,13 +50,14 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
 }
 
-template <int RR, int XT>
+template <int RR, int XT, bool SAMEXY>
 __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
     k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
-             const Taps taps) {
+             const Taps tx, const Taps ty) {
   using G = XYGeom<RR, XT>;
   constexpr int kTB = G::TB;
   constexpr int kXT = XT;
+  const Taps& TY = SAMEXY ? tx : ty;  // isotropic runs read one tap set
   extern __shared__ __align__(16) float smem[];
   float* stage = smem;                              // [kStages][kTB][XS]
   float* sx = smem + kStages * kTB * G::XS;         // [kTB][SXS]
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
           const int j = 4 * j4 + e;  // input index; contributes to outputs i with 0 <= j - i <= 2R
 #pragma unroll
           for (int i = 0; i < 8; ++i)
-            if (j - i >= 0 && j - i <= 2 * RR) acc[i] = fmaf(taps.w[j - i], vv[e], acc[i]);
+            if (j - i >= 0 && j - i <= 2 * RR) acc[i] = fmaf(tx.w[j - i], vv[e], acc[i]);
         }
       }
       float4* d = reinterpret_cast<float4*>(sx + row * G::SXS + xseg * 8);
@@ -170,19 +173,19 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
 #if CT_XY_CHAINS == 1
 #pragma unroll
       for (int i = 0; i < kTB; ++i) {
-        float a = taps.w[0] * win[i];
+        float a = TY.w[0] * win[i];
 #pragma unroll
-        for (int k = 1; k <= 2 * RR; ++k) a = fmaf(taps.w[k], win[i + k], a);
+        for (int k = 1; k <= 2 * RR; ++k) a = fmaf(TY.w[k], win[i + k], a);
         if (xok && m + i < L) obase[(m + i) * ostride] = a;
       }
 #elif CT_XY_CHAINS == 2
 #pragma unroll
       for (int i = 0; i < kTB; ++i) {
-        float a0 = taps.w[0] * win[i], a1 = taps.w[1] * win[i + 1];
+        float a0 = TY.w[0] * win[i], a1 = TY.w[1] * win[i + 1];
 #pragma unroll
         for (int k = 2; k <= 2 * RR; k += 2) {
-          a0 = fmaf(taps.w[k], win[i + k], a0);
-          if (k + 1 <= 2 * RR) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
+          a0 = fmaf(TY.w[k], win[i + k], a0);
+          if (k + 1 <= 2 * RR) a1 = fmaf(TY.w[k + 1], win[i + k + 1], a1);
         }
         if (xok && m + i < L) obase[(m + i) * ostride] = a0 + a1;
       }
@@ -192,10 +195,10 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
         for (int k = 0; k <= 2 * RR; k += 4) {
-          a0 = fmaf(taps.w[k], win[i + k], a0);
-          if (k + 1 <= 2 * RR) a1 = fmaf(taps.w[k + 1], win[i + k + 1], a1);
-          if (k + 2 <= 2 * RR) a2 = fmaf(taps.w[k + 2], win[i + k + 2], a2);
-          if (k + 3 <= 2 * RR) a3 = fmaf(taps.w[k + 3], win[i + k + 3], a3);
+          a0 = fmaf(TY.w[k], win[i + k], a0);
+          if (k + 1 <= 2 * RR) a1 = fmaf(TY.w[k + 1], win[i + k + 1], a1);
+          if (k + 2 <= 2 * RR) a2 = fmaf(TY.w[k + 2], win[i + k + 2], a2);
+          if (k + 3 <= 2 * RR) a3 = fmaf(TY.w[k + 3], win[i + k + 3], a3);
         }
         if (xok && m + i < L) obase[(m + i) * ostride] = (a0 + a1) + (a2 + a3);
       }
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
 
 template <int RR, int XT>
 static cudaError_t launch_xy_rt(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
-                                const Taps& taps, cudaStream_t st) {
+                                const Taps& tx, const Taps& ty, cudaStream_t st) {
   using G = XYGeom<RR, XT>;
   constexpr int kTB = G::TB;
   const size_t smem = sizeof(float) * (kStages * kTB * G::XS + kTB * G::SXS);
@@ -218,7 +221,10 @@ static cudaError_t launch_xy_rt(const float* in, const Box& ib, const int dims[3
   while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ob.n[1] / (nseg * 2) >= 8 * kTB) nseg *= 2;
   const int seg = (ob.n[1] + nseg - 1) / nseg;
   dim3 grid((ob.n[0] + XT - 1) / XT, (unsigned)rows, (ob.n[1] + seg - 1) / seg);
-  k_rho_xy<RR, XT><<<grid, XT, smem, st>>>(in, ib, dims[0], dims[1], out, ob, seg, taps);
+  if (std::memcmp(&tx, &ty, sizeof(Taps)) == 0)
+    k_rho_xy<RR, XT, true><<<grid, XT, smem, st>>>(in, ib, dims[0], dims[1], out, ob, seg, tx, ty);
+  else
+    k_rho_xy<RR, XT, false><<<grid, XT, smem, st>>>(in, ib, dims[0], dims[1], out, ob, seg, tx, ty);
   return cudaGetLastError();
 }
 
@@ -230,21 +236,26 @@ static bool narrow_xy(int n0) {
 
 template <int RR>
 static cudaError_t launch_xy_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
-                               const Taps& taps, cudaStream_t st) {
+                               const Taps& tx, const Taps& ty, cudaStream_t st) {
   if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  return narrow_xy(ob.n[0]) ? launch_xy_rt<RR, 128>(in, ib, dims, out, ob, taps, st)
-                            : launch_xy_rt<RR, 256>(in, ib, dims, out, ob, taps, st);
+  return narrow_xy(ob.n[0]) ? launch_xy_rt<RR, 128>(in, ib, dims, out, ob, tx, ty, st)
+                            : launch_xy_rt<RR, 256>(in, ib, dims, out, ob, tx, ty, st);
+}
+
+template <int RR, int XT>
+static cudaError_t prepare_xy_rt() {
+  using G = XYGeom<RR, XT>;
+  const int smem = (int)(sizeof(float) * (kStages * G::TB * G::XS + G::TB * G::SXS));
+  cudaError_t e = cudaFuncSetAttribute(k_rho_xy<RR, XT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rho_xy<RR, XT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
 }
 
 template <int RR>
 static cudaError_t prepare_xy_r() {
-  using G2 = XYGeom<RR, 256>;
-  using G1 = XYGeom<RR, 128>;
-  cudaError_t e = cudaFuncSetAttribute(k_rho_xy<RR, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float) * (kStages * G2::TB * G2::XS + G2::TB * G2::SXS)));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_rho_xy<RR, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * (kStages * G1::TB * G1::XS + G1::TB * G1::SXS)));
+  cudaError_t e = prepare_xy_rt<RR, 256>();
+  if (e == cudaSuccess) e = prepare_xy_rt<RR, 128>();
   return e;
 }
 
@@ -261,17 +272,17 @@ cudaError_t prepare_rho_xy_kernels() {
 }
 
 cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
-                          const Taps& taps, int rk, cudaStream_t st) {
+                          const Taps& tx, const Taps& ty, int rk, cudaStream_t st) {
   if (box_vox(ob) == 0) return cudaSuccess;
   switch (rk) {
-    case 4: return launch_xy_r<4>(in, ib, dims, out, ob, taps, st);
-    case 6: return launch_xy_r<6>(in, ib, dims, out, ob, taps, st);
-    case 8: return launch_xy_r<8>(in, ib, dims, out, ob, taps, st);
-    case 12: return launch_xy_r<12>(in, ib, dims, out, ob, taps, st);
-    case 16: return launch_xy_r<16>(in, ib, dims, out, ob, taps, st);
-    case 24: return launch_xy_r<24>(in, ib, dims, out, ob, taps, st);
-    case 32: return launch_xy_r<32>(in, ib, dims, out, ob, taps, st);
-    case 36: return launch_xy_r<36>(in, ib, dims, out, ob, taps, st);
+    case 4: return launch_xy_r<4>(in, ib, dims, out, ob, tx, ty, st);
+    case 6: return launch_xy_r<6>(in, ib, dims, out, ob, tx, ty, st);
+    case 8: return launch_xy_r<8>(in, ib, dims, out, ob, tx, ty, st);
+    case 12: return launch_xy_r<12>(in, ib, dims, out, ob, tx, ty, st);
+    case 16: return launch_xy_r<16>(in, ib, dims, out, ob, tx, ty, st);
+    case 24: return launch_xy_r<24>(in, ib, dims, out, ob, tx, ty, st);
+    case 32: return launch_xy_r<32>(in, ib, dims, out, ob, tx, ty, st);
+    case 36: return launch_xy_r<36>(in, ib, dims, out, ob, tx, ty, st);
     default: return cudaErrorInvalidValue;
   }
 }

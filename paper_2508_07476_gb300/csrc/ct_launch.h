@@ -26,10 +26,12 @@ cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int d
 // (3 planes over ab = grad_partial_box(ob, vb, R, dims[2])) of vol; launch_grad_z
 // takes their z pass and writes J (6 planes over ob), as launch_grad_products does.
 Box grad_partial_box(const Box& ob, const Box& vb, int rs, int dimz);
+// tx / ty / tz: the taps of each axis (anisotropic voxels); scale: the factor of
+// each product (1 / (spacing_a spacing_b), xx yy zz xy xz yz).
 cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
-                           const Taps& taps, int rk, cudaStream_t st);
-cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps, int rk, bool mixed,
-                          cudaStream_t st);
+                           const Taps& tx, const Taps& ty, int rk, cudaStream_t st);
+cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& tz,
+                          const float scale[6], int rk, bool mixed, cudaStream_t st);
 
 // rho pass along x: out (6 planes over ob) from in (6 planes over ib).
 cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
@@ -37,7 +39,7 @@ cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], floa
 
 // rho passes along x and y fused: out (6 planes over ob) from in (6 planes over ib).
 cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
-                          const Taps& taps, int rk, cudaStream_t st);
+                          const Taps& tx, const Taps& ty, int rk, cudaStream_t st);
 
 // rho pass along axis 1 (y) or 2 (z), streaming register windows of block_t (8 or 16) outputs.
 cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,

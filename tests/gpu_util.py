@@ -61,11 +61,12 @@ def _out_dtype(t):
 
 def fused(vol, sigma, rho, center, axis, mask=None, precision=_lib.CT_PREC_FP32, chunk=(0, 0, 0), on_host=False,
           vec_type=_lib.CT_OUT_F32, angle_type=_lib.CT_OUT_F32, fa_type=_lib.CT_OUT_F32, fill=math.nan,
-          outputs=("v", "ha", "ia", "fa"), raw=False):
+          outputs=("v", "ha", "ia", "fa"), raw=False, spacing=(0.0, 0.0, 0.0), lv_centres=None):
     """Whole pipeline through ct_run_chunks; numpy outputs (decoded to float unless raw)."""
     torch = torch_mod()
     nz, ny, nx = vol.shape
-    p = _lib.make_params(sigma, rho, center, axis, precision, vec_type, angle_type, fa_type, fill, chunk=chunk)
+    p = _lib.make_params(sigma, rho, center, axis, precision, vec_type, angle_type, fa_type, fill, chunk=chunk,
+                         spacing=spacing, lv_centres=lv_centres)
     plan = _lib.ct_plan_create(p, (nx, ny, nz))
     try:
         kw = dict(device="cpu", pin_memory=True) if on_host else dict(device="cuda")
