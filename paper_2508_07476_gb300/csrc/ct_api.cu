@@ -193,6 +193,7 @@ struct ct_plan_s {
   bool fuse_z_eig = false;  // z pass fused with the eigen stage, or split (tuning choice)
   bool fuse_xy = true;      // x and y passes in one kernel, or two (tuning choice)
   bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
+  int tc_rho = 4;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -389,7 +390,18 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
     CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts[0], sc.rks, mixed, st),
               "gradient kernel launch");
   }
-  if (P->fuse_xy) {
+  if (P->tc_rho & 3) {  // x and y as separate passes, each on the tensor cores or the FP32 stencil
+    if (P->tc_rho & 1)
+      CT_LAUNCH(P, st, "rho_x_tc", launch_rho_tc(A, G, dims, B, Bx, 0, sc.tr[0], sc.rkr, st), "rho x kernel launch");
+    else
+      CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr[0], sc.rkr, st), "rho x kernel launch");
+    if (P->tc_rho & 2)
+      CT_LAUNCH(P, st, "rho_y_tc", launch_rho_tc(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, st), "rho y kernel launch");
+    else
+      CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
+                "rho y kernel launch");
+    *Sxy = A;
+  } else if (P->fuse_xy) {
     CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr[0], sc.tr[1], sc.rkr, st), "rho xy kernel launch");
     *Sxy = B;
   } else {
@@ -402,6 +414,17 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
   return CT_OK;
 }
 
+// The z pass of rho: S (6 planes over ob) from S_xy (6 planes over Bxy).
+ct_status z_pass(ct_plan P, const Scale& sc, const int dims[3], const float* Sxy, const Box& Bxy, float* S,
+                 const Box& ob, cudaStream_t st) {
+  if (P->tc_rho & 4)
+    CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, st), "rho z kernel launch");
+  else
+    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
+              "rho z kernel launch");
+  return CT_OK;
+}
+
 // The whole smoothing chain into S (6 planes over ob): the stage API.
 ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
                         const Box& ob, float* S_out, int slot, bool mixed, cudaStream_t st) {
@@ -409,9 +432,7 @@ ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uin
   Box Bxy;
   ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
   if (rc) return rc;
-  CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S_out, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
-            "rho z kernel launch");
-  return CT_OK;
+  return z_pass(P, sc, dims, Sxy, Bxy, S_out, ob, st);
 }
 
 ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
@@ -428,8 +449,7 @@ ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint
   if (rc) return rc;
   if (!P->fuse_z_eig) {  // split: z pass into the free buffer, then the eigen stage
     float* S = Sxy == P->buf[slot][0] ? P->buf[slot][1] : P->buf[slot][0];
-    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
-              "rho z kernel launch");
+    if ((rc = z_pass(P, sc, dims, Sxy, Bxy, S, ob, st))) return rc;
     return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
   }
   if ((rc = ensure_fused_fallback(P, slot, box_vox(ob)))) return rc;
@@ -482,6 +502,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
     cudaError_t e = prepare_sigma_kernels();
     if (e == cudaSuccess) e = prepare_rho_xy_kernels();
     if (e == cudaSuccess) e = prepare_grad_split_kernels();
+    if (e == cudaSuccess) e = prepare_rho_tc_kernels();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attribute set-up");
   }
   ct_plan P = new (std::nothrow) ct_plan_s();
@@ -512,6 +533,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_FUSE_Z_EIG")) P->fuse_z_eig = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_FUSE_XY")) P->fuse_xy = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_SPLIT_GRAD")) P->split_grad = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_TC_RHO")) P->tc_rho = std::atoi(e) & 7;
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;
@@ -960,6 +982,8 @@ ct_status ct_plan_sync(ct_plan P) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "device work");
+  if (const unsigned int n = tc_timeouts(true))
+    return fail(CT_ERR_CUDA, "%u tensor-core CTAs gave up waiting for their MMAs (results are invalid)", n);
   return CT_OK;
 }
 

@@ -45,6 +45,16 @@ cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], flo
 cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
                               const Taps& taps, int rk, int block_t, cudaStream_t st);
 
+// rho pass along axis 0, 1 or 2 on the tensor cores (banded Toeplitz product,
+// TF32 split operands, FP32 accumulation): same contract as launch_rho_x /
+// launch_rho_stream.  prepare_rho_tc_kernels sets the shared-memory
+// attributes (call before any capture); tc_timeouts returns how many CTAs
+// gave up waiting for their MMAs since the last reset.
+cudaError_t prepare_rho_tc_kernels();
+cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
+                          const Taps& taps, int rk, cudaStream_t st);
+unsigned int tc_timeouts(bool reset);
+
 struct EigOut {
   void* vec;
   void* ha;
