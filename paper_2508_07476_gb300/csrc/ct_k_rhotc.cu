@@ -3,9 +3,10 @@
 // Toeplitz product per tile instead of the FP32 stencil.
 //
 // A tile is M = 128 lines (for y / z: consecutive x of one (component, other)
-// row; for x: 128 consecutive (component, z, y) rows) by N = 32 outputs along
-// the axis.  With the window of W = 32 + 2 RA input positions of a tile (RA =
-// the radius rounded up to a multiple of 4, so that W is a multiple of 8),
+// row; for x: 128 consecutive (component, z, y) rows) by N = NT outputs along
+// the axis (NT = 64, or 32 for the largest radius).  With the window of
+// W = NT + 2 RA input positions of a tile (RA = the radius rounded up to a
+// multiple of 4, so that W is a multiple of 8),
 //   D[m][n] = sum_k A[m][k] B[n][k],   A[m][k] = in(line m, first - RA + k),
 //   B[n][k] = w[k - n - (RA - R)] (zero off the band of 2R + 1 taps),
 // one M x N x W product.  Each operand is split into a TF32 head and the FP32
@@ -15,22 +16,29 @@
 // remainders to 11 significant bits; the dropped A_lo B_lo is below 2^-22),
 // comparable with the FP32 stencil's own rounding.
 //
-// A_hi lives in tensor memory (lane m = line m, one column per position) and
-// A_lo in shared memory (K-major core matrices of 8 lines x 4 positions);
-// both are rings of W columns indexed by position mod W.  Since tiles advance
-// by 32 positions and the ring holds one window, each tile writes only its 32
-// new positions, into the slots of the 32 its predecessor no longer needs; a
-// k-step of 8 positions starts on a multiple of 8 and never straddles the
-// wrap.  B_hi / B_lo are fixed for the launch and staged once per CTA.
+// A_hi and A_lo live in tensor memory (lane m = line m, one column per
+// position), each a ring of WR = W + NT columns indexed by position mod WR.
+// Tiles advance by NT positions, so staging tile t writes the slots of
+// positions that only tiles up to t - 2 read: a tile can be staged while its
+// predecessor's product runs.  A k-step of 8 positions starts on a multiple of
+// 8 and never straddles the wrap.  B_hi / B_lo are fixed for the launch and
+// staged once per CTA in shared memory (K-major core matrices of 8 outputs x
+// 4 positions).
 //
-// Per tile: every thread splits its 32 new values (loaded during the previous
-// tile's product) and writes them to the rings; one thread issues the
-// 3 W / 8 MMAs and commits them to an mbarrier; the next tile's loads go out;
-// after the (bounded) wait every warp reads its 32 lanes of D and stores the
-// outputs.  For x the loads and stores go through a padded shared-memory
-// transpose so that global accesses stay coalesced.  A CTA walks whole
-// segments of a line group (persistent grid), so the ring is filled once per
-// segment.
+// The CTA is warp-specialised, one CTA per SM holding all 512 tensor-memory
+// columns.  Four producer warps own the 128 lines: they copy NT-position
+// chunks of their lines into shared memory with cp.async (16-byte copies when
+// the boxes are 16-byte aligned), several chunks ahead in one stream that runs
+// on across work units, then split a landed chunk, write both rings and arrive
+// on the tile's "staged" mbarrier.  An MMA warp waits on it, issues the
+// 3 W / 8 MMAs (one elected lane, the loop in warp-uniform control flow) into
+// one of two accumulators and commits them to that accumulator's mbarrier.
+// Four epilogue warps wait on it, read their 32 lanes of D, free the
+// accumulator (a third mbarrier) and store the outputs.  For x the chunks are
+// copied row by row and read back by line, and the outputs go through a
+// padded shared-memory transpose, so that global accesses stay coalesced.
+// Every wait is bounded; a CTA that gives up raises a flag that ends the other
+// roles' waits, drains its MMAs and releases the tensor memory.
 #include <algorithm>
 
 #include "ct_common.cuh"
@@ -40,37 +48,45 @@ namespace ct {
 
 namespace {
 
-constexpr int kTcThreads = 128;              // = M: thread / TMEM lane m owns line m
-constexpr int kTcNT = 32;                    // outputs per tile along the axis (MMA N)
-constexpr uint32_t kTcWaitLimit = 1u << 20;  // mbarrier polls before a CTA gives up
-constexpr uint32_t kTcSuspendNs = 500;       // a waiting thread sleeps up to this long per poll
+constexpr int kTcLines = 128;                  // = M: producer thread / TMEM lane m owns line m
+constexpr int kTcThreads = 2 * kTcLines + 32;  // producer warps 0-3, epilogue warps 4-7, MMA warp 8
+constexpr int kTcND = 2;                       // accumulators: tile t + 1's product runs while tile t is read
+constexpr uint32_t kTcWaitLimit = 1u << 20;    // mbarrier polls before a CTA gives up
+constexpr uint32_t kTcSuspendNs = 500;         // a waiting thread sleeps up to this long per poll
 
-// CTAs that gave up waiting for their MMAs (read and cleared by tc_timeouts()).
+// CTAs that gave up waiting (read and cleared by tc_timeouts()).
 __device__ unsigned int g_tc_timeouts = 0;
 
 template <int RR>
 struct TcGeom {
-  static constexpr int RA = (RR + 3) / 4 * 4;  // window margin: W is a multiple of 8
-  static constexpr int W = kTcNT + 2 * RA;     // ring / window positions
-  static constexpr int KC = W / 4;             // core-matrix columns of a K-major operand
-  static constexpr int KS = W / 8;             // k-steps per tile
-  static constexpr int TCOLS = W + kTcNT <= 128 ? 128 : 256;  // tensor-memory columns held
-  static constexpr int DCOL = TCOLS - kTcNT;                  // accumulator columns
-  static constexpr int MAX_CTAS = 512 / TCOLS;                // CTAs per SM that fit in TMEM
-  static constexpr int ALO_BYTES = kTcThreads * W * 4;
-  static constexpr int B_BYTES = kTcNT * W * 4;
-  static constexpr int T_STRIDE = 33;  // padded row of the x-pass transpose
-  static constexpr int T_BYTES = kTcThreads * T_STRIDE * 4;
-  static constexpr int ROW_BYTES = kTcThreads * 8 * 2;  // x form: each row's input and output pointers
-  static constexpr int need(bool xaxis) { return ALO_BYTES + 2 * B_BYTES + (xaxis ? T_BYTES + ROW_BYTES : 0); }
-  // dynamic shared memory requested: at least enough that no more than
-  // MAX_CTAS CTAs fit on an SM (233472 bytes, 1 KB reserved per CTA)
-  static constexpr int smem(bool xaxis) {
-    return need(xaxis) > 233472 / (MAX_CTAS + 1) ? need(xaxis) : 233472 / (MAX_CTAS + 1);
+  static constexpr int RA = (RR + 3) / 4 * 4;    // window margin: W is a multiple of 8
+  static constexpr int NT = RR <= 32 ? 64 : 32;  // outputs per tile (MMA N)
+  static constexpr int W = NT + 2 * RA;          // window positions of a tile
+  static constexpr int WR = W + NT;              // ring positions
+  static constexpr int KCB = W / 4;              // core-matrix columns of B
+  static constexpr int KS = W / 8;               // k-steps per tile
+  static constexpr int P = (2 * RA + NT - 1) / NT;  // NT-position chunks that fill the ring
+  static constexpr int LO = WR;                     // tensor memory: A_hi ring, A_lo ring, kTcND D
+  static constexpr int DCOL = 2 * WR;
+  static constexpr int TCOLS = 512;  // one CTA per SM holds all of it
+  static_assert(DCOL + kTcND * NT <= TCOLS, "tensor memory");
+  static constexpr int B_BYTES = NT * W * 4;
+  static constexpr int XS = NT + 4;  // x-form chunk row: 16-byte aligned, conflict-free by line
+  static constexpr int TE = NT + 1;  // x-form output transpose row
+  static constexpr int ROW_BYTES = kTcLines * 8;
+  // one chunk: y / z [NT positions][128 lines]; x [128 lines][XS]
+  static constexpr int raw_floats(bool xaxis) { return xaxis ? kTcLines * XS : NT * kTcLines; }
+  static constexpr int stages(bool xaxis) { return xaxis ? 3 : 4; }  // chunks in flight
+  static constexpr int need(bool xaxis) {
+    return 2 * B_BYTES + stages(xaxis) * raw_floats(xaxis) * 4 + (xaxis ? kTcLines * TE * 4 + 2 * ROW_BYTES : 0);
   }
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
+}
 
 // Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride of
 // core matrices along K, sbo = along M/N.
@@ -95,31 +111,54 @@ __host__ __device__ __forceinline__ int core_index(int r, int k, int kc) {
   return ((r >> 3) * kc + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
 }
 
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
+// One k-step of the split product into D, issued by one elected lane of a
+// warp that runs this in uniform control flow (operands stay warp-uniform):
+// D (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi, with A_hi / A_lo from tensor memory.
+__device__ __forceinline__ void mma_kstep(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint64_t b_hi, uint64_t b_lo,
+                                          uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc));
+      "{\n.reg .pred p, q, e;\nelect.sync _|e, 0xffffffff;\nsetp.ne.b32 p, %6, 0;\nsetp.eq.b32 q, 0, 0;\n"
+      "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %3, %5, p;\n"
+      "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %4, %5, q;\n"
+      "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%2], %3, %5, q;\n}\n" ::"r"(d),
+      "r"(a_hi), "r"(a_lo), "l"(b_hi), "l"(b_lo), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// Commit the MMAs the elected lane issued to an mbarrier (same lane as mma_kstep).
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+      "{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity), "r"(kTcSuspendNs)
+      : "memory");
+  return done != 0;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t i = 0; i < kTcWaitLimit; ++i)
+    if (mbar_try(mbar, parity)) return true;
+  return false;
+}
+
+// Bounded wait that also gives up once another thread of the CTA has raised *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int* abort) {
   for (uint32_t i = 0; i < kTcWaitLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity), "r"(kTcSuspendNs)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(mbar, parity)) return true;
+    if (*abort) return false;
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float v[8]) {
@@ -145,42 +184,67 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// One unit's geometry as seen by line m: the segment, and the line's input
+// (relative position 0) and output (position a_lo) addresses with their strides.
+struct TcUnit {
+  int p0, nt;  // first tile start (absolute, a multiple of NT), tiles
+  const float* src;
+  float* dst;
+  int64_t istride, ostride;
+  bool lok;  // line m exists
+};
+
 // One 1-D pass of the integration-scale Gaussian along `axis` (0, 1 or 2; XAXIS
 // selects the row-transposing x form): out (6 planes over ob) from in (6 planes
 // over ib), positions clamped to the volume [0, dim_axis) and to ib.  Work
-// unit = (line group, segment of `seg` outputs, a multiple of 32).  Tiles
-// start at absolute multiples of 32 along the axis, so that an output's taps
+// unit = (line group, segment of `seg` outputs, a multiple of NT).  Tiles
+// start at absolute multiples of NT along the axis, so that an output's taps
 // meet the same k-steps whatever box it is computed in: chunked runs
-// reproduce the whole-volume result bit for bit.
+// reproduce the whole-volume result bit for bit.  vec: the boxes allow 16-byte
+// copies (checked on the host).
 template <int RR, bool XAXIS>
-__global__ void __launch_bounds__(kTcThreads, 3)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
-             const __grid_constant__ Taps taps) {
+             int vec, const __grid_constant__ Taps taps) {
   using G = TcGeom<RR>;
+  constexpr int NT = G::NT;
+  constexpr int S = G::stages(XAXIS);
+  constexpr int RAWF = G::raw_floats(XAXIS);
   extern __shared__ __align__(128) unsigned char smem[];
-  float* sAlo = reinterpret_cast<float*>(smem);
-  float* sBhi = reinterpret_cast<float*>(smem + G::ALO_BYTES);
-  float* sBlo = reinterpret_cast<float*>(smem + G::ALO_BYTES + G::B_BYTES);
-  float* sT = reinterpret_cast<float*>(smem + G::ALO_BYTES + 2 * G::B_BYTES);
-  const float** sSrc = reinterpret_cast<const float**>(smem + G::ALO_BYTES + 2 * G::B_BYTES + G::T_BYTES);
-  float** sDst = reinterpret_cast<float**>(smem + G::ALO_BYTES + 2 * G::B_BYTES + G::T_BYTES + kTcThreads * 8);
-  __shared__ __align__(8) uint64_t mbar;
+  float* sBhi = reinterpret_cast<float*>(smem);
+  float* sBlo = reinterpret_cast<float*>(smem + G::B_BYTES);
+  float* sRaw = reinterpret_cast<float*>(smem + 2 * G::B_BYTES);
+  unsigned char* xs = smem + 2 * G::B_BYTES + S * RAWF * 4;  // x form only
+  float* sTe = reinterpret_cast<float*>(xs);
+  const float** sSrc = reinterpret_cast<const float**>(xs + kTcLines * G::TE * 4);
+  float** sDst = reinterpret_cast<float**>(xs + kTcLines * G::TE * 4 + G::ROW_BYTES);
+  __shared__ __align__(8) uint64_t bar_staged[kTcND];  // the producers have staged tile g
+  __shared__ __align__(8) uint64_t bar_mma[kTcND];     // tile g's product is in D[g % kTcND]
+  __shared__ __align__(8) uint64_t bar_dfree[kTcND];   // the epilogue has read D[a]
   __shared__ uint32_t tmem_base;
-  const int m = threadIdx.x, w = m >> 5, lane = m & 31;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int role = w < 4 ? 0 : (w < 8 ? 1 : 2);  // producer, epilogue, MMA
+  const int m = tid & (kTcLines - 1);            // line / TMEM lane (roles 0 and 1)
+  const int wq = w & 3;                          // lane quadrant of this warp
 
   // B = the banded Toeplitz matrix of the taps, split into TF32 head and remainder
-  for (int e = m; e < kTcNT * G::W; e += kTcThreads) {
+  for (int e = tid; e < NT * G::W; e += kTcThreads) {
     const int n = e / G::W, k = e % G::W;
     const int j = k - n - (G::RA - RR);
     const float v = (j >= 0 && j <= 2 * RR) ? taps.w[j] : 0.f;
     const float hi = tf32_round(v);
-    const int c = core_index(n, k, G::KC);
+    const int c = core_index(n, k, G::KCB);
     sBhi[c] = hi;
     sBlo[c] = v - hi;
   }
-  const uint32_t mbar_a = smem_u32(&mbar);
-  if (m == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+  if (tid == 0) {
+    for (int a = 0; a < kTcND; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(kTcLines));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma[a])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[a])), "n"(kTcLines));
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) {
@@ -193,187 +257,280 @@ __global__ void __launch_bounds__(kTcThreads, 3)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tm = tmem_base;
-  const uint32_t tlane = tm + ((uint32_t)(w * 32) << 16);  // this warp's 32 lanes
-  constexpr uint32_t kC = G::KC * 128;                     // byte stride of 8-row core groups
-  const uint64_t bhi_d = umma_desc(smem_u32(sBhi), 128, kC);
-  const uint64_t blo_d = umma_desc(smem_u32(sBlo), 128, kC);
-  const uint64_t alo_d = umma_desc(smem_u32(sAlo), 128, kC);
-  constexpr uint32_t kIdesc = idesc_tf32(kTcThreads, kTcNT);
+  const uint32_t tlane = tm + ((uint32_t)(wq * 32) << 16);  // this warp's 32 lanes
+  // mbarriers of tile g, and the parity of its phase
+  auto staged_bar = [&](uint32_t g) { return smem_u32(&bar_staged[g % kTcND]); };
+  auto mma_bar = [&](uint32_t g) { return smem_u32(&bar_mma[g % kTcND]); };
+  auto dfree_bar = [&](uint32_t g) { return smem_u32(&bar_dfree[g % kTcND]); };
+  auto par = [](uint32_t g) { return (g / kTcND) & 1u; };
 
   // line groups and segments
   const int a_lo = ob.lo[axis], a_end = ob.lo[axis] + ob.n[axis];
-  const int a_first = a_lo & ~(kTcNT - 1);  // first tile start (a_lo >= 0)
+  const int a_first = a_lo & ~(NT - 1);  // first tile start (a_lo >= 0)
   const int other = XAXIS ? 1 : 3 - axis;
   const int64_t n_rows = XAXIS ? 6 * (int64_t)ob.n[1] * ob.n[2] : 0;
-  const int ngx = (ob.n[0] + kTcThreads - 1) / kTcThreads;
-  const int64_t n_groups = XAXIS ? (n_rows + kTcThreads - 1) / kTcThreads : 6 * (int64_t)ob.n[other] * ngx;
+  const int ngx = (ob.n[0] + kTcLines - 1) / kTcLines;
+  const int64_t n_groups = XAXIS ? (n_rows + kTcLines - 1) / kTcLines : 6 * (int64_t)ob.n[other] * ngx;
   const int64_t n_units = n_groups * ((a_end - a_first + seg - 1) / seg);
   const int alo = ib.lo[axis], an = ib.n[axis];
   const int qlo = max(0, alo) - alo, qhi = min(dim_axis - 1, alo + an - 1) - alo;  // clamp range, relative
 
-  uint32_t parity = 0;
-  bool ok = true;    // CTA-uniform: cleared only from a barrier's vote
-  bool mine = true;  // this thread's waits all completed
-  for (int64_t unit = blockIdx.x; unit < n_units && ok; unit += gridDim.x) {
+  auto decode = [&](int64_t unit) {
+    TcUnit U;
     const int sgi = (int)(unit / n_groups);
     const int64_t grp = unit % n_groups;
-    const int p0 = a_first + sgi * seg;  // first tile start of the segment
-    const int L = min(seg, a_end - p0);
-    const int nt = (L + kTcNT - 1) / kTcNT;
-    const float* src;  // this thread's line at relative position 0 (stride istride)
-    float* dst;        // this thread's line at output position a_lo (stride ostride)
-    int64_t istride = 1, ostride = 1;
-    bool lok;
+    U.p0 = a_first + sgi * seg;
+    U.nt = (min(seg, a_end - U.p0) + NT - 1) / NT;
+    U.istride = U.ostride = 1;
     if (XAXIS) {
-      const int64_t r = grp * kTcThreads + m;
-      lok = r < n_rows;
-      const int64_t rc = lok ? r : n_rows - 1;
+      const int64_t r = grp * kTcLines + m;
+      U.lok = r < n_rows;
+      const int64_t rc = U.lok ? r : n_rows - 1;
       const int yy = ob.lo[1] + (int)(rc % ob.n[1]);
       const int64_t t2 = rc / ob.n[1];
       const int zz = ob.lo[2] + (int)(t2 % ob.n[2]);
       const int comp = (int)(t2 / ob.n[2]);
-      src = in + comp * box_vox(ib) + box_index(ib, ib.lo[0], yy, zz);
-      dst = out + comp * box_vox(ob) + box_index(ob, a_lo, yy, zz);
-      __syncwarp();  // the warp's previous unit is done with the table
-      sSrc[m] = src;
-      sDst[m] = lok ? dst : nullptr;
-      __syncwarp();
+      U.src = in + comp * box_vox(ib) + box_index(ib, ib.lo[0], yy, zz);
+      U.dst = out + comp * box_vox(ob) + box_index(ob, a_lo, yy, zz);
     } else {
       const int xg = (int)(grp % ngx);
       const int64_t co = grp / ngx;
       const int comp = (int)(co / ob.n[other]);
       const int o = ob.lo[other] + (int)(co % ob.n[other]);
-      const int x = ob.lo[0] + xg * kTcThreads + m;
-      lok = x < ob.lo[0] + ob.n[0];
+      const int x = ob.lo[0] + xg * kTcLines + m;
+      U.lok = x < ob.lo[0] + ob.n[0];
       const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
       const int yb = axis == 1 ? ib.lo[1] : o, zb = axis == 1 ? o : ib.lo[2];
-      src = in + comp * box_vox(ib) + box_index(ib, xi, yb, zb);
-      istride = axis == 1 ? ib.n[0] : (int64_t)ib.n[0] * ib.n[1];
+      U.src = in + comp * box_vox(ib) + box_index(ib, xi, yb, zb);
+      U.istride = axis == 1 ? ib.n[0] : (int64_t)ib.n[0] * ib.n[1];
       const int yo = axis == 1 ? a_lo : o, zo = axis == 1 ? o : a_lo;
-      dst = out + comp * box_vox(ob) + box_index(ob, xi, yo, zo);
-      ostride = axis == 1 ? ob.n[0] : (int64_t)ob.n[0] * ob.n[1];
+      U.dst = out + comp * box_vox(ob) + box_index(ob, xi, yo, zo);
+      U.ostride = axis == 1 ? ob.n[0] : (int64_t)ob.n[0] * ob.n[1];
     }
-    const int q0 = p0 - G::RA - alo;  // relative input position of window position 0
+    return U;
+  };
 
-    // pf: 32 consecutive window positions from q (y / z: of this thread's line;
-    // x: position q + lane of each of the warp's 32 rows)
-    float pf[32];
-    auto load32 = [&](int q) {
-      const int qs = q0 + q;
+  uint32_t g = 0;          // tiles this thread's role has handled (every role counts the same sequence)
+  uint32_t committed = 0;  // MMA warp: tiles whose MMAs it has committed
+  if (role == 0) {
+    // the copy stream: chunk ic of unit iu (window positions NT ic for ic < P,
+    // then tile ic - P's NT), one cp.async group per chunk, stage k mod S
+    int64_t iu = blockIdx.x;
+    int ic = 0, iC = 0, iq0 = 0;
+    TcUnit IU;
+    auto enter = [&](int64_t u) {
+      iu = u;
+      ic = 0;
+      if (u >= n_units) return;
+      IU = decode(u);
+      iC = G::P + IU.nt;
+      iq0 = IU.p0 - G::RA - alo;
       if (XAXIS) {
-        const int rel = min(max(qs + lane, qlo), qhi);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) pf[i] = __ldg(sSrc[32 * w + i] + rel);
-      } else if (qs >= qlo && qs + 31 <= qhi) {  // inside the input box: no clamping
-        const float* p = src + qs * istride;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) pf[j] = __ldg(p + j * istride);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) pf[j] = __ldg(src + min(max(qs + j, qlo), qhi) * istride);
+        __syncwarp();  // the warp's copies of the previous unit have been issued
+        sSrc[m] = IU.src;
+        __syncwarp();
       }
     };
-    // split positions q .. q + 31 and write them to the rings (slots mod W)
-    auto stage32 = [&](int q) {
-      float v[32];
-      if (XAXIS) {
+    uint32_t k_issue = 0;
+    auto issue_next = [&]() {
+      if (iu < n_units) {
+        float* rb = sRaw + (k_issue % S) * RAWF;
+        const int qs = iq0 + (ic < G::P ? NT * ic : 2 * G::RA + NT * (ic - G::P));
+        const bool inside = qs >= qlo && qs + NT - 1 <= qhi;  // no clamping in this chunk
+        if (XAXIS) {
+          if (vec && inside) {  // 16 bytes per copy: NT / 4 lanes per row
+            constexpr int LPR = NT / 4, RPI = 32 / LPR;  // lanes per row, rows per instruction
+            const int sub = lane / LPR, qq = lane % LPR;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) sT[(32 * w + i) * G::T_STRIDE + lane] = pf[i];
-        __syncwarp();
+            for (int i2 = 0; i2 < 32 / RPI; ++i2) {
+              const int row = 32 * wq + RPI * i2 + sub;
+              cp_async16(smem_u32(rb + row * G::XS + 4 * qq), sSrc[row] + qs + 4 * qq);
+            }
+          } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = sT[m * G::T_STRIDE + j];
-        __syncwarp();
-      } else {
+            for (int h = 0; h < NT / 32; ++h) {
+              const int rel = min(max(qs + 32 * h + lane, qlo), qhi);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = pf[j];
-      }
+              for (int i = 0; i < 32; ++i)
+                cp_async4(smem_u32(rb + (32 * wq + i) * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
+            }
+          }
+        } else if (vec && inside) {  // 16 bytes (4 lines) per copy, within the warp's own 32 lines
+                                     // (the stage hand-off is warp-local): lane -> lines
+                                     // 32 wq + 4 (lane % 8).., positions lane / 8 + 4 i
+          const int qd = lane & 7, pg = lane >> 3;
+          const float* p = IU.src + (4 * qd - lane) + (int64_t)qs * IU.istride;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int slot = (q + 8 * c) % G::W;
-        float hi[8], lo[8];
+          for (int i = 0; i < NT / 4; ++i) {
+            const int pos = pg + 4 * i;
+            cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + pos * IU.istride);
+          }
+        } else if (inside) {
+          const float* p = IU.src + qs * IU.istride;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          hi[j] = tf32_round(v[8 * c + j]);
-          lo[j] = v[8 * c + j] - hi[j];
-        }
-        tmem_st8(tlane + slot, hi);
-        float4* d = reinterpret_cast<float4*>(sAlo + core_index(m, slot, G::KC));
-        d[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        d[8] = make_float4(lo[4], lo[5], lo[6], lo[7]);  // next core column: +32 floats
-      }
-    };
-
-    // fill the ring with the first 2 RA positions, then fetch tile 0's
-    for (int q = 0; q < 2 * G::RA; q += 32) {
-      load32(q);
-      stage32(q);
-    }
-    load32(2 * G::RA);
-    int base = 0;  // ring slot of the current tile's first window position
-    for (int t = 0; t < nt; ++t) {
-      stage32(2 * G::RA + kTcNT * t);
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      if (!__syncthreads_and(mine)) {
-        ok = false;
-        break;
-      }
-      if (m == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        int slot = base;
-#pragma unroll
-        for (int ks = 0; ks < G::KS; ++ks) {
-          const uint64_t bo = (uint64_t)(ks * 16);   // 256 bytes per k-step, in 16-byte units
-          const uint64_t ao = (uint64_t)(slot * 2);  // slot / 4 core columns of 128 bytes
-          mma_ts(tm + G::DCOL, tm + slot, bhi_d + bo, kIdesc, ks > 0);
-          mma_ts(tm + G::DCOL, tm + slot, blo_d + bo, kIdesc, 1);
-          mma_ss(tm + G::DCOL, alo_d + ao, bhi_d + bo, kIdesc, 1);
-          slot = slot + 8 >= G::W ? slot + 8 - G::W : slot + 8;
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
-                     : "memory");
-      }
-      if (t + 1 < nt) load32(2 * G::RA + kTcNT * (t + 1));
-      mine = mbar_wait(mbar_a, parity) && mine;
-      parity ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float r[32];
-      tmem_ld32(tlane + G::DCOL, r);
-      const int pt = p0 + kTcNT * t;  // absolute position of output 0 of the tile
-      const int nlo = max(0, a_lo - pt), nhi = min(kTcNT, a_end - pt);  // stored outputs [nlo, nhi)
-      const int64_t off = pt - a_lo;
-      if (XAXIS) {
-#pragma unroll
-        for (int n = 0; n < 32; ++n) sT[m * G::T_STRIDE + n] = r[n];
-        __syncwarp();
-        const bool col = lane >= nlo && lane < nhi;
-#pragma unroll 8
-        for (int i = 0; i < 32; ++i) {
-          float* rd = sDst[32 * w + i];
-          if (rd && col) rd[off + lane] = sT[(32 * w + i) * G::T_STRIDE + lane];
-        }
-        __syncwarp();
-      } else if (lok) {
-        float* d = dst + off * ostride;
-        if (nlo == 0 && nhi == kTcNT) {
-#pragma unroll
-          for (int n = 0; n < 32; ++n) d[n * ostride] = r[n];
+          for (int j = 0; j < NT; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
         } else {
 #pragma unroll
-          for (int n = 0; n < 32; ++n)
-            if (n >= nlo && n < nhi) d[n * ostride] = r[n];
+          for (int j = 0; j < NT; ++j)
+            cp_async4(smem_u32(rb + j * kTcLines + m), IU.src + min(max(qs + j, qlo), qhi) * IU.istride);
+        }
+        if (++ic == iC) enter(iu + gridDim.x);
+      }
+      cp_async_commit();
+      ++k_issue;
+    };
+    enter(blockIdx.x);
+#pragma unroll 1
+    for (int i = 0; i < S; ++i) issue_next();
+    uint32_t k = 0;  // chunks consumed
+    bool go = true;
+    for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
+      const int nt = decode(unit).nt;
+      for (int c = 0; c < G::P + nt; ++c, ++k) {
+        cp_async_wait<S - 1>();  // chunk k has landed
+        __syncwarp();            // and so have the other lanes' copies (each warp copies only its own lines)
+        const float* rb = sRaw + (k % S) * RAWF;
+        float v[NT];
+        if (XAXIS) {
+#pragma unroll
+          for (int j = 0; j < NT; j += 4) {
+            const float4 f = *reinterpret_cast<const float4*>(rb + m * G::XS + j);
+            v[j] = f.x;
+            v[j + 1] = f.y;
+            v[j + 2] = f.z;
+            v[j + 3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NT; ++j) v[j] = rb[j * kTcLines + m];
+        }
+        __syncwarp();  // every lane has read the stage before it is refilled
+        issue_next();
+        const int t = c - G::P;  // tile of this chunk (< 0: ring fill)
+        bool ok = true;
+        if (c == 0) {  // the ring restarts: every MMA of the previous unit must have read it
+          if (g >= 1) ok = mbar_wait_or_abort(mma_bar(g - 1), par(g - 1), &abort_flag);
+          if (g >= 2) ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag) && ok;
+        } else if (t >= 2) {  // tile t's positions take the slots that only tiles up to t - 2 read
+          ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag);
+        }
+        if (!ok) {
+          abort_flag = 1;
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // split and write both rings (slots mod WR)
+        const int q = c < G::P ? NT * c : 2 * G::RA + NT * t;
+#pragma unroll
+        for (int cc = 0; cc < NT / 8; ++cc) {
+          const int slot = (q + 8 * cc) % G::WR;
+          float hi[8], lo[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            hi[j] = tf32_round(v[8 * cc + j]);
+            lo[j] = v[8 * cc + j] - hi[j];
+          }
+          tmem_st8(tlane + slot, hi);
+          tmem_st8(tlane + G::LO + slot, lo);
+        }
+        if (t < 0) continue;
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(staged_bar(g));
+        ++g;
+      }
+    }
+    cp_async_wait<0>();  // no copy is left in flight
+  } else if (role == 2) {
+    const uint64_t bhi_d = umma_desc(smem_u32(sBhi), 128, G::KCB * 128);
+    const uint64_t blo_d = umma_desc(smem_u32(sBlo), 128, G::KCB * 128);
+    constexpr uint32_t kIdesc = idesc_tf32(kTcLines, NT);
+    bool go = true;
+    for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
+      const int nt = decode(unit).nt;
+      for (int t = 0; t < nt; ++t, ++g) {
+        // the tile is staged, and D[g % kTcND] has been read (tile g - kTcND)
+        bool ok = mbar_wait_or_abort(staged_bar(g), par(g), &abort_flag);
+        if (ok && g >= kTcND) ok = mbar_wait_or_abort(dfree_bar(g - kTcND), par(g - kTcND), &abort_flag);
+        if (!__all_sync(0xffffffffu, ok)) {
+          abort_flag = 1;
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tm + G::DCOL + (g % kTcND) * NT;
+        int slot = (NT * t) % G::WR;
+#pragma unroll
+        for (int ks = 0; ks < G::KS; ++ks) {
+          const uint64_t bo = (uint64_t)(ks * 16);  // 256 bytes per k-step, in 16-byte units
+          mma_kstep(d, tm + slot, tm + G::LO + slot, bhi_d + bo, blo_d + bo, kIdesc, ks > 0);
+          slot = slot + 8 >= G::WR ? slot + 8 - G::WR : slot + 8;
+        }
+        mma_commit(mma_bar(g));
+        committed = g + 1;
+      }
+    }
+  } else {
+    bool go = true;
+    for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
+      const TcUnit U = decode(unit);
+      if (XAXIS) {
+        __syncwarp();  // the warp's previous unit is done with its table
+        sDst[m] = U.lok ? U.dst : nullptr;
+        __syncwarp();
+      }
+      for (int t = 0; t < U.nt; ++t, ++g) {
+        if (!mbar_wait_or_abort(mma_bar(g), par(g), &abort_flag)) {
+          abort_flag = 1;
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float r[NT];
+#pragma unroll
+        for (int h = 0; h < NT / 32; ++h) tmem_ld32(tlane + G::DCOL + (g % kTcND) * NT + 32 * h, r + 32 * h);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(dfree_bar(g));
+        const int pt = U.p0 + NT * t;  // absolute position of output 0 of the tile
+        const int nlo = max(0, a_lo - pt), nhi = min(NT, a_end - pt);  // stored outputs [nlo, nhi)
+        const int64_t off = pt - a_lo;
+        if (XAXIS) {
+#pragma unroll
+          for (int n = 0; n < NT; ++n) sTe[m * G::TE + n] = r[n];
+          __syncwarp();
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i) {
+            float* rd = sDst[32 * wq + i];
+            if (rd) {
+#pragma unroll
+              for (int h = 0; h < NT / 32; ++h) {
+                const int n = 32 * h + lane;
+                if (n >= nlo && n < nhi) rd[off + n] = sTe[(32 * wq + i) * G::TE + n];
+              }
+            }
+          }
+          __syncwarp();
+        } else if (U.lok) {
+          float* d = U.dst + off * U.ostride;
+          if (nlo == 0 && nhi == NT) {
+#pragma unroll
+            for (int n = 0; n < NT; ++n) d[n * U.ostride] = r[n];
+          } else {
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+              if (n >= nlo && n < nhi) d[n * U.ostride] = r[n];
+          }
         }
       }
-      base = base + kTcNT >= G::W ? base + kTcNT - G::W : base + kTcNT;
     }
   }
-  // a CTA whose MMAs did not complete waits once more (bounded) before it
-  // releases the tensor memory they write, and reports itself
-  ok = __syncthreads_and(ok && mine);
-  if (!ok) {
-    mbar_wait(mbar_a, parity ^ 1u);
-    if (m == 0) atomicAdd(&g_tc_timeouts, 1u);
+  // a CTA that gave up waits once more (bounded) for the last product it
+  // committed before it releases the tensor memory, and reports itself
+  __syncthreads();
+  if (abort_flag && w == 8) {
+    if (committed >= 1) mbar_wait(mma_bar(committed - 1), par(committed - 1));
+    if (lane == 0) atomicAdd(&g_tc_timeouts, 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -382,49 +539,45 @@ __global__ void __launch_bounds__(kTcThreads, 3)
 
 template <int RR, bool XAXIS>
 struct TcLaunch {
-  static int ctas_per_sm;  // resident CTAs per SM (0 until prepared)
+  static bool ready;
   static cudaError_t prepare() {
-    if (ctas_per_sm > 0) return cudaSuccess;
-    const int smem = TcGeom<RR>::smem(XAXIS);
-    cudaError_t e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (ready) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcGeom<RR>::need(XAXIS));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_rho_tc<RR, XAXIS>);
-    int dev = 0, smem_sm = 0, regs_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    // resident CTAs: shared memory (1 KB reserved per CTA), registers (allocated
-    // in units of 8 per thread) and tensor memory, whichever binds first
-    const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + 1024);
-    const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * kTcThreads);
-    ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_regs), TcGeom<RR>::MAX_CTAS));
+    ready = true;
     return cudaSuccess;
   }
   static cudaError_t run(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
                          const Taps& taps, cudaStream_t st) {
+    using G = TcGeom<RR>;
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int64_t cap = (int64_t)sms * ctas_per_sm;
-    const int a_n = ob.lo[axis] + ob.n[axis] - (ob.lo[axis] & ~(kTcNT - 1));  // aligned extent
-    const int64_t groups = axis == 0 ? (6 * (int64_t)ob.n[1] * ob.n[2] + kTcThreads - 1) / kTcThreads
-                                     : 6 * (int64_t)ob.n[3 - axis] * ((ob.n[0] + kTcThreads - 1) / kTcThreads);
+    // one CTA per SM (it holds all of the SM's tensor memory)
+    const int a_n = ob.lo[axis] + ob.n[axis] - (ob.lo[axis] & ~(G::NT - 1));  // aligned extent
+    const int64_t groups = axis == 0 ? (6 * (int64_t)ob.n[1] * ob.n[2] + kTcLines - 1) / kTcLines
+                                     : 6 * (int64_t)ob.n[3 - axis] * ((ob.n[0] + kTcLines - 1) / kTcLines);
     int seg = 512;  // outputs per unit: long enough to amortise the ring fill, short enough to spread
-    while (seg > kTcNT && groups * ((a_n + seg - 1) / seg) < 2 * cap) seg /= 2;
+    while (seg > G::NT && groups * ((a_n + seg - 1) / seg) < 2 * sms) seg /= 2;
     const int64_t units = groups * ((a_n + seg - 1) / seg);
-    const int grid = (int)std::min<int64_t>(units, cap);
-    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, TcGeom<RR>::smem(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg,
-                                                                          taps);
+    const int grid = (int)std::min<int64_t>(units, sms);
+    // 16-byte copies: the input rows start on 16-byte boundaries, and so do
+    // the copied pieces (y / z: quads of whole line groups; x: the windows)
+    const bool rows16 = ((uintptr_t)in % 16) == 0 && ib.n[0] % 4 == 0;
+    const bool vec = axis == 0 ? rows16 && ib.lo[0] % 4 == 0
+                               : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0 && ob.n[0] % kTcLines == 0;
+    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::need(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg, vec ? 1 : 0,
+                                                                  taps);
     return cudaGetLastError();
   }
 };
 template <int RR, bool XAXIS>
-int TcLaunch<RR, XAXIS>::ctas_per_sm = 0;
+bool TcLaunch<RR, XAXIS>::ready = false;
 
 template <int RR>
 cudaError_t run_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,

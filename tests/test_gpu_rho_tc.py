@@ -54,7 +54,7 @@ def _rel(S, S_o):
 @pytest.mark.parametrize("mask", MASKS)
 @pytest.mark.parametrize("shape,sigma,rho", [((23, 29, 37), 1.0, 1.0), ((9, 8, 130), 0.8, 1.7),
                                              ((40, 17, 70), 1.5, 3.0), ((70, 33, 45), 2.0, 6.0),
-                                             ((20, 150, 11), 1.0, 9.0)])
+                                             ((20, 150, 11), 1.0, 9.0), ((40, 24, 256), 2.0, 6.0)])
 def test_tc_structure_tensor_ragged(tc, mask, shape, sigma, rho):
     tc(mask)
     vol = _rand_vol(shape, seed=sum(shape))
@@ -84,6 +84,26 @@ def test_tc_sub_box_matches_oracle_and_whole(tc, mask):
     np.testing.assert_array_equal(g["S"], full["S"][sl])
 
 
+@pytest.mark.parametrize("mask", MASKS)
+def test_tc_aligned_sub_box_matches_oracle_and_whole(tc, mask):
+    # boxes on 16-byte boundaries with whole 128-line groups: the 16-byte copy path
+    tc(mask)
+    vol = _rand_vol((48, 60, 192), seed=13)
+    sigma, rho = 1.0, 3.0
+    h = O.radius(sigma) + O.radius(rho)
+    assert h == 16
+    out_lo, out_n = (16, 20, 16), (128, 20, 16)
+    in_lo = tuple(a - h for a in out_lo)
+    in_n = tuple(n + 2 * h for n in out_n)
+    g = G.stages(vol, sigma, rho, (0, 0, 0), (0, 0, 1), in_box=(in_lo, in_n), out_box=(out_lo, out_n))
+    S_o = O.structure_tensor(vol, sigma, rho, lo=out_lo, n=out_n)
+    assert _rel(g["S"], S_o) <= 2e-5
+    full = G.stages(vol, sigma, rho, (0, 0, 0), (0, 0, 1))
+    sl = (slice(None), slice(out_lo[2], out_lo[2] + out_n[2]), slice(out_lo[1], out_lo[1] + out_n[1]),
+          slice(out_lo[0], out_lo[0] + out_n[0]))
+    np.testing.assert_array_equal(g["S"], full["S"][sl])
+
+
 @pytest.mark.parametrize("prec,tol", [(FP32, 2e-5), (MIXED, 2e-3)])
 def test_tc_helix64(tc, prec, tol):
     tc(7)
@@ -99,6 +119,18 @@ def test_tc_agrees_with_stencil(tc):
     # the same plan settings with and without the tensor cores: tensors agree
     # to the FP32 stage tolerance on a volume with a 512-long z line
     vol = _rand_vol((512, 12, 130), seed=5)
+    out = {}
+    for mask in (0, 7):
+        tc(mask)
+        out[mask] = G.stages(vol, 2.0, 6.0, (0, 0, 0), (0, 0, 1))["S"].astype(np.float64)
+    rel = np.abs(out[7] - out[0]) / (out[0][0] + out[0][1] + out[0][2])[None]
+    assert rel.max() <= 2e-5, rel.max()
+
+
+def test_tc_many_units_aligned_agrees_with_stencil(tc):
+    # 16-byte copies and many work units per CTA on every axis (the regime of
+    # the full-size runs): the tensor-core tensors agree with the stencil's
+    vol = _rand_vol((96, 256, 512), seed=17)
     out = {}
     for mask in (0, 7):
         tc(mask)
