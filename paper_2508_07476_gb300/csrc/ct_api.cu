@@ -193,7 +193,7 @@ struct ct_plan_s {
   bool fuse_z_eig = false;  // z pass fused with the eigen stage, or split (tuning choice)
   bool fuse_xy = true;      // x and y passes in one kernel, or two (tuning choice)
   bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
-  int tc_rho = 4;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
+  int tc_rho = 7;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {

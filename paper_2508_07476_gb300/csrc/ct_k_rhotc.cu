@@ -34,9 +34,11 @@
 // 3 W / 8 MMAs (one elected lane, the loop in warp-uniform control flow) into
 // one of two accumulators and commits them to that accumulator's mbarrier.
 // Four epilogue warps wait on it, read their 32 lanes of D, free the
-// accumulator (a third mbarrier) and store the outputs.  For x the chunks are
-// copied row by row and read back by line, and the outputs go through a
-// padded shared-memory transpose, so that global accesses stay coalesced.
+// accumulator (a third mbarrier) and store the outputs.  For x each line is a
+// row: a producer thread fetches its row's chunk with one bulk copy (TMA,
+// completing on the stage's mbarrier) and an epilogue thread writes its row of
+// outputs with one bulk store; unaligned or clamped pieces go through
+// coalesced per-element copies and a padded shared-memory transpose.
 // Every wait is bounded; a CTA that gives up raises a flag that ends the other
 // roles' waits, drains its MMAs and releases the tensor memory.
 #include <algorithm>
@@ -72,7 +74,7 @@ struct TcGeom {
   static_assert(DCOL + kTcND * NT <= TCOLS, "tensor memory");
   static constexpr int B_BYTES = NT * W * 4;
   static constexpr int XS = NT + 4;  // x-form chunk row: 16-byte aligned, conflict-free by line
-  static constexpr int TE = NT + 1;  // x-form output transpose row
+  static constexpr int TE = NT + 4;  // x-form output row: 16-byte aligned, float4 writes conflict-free
   static constexpr int ROW_BYTES = kTcLines * 8;
   // one chunk: y / z [NT positions][128 lines]; x [128 lines][XS]
   static constexpr int raw_floats(bool xaxis) { return xaxis ? kTcLines * XS : NT * kTcLines; }
@@ -87,6 +89,24 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
 }
+
+// Bulk copy global -> shared on the TMA engine, completing `bytes` on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t smem_dst, const float* gsrc, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_dst),
+      "l"(gsrc), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+// Bulk copy shared -> global (bulk group of the issuing thread).
+__device__ __forceinline__ void bulk_s2g(float* gdst, uint32_t smem_src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(smem_src), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// This thread's bulk stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_s2g_read_done() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride of
 // core matrices along K, sbo = along M/N.
@@ -161,6 +181,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float v[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
                "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
@@ -200,8 +224,9 @@ struct TcUnit {
 // unit = (line group, segment of `seg` outputs, a multiple of NT).  Tiles
 // start at absolute multiples of NT along the axis, so that an output's taps
 // meet the same k-steps whatever box it is computed in: chunked runs
-// reproduce the whole-volume result bit for bit.  vec: the boxes allow 16-byte
-// copies (checked on the host).
+// reproduce the whole-volume result bit for bit.  vec: bit 0, the input box
+// allows 16-byte copies; bit 1 (x form), the output rows start on 16-byte
+// boundaries (both checked on the host).
 template <int RR, bool XAXIS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
@@ -218,6 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float* sTe = reinterpret_cast<float*>(xs);
   const float** sSrc = reinterpret_cast<const float**>(xs + kTcLines * G::TE * 4);
   float** sDst = reinterpret_cast<float**>(xs + kTcLines * G::TE * 4 + G::ROW_BYTES);
+  __shared__ __align__(8) uint64_t bar_chunk[4];        // x form: chunk stage s has landed
   __shared__ __align__(8) uint64_t bar_staged[kTcND];  // the producers have staged tile g
   __shared__ __align__(8) uint64_t bar_mma[kTcND];     // tile g's product is in D[g % kTcND]
   __shared__ __align__(8) uint64_t bar_dfree[kTcND];   // the epilogue has read D[a]
@@ -239,6 +265,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     sBlo[c] = v - hi;
   }
   if (tid == 0) {
+    for (int a = 0; a < S; ++a)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_chunk[a])), "n"(kTcLines));
     for (int a = 0; a < kTcND; ++a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(kTcLines));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma[a])));
@@ -338,15 +366,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int qs = iq0 + (ic < G::P ? NT * ic : 2 * G::RA + NT * (ic - G::P));
         const bool inside = qs >= qlo && qs + NT - 1 <= qhi;  // no clamping in this chunk
         if (XAXIS) {
-          if (vec && inside) {  // 16 bytes per copy: NT / 4 lanes per row
-            constexpr int LPR = NT / 4, RPI = 32 / LPR;  // lanes per row, rows per instruction
-            const int sub = lane / LPR, qq = lane % LPR;
-#pragma unroll
-            for (int i2 = 0; i2 < 32 / RPI; ++i2) {
-              const int row = 32 * wq + RPI * i2 + sub;
-              cp_async16(smem_u32(rb + row * G::XS + 4 * qq), sSrc[row] + qs + 4 * qq);
-            }
+          const uint32_t cb = smem_u32(&bar_chunk[k_issue % S]);
+          const int a = max(qs, qlo), b = min(qs + NT - 1, qhi);  // the chunk's part inside the box
+          if ((vec & 1) && b >= a) {  // one bulk copy of that part of this thread's own row; the reader
+                                      // replicates the edge (start and length stay multiples of 4)
+            mbar_arrive_tx(cb, (b - a + 1) * 4);
+            bulk_g2s(smem_u32(rb + m * G::XS + (a - qs)), IU.src + a, (b - a + 1) * 4, cb);
           } else {
+            mbar_arrive(cb);
 #pragma unroll
             for (int h = 0; h < NT / 32; ++h) {
               const int rel = min(max(qs + 32 * h + lane, qlo), qhi);
@@ -355,7 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 cp_async4(smem_u32(rb + (32 * wq + i) * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
             }
           }
-        } else if (vec && inside) {  // 16 bytes (4 lines) per copy, within the warp's own 32 lines
+        } else if ((vec & 1) && inside) {  // 16 bytes (4 lines) per copy, within the warp's own 32 lines
                                      // (the stage hand-off is warp-local): lane -> lines
                                      // 32 wq + 4 (lane % 8).., positions lane / 8 + 4 i
           const int qd = lane & 7, pg = lane >> 3;
@@ -385,10 +412,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint32_t k = 0;  // chunks consumed
     bool go = true;
     for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
-      const int nt = decode(unit).nt;
+      const TcUnit CU = decode(unit);
+      const int nt = CU.nt;
+      const int q0u = CU.p0 - G::RA - alo;  // relative input position of window position 0
       for (int c = 0; c < G::P + nt; ++c, ++k) {
         cp_async_wait<S - 1>();  // chunk k has landed
         __syncwarp();            // and so have the other lanes' copies (each warp copies only its own lines)
+        if (XAXIS && !mbar_wait_or_abort(smem_u32(&bar_chunk[k % S]), (k / S) & 1u, &abort_flag)) {
+          abort_flag = 1;
+          go = false;
+          break;
+        }
         const float* rb = sRaw + (k % S) * RAWF;
         float v[NT];
         if (XAXIS) {
@@ -399,6 +433,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             v[j + 1] = f.y;
             v[j + 2] = f.z;
             v[j + 3] = f.w;
+          }
+          const int qs = q0u + (c < G::P ? NT * c : 2 * G::RA + NT * (c - G::P));
+          const int jlo = max(0, qlo - qs), jhi = min(NT - 1, qhi - qs);
+          if ((vec & 1) && jhi >= jlo) {  // a bulk chunk: positions outside the box take the edge value
+            if (jlo > 0 || jhi < NT - 1) {
+              const float elo = rb[m * G::XS + jlo], ehi = rb[m * G::XS + jhi];
+#pragma unroll
+              for (int j = 0; j < NT; ++j) v[j] = j < jlo ? elo : (j > jhi ? ehi : v[j]);
+            }
           }
         } else {
 #pragma unroll
@@ -496,21 +539,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int nlo = max(0, a_lo - pt), nhi = min(NT, a_end - pt);  // stored outputs [nlo, nhi)
         const int64_t off = pt - a_lo;
         if (XAXIS) {
+          bulk_s2g_read_done();  // this row's previous bulk store has read its source
+          __syncwarp();          // and the warp's transposed stores have read theirs
 #pragma unroll
-          for (int n = 0; n < NT; ++n) sTe[m * G::TE + n] = r[n];
-          __syncwarp();
+          for (int n = 0; n < NT; n += 4)
+            *reinterpret_cast<float4*>(sTe + m * G::TE + n) = make_float4(r[n], r[n + 1], r[n + 2], r[n + 3]);
+          if ((vec & 2) && nlo == 0 && nhi == NT) {  // a whole aligned tile: one bulk store per row
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (U.lok) bulk_s2g(U.dst + off, smem_u32(sTe + m * G::TE), NT * 4);
+          } else {
+            __syncwarp();
 #pragma unroll 4
-          for (int i = 0; i < 32; ++i) {
-            float* rd = sDst[32 * wq + i];
-            if (rd) {
+            for (int i = 0; i < 32; ++i) {
+              float* rd = sDst[32 * wq + i];
+              if (rd) {
 #pragma unroll
-              for (int h = 0; h < NT / 32; ++h) {
-                const int n = 32 * h + lane;
-                if (n >= nlo && n < nhi) rd[off + n] = sTe[(32 * wq + i) * G::TE + n];
+                for (int h = 0; h < NT / 32; ++h) {
+                  const int n = 32 * h + lane;
+                  if (n >= nlo && n < nhi) rd[off + n] = sTe[(32 * wq + i) * G::TE + n];
+                }
               }
             }
           }
-          __syncwarp();
         } else if (U.lok) {
           float* d = U.dst + off * U.ostride;
           if (nlo == 0 && nhi == NT) {
@@ -525,6 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   }
+  if (XAXIS && role == 1) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores complete
   // a CTA that gave up waits once more (bounded) for the last product it
   // committed before it releases the tensor memory, and reports itself
   __syncthreads();
@@ -569,10 +620,11 @@ struct TcLaunch {
     // 16-byte copies: the input rows start on 16-byte boundaries, and so do
     // the copied pieces (y / z: quads of whole line groups; x: the windows)
     const bool rows16 = ((uintptr_t)in % 16) == 0 && ib.n[0] % 4 == 0;
-    const bool vec = axis == 0 ? rows16 && ib.lo[0] % 4 == 0
+    const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0
                                : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0 && ob.n[0] % kTcLines == 0;
-    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::need(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg, vec ? 1 : 0,
-                                                                  taps);
+    const bool vout = axis == 0 && ((uintptr_t)out % 16) == 0 && ob.n[0] % 4 == 0 && ob.lo[0] % 4 == 0;
+    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::need(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg,
+                                                                  (vin ? 1 : 0) | (vout ? 2 : 0), taps);
     return cudaGetLastError();
   }
 };

@@ -2,7 +2,7 @@
 with TF32 split operands), called through the C ABI, against the FP64 oracle.
 
 CT_TUNE_TC_RHO selects, per plan, which axes run on the tensor cores (bit a
-for axis a; the library default is 4, the z pass); the oracle cases run each
+for axis a; the library default is 7, all three); the oracle cases run each
 single axis, all three and none (the FP32 stencils), so a wrong ring slot,
 band offset, transpose or clamp on any axis fails.  Tolerances are
 the FP32 stage tolerances of test_gpu_parity.py: the split keeps each product
