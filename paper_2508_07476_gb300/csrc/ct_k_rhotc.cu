@@ -82,6 +82,10 @@ struct TcGeom {
   static constexpr int need(bool xaxis) {
     return 2 * B_BYTES + stages(xaxis) * raw_floats(xaxis) * 4 + (xaxis ? kTcLines * TE * 4 + 2 * ROW_BYTES : 0);
   }
+  // dynamic shared memory requested: at least half an SM's (233472 bytes,
+  // 1 KB reserved per CTA), so that one CTA, holding all the tensor memory,
+  // is resident per SM
+  static constexpr int smem(bool xaxis) { return need(xaxis) > 233472 / 2 ? need(xaxis) : 233472 / 2; }
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -594,7 +598,7 @@ struct TcLaunch {
   static cudaError_t prepare() {
     if (ready) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcGeom<RR>::need(XAXIS));
+                                         TcGeom<RR>::smem(XAXIS));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
@@ -623,7 +627,7 @@ struct TcLaunch {
     const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0
                                : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0 && ob.n[0] % kTcLines == 0;
     const bool vout = axis == 0 && ((uintptr_t)out % 16) == 0 && ob.n[0] % 4 == 0 && ob.lo[0] % 4 == 0;
-    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::need(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg,
+    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::smem(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg,
                                                                   (vin ? 1 : 0) | (vout ? 2 : 0), taps);
     return cudaGetLastError();
   }
