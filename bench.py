@@ -281,7 +281,9 @@ def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int):
 # DRAM bytes per output voxel of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch / voxels of the
 # capture); valid only for the kernel version summarised in the named file.
-MEASURED_TRAFFIC = {"rho_xy": (45.0, "profiles/kernels_annulus256.md")}
+MEASURED_TRAFFIC = {"rho_x_tc": (45.0, "profiles/kernels_annulus256.md"),
+                    "rho_y_tc": (44.8, "profiles/kernels_annulus256.md"),
+                    "rho_z_tc": (44.9, "profiles/kernels_annulus256.md")}
 
 
 def run_ours(args):
@@ -420,8 +422,10 @@ def run_ours(args):
                                    f"{sm_mhz_max:.0f} MHz ({peak_kind} sm_max_mhz)"}
     else:
         ach = byts / avg_s / 1e9
+        tr = MEASURED_TRAFFIC.get(dom)
         roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None if tr is None else tr[0] * nvox,
+                    "traffic_source": None if tr is None else tr[1], "peak_source": f"{peak_kind} hbm_gbs"}
     # the launched kernel sequence's own floor: its algorithmic HBM bytes per voxel
     path_bytes = sum(_kernel_algorithmic(k, 1, rs, rr)[1] * km[k]["launches"] / args.steps for k in km)
     path_hbm = {"voxels_per_s_roofline": peaks["hbm_gbs"] * 1e9 / path_bytes, "bytes_per_voxel": path_bytes,
