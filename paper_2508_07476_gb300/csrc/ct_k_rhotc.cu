@@ -41,7 +41,10 @@
 // coalesced per-element copies and a padded shared-memory transpose.
 // Every wait is bounded; a CTA that gives up raises a flag that ends the other
 // roles' waits, drains its MMAs and releases the tensor memory.
+#include <cuda.h>  // CUtensorMap and its enums; the encoder is fetched from the driver at run time
+
 #include <algorithm>
+#include <cstring>
 
 #include "ct_common.cuh"
 #include "ct_launch.h"
@@ -76,11 +79,17 @@ struct TcGeom {
   static constexpr int XS = NT + 4;  // x-form chunk row: 16-byte aligned, conflict-free by line
   static constexpr int TE = NT + 4;  // x-form output row: 16-byte aligned, float4 writes conflict-free
   static constexpr int ROW_BYTES = kTcLines * 8;
-  // one chunk: y / z [NT positions][128 lines]; x [128 lines][XS]
-  static constexpr int raw_floats(bool xaxis) { return xaxis ? kTcLines * XS : NT * kTcLines; }
+  // x form: each warp owns one 1024-byte-aligned slice of a chunk stage or of the
+  // output buffer, whichever layout a chunk uses (32 padded rows of XS floats, or
+  // NT / 32 swizzled 32 x 32 boxes), so that every hand-off stays within the warp
+  static constexpr int WS = (32 * XS * 4 + 1023) / 1024 * 1024;
+  // one chunk: y / z [NT positions][128 lines]; x four warp slices
+  static constexpr int raw_floats(bool xaxis) { return xaxis ? 4 * WS / 4 : NT * kTcLines; }
   static constexpr int stages(bool xaxis) { return xaxis ? 3 : 4; }  // chunks in flight
+  static_assert((2 * B_BYTES) % 1024 == 0 && NT * 32 * 4 <= WS && TE == XS, "x-form slices");
   static constexpr int need(bool xaxis) {
-    return 2 * B_BYTES + stages(xaxis) * raw_floats(xaxis) * 4 + (xaxis ? kTcLines * TE * 4 + 2 * ROW_BYTES : 0);
+    return 1024 + 2 * B_BYTES + stages(xaxis) * raw_floats(xaxis) * 4 +
+           (xaxis ? 4 * WS + 2 * ROW_BYTES : 0);  // + slack to align the base to 1024 bytes
   }
   // dynamic shared memory requested: at least half an SM's (233472 bytes,
   // 1 KB reserved per CTA), so that one CTA, holding all the tensor memory,
@@ -111,6 +120,27 @@ __device__ __forceinline__ void bulk_s2g(float* gdst, uint32_t smem_src, uint32_
 
 // This thread's bulk stores have read their shared-memory source.
 __device__ __forceinline__ void bulk_s2g_read_done() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Tensor (TMA) copies of a 3-D box (x, row, component), completing on an mbarrier / bulk group.
+__device__ __forceinline__ void tma_load3(uint32_t smem_dst, const CUtensorMap* map, int x, int y, int z,
+                                          uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(smem_dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, int x, int y, int z, uint32_t smem_src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(smem_src)
+               : "memory");
+}
+
+// Byte offset of float x (0..31) of row r (0..31) in a 32 x 32 box stored with
+// the 128-byte swizzle (16-byte chunk index XOR row mod 8; 1024-byte aligned).
+__device__ __forceinline__ int swz(int r, int x) { return r * 128 + ((((x >> 2) ^ r) & 7) << 4) + ((x & 3) << 2); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; lbo = byte stride of
 // core matrices along K, sbo = along M/N.
@@ -230,23 +260,26 @@ struct TcUnit {
 // meet the same k-steps whatever box it is computed in: chunked runs
 // reproduce the whole-volume result bit for bit.  vec: bit 0, the input box
 // allows 16-byte copies; bit 1 (x form), the output rows start on 16-byte
-// boundaries (both checked on the host).
+// boundaries; bits 2 / 3 (x form), tin / tout map the 128-row groups as
+// (x, row, component) boxes of the input / output (all checked on the host).
 template <int RR, bool XAXIS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
-             int vec, const __grid_constant__ Taps taps) {
+             int vec, const __grid_constant__ Taps taps, const __grid_constant__ CUtensorMap tin,
+             const __grid_constant__ CUtensorMap tout) {
   using G = TcGeom<RR>;
   constexpr int NT = G::NT;
   constexpr int S = G::stages(XAXIS);
   constexpr int RAWF = G::raw_floats(XAXIS);
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* sBhi = reinterpret_cast<float*>(smem);
   float* sBlo = reinterpret_cast<float*>(smem + G::B_BYTES);
   float* sRaw = reinterpret_cast<float*>(smem + 2 * G::B_BYTES);
   unsigned char* xs = smem + 2 * G::B_BYTES + S * RAWF * 4;  // x form only
   float* sTe = reinterpret_cast<float*>(xs);
-  const float** sSrc = reinterpret_cast<const float**>(xs + kTcLines * G::TE * 4);
-  float** sDst = reinterpret_cast<float**>(xs + kTcLines * G::TE * 4 + G::ROW_BYTES);
+  const float** sSrc = reinterpret_cast<const float**>(xs + 4 * G::WS);
+  float** sDst = reinterpret_cast<float**>(xs + 4 * G::WS + G::ROW_BYTES);
   __shared__ __align__(8) uint64_t bar_chunk[4];        // x form: chunk stage s has landed
   __shared__ __align__(8) uint64_t bar_staged[kTcND];  // the producers have staged tile g
   __shared__ __align__(8) uint64_t bar_mma[kTcND];     // tile g's product is in D[g % kTcND]
@@ -306,6 +339,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int64_t n_units = n_groups * ((a_end - a_first + seg - 1) / seg);
   const int alo = ib.lo[axis], an = ib.n[axis];
   const int qlo = max(0, alo) - alo, qhi = min(dim_axis - 1, alo + an - 1) - alo;  // clamp range, relative
+  // x form with tensor maps: a group's rows are contiguous rows of the (x, row, component) views
+  const int64_t rows_pc = (int64_t)ob.n[1] * ob.n[2];                  // output rows per component
+  const int64_t row_off = (int64_t)(ob.lo[2] - ib.lo[2]) * ib.n[1];    // input row of output row 0
 
   auto decode = [&](int64_t unit) {
     TcUnit U;
@@ -372,10 +408,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (XAXIS) {
           const uint32_t cb = smem_u32(&bar_chunk[k_issue % S]);
           const int a = max(qs, qlo), b = min(qs + NT - 1, qhi);  // the chunk's part inside the box
-          if ((vec & 1) && b >= a) {  // one bulk copy of that part of this thread's own row; the reader
+          if ((vec & 4) && inside) {  // two swizzled 32 x 32 boxes per warp, issued by one lane
+            if (lane == 0) {
+              const int64_t r0 = (iu % n_groups) * kTcLines + 32 * wq;  // the warp's first output row
+              const int row = (int)(row_off + r0 % rows_pc), comp = (int)(r0 / rows_pc);
+              mbar_arrive_tx(cb, NT * 32 * 4);
+#pragma unroll
+              for (int h = 0; h < NT / 32; ++h)
+                tma_load3(smem_u32(reinterpret_cast<unsigned char*>(rb) + wq * G::WS + h * 4096), &tin,
+                          qs + 32 * h, row, comp, cb);
+            } else {
+              mbar_arrive(cb);
+            }
+          } else if ((vec & 1) && b >= a) {  // one bulk copy of that part of this thread's own row; the reader
                                       // replicates the edge (start and length stay multiples of 4)
             mbar_arrive_tx(cb, (b - a + 1) * 4);
-            bulk_g2s(smem_u32(rb + m * G::XS + (a - qs)), IU.src + a, (b - a + 1) * 4, cb);
+            bulk_g2s(smem_u32(rb + wq * (G::WS / 4) + lane * G::XS + (a - qs)), IU.src + a, (b - a + 1) * 4, cb);
           } else {
             mbar_arrive(cb);
 #pragma unroll
@@ -383,7 +431,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               const int rel = min(max(qs + 32 * h + lane, qlo), qhi);
 #pragma unroll
               for (int i = 0; i < 32; ++i)
-                cp_async4(smem_u32(rb + (32 * wq + i) * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
+                cp_async4(smem_u32(rb + wq * (G::WS / 4) + i * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
             }
           }
         } else if ((vec & 1) && inside) {  // 16 bytes (4 lines) per copy, within the warp's own 32 lines
@@ -430,19 +478,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const float* rb = sRaw + (k % S) * RAWF;
         float v[NT];
         if (XAXIS) {
+          const int qs = q0u + (c < G::P ? NT * c : 2 * G::RA + NT * (c - G::P));
+          const int jlo = max(0, qlo - qs), jhi = min(NT - 1, qhi - qs);
+          const bool tma = (vec & 4) && jlo == 0 && jhi == NT - 1;
 #pragma unroll
           for (int j = 0; j < NT; j += 4) {
-            const float4 f = *reinterpret_cast<const float4*>(rb + m * G::XS + j);
+            const float* src4 = tma ? reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(rb) +
+                                                                   wq * G::WS + (j / 32) * 4096 + swz(lane, j & 31))
+                                    : rb + wq * (G::WS / 4) + lane * G::XS + j;
+            const float4 f = *reinterpret_cast<const float4*>(src4);
             v[j] = f.x;
             v[j + 1] = f.y;
             v[j + 2] = f.z;
             v[j + 3] = f.w;
           }
-          const int qs = q0u + (c < G::P ? NT * c : 2 * G::RA + NT * (c - G::P));
-          const int jlo = max(0, qlo - qs), jhi = min(NT - 1, qhi - qs);
-          if ((vec & 1) && jhi >= jlo) {  // a bulk chunk: positions outside the box take the edge value
+          if (!tma && (vec & 1) && jhi >= jlo) {  // a bulk chunk: positions outside the box take the edge value
             if (jlo > 0 || jhi < NT - 1) {
-              const float elo = rb[m * G::XS + jlo], ehi = rb[m * G::XS + jhi];
+              const float* row = rb + wq * (G::WS / 4) + lane * G::XS;
+              const float elo = row[jlo], ehi = row[jhi];
 #pragma unroll
               for (int j = 0; j < NT; ++j) v[j] = j < jlo ? elo : (j > jhi ? ehi : v[j]);
             }
@@ -543,14 +596,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int nlo = max(0, a_lo - pt), nhi = min(NT, a_end - pt);  // stored outputs [nlo, nhi)
         const int64_t off = pt - a_lo;
         if (XAXIS) {
-          bulk_s2g_read_done();  // this row's previous bulk store has read its source
+          bulk_s2g_read_done();  // this thread's previous bulk stores have read their source
           __syncwarp();          // and the warp's transposed stores have read theirs
+          if ((vec & 8) && nlo == 0 && nhi == NT) {  // a whole tile: two swizzled box stores per warp
+            unsigned char* eb = reinterpret_cast<unsigned char*>(sTe) + wq * G::WS;
+#pragma unroll
+            for (int n = 0; n < NT; n += 4)
+              *reinterpret_cast<float4*>(eb + (n / 32) * 4096 + swz(lane, n & 31)) =
+                  make_float4(r[n], r[n + 1], r[n + 2], r[n + 3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              const int64_t r0 = (unit % n_groups) * kTcLines + 32 * wq;
+#pragma unroll
+              for (int h = 0; h < NT / 32; ++h)
+                tma_store3(&tout, pt - ob.lo[0] + 32 * h, (int)(r0 % rows_pc), (int)(r0 / rows_pc),
+                           smem_u32(eb + h * 4096));
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+            continue;
+          }
+          float* er = sTe + wq * (G::WS / 4);  // this warp's slice: its 32 rows at stride TE
 #pragma unroll
           for (int n = 0; n < NT; n += 4)
-            *reinterpret_cast<float4*>(sTe + m * G::TE + n) = make_float4(r[n], r[n + 1], r[n + 2], r[n + 3]);
+            *reinterpret_cast<float4*>(er + lane * G::TE + n) = make_float4(r[n], r[n + 1], r[n + 2], r[n + 3]);
           if ((vec & 2) && nlo == 0 && nhi == NT) {  // a whole aligned tile: one bulk store per row
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (U.lok) bulk_s2g(U.dst + off, smem_u32(sTe + m * G::TE), NT * 4);
+            if (U.lok) bulk_s2g(U.dst + off, smem_u32(er + lane * G::TE), NT * 4);
           } else {
             __syncwarp();
 #pragma unroll 4
@@ -560,7 +632,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int h = 0; h < NT / 32; ++h) {
                   const int n = 32 * h + lane;
-                  if (n >= nlo && n < nhi) rd[off + n] = sTe[(32 * wq + i) * G::TE + n];
+                  if (n >= nlo && n < nhi) rd[off + n] = er[i * G::TE + n];
                 }
               }
             }
@@ -590,6 +662,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "n"(G::TCOLS));
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder (nullptr if the driver does not offer it).
+EncodeTiled tensor_map_encoder() {
+  static const EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiled) nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// 6 planes over box b seen as (x, row = (z, y) flattened, component), in 32 x 32
+// boxes with the 128-byte swizzle.  False if the encoder refuses.
+bool rows_map(CUtensorMap* map, const float* base, const Box& b) {
+  const EncodeTiled enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)b.n[0], (cuuint64_t)b.n[1] * b.n[2], 6};
+  const cuuint64_t strides[2] = {(cuuint64_t)b.n[0] * 4, (cuuint64_t)box_vox(b) * 4};
+  const cuuint32_t box[3] = {32, 32, 1}, estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int RR, bool XAXIS>
@@ -627,8 +729,18 @@ struct TcLaunch {
     const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0
                                : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0 && ob.n[0] % kTcLines == 0;
     const bool vout = axis == 0 && ((uintptr_t)out % 16) == 0 && ob.n[0] % 4 == 0 && ob.lo[0] % 4 == 0;
-    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::smem(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg,
-                                                                  (vin ? 1 : 0) | (vout ? 2 : 0), taps);
+    int flags = (vin ? 1 : 0) | (vout ? 2 : 0);
+    // x form: tensor maps when each 128-row group is 128 consecutive rows of one component,
+    // in the input box (its y extent is the output's) and in the output box
+    CUtensorMap tin, tout;
+    std::memset(&tin, 0, sizeof tin);
+    std::memset(&tout, 0, sizeof tout);
+    if (axis == 0 && ((int64_t)ob.n[1] * ob.n[2]) % kTcLines == 0) {
+      if (vin && ob.lo[1] == ib.lo[1] && ob.n[1] == ib.n[1] && rows_map(&tin, in, ib)) flags |= 4;
+      if (vout && rows_map(&tout, out, ob)) flags |= 8;
+    }
+    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::smem(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg, flags, taps,
+                                                                  tin, tout);
     return cudaGetLastError();
   }
 };

@@ -54,7 +54,8 @@ def _rel(S, S_o):
 @pytest.mark.parametrize("mask", MASKS)
 @pytest.mark.parametrize("shape,sigma,rho", [((23, 29, 37), 1.0, 1.0), ((9, 8, 130), 0.8, 1.7),
                                              ((40, 17, 70), 1.5, 3.0), ((70, 33, 45), 2.0, 6.0),
-                                             ((20, 150, 11), 1.0, 9.0), ((40, 24, 256), 2.0, 6.0)])
+                                             ((20, 150, 11), 1.0, 9.0), ((40, 24, 256), 2.0, 6.0),
+                                             ((16, 64, 256), 1.0, 3.0)])  # last: x rows through tensor maps
 def test_tc_structure_tensor_ragged(tc, mask, shape, sigma, rho):
     tc(mask)
     vol = _rand_vol(shape, seed=sum(shape))
