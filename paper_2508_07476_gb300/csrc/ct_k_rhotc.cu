@@ -55,7 +55,10 @@ namespace {
 
 constexpr int kTcLines = 128;                  // = M: producer thread / TMEM lane m owns line m
 constexpr int kTcThreads = 2 * kTcLines + 32;  // producer warps 0-3, epilogue warps 4-7, MMA warp 8
-constexpr int kTcND = 2;                       // accumulators: tile t + 1's product runs while tile t is read
+constexpr int kTcNB = 4;                       // mbarriers per hand-off, used by tiles g mod 4 in turn
+#ifndef CT_TC_BIG_RING
+#define CT_TC_BIG_RING 1  // tuning: 0 restarts a W + NT ring at every work unit
+#endif
 constexpr uint32_t kTcWaitLimit = 1u << 20;    // mbarrier polls before a CTA gives up
 constexpr uint32_t kTcSuspendNs = 500;         // a waiting thread sleeps up to this long per poll
 
@@ -67,14 +70,23 @@ struct TcGeom {
   static constexpr int RA = (RR + 3) / 4 * 4;    // window margin: W is a multiple of 8
   static constexpr int NT = RR <= 32 ? 64 : 32;  // outputs per tile (MMA N)
   static constexpr int W = NT + 2 * RA;          // window positions of a tile
-  static constexpr int WR = W + NT;              // ring positions
   static constexpr int KCB = W / 4;              // core-matrix columns of B
   static constexpr int KS = W / 8;               // k-steps per tile
   static constexpr int P = (2 * RA + NT - 1) / NT;  // NT-position chunks that fill the ring
-  static constexpr int LO = WR;                     // tensor memory: A_hi ring, A_lo ring, kTcND D
+  // The ring runs on across work units (window positions numbered globally)
+  // when it can hold the last two windows of one unit plus the halo and first
+  // tile of the next, beside two accumulators: then no unit start waits for
+  // the previous unit's last products.  Otherwise it restarts at every unit,
+  // after those products (at R = 24 the longer ring would leave room for one
+  // accumulator only, which measured slower: 1.21 / 1.17 vs 1.12 / 1.13 ms
+  // for the y / z passes at 512^3).
+  static constexpr bool BIG = CT_TC_BIG_RING && P == 1 && 2 * (W + NT + 2 * RA) + 2 * NT <= 512;
+  static constexpr int WR = BIG ? W + NT + 2 * RA : W + NT;  // ring positions
+  static constexpr int ND = 2 * WR + 2 * NT <= 512 ? 2 : 1;   // accumulators
+  static constexpr int LO = WR;                              // tensor memory: A_hi ring, A_lo ring, ND D
   static constexpr int DCOL = 2 * WR;
   static constexpr int TCOLS = 512;  // one CTA per SM holds all of it
-  static_assert(DCOL + kTcND * NT <= TCOLS, "tensor memory");
+  static_assert(DCOL + ND * NT <= TCOLS && WR % 8 == 0, "tensor memory");
   static constexpr int B_BYTES = NT * W * 4;
   static constexpr int XS = NT + 4;  // x-form chunk row: 16-byte aligned, conflict-free by line
   static constexpr int TE = NT + 4;  // x-form output row: 16-byte aligned, float4 writes conflict-free
@@ -281,9 +293,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const float** sSrc = reinterpret_cast<const float**>(xs + 4 * G::WS);
   float** sDst = reinterpret_cast<float**>(xs + 4 * G::WS + G::ROW_BYTES);
   __shared__ __align__(8) uint64_t bar_chunk[4];        // x form: chunk stage s has landed
-  __shared__ __align__(8) uint64_t bar_staged[kTcND];  // the producers have staged tile g
-  __shared__ __align__(8) uint64_t bar_mma[kTcND];     // tile g's product is in D[g % kTcND]
-  __shared__ __align__(8) uint64_t bar_dfree[kTcND];   // the epilogue has read D[a]
+  __shared__ __align__(8) uint64_t bar_staged[kTcNB];  // the producers have staged tile g
+  __shared__ __align__(8) uint64_t bar_mma[kTcNB];     // tile g's product is in D[g % ND]
+  __shared__ __align__(8) uint64_t bar_dfree[kTcNB];   // the epilogue has read tile g's D
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -304,7 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int a = 0; a < S; ++a)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_chunk[a])), "n"(kTcLines));
-    for (int a = 0; a < kTcND; ++a) {
+    for (int a = 0; a < kTcNB; ++a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(kTcLines));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma[a])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[a])), "n"(kTcLines));
@@ -324,10 +336,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tm = tmem_base;
   const uint32_t tlane = tm + ((uint32_t)(wq * 32) << 16);  // this warp's 32 lanes
   // mbarriers of tile g, and the parity of its phase
-  auto staged_bar = [&](uint32_t g) { return smem_u32(&bar_staged[g % kTcND]); };
-  auto mma_bar = [&](uint32_t g) { return smem_u32(&bar_mma[g % kTcND]); };
-  auto dfree_bar = [&](uint32_t g) { return smem_u32(&bar_dfree[g % kTcND]); };
-  auto par = [](uint32_t g) { return (g / kTcND) & 1u; };
+  auto staged_bar = [&](uint32_t g) { return smem_u32(&bar_staged[g % kTcNB]); };
+  auto mma_bar = [&](uint32_t g) { return smem_u32(&bar_mma[g % kTcNB]); };
+  auto dfree_bar = [&](uint32_t g) { return smem_u32(&bar_dfree[g % kTcNB]); };
+  auto par = [](uint32_t g) { return (g / kTcNB) & 1u; };
 
   // line groups and segments
   const int a_lo = ob.lo[axis], a_end = ob.lo[axis] + ob.n[axis];
@@ -463,9 +475,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int i = 0; i < S; ++i) issue_next();
     uint32_t k = 0;  // chunks consumed
     bool go = true;
+    int gbase = 0;  // ring position of this unit's window position 0 (continuous ring: runs on)
+    int ws1 = 0, ws2 = 0, ws3 = 0, ws4 = 0;  // continuous ring: window starts of tiles g-1 .. g-4
     for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
       const TcUnit CU = decode(unit);
       const int nt = CU.nt;
+      if (!G::BIG) gbase = 0;
       const int q0u = CU.p0 - G::RA - alo;  // relative input position of window position 0
       for (int c = 0; c < G::P + nt; ++c, ++k) {
         cp_async_wait<S - 1>();  // chunk k has landed
@@ -507,8 +522,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();  // every lane has read the stage before it is refilled
         issue_next();
         const int t = c - G::P;  // tile of this chunk (< 0: ring fill)
+        const int q = c < G::P ? NT * c : 2 * G::RA + NT * t;
+        const int nw = c < G::P ? min(NT, 2 * G::RA - q) : NT;  // positions written (a fill chunk: its halo part)
         bool ok = true;
-        if (c == 0) {  // the ring restarts: every MMA of the previous unit must have read it
+        if (G::BIG) {
+          // the slots of positions [gbase + q, + nw) last held positions WR lower: wait for the
+          // latest tile whose window starts below their end (window starts increase; it is
+          // never more than four tiles back)
+          const int lim = gbase + q + nw - G::WR;
+          int back = 0;
+          if (g >= 1 && ws1 < lim)
+            back = 1;
+          else if (g >= 2 && ws2 < lim)
+            back = 2;
+          else if (g >= 3 && ws3 < lim)
+            back = 3;
+          else if (g >= 4 && ws4 < lim)
+            back = 4;
+          if (back) ok = mbar_wait_or_abort(mma_bar(g - back), par(g - back), &abort_flag);
+        } else if (c == 0) {  // the ring restarts: every MMA of the previous unit must have read it
           if (g >= 1) ok = mbar_wait_or_abort(mma_bar(g - 1), par(g - 1), &abort_flag);
           if (g >= 2) ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag) && ok;
         } else if (t >= 2) {  // tile t's positions take the slots that only tiles up to t - 2 read
@@ -521,10 +553,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // split and write both rings (slots mod WR)
-        const int q = c < G::P ? NT * c : 2 * G::RA + NT * t;
 #pragma unroll
         for (int cc = 0; cc < NT / 8; ++cc) {
-          const int slot = (q + 8 * cc) % G::WR;
+          if (8 * cc >= nw) break;  // uniform across the warp
+          const int slot = (gbase + q + 8 * cc) % G::WR;
           float hi[8], lo[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -538,8 +570,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(staged_bar(g));
+        ws4 = ws3;
+        ws3 = ws2;
+        ws2 = ws1;
+        ws1 = gbase + NT * t;
         ++g;
       }
+      gbase += 2 * G::RA + NT * nt;
     }
     cp_async_wait<0>();  // no copy is left in flight
   } else if (role == 2) {
@@ -547,20 +584,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint64_t blo_d = umma_desc(smem_u32(sBlo), 128, G::KCB * 128);
     constexpr uint32_t kIdesc = idesc_tf32(kTcLines, NT);
     bool go = true;
+    int gbase = 0;
     for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
       const int nt = decode(unit).nt;
+      if (!G::BIG) gbase = 0;
       for (int t = 0; t < nt; ++t, ++g) {
-        // the tile is staged, and D[g % kTcND] has been read (tile g - kTcND)
+        // the tile is staged, and D[g % ND] has been read (tile g - ND)
         bool ok = mbar_wait_or_abort(staged_bar(g), par(g), &abort_flag);
-        if (ok && g >= kTcND) ok = mbar_wait_or_abort(dfree_bar(g - kTcND), par(g - kTcND), &abort_flag);
+        if (ok && g >= G::ND) ok = mbar_wait_or_abort(dfree_bar(g - G::ND), par(g - G::ND), &abort_flag);
         if (!__all_sync(0xffffffffu, ok)) {
           abort_flag = 1;
           go = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tm + G::DCOL + (g % kTcND) * NT;
-        int slot = (NT * t) % G::WR;
+        const uint32_t d = tm + G::DCOL + (g % G::ND) * NT;
+        int slot = (gbase + NT * t) % G::WR;
 #pragma unroll
         for (int ks = 0; ks < G::KS; ++ks) {
           const uint64_t bo = (uint64_t)(ks * 16);  // 256 bytes per k-step, in 16-byte units
@@ -570,6 +609,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mma_commit(mma_bar(g));
         committed = g + 1;
       }
+      gbase += 2 * G::RA + NT * nt;
     }
   } else {
     bool go = true;
@@ -589,7 +629,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float r[NT];
 #pragma unroll
-        for (int h = 0; h < NT / 32; ++h) tmem_ld32(tlane + G::DCOL + (g % kTcND) * NT + 32 * h, r + 32 * h);
+        for (int h = 0; h < NT / 32; ++h) tmem_ld32(tlane + G::DCOL + (g % G::ND) * NT + 32 * h, r + 32 * h);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(dfree_bar(g));
         const int pt = U.p0 + NT * t;  // absolute position of output 0 of the tile
