@@ -194,6 +194,8 @@ struct ct_plan_s {
   bool fuse_xy = true;      // x and y passes in one kernel, or two (tuning choice)
   bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
   int tc_rho = 7;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
+  int tc_min_r = 24;        // ... for rho radii of at least this (tuning choice)
+  bool tc_any_box = false;  // ... and volumes of any x extent (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -359,6 +361,21 @@ Fallback fallback_of(ct_plan P, int slot) {
     (P)->stats.launches += 1;                                               \
   } while (0)
 
+// Whether the rho pass along axis of a volume dims[] runs on the tensor cores:
+// a function of the plan, the volume's extent and the scale, never of the box,
+// so that every chunk and sub-box of a volume takes the same arithmetic as the
+// whole and their results agree bit for bit.  Those passes are bound by HBM at
+// 48 B per voxel when the boxes allow 16-byte copies (x extents of 4-voxel
+// multiples; for y and z, of whole 128-line groups) and several times slower
+// otherwise; the FP32 stencils cost 6 (2R+1) FMAs per voxel and pass, so
+// below R ~ 17 they are the faster.  Measured on 200 uneven crops (R = 8..32,
+// x extents 64..384, mostly unaligned): all stencils 7.2e9 voxels/s, all
+// tensor cores 6.0e9, tensor cores for R = 32 only 7.0e9.  tc_any_box drops
+// the extent condition (tests drive every copy path with it).
+bool use_tc(const ct_plan P, const Scale& sc, const int dims[3], int axis) {
+  return (P->tc_rho >> axis & 1) && sc.rkr >= P->tc_min_r && (P->tc_any_box || rho_tc_volume_aligned(dims[0], axis));
+}
+
 // Gradient, products and the x, y passes of rho: J over G (first buffer), then
 // S_xy over Bxy (returned with its box; the second buffer when x and y are
 // fused, the first otherwise).  vol covers vb.
@@ -390,25 +407,24 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
     CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts[0], sc.rks, mixed, st),
               "gradient kernel launch");
   }
-  if (P->tc_rho & 3) {  // x and y as separate passes, each on the tensor cores or the FP32 stencil
-    if (P->tc_rho & 1)
+  // x and y on the tensor cores together, or as one fused FP32 stencil; a mask
+  // that selects one of the two axes (tuning, tests) runs them as separate passes
+  const bool tcx = use_tc(P, sc, dims, 0), tcy = use_tc(P, sc, dims, 1);
+  const bool one_axis = (P->tc_rho & 3) == 1 || (P->tc_rho & 3) == 2;
+  if ((tcx && tcy) || (one_axis && (tcx || tcy)) || !P->fuse_xy) {
+    if (tcx)
       CT_LAUNCH(P, st, "rho_x_tc", launch_rho_tc(A, G, dims, B, Bx, 0, sc.tr[0], sc.rkr, st), "rho x kernel launch");
     else
       CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr[0], sc.rkr, st), "rho x kernel launch");
-    if (P->tc_rho & 2)
+    if (tcy)
       CT_LAUNCH(P, st, "rho_y_tc", launch_rho_tc(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, st), "rho y kernel launch");
     else
       CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
                 "rho y kernel launch");
     *Sxy = A;
-  } else if (P->fuse_xy) {
+  } else {
     CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr[0], sc.tr[1], sc.rkr, st), "rho xy kernel launch");
     *Sxy = B;
-  } else {
-    CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr[0], sc.rkr, st), "rho x kernel launch");
-    CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
-              "rho y kernel launch");
-    *Sxy = A;
   }
   *Bxy_out = Bxy;
   return CT_OK;
@@ -417,7 +433,7 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
 // The z pass of rho: S (6 planes over ob) from S_xy (6 planes over Bxy).
 ct_status z_pass(ct_plan P, const Scale& sc, const int dims[3], const float* Sxy, const Box& Bxy, float* S,
                  const Box& ob, cudaStream_t st) {
-  if (P->tc_rho & 4)
+  if (use_tc(P, sc, dims, 2))
     CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, st), "rho z kernel launch");
   else
     CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
@@ -534,6 +550,8 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_FUSE_XY")) P->fuse_xy = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_SPLIT_GRAD")) P->split_grad = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_RHO")) P->tc_rho = std::atoi(e) & 7;
+  if (const char* e = std::getenv("CT_TUNE_TC_ANY_BOX")) P->tc_any_box = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_TC_MIN_R")) P->tc_min_r = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;

@@ -831,6 +831,8 @@ cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], flo
   }
 }
 
+bool rho_tc_volume_aligned(int nx, int axis) { return axis == 0 ? nx % 4 == 0 : nx % kTcLines == 0; }
+
 unsigned int tc_timeouts(bool reset) {
   unsigned int v = 0;
   if (cudaMemcpyFromSymbol(&v, g_tc_timeouts, sizeof v) != cudaSuccess) return 0;

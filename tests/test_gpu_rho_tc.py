@@ -2,7 +2,8 @@
 with TF32 split operands), called through the C ABI, against the FP64 oracle.
 
 CT_TUNE_TC_RHO selects, per plan, which axes run on the tensor cores (bit a
-for axis a; the library default is 7, all three); the oracle cases run each
+for axis a; the library default is 7, all three, for rho radii of 24 and up
+on volumes whose x extent suits 16-byte copies); the oracle cases run each
 single axis, all three and none (the FP32 stencils), so a wrong ring slot,
 band offset, transpose or clamp on any axis fails.  Tolerances are
 the FP32 stage tolerances of test_gpu_parity.py: the split keeps each product
@@ -33,8 +34,13 @@ def _ready():
 
 @pytest.fixture
 def tc(monkeypatch):
+    # the library picks the tensor cores for R >= 24 and volumes whose x extent
+    # suits the 16-byte copies; these tests force them (or the stencils, mask 0)
+    # at every radius and extent
     def use(mask):
         monkeypatch.setenv("CT_TUNE_TC_RHO", str(mask))
+        monkeypatch.setenv("CT_TUNE_TC_MIN_R", "0")
+        monkeypatch.setenv("CT_TUNE_TC_ANY_BOX", "1")
     return use
 
 
@@ -187,3 +193,38 @@ def test_tc_constant_volume_gives_zero_tensor(tc):
     st = G.stages(vol, 1.0, 3.0, (10, 10, 10), (0, 0, 1))
     assert np.all(st["S"] == 0.0)
     assert np.all(st["fa"] == 0.0)
+
+
+def _kernels_and_outputs(vol, sigma, rho, chunk=(0, 0, 0)):
+    nz, ny, nx = vol.shape
+    p = _lib.make_params(sigma, rho, (nx / 2, ny / 2, nz / 2), (0, 0, 1), FP32, chunk=chunk)
+    plan = _lib.ct_plan_create(p, (nx, ny, nz))
+    try:
+        _lib.ct_plan_profile(plan, True)
+        fa = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+        vec = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+        _lib.ct_run_chunks(plan, [_lib.make_item(G.dev_u16(vol), (nx, ny, nz), None, vec, None, None, fa)], False)
+        torch.cuda.synchronize()
+        _lib.ct_plan_sync(plan)
+        names = set(_lib.ct_plan_kernel_times(plan))
+    finally:
+        _lib.ct_plan_destroy(plan)
+    return names, vec.cpu().numpy(), fa.cpu().numpy()
+
+
+@pytest.mark.parametrize("nx,rho,expect_tc", [(128, 6.0, "xyz"), (256, 8.0, "xyz"), (100, 6.0, "x"),
+                                              (126, 6.0, ""), (128, 3.0, "")])
+def test_default_selection_is_per_volume(nx, rho, expect_tc):
+    # with the library's own settings the tensor cores take rho radii >= 24 on
+    # volumes whose x extent suits the 16-byte copies (x: multiples of 4, which
+    # alone keeps the fused x / y stencil; y / z: multiples of 128); chunks of
+    # any shape take the whole volume's passes and match it bit for bit
+    vol = _rand_vol((40, 36, nx), seed=nx)
+    names, v, fa = _kernels_and_outputs(vol, 1.0, rho)
+    tc_axes = "".join(a for a in "xyz" if f"rho_{a}_tc" in names)
+    assert tc_axes == ("xyz" if expect_tc == "xyz" else ""), names
+    assert ("rho_xy" in names) == (expect_tc != "xyz"), names
+    names_c, v_c, fa_c = _kernels_and_outputs(vol, 1.0, rho, chunk=(44, 20, 16))
+    assert {n for n in names_c if n.startswith("rho")} == {n for n in names if n.startswith("rho")}
+    np.testing.assert_array_equal(v_c, v)
+    np.testing.assert_array_equal(fa_c, fa)
