@@ -196,6 +196,7 @@ struct ct_plan_s {
   int tc_rho = 7;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
   int tc_min_r = 24;        // ... for rho radii of at least this (tuning choice)
   bool tc_any_box = false;  // ... and volumes of any x extent (tuning choice)
+  bool eig_compact = true;  // masked eigen stage over compacted inside voxels (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -484,7 +485,8 @@ ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mas
                     const EigOut& o, int slot, bool mixed, cudaStream_t st) {
   Fallback fb = fallback_of(P, slot);
   CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
-  CT_LAUNCH(P, st, "eig_angles", launch_eig_angles(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, st),
+  CT_LAUNCH(P, st, "eig_angles",
+            launch_eig_angles(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, P->eig_compact, st),
             "eigen kernel launch");
   CT_LAUNCH(P, st, "eig_resolve",
             launch_eig_angles_fallback(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, box_vox(ob), st),
@@ -551,6 +553,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_SPLIT_GRAD")) P->split_grad = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_RHO")) P->tc_rho = std::atoi(e) & 7;
   if (const char* e = std::getenv("CT_TUNE_TC_ANY_BOX")) P->tc_any_box = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_EIG_COMPACT")) P->eig_compact = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_MIN_R")) P->tc_min_r = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));

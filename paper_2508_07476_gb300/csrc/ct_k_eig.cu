@@ -138,6 +138,80 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
   write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
 
+// The masked form: a CTA of 256 threads takes kEigSpan consecutive voxels of
+// one row (voxel x0 + t + 256 k for thread t, so that the mask loads and the
+// fill stores stay coalesced), writes the fill outputs of those outside the
+// mask at once and lists the inside ones in shared memory, in x order (warp
+// ballots and a scan of the per-warp counts).  The eigen solve then runs over
+// the list, so that only the last warp of a row segment has idle lanes,
+// where a warp per 32 voxels would idle wherever the wall boundary cuts it.
+// Each voxel's arithmetic is that of k_eig_angles32; only the thread that
+// does it differs.
+constexpr int kEigSpanK = 2;
+constexpr int kEigSpan = 256 * kEigSpanK;
+
+template <int VT, int AT, int FT, bool PLAIN>
+__global__ void __launch_bounds__(256, CT_EIG_MINB)
+    k_eig_angles_compact(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
+                         Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
+  __shared__ uint16_t list[kEigSpan];
+  __shared__ int cnt[8 * kEigSpanK];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int x0 = ob.lo[0] + blockIdx.x * kEigSpan;
+  const int xend = ob.lo[0] + ob.n[0];
+  const int y = ob.lo[1] + blockIdx.y, z = ob.lo[2] + blockIdx.z;
+  unsigned in_bits[kEigSpanK];
+#pragma unroll
+  for (int k = 0; k < kEigSpanK; ++k) {
+    const int x = x0 + t + 256 * k;
+    const bool valid = x < xend;
+    const bool inside = valid && __ldg(mask + box_index32(mb, x, y, z)) != 0;
+    if (valid && !inside) {
+      float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
+      write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), false, F, x, y, z, l, v, fill);
+    }
+    in_bits[k] = __ballot_sync(0xffffffffu, inside);
+    if (lane == 0) cnt[k * 8 + warp] = __popc(in_bits[k]);
+  }
+  __syncthreads();
+  // exclusive scan of the 8 K counts, in (k, warp) order = x order, by warp 0
+  if (warp == 0) {
+    const int c = lane < 8 * kEigSpanK ? cnt[lane] : 0;
+    int incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += u;
+    }
+    if (lane < 8 * kEigSpanK) cnt[lane] = incl - c;
+    if (lane == 31) list[kEigSpan - 1] = (uint16_t)incl;  // the total, read before any list write below
+  }
+  __syncthreads();
+  const int total = list[kEigSpan - 1];
+  __syncthreads();
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+  for (int k = 0; k < kEigSpanK; ++k)
+    if (in_bits[k] >> lane & 1u) list[cnt[k * 8 + warp] + __popc(in_bits[k] & below)] = (uint16_t)(t + 256 * k);
+  __syncthreads();
+  const int ns = sb.n[0] * sb.n[1] * sb.n[2];
+  for (int i = t; i < total; i += 256) {
+    const int x = x0 + list[i];
+    const int si = box_index32(sb, x, y, z);
+    Sym3<float> s;
+    s.a = __ldg(S + si);
+    s.b = __ldg(S + ns + si);
+    s.c = __ldg(S + 2 * ns + si);
+    s.d = __ldg(S + 3 * ns + si);
+    s.e = __ldg(S + 4 * ns + si);
+    s.f = __ldg(S + 5 * ns + si);
+    float l[3], v[3];
+    if (!eig_closed<float>(s, l, v))
+      push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
+    write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
+  }
+}
+
 __global__ void __launch_bounds__(128)
     k_eig_angles_fallback(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
                           Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
@@ -163,7 +237,7 @@ static int grid_for(int64_t n, int threads) {
 
 cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, const uint8_t* mask, const Box& mb,
                               const Frame& F, float fill, const EigOut& o, bool mixed, const Fallback& fb,
-                              cudaStream_t st) {
+                              bool compact, cudaStream_t st) {
   int64_t n = box_vox(ob);
   if (n == 0) return cudaSuccess;
   const int rows = ob.n[1] * ob.n[2];
@@ -178,6 +252,25 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
     dim3 g3((ob.n[0] + nt - 1) / nt, ob.n[1], ob.n[2]);
     // unit voxels and a fixed centre take the plain frame
     const bool plain = F.sp[0] == 1.f && F.sp[1] == 1.f && F.sp[2] == 1.f && F.centres == nullptr;
+    if (mask != nullptr && compact) {
+      dim3 gc((ob.n[0] + kEigSpan - 1) / kEigSpan, ob.n[1], ob.n[2]);
+      if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32) {
+        if (plain)
+          k_eig_angles_compact<0, 0, 0, true><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+        else
+          k_eig_angles_compact<0, 0, 0, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+      } else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16) {
+        if (plain)
+          k_eig_angles_compact<1, 1, 1, true><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+        else
+          k_eig_angles_compact<1, 1, 1, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+      } else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16) {
+        k_eig_angles_compact<-1, 2, 1, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+      } else {
+        k_eig_angles_compact<-1, -1, -1, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+      }
+      return cudaGetLastError();
+    }
     if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32) {
       if (plain)
         k_eig_angles32<0, 0, 0, true><<<g3, nt, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);

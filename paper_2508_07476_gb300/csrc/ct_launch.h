@@ -95,9 +95,11 @@ cudaError_t launch_fallback_s(const Box& ob, const Frame& F, float fill, const E
 
 // Per-voxel eigen-solve + HA/IA/FA over ob from S (6 planes over sb); mask
 // array (nullable) covers mb.  Near-degenerate voxels are appended to fb.
+// compact: with a mask, each row segment lists its inside voxels first and
+// solves them with full warps (the same arithmetic per voxel).
 cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, const uint8_t* mask, const Box& mb,
                               const Frame& F, float fill, const EigOut& o, bool mixed, const Fallback& fb,
-                              cudaStream_t st);
+                              bool compact, cudaStream_t st);
 // Re-solve the listed voxels (FP32 Jacobi, or FP64 in the mixed form) and rewrite their outputs.
 cudaError_t launch_eig_angles_fallback(const float* S, const Box& sb, const Box& ob, const uint8_t* mask,
                                        const Box& mb, const Frame& F, float fill, const EigOut& o, bool mixed,
