@@ -260,12 +260,15 @@ __device__ __noinline__ void eig_jacobi(const Sym3<T>& s, T l[3], T v[3]) {
 }
 
 // Fractional anisotropy from eigenvalues clamped at zero; 0 for the zero tensor.
+// The square root is taken as q rsqrt(q) (within a few 1e-7 of it), since FA
+// is reported to far coarser than that.
 __device__ __forceinline__ float fa_of(const float l[3]) {
   float l1 = fmaxf(l[0], 0.f), l2 = fmaxf(l[1], 0.f), l3 = fmaxf(l[2], 0.f);
   float den = l1 * l1 + l2 * l2 + l3 * l3;
   if (den == 0.f) return 0.f;
   float num = (l1 - l2) * (l1 - l2) + (l2 - l3) * (l2 - l3) + (l3 - l1) * (l3 - l1);
-  return sqrtf(__fdividef(0.5f * num, den));
+  const float q = __fdividef(0.5f * num, den);
+  return q > 0.f ? q * rsqrtf(q) : 0.f;
 }
 
 // Cylindrical left-ventricle frame (unit axis, centre), per launch.

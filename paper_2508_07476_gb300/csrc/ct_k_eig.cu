@@ -174,25 +174,22 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
     if (lane == 0) cnt[k * 8 + warp] = __popc(in_bits[k]);
   }
   __syncthreads();
-  // exclusive scan of the 8 K counts, in (k, warp) order = x order, by warp 0
-  if (warp == 0) {
-    const int c = lane < 8 * kEigSpanK ? cnt[lane] : 0;
-    int incl = c;
+  // every warp scans the 8 K counts, in (k, warp) order = x order, itself
+  constexpr int NC = 8 * kEigSpanK;
+  const int c = lane < NC ? cnt[lane] : 0;
+  int incl = c;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= d) incl += u;
-    }
-    if (lane < 8 * kEigSpanK) cnt[lane] = incl - c;
-    if (lane == 31) list[kEigSpan - 1] = (uint16_t)incl;  // the total, read before any list write below
+  for (int d = 1; d < NC; d <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += u;
   }
-  __syncthreads();
-  const int total = list[kEigSpan - 1];
-  __syncthreads();
+  const int total = __shfl_sync(0xffffffffu, incl, NC - 1);
   const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-  for (int k = 0; k < kEigSpanK; ++k)
-    if (in_bits[k] >> lane & 1u) list[cnt[k * 8 + warp] + __popc(in_bits[k] & below)] = (uint16_t)(t + 256 * k);
+  for (int k = 0; k < kEigSpanK; ++k) {
+    const int base = __shfl_sync(0xffffffffu, incl - c, k * 8 + warp);
+    if (in_bits[k] >> lane & 1u) list[base + __popc(in_bits[k] & below)] = (uint16_t)(t + 256 * k);
+  }
   __syncthreads();
   const int ns = sb.n[0] * sb.n[1] * sb.n[2];
   for (int i = t; i < total; i += 256) {
