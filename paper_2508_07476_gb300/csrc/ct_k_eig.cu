@@ -147,8 +147,15 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
 // where a warp per 32 voxels would idle wherever the wall boundary cuts it.
 // Each voxel's arithmetic is that of k_eig_angles32; only the thread that
 // does it differs.
-constexpr int kEigSpanK = 2;
+#ifndef CT_EIG_SPAN_K
+#define CT_EIG_SPAN_K 2
+#endif
+#ifndef CT_EIG_ILP
+#define CT_EIG_ILP 1
+#endif
+constexpr int kEigSpanK = CT_EIG_SPAN_K;  // voxels per thread per segment (tuning choice)
 constexpr int kEigSpan = 256 * kEigSpanK;
+constexpr int kEigIlp = CT_EIG_ILP;       // list entries per thread whose tensors load together (tuning choice)
 
 template <int VT, int AT, int FT, bool PLAIN>
 __global__ void __launch_bounds__(256, CT_EIG_MINB)
@@ -192,20 +199,30 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
   }
   __syncthreads();
   const int ns = sb.n[0] * sb.n[1] * sb.n[2];
-  for (int i = t; i < total; i += 256) {
-    const int x = x0 + list[i];
-    const int si = box_index32(sb, x, y, z);
-    Sym3<float> s;
-    s.a = __ldg(S + si);
-    s.b = __ldg(S + ns + si);
-    s.c = __ldg(S + 2 * ns + si);
-    s.d = __ldg(S + 3 * ns + si);
-    s.e = __ldg(S + 4 * ns + si);
-    s.f = __ldg(S + 5 * ns + si);
-    float l[3], v[3];
-    if (!eig_closed<float>(s, l, v))
-      push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
-    write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
+  for (int i0 = t; i0 < total; i0 += 256 * kEigIlp) {
+    int xs[kEigIlp];
+    Sym3<float> s[kEigIlp];
+#pragma unroll
+    for (int u = 0; u < kEigIlp; ++u) {
+      const int i = i0 + 256 * u;
+      xs[u] = x0 + list[i < total ? i : i0];
+      const int si = box_index32(sb, xs[u], y, z);
+      s[u].a = __ldg(S + si);
+      s[u].b = __ldg(S + ns + si);
+      s[u].c = __ldg(S + 2 * ns + si);
+      s[u].d = __ldg(S + 3 * ns + si);
+      s[u].e = __ldg(S + 4 * ns + si);
+      s[u].f = __ldg(S + 5 * ns + si);
+    }
+#pragma unroll
+    for (int u = 0; u < kEigIlp; ++u) {
+      if (i0 + 256 * u >= total) break;
+      const int x = xs[u];
+      float l[3], v[3];
+      if (!eig_closed<float>(s[u], l, v))
+        push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
+      write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
+    }
   }
 }
 
