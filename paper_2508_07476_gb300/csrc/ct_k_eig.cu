@@ -138,31 +138,42 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
   write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
 
-// The masked form: a CTA of 256 threads takes kEigSpan consecutive voxels of
-// one row (voxel x0 + t + 256 k for thread t, so that the mask loads and the
-// fill stores stay coalesced), writes the fill outputs of those outside the
-// mask at once and lists the inside ones in shared memory, in x order (warp
-// ballots and a scan of the per-warp counts).  The eigen solve then runs over
-// the list, so that only the last warp of a row segment has idle lanes,
-// where a warp per 32 voxels would idle wherever the wall boundary cuts it.
-// Each voxel's arithmetic is that of k_eig_angles32; only the thread that
-// does it differs.
+// The masked form: a CTA of kEigThreads threads takes kEigSpan consecutive
+// voxels of one row (voxel x0 + t + kEigThreads k for thread t, so that the
+// mask loads and the fill stores stay coalesced), writes the fill outputs of
+// those outside the mask at once and lists the inside ones in shared memory,
+// in x order (warp ballots; every warp scans the per-warp counts itself).
+// The eigen solve then runs over the list, so that only the last warp of a row
+// segment has idle lanes, where a warp per 32 voxels would idle wherever the
+// wall boundary cuts it.  Each voxel's arithmetic is that of k_eig_angles32;
+// only the thread that does it differs.
+// Two-warp CTAs over 512 voxels: 32 CTAs per SM, whose barriers and list
+// phases interleave (512^3: 0.97 ms, against 1.09 for 256 threads x 2 voxels,
+// 1.01 for 128 x 4, 0.99 for 64 x 4, 1.04 for 64 x 16)
+#ifndef CT_EIG_THREADS
+#define CT_EIG_THREADS 64
+#endif
 #ifndef CT_EIG_SPAN_K
-#define CT_EIG_SPAN_K 2
+#define CT_EIG_SPAN_K 8
 #endif
 #ifndef CT_EIG_ILP
 #define CT_EIG_ILP 1
 #endif
-constexpr int kEigSpanK = CT_EIG_SPAN_K;  // voxels per thread per segment (tuning choice)
-constexpr int kEigSpan = 256 * kEigSpanK;
-constexpr int kEigIlp = CT_EIG_ILP;       // list entries per thread whose tensors load together (tuning choice)
+constexpr int kEigThreads = CT_EIG_THREADS;        // threads per CTA (tuning choice)
+constexpr int kEigSpanK = CT_EIG_SPAN_K;           // voxels per thread per segment (tuning choice)
+constexpr int kEigSpan = kEigThreads * kEigSpanK;  // voxels per segment
+constexpr int kEigIlp = CT_EIG_ILP;                // list entries per thread whose tensors load together (tuning choice)
+constexpr int kEigWarps = kEigThreads / 32;
+static_assert(kEigWarps * kEigSpanK <= 32, "one warp scans the per-warp counts");
+static_assert(kEigSpan <= 65536, "list entries are 16-bit");
 
 template <int VT, int AT, int FT, bool PLAIN>
-__global__ void __launch_bounds__(256, CT_EIG_MINB)
+__global__ void __launch_bounds__(kEigThreads, CT_EIG_MINB * 256 / kEigThreads)
     k_eig_angles_compact(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
                          Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
+  constexpr int NC = kEigWarps * kEigSpanK;
   __shared__ uint16_t list[kEigSpan];
-  __shared__ int cnt[8 * kEigSpanK];
+  __shared__ int cnt[NC];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int x0 = ob.lo[0] + blockIdx.x * kEigSpan;
   const int xend = ob.lo[0] + ob.n[0];
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
   unsigned in_bits[kEigSpanK];
 #pragma unroll
   for (int k = 0; k < kEigSpanK; ++k) {
-    const int x = x0 + t + 256 * k;
+    const int x = x0 + t + kEigThreads * k;
     const bool valid = x < xend;
     const bool inside = valid && __ldg(mask + box_index32(mb, x, y, z)) != 0;
     if (valid && !inside) {
@@ -178,11 +189,10 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
       write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), false, F, x, y, z, l, v, fill);
     }
     in_bits[k] = __ballot_sync(0xffffffffu, inside);
-    if (lane == 0) cnt[k * 8 + warp] = __popc(in_bits[k]);
+    if (lane == 0) cnt[k * kEigWarps + warp] = __popc(in_bits[k]);
   }
   __syncthreads();
-  // every warp scans the 8 K counts, in (k, warp) order = x order, itself
-  constexpr int NC = 8 * kEigSpanK;
+  // every warp scans the counts, in (k, warp) order = x order, itself
   const int c = lane < NC ? cnt[lane] : 0;
   int incl = c;
 #pragma unroll
@@ -194,17 +204,17 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
   const unsigned below = (1u << lane) - 1u;
 #pragma unroll
   for (int k = 0; k < kEigSpanK; ++k) {
-    const int base = __shfl_sync(0xffffffffu, incl - c, k * 8 + warp);
-    if (in_bits[k] >> lane & 1u) list[base + __popc(in_bits[k] & below)] = (uint16_t)(t + 256 * k);
+    const int base = __shfl_sync(0xffffffffu, incl - c, k * kEigWarps + warp);
+    if (in_bits[k] >> lane & 1u) list[base + __popc(in_bits[k] & below)] = (uint16_t)(t + kEigThreads * k);
   }
   __syncthreads();
   const int ns = sb.n[0] * sb.n[1] * sb.n[2];
-  for (int i0 = t; i0 < total; i0 += 256 * kEigIlp) {
+  for (int i0 = t; i0 < total; i0 += kEigThreads * kEigIlp) {
     int xs[kEigIlp];
     Sym3<float> s[kEigIlp];
 #pragma unroll
     for (int u = 0; u < kEigIlp; ++u) {
-      const int i = i0 + 256 * u;
+      const int i = i0 + kEigThreads * u;
       xs[u] = x0 + list[i < total ? i : i0];
       const int si = box_index32(sb, xs[u], y, z);
       s[u].a = __ldg(S + si);
@@ -216,7 +226,7 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
     }
 #pragma unroll
     for (int u = 0; u < kEigIlp; ++u) {
-      if (i0 + 256 * u >= total) break;
+      if (i0 + kEigThreads * u >= total) break;
       const int x = xs[u];
       float l[3], v[3];
       if (!eig_closed<float>(s[u], l, v))
@@ -270,18 +280,18 @@ cudaError_t launch_eig_angles(const float* S, const Box& sb, const Box& ob, cons
       dim3 gc((ob.n[0] + kEigSpan - 1) / kEigSpan, ob.n[1], ob.n[2]);
       if (o.vec_t == CT_OUT_F32 && o.ang_t == CT_OUT_F32 && o.fa_t == CT_OUT_F32) {
         if (plain)
-          k_eig_angles_compact<0, 0, 0, true><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+          k_eig_angles_compact<0, 0, 0, true><<<gc, kEigThreads, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
         else
-          k_eig_angles_compact<0, 0, 0, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+          k_eig_angles_compact<0, 0, 0, false><<<gc, kEigThreads, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
       } else if (o.vec_t == CT_OUT_F16 && o.ang_t == CT_OUT_F16 && o.fa_t == CT_OUT_F16) {
         if (plain)
-          k_eig_angles_compact<1, 1, 1, true><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+          k_eig_angles_compact<1, 1, 1, true><<<gc, kEigThreads, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
         else
-          k_eig_angles_compact<1, 1, 1, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+          k_eig_angles_compact<1, 1, 1, false><<<gc, kEigThreads, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
       } else if (o.ang_t == CT_OUT_U8Q && o.fa_t == CT_OUT_F16) {
-        k_eig_angles_compact<-1, 2, 1, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+        k_eig_angles_compact<-1, 2, 1, false><<<gc, kEigThreads, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
       } else {
-        k_eig_angles_compact<-1, -1, -1, false><<<gc, 256, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+        k_eig_angles_compact<-1, -1, -1, false><<<gc, kEigThreads, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
       }
       return cudaGetLastError();
     }
