@@ -312,6 +312,9 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
 }
 
 // ---------------------------------------------------------------- launch
+#ifndef CT_GXY_XT
+#define CT_GXY_XT 128  // columns (threads) per gradient x/y CTA (tuning choice)
+#endif
 template <int RS, int XT>
 static cudaError_t set_xy_attr() {
   return cudaFuncSetAttribute(k_grad_xy<RS, XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -325,7 +328,7 @@ static size_t gz_smem() {
 
 template <int RS>
 static cudaError_t prepare_gs() {
-  cudaError_t e = set_xy_attr<RS, 128>();
+  cudaError_t e = set_xy_attr<RS, CT_GXY_XT>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_grad_z<RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gz_smem<RS>());
   if (e == cudaSuccess)
@@ -374,7 +377,7 @@ static cudaError_t launch_gxy_t(const uint16_t* vol, const Box& vb, const int di
 template <int RS>
 static cudaError_t launch_gxy_r(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
                                 const Taps& tx, const Taps& ty, cudaStream_t st) {
-  return launch_gxy_t<RS, 128>(vol, vb, dims, F, ab, tx, ty, st);
+  return launch_gxy_t<RS, CT_GXY_XT>(vol, vb, dims, F, ab, tx, ty, st);
 }
 
 template <int RS>
