@@ -89,6 +89,12 @@ __device__ __forceinline__ float atan2_right(float y, float x) {
 // fraction of the spread (l3 - l1) is re-solved, since the trigonometric form
 // loses about half of its digits as the two smallest eigenvalues meet.
 constexpr float kDegenerateGap = 5e-2f;
+// The same for the FP64 closed form (the mixed form's re-solve).  Near a double
+// root an error eps in det(B) / 2 moves l1 by about eps p^2 / gap and the null
+// vector by that over the gap, eps (p / gap)^2: at a gap of 1e-4 of the spread
+// and eps = 1.1e-16 that is ~1e-8, far below the FP32 outputs' resolution,
+// so only voxels closer than that go on to FP64 Jacobi.
+constexpr double kDegenerateGap64 = 1e-4;
 
 template <typename T>
 struct Sym3 {
@@ -207,7 +213,7 @@ __device__ __forceinline__ bool eig_closed<double>(const Sym3<double>& s, double
   if (l3 < l2) { double t = l2; l2 = l3; l3 = t; }
   l[0] = l1; l[1] = l2; l[2] = l3;
   const double bn = null_vector(s, l1, v);
-  return (l2 - l1) >= (double)kDegenerateGap * (l3 - l1) && bn > 0.0;
+  return (l2 - l1) >= kDegenerateGap64 * (l3 - l1) && bn > 0.0;
 }
 
 // Cyclic Jacobi (Golub & Van Loan, Matrix Computations, section 8.5) on a

@@ -20,22 +20,33 @@
 namespace ct {
 
 // ---------------------------------------------------------------- x and y
+// The arithmetic runs on FP32 pairs (packed add / fma: one instruction, two
+// lanes, each rounded as the scalar operation would be):
+//   x pass  the staged rows hold every voxel twice, (v, v), so that one packed
+//           fma forms (v[m+k] - v[m-k], v[m+k] + v[m-k]) and another adds tap k
+//           of both filters to the pair (c_x I, w_x I) of an output;
+//   y pass  the window holds those pairs, so that the two smoothing outputs
+//           (w_y c_x I, w_y w_x I) share one packed add and one packed fma per
+//           tap; the derivative output (c_y w_x I) stays scalar.
+// Every output takes the same operations in the same order as the scalar
+// form, so its value is the same to the bit.
 template <int RS, int XT>
 struct GXYGeom {
-  static constexpr int TB = 16;                           // rows per block
+  static constexpr int TB = RS <= 8 ? 16 : 8;              // rows per block (window registers)
   static constexpr int XA = (RS + 7) / 8 * 8;              // staged columns left of the first output
-  static constexpr int CW = XT + 2 * XA;                   // staged row width (a multiple of 8)
-  static constexpr int QW = CW / 8;                        // 8-column chunks per staged row
+  static constexpr int CW = XT + 2 * XA;                   // staged row width in voxels (a multiple of 8)
+  static constexpr int QW = CW / 8;                        // 8-voxel chunks per staged row
   static constexpr int NQ = (TB * QW + XT - 1) / XT;       // chunks per thread per block
-  static constexpr int XS = CW + 4;                        // staged row stride (floats), = 4 (mod 8)
-  static constexpr int SXS = XT + 4;                       // x-pass output row stride
+  static constexpr int XS = 2 * CW + 4;                    // staged row stride (floats, each voxel twice), = 4 (mod 8)
+  static constexpr int SXS = 2 * XT + 4;                   // x-pass output row stride (floats, (c, w) pairs)
   static constexpr int W = (2 * RS + TB - 1) / TB;         // warm-up blocks
   static constexpr int PAD = W * TB - 2 * RS;              // extra leading rows
   static constexpr int WN = TB + 2 * RS;                   // y window
   static constexpr int OFF = XA - RS;                      // first needed staged column of output 0
-  static constexpr int B4 = OFF / 4 * 4, O4 = OFF % 4;     // 16-byte aligned start, remainder
-  static constexpr int NV = (8 + 2 * RS + O4 + 3) / 4;     // float4 loads per x-pass row
-  static constexpr size_t SMEM = sizeof(float) * (TB * XS + 2 * TB * SXS);
+  static constexpr int XH = RS <= 6 ? 8 : 4;               // x-pass outputs per sub-pass (registers)
+  static constexpr int B2 = OFF / 2 * 2, O2 = OFF % 2;     // 16-byte aligned start (2 voxels), remainder
+  static constexpr int NV = (XH + 2 * RS + O2 + 1) / 2;    // float4 loads (2 voxel pairs each) per sub-pass
+  static constexpr size_t SMEM = sizeof(float) * (TB * XS + TB * SXS);
 };
 
 // 8 uint16 (one 16-byte chunk) -> 8 floats, exact.
@@ -55,9 +66,8 @@ __global__ void __launch_bounds__(XT, 512 / XT)
   using G = GXYGeom<RS, XT>;
   constexpr int TB = G::TB;
   extern __shared__ __align__(16) float gsm[];
-  float* stage = gsm;                  // [TB][XS] staged rows as float
-  float* sx = gsm + TB * G::XS;        // [2][TB][SXS]: w_x and c_x rows
-
+  float* stage = gsm;                  // [TB][XS] staged rows, (v, v) per voxel
+  float* sx = gsm + TB * G::XS;        // [TB][SXS] x-pass rows, (c_x I, w_x I) per voxel
   const int t = threadIdx.x;
   const int x0 = ab.lo[0] + blockIdx.x * XT;
   const int xend = ab.lo[0] + ab.n[0];
@@ -65,23 +75,22 @@ __global__ void __launch_bounds__(XT, 512 / XT)
   const int p0 = ab.lo[1] + blockIdx.z * seg;
   const int L = min(seg, ab.lo[1] + ab.n[1] - p0);
   if (L <= 0) return;
-
   const uint16_t* plane = vol + (int64_t)(z - vb.lo[2]) * vb.n[0] * vb.n[1];
   const int ylo = max(0, vb.lo[1]), yhi = min(dimy - 1, vb.lo[1] + vb.n[1] - 1);
   const int xlo_ok = max(0, vb.lo[0]), xhi_ok = min(dimx, vb.lo[0] + vb.n[0]);
   const int nblocks = G::W + (L + TB - 1) / TB;
   const bool aligned = (vb.n[0] % 8) == 0 && ((reinterpret_cast<uintptr_t>(vol) & 15) == 0);
-
-  // this thread's 16-byte chunks of a block: chunk q = t + XT i is row q / QW,
-  // columns x0 - XA + 8 (q % QW) .. +7 (loaded whole when inside the box and
-  // aligned, else element by element with clamping)
+  // this thread's 16-byte chunks of a block: chunk q = t + XT i is row q % TB,
+  // columns x0 - XA + 8 (q / TB) .. +7 (the 8 lanes of a shared-memory phase
+  // then write 8 different rows); loaded whole when inside the box and
+  // aligned, else element by element with clamping
   int q_row[G::NQ], q_col[G::NQ];
   bool q_fast[G::NQ];
 #pragma unroll
   for (int i = 0; i < G::NQ; ++i) {
     const int q = t + XT * i;
-    q_row[i] = q < TB * G::QW ? q / G::QW : -1;
-    q_col[i] = x0 - G::XA + 8 * (q % G::QW);
+    q_row[i] = q < TB * G::QW ? q % TB : -1;
+    q_col[i] = x0 - G::XA + 8 * (q / TB);
     q_fast[i] = aligned && q_col[i] >= xlo_ok && q_col[i] + 7 < xhi_ok && ((q_col[i] - vb.lo[0]) % 8) == 0;
   }
   uint4 pre[G::NQ];
@@ -101,90 +110,88 @@ __global__ void __launch_bounds__(XT, 512 / XT)
       }
     }
   };
-  auto store_block = [&]() {  // registers -> staged float rows
+  auto store_block = [&]() {  // registers -> staged rows, every voxel twice
 #pragma unroll
     for (int i = 0; i < G::NQ; ++i) {
       if (q_row[i] < 0) continue;
       float f[8];
       u16x8_to_f32(pre[i], f);
-      float4* d = reinterpret_cast<float4*>(stage + q_row[i] * G::XS + (q_col[i] - (x0 - G::XA)));
-      d[0] = make_float4(f[0], f[1], f[2], f[3]);
-      d[1] = make_float4(f[4], f[5], f[6], f[7]);
+      float4* d = reinterpret_cast<float4*>(stage + q_row[i] * G::XS + 2 * (q_col[i] - (x0 - G::XA)));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[e] = make_float4(f[2 * e], f[2 * e], f[2 * e + 1], f[2 * e + 1]);
     }
   };
-
-  // y windows of this thread's column: c_x rows and w_x rows
-  float wc[G::WN], ww[G::WN];
+  // y window of this thread's column: (c_x I, w_x I) rows
+  float2 wp[G::WN];
 #pragma unroll
-  for (int j = 0; j < G::WN; ++j) { wc[j] = 0.f; ww[j] = 0.f; }
+  for (int j = 0; j < G::WN; ++j) wp[j] = make_float2(0.f, 0.f);
   const int xr = t % 8;
   const int xseg = t / 8;
   const bool xok = x0 + t < xend;
   const int64_t nab = box_vox(ab);
   float* obase = F + box_index(ab, min(x0 + t, xend - 1), p0, z);
   const int ostride = ab.n[0];
-
+  const float2 cw0 = make_float2(0.f, tx.w[RS]);  // centre tap of (c_x, w_x)
+  const float2 sgn = make_float2(-1.f, 1.f);
+  const float2 wy0 = make_float2(ty.w[RS], ty.w[RS]);
   load_block(0);
   for (int b = 0; b < nblocks; ++b) {
     store_block();                           // the staged rows were last read before the previous barrier
     if (b + 1 < nblocks) load_block(b + 1);  // in flight during this block's passes
     __syncthreads();                         // staged rows complete; x-pass rows free
-    // x pass: 8 outputs of row xr (+ 8 r), columns xseg*8 .. +7, smoothing and derivative
+    // x pass: 8 outputs of row xr (+ 8 r), columns xseg*8 .. +7, in sub-passes of XH
 #pragma unroll
     for (int r8 = 0; r8 < TB / 8; ++r8) {
       const int row = xr + 8 * r8;
-      const float* src = stage + row * G::XS + 8 * xseg + G::B4;
-      float v[4 * G::NV];
 #pragma unroll
-      for (int j4 = 0; j4 < G::NV; ++j4) {
-        const float4 q = *reinterpret_cast<const float4*>(src + 4 * j4);
-        v[4 * j4] = q.x; v[4 * j4 + 1] = q.y; v[4 * j4 + 2] = q.z; v[4 * j4 + 3] = q.w;
-      }
-      float sw[8], sc[8];
+      for (int h = 0; h < 8; h += G::XH) {
+        const float* src = stage + row * G::XS + 2 * (8 * xseg + h + G::B2);
+        float2 d[2 * G::NV];  // (v, v) of voxels B2 + h + j
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int m = G::O4 + i + RS;  // centre of output i in v
-        sw[i] = tx.w[RS] * v[m];
-        sc[i] = 0.f;
-#pragma unroll
-        for (int k = 1; k <= RS; ++k) {
-          sw[i] = fmaf(tx.w[RS + k], v[m + k] + v[m - k], sw[i]);
-          sc[i] = fmaf(tx.c[RS + k], v[m + k] - v[m - k], sc[i]);
+        for (int j4 = 0; j4 < G::NV; ++j4) {
+          const float4 q = *reinterpret_cast<const float4*>(src + 4 * j4);
+          d[2 * j4] = make_float2(q.x, q.y);
+          d[2 * j4 + 1] = make_float2(q.z, q.w);
         }
+        float2 acc[G::XH];  // (c_x I, w_x I)
+#pragma unroll
+        for (int i = 0; i < G::XH; ++i) {
+          const int m = G::O2 + i + RS;  // centre of output h + i in d
+          acc[i] = __fmul2_rn(cw0, d[m]);
+#pragma unroll
+          for (int k = 1; k <= RS; ++k) {
+            const float2 dk = __ffma2_rn(d[m - k], sgn, d[m + k]);  // (v+ - v-, v+ + v-)
+            acc[i] = __ffma2_rn(make_float2(tx.c[RS + k], tx.w[RS + k]), dk, acc[i]);
+          }
+        }
+        float4* o = reinterpret_cast<float4*>(sx + row * G::SXS + 2 * (8 * xseg + h));
+#pragma unroll
+        for (int i = 0; i < G::XH; i += 2) o[i / 2] = make_float4(acc[i].x, acc[i].y, acc[i + 1].x, acc[i + 1].y);
       }
-      float4* dw = reinterpret_cast<float4*>(sx + row * G::SXS + 8 * xseg);
-      float4* dc = reinterpret_cast<float4*>(sx + (TB + row) * G::SXS + 8 * xseg);
-      dw[0] = make_float4(sw[0], sw[1], sw[2], sw[3]);
-      dw[1] = make_float4(sw[4], sw[5], sw[6], sw[7]);
-      dc[0] = make_float4(sc[0], sc[1], sc[2], sc[3]);
-      dc[1] = make_float4(sc[4], sc[5], sc[6], sc[7]);
     }
     __syncthreads();  // x-pass rows complete
-    // y pass: slide the windows by TB, append this column's rows
+    // y pass: slide the window by TB, append this column's rows
 #pragma unroll
-    for (int j = 0; j < 2 * RS; ++j) { ww[j] = ww[j + TB]; wc[j] = wc[j + TB]; }
+    for (int j = 0; j < 2 * RS; ++j) wp[j] = wp[j + TB];
 #pragma unroll
-    for (int r = 0; r < TB; ++r) {
-      ww[2 * RS + r] = sx[r * G::SXS + t];
-      wc[2 * RS + r] = sx[(TB + r) * G::SXS + t];
-    }
+    for (int r = 0; r < TB; ++r) wp[2 * RS + r] = *reinterpret_cast<const float2*>(sx + r * G::SXS + 2 * t);
     if (b >= G::W) {
       const int m0 = (b - G::W) * TB;  // first output row of this block, relative to p0
 #pragma unroll
       for (int i = 0; i < TB; ++i) {
         const int m = i + RS;
-        float f0 = ty.w[RS] * wc[m], f2 = ty.w[RS] * ww[m], f1 = 0.f;
+        float2 f02 = __fmul2_rn(wy0, wp[m]);  // (w_y c_x I, w_y w_x I)
+        float f1 = 0.f;
 #pragma unroll
         for (int k = 1; k <= RS; ++k) {
-          f0 = fmaf(ty.w[RS + k], wc[m + k] + wc[m - k], f0);
-          f1 = fmaf(ty.c[RS + k], ww[m + k] - ww[m - k], f1);
-          f2 = fmaf(ty.w[RS + k], ww[m + k] + ww[m - k], f2);
+          f02 = __ffma2_rn(make_float2(ty.w[RS + k], ty.w[RS + k]), __fadd2_rn(wp[m + k], wp[m - k]), f02);
+          f1 = fmaf(ty.c[RS + k], wp[m + k].y - wp[m - k].y, f1);
         }
         if (xok && m0 + i < L) {
           float* o = obase + (int64_t)(m0 + i) * ostride;
-          o[0] = f0;
+          o[0] = f02.x;
           o[nab] = f1;
-          o[2 * nab] = f2;
+          o[2 * nab] = f02.y;
         }
       }
     }
