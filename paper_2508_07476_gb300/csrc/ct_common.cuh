@@ -71,7 +71,7 @@ __device__ __forceinline__ float atan2_right(float y, float x) {
   const float nn = red ? fmaf(1.7320508075688772f, n, -d) : n;
   const float dd = red ? fmaf(1.7320508075688772f, d, n) : d;
   const float u = d > 0.f ? __fdividef(nn, dd) : 0.f;
-  const float t = u * u;
+  const float t = __fmul_rn(u, u);
   float p = fmaf(t, 1.f / 9.f, -1.f / 7.f);
   p = fmaf(t, p, 1.f / 5.f);
   p = fmaf(t, p, -1.f / 3.f);
@@ -268,13 +268,16 @@ __device__ __noinline__ void eig_jacobi(const Sym3<T>& s, T l[3], T v[3]) {
 // Fractional anisotropy from eigenvalues clamped at zero; 0 for the zero tensor.
 // The square root is taken as q rsqrt(q) (within a few 1e-7 of it), since FA
 // is reported to far coarser than that.
+// Every operation is explicit (fmaf, __fmul_rn), so that each kernel that
+// inlines it rounds the same way.
 __device__ __forceinline__ float fa_of(const float l[3]) {
-  float l1 = fmaxf(l[0], 0.f), l2 = fmaxf(l[1], 0.f), l3 = fmaxf(l[2], 0.f);
-  float den = l1 * l1 + l2 * l2 + l3 * l3;
+  const float l1 = fmaxf(l[0], 0.f), l2 = fmaxf(l[1], 0.f), l3 = fmaxf(l[2], 0.f);
+  const float den = fmaf(l1, l1, fmaf(l2, l2, __fmul_rn(l3, l3)));
   if (den == 0.f) return 0.f;
-  float num = (l1 - l2) * (l1 - l2) + (l2 - l3) * (l2 - l3) + (l3 - l1) * (l3 - l1);
+  const float d12 = l1 - l2, d23 = l2 - l3, d31 = l3 - l1;
+  const float num = fmaf(d12, d12, fmaf(d23, d23, __fmul_rn(d31, d31)));
   const float q = __fdividef(0.5f * num, den);
-  return q > 0.f ? q * rsqrtf(q) : 0.f;
+  return q > 0.f ? __fmul_rn(q, rsqrtf(q)) : 0.f;
 }
 
 // Cylindrical left-ventricle frame (unit axis, centre), per launch.
@@ -286,40 +289,43 @@ struct Frame {
 };
 
 // HA / IA (degrees) of v at voxel (x, y, z) (global indices; the frame is in
-// the units of the voxel size); orients v so that v.e_t > 0.
+// the units of the voxel size); orients v so that v.e_t > 0.  Every operation
+// is explicit (fmaf, __fmul_rn), so that each kernel that inlines it (and
+// encodes its angles) rounds the same way.
 // Returns false on the axis, where the frame does not exist.
 // PLAIN: unit voxels and a fixed centre, known at compile time (the same
 // arithmetic as the general form with spacing 1, without its work).
 template <bool PLAIN = false>
 __device__ __forceinline__ bool ha_ia(const Frame& F, int x, int y, int z, float v[3], float& ha, float& ia) {
-  const float px = PLAIN ? (float)x : (float)x * F.sp[0];
-  const float py = PLAIN ? (float)y : (float)y * F.sp[1];
-  const float pz = PLAIN ? (float)z : (float)z * F.sp[2];
+  const float px = PLAIN ? (float)x : __fmul_rn((float)x, F.sp[0]);
+  const float py = PLAIN ? (float)y : __fmul_rn((float)y, F.sp[1]);
+  const float pz = PLAIN ? (float)z : __fmul_rn((float)z, F.sp[2]);
   float cx = F.c[0], cy = F.c[1], cz = F.c[2];
   if (!PLAIN && F.centres) {  // this slice's centre on the centreline
     cx = __ldg(F.centres + 2 * z);
     cy = __ldg(F.centres + 2 * z + 1);
     cz = pz;
   }
-  float dx = px - cx, dy = py - cy, dz = pz - cz;
-  float h = dx * F.a[0] + dy * F.a[1] + dz * F.a[2];
-  float rx = dx - h * F.a[0], ry = dy - h * F.a[1], rz = dz - h * F.a[2];
-  float rr = rx * rx + ry * ry + rz * rz;
+  const float dx = px - cx, dy = py - cy, dz = pz - cz;
+  const float h = fmaf(dx, F.a[0], fmaf(dy, F.a[1], __fmul_rn(dz, F.a[2])));
+  float rx = fmaf(-h, F.a[0], dx), ry = fmaf(-h, F.a[1], dy), rz = fmaf(-h, F.a[2], dz);
+  const float rr = fmaf(rx, rx, fmaf(ry, ry, __fmul_rn(rz, rz)));
   if (rr == 0.f) return false;
-  float inv = rsqrtf(rr);
-  rx *= inv; ry *= inv; rz *= inv;
-  float tx = F.a[1] * rz - F.a[2] * ry, ty = F.a[2] * rx - F.a[0] * rz, tz = F.a[0] * ry - F.a[1] * rx;
-  float vr = v[0] * rx + v[1] * ry + v[2] * rz;
-  float vt = v[0] * tx + v[1] * ty + v[2] * tz;
-  float vz = v[0] * F.a[0] + v[1] * F.a[1] + v[2] * F.a[2];
+  const float inv = rsqrtf(rr);
+  rx = __fmul_rn(rx, inv); ry = __fmul_rn(ry, inv); rz = __fmul_rn(rz, inv);
+  const float tx = fmaf(F.a[1], rz, -__fmul_rn(F.a[2], ry)), ty = fmaf(F.a[2], rx, -__fmul_rn(F.a[0], rz)),
+              tz = fmaf(F.a[0], ry, -__fmul_rn(F.a[1], rx));
+  float vr = fmaf(v[0], rx, fmaf(v[1], ry, __fmul_rn(v[2], rz)));
+  float vt = fmaf(v[0], tx, fmaf(v[1], ty, __fmul_rn(v[2], tz)));
+  float vz = fmaf(v[0], F.a[0], fmaf(v[1], F.a[1], __fmul_rn(v[2], F.a[2])));
   if (vt < 0.f || (vt == 0.f && vz < 0.f)) {
     vr = -vr; vt = -vt; vz = -vz;
     v[0] = -v[0]; v[1] = -v[1]; v[2] = -v[2];
   }
   const float rad2deg = 57.295779513082320877f;
-  ha = atan2_right(vz, vt) * rad2deg;
-  const float pp = vt * vt + vz * vz;  // IA = asin(vr) as the angle of v out of the (e_t, e_z) plane
-  ia = atan2_right(vr, pp > 0.f ? pp * rsqrtf(pp) : 0.f) * rad2deg;
+  ha = __fmul_rn(atan2_right(vz, vt), rad2deg);
+  const float pp = fmaf(vt, vt, __fmul_rn(vz, vz));  // IA = asin(vr) as the angle of v out of the (e_t, e_z) plane
+  ia = __fmul_rn(atan2_right(vr, pp > 0.f ? __fmul_rn(pp, rsqrtf(pp)) : 0.f), rad2deg);
   return true;
 }
 
@@ -350,7 +356,7 @@ __device__ __forceinline__ void store_angle(void* base, IT i, int type, float de
   const int ty = TYPE >= 0 ? TYPE : type;
   if (ty == 2) {
     uint8_t code = 0;
-    if (valid) code = (uint8_t)(((int)rintf((deg + 90.f) * (256.f / 180.f))) & 255);
+    if (valid) code = (uint8_t)(((int)rintf(__fmul_rn(__fadd_rn(deg, 90.f), 256.f / 180.f))) & 255);
     reinterpret_cast<uint8_t*>(base)[i] = code;
   } else {
     store_val<TYPE, IT>(base, i, ty, deg);
