@@ -30,9 +30,15 @@ namespace ct {
 //           tap; the derivative output (c_y w_x I) stays scalar.
 // Every output takes the same operations in the same order as the scalar
 // form, so its value is the same to the bit.
+#ifndef CT_GXY_TB
+#define CT_GXY_TB 0  // rows per block, 0: by radius (tuning choice)
+#endif
+#ifndef CT_GXY_XH
+#define CT_GXY_XH 0  // x-pass outputs per sub-pass, 0: by radius (tuning choice)
+#endif
 template <int RS, int XT>
 struct GXYGeom {
-  static constexpr int TB = RS <= 8 ? 16 : 8;              // rows per block (window registers)
+  static constexpr int TB = CT_GXY_TB > 0 ? CT_GXY_TB : RS <= 8 ? 16 : 8;  // rows per block (window registers)
   static constexpr int XA = (RS + 7) / 8 * 8;              // staged columns left of the first output
   static constexpr int CW = XT + 2 * XA;                   // staged row width in voxels (a multiple of 8)
   static constexpr int QW = CW / 8;                        // 8-voxel chunks per staged row
@@ -43,7 +49,7 @@ struct GXYGeom {
   static constexpr int PAD = W * TB - 2 * RS;              // extra leading rows
   static constexpr int WN = TB + 2 * RS;                   // y window
   static constexpr int OFF = XA - RS;                      // first needed staged column of output 0
-  static constexpr int XH = RS <= 6 ? 8 : 4;               // x-pass outputs per sub-pass (registers)
+  static constexpr int XH = CT_GXY_XH > 0 ? CT_GXY_XH : RS <= 6 ? 8 : 4;  // x-pass outputs per sub-pass (registers)
   static constexpr int B2 = OFF / 2 * 2, O2 = OFF % 2;     // 16-byte aligned start (2 voxels), remainder
   static constexpr int NV = (XH + 2 * RS + O2 + 1) / 2;    // float4 loads (2 voxel pairs each) per sub-pass
   static constexpr size_t SMEM = sizeof(float) * (TB * XS + TB * SXS);
