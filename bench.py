@@ -558,7 +558,15 @@ def run_crops(args):
             st = _lib.ct_plan_stats(plan, reset=True)
             ms = e0.elapsed_time(e1) / args.steps
             res[mode] = {"ms_per_step": ms, "voxels_per_s": total / (ms * 1e-3),
-                         "launches_per_step": st["launches"] / args.steps}
+                         "launches_per_step": st["launches"] / args.steps,
+                         "fallback_voxels_per_step": st["fallback_voxels"] / args.steps}
+            if mode == "per_crop":  # where the time goes: one more step with per-kernel events
+                _lib.ct_plan_profile(plan, True)
+                _lib.ct_run_chunks(plan, items, False)
+                torch.cuda.synchronize()
+                kt = _lib.ct_plan_kernel_times(plan)
+                _lib.ct_plan_profile(plan, False)
+                res[mode]["kernel_ms_per_step"] = {k: round(v[1], 3) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])}
         finally:
             _lib.ct_plan_destroy(plan)
     _line("voxels/s, 200 uneven crops, one graph-batched call", res["graph"]["voxels_per_s"], UNIT, args,
