@@ -366,9 +366,8 @@ Fallback fallback_of(ct_plan P, int slot) {
 // a function of the plan, the volume's extent and the scale, never of the box,
 // so that every chunk and sub-box of a volume takes the same arithmetic as the
 // whole and their results agree bit for bit.  Those passes are bound by HBM at
-// 48 B per voxel when the boxes allow 16-byte copies (x extents of 4-voxel
-// multiples; for y and z, of whole 128-line groups) and several times slower
-// otherwise; the FP32 stencils cost 6 (2R+1) FMAs per voxel and pass, so
+// 48 B per voxel on whole 128-line groups with 16-byte copies (x extents that
+// are multiples of 128) and several times slower otherwise; the FP32 stencils cost 6 (2R+1) FMAs per voxel and pass, so
 // below R ~ 17 they are the faster.  Measured on 200 uneven crops (R = 8..32,
 // x extents 64..384, mostly unaligned): all stencils 7.2e9 voxels/s, all
 // tensor cores 6.0e9, tensor cores for R = 32 only 7.0e9.  tc_any_box drops

@@ -261,7 +261,8 @@ struct TcUnit {
   const float* src;
   float* dst;
   int64_t istride, ostride;
-  bool lok;  // line m exists
+  bool lok;    // line m exists
+  bool wfull;  // y / z: all 32 lines of this thread's warp exist (16-byte copies read 4 lines)
 };
 
 // One 1-D pass of the integration-scale Gaussian along `axis` (0, 1 or 2; XAXIS
@@ -379,6 +380,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int o = ob.lo[other] + (int)(co % ob.n[other]);
       const int x = ob.lo[0] + xg * kTcLines + m;
       U.lok = x < ob.lo[0] + ob.n[0];
+      U.wfull = xg * kTcLines + 32 * (m >> 5) + 32 <= ob.n[0];
       const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
       const int yb = axis == 1 ? ib.lo[1] : o, zb = axis == 1 ? o : ib.lo[2];
       U.src = in + comp * box_vox(ib) + box_index(ib, xi, yb, zb);
@@ -446,9 +448,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 cp_async4(smem_u32(rb + wq * (G::WS / 4) + i * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
             }
           }
-        } else if ((vec & 1) && inside) {  // 16 bytes (4 lines) per copy, within the warp's own 32 lines
-                                     // (the stage hand-off is warp-local): lane -> lines
-                                     // 32 wq + 4 (lane % 8).., positions lane / 8 + 4 i
+        } else if ((vec & 1) && inside && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
+                                                 // own 32 lines (the stage hand-off is warp-local):
+                                                 // lane -> lines 32 wq + 4 (lane % 8).., positions
+                                                 // lane / 8 + 4 i; a warp with lines past the box
+                                                 // copies its own line, clamped, below
           const int qd = lane & 7, pg = lane >> 3;
           const float* p = IU.src + (4 * qd - lane) + (int64_t)qs * IU.istride;
 #pragma unroll
@@ -764,10 +768,10 @@ struct TcLaunch {
     const int64_t units = groups * ((a_n + seg - 1) / seg);
     const int grid = (int)std::min<int64_t>(units, sms);
     // 16-byte copies: the input rows start on 16-byte boundaries, and so do
-    // the copied pieces (y / z: quads of whole line groups; x: the windows)
+    // the copied pieces (y / z: quads of lines, in warps whose 32 lines all
+    // lie in the box; x: the windows)
     const bool rows16 = ((uintptr_t)in % 16) == 0 && ib.n[0] % 4 == 0;
-    const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0
-                               : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0 && ob.n[0] % kTcLines == 0;
+    const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0 : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0;
     const bool vout = axis == 0 && ((uintptr_t)out % 16) == 0 && ob.n[0] % 4 == 0 && ob.lo[0] % 4 == 0;
     int flags = (vin ? 1 : 0) | (vout ? 2 : 0);
     // x form: tensor maps when each 128-row group is 128 consecutive rows of one component,
@@ -831,7 +835,11 @@ cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], flo
   }
 }
 
-bool rho_tc_volume_aligned(int nx, int axis) { return axis == 0 ? nx % 4 == 0 : nx % kTcLines == 0; }
+// The tensor cores take volumes whose x extent is a multiple of 128 (whole line
+// groups on the y / z passes): at 400^3 their y / z passes took 2.27 ms each
+// against the z stencil's 0.90 (a mostly empty last group, whose warps copy
+// line by line), and at 200^3 the path took 1.03 ms against 0.71.
+bool rho_tc_volume_aligned(int nx, int axis) { return (void)axis, nx % kTcLines == 0; }
 
 unsigned int tc_timeouts(bool reset) {
   unsigned int v = 0;

@@ -54,9 +54,8 @@ cudaError_t prepare_rho_tc_kernels();
 cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
                           const Taps& taps, int rk, cudaStream_t st);
 unsigned int tc_timeouts(bool reset);
-// Whether the whole-volume boxes of a volume nx voxels wide take the 16-byte
-// copies of launch_rho_tc along axis (x: rows of 4-voxel multiples; y / z:
-// also whole 128-line groups).
+// Whether a volume nx voxels wide suits launch_rho_tc along axis: 16-byte copies
+// of whole 128-line groups (x extent a multiple of 128).
 bool rho_tc_volume_aligned(int nx, int axis);
 
 struct EigOut {

@@ -61,7 +61,8 @@ def _rel(S, S_o):
 @pytest.mark.parametrize("shape,sigma,rho", [((23, 29, 37), 1.0, 1.0), ((9, 8, 130), 0.8, 1.7),
                                              ((40, 17, 70), 1.5, 3.0), ((70, 33, 45), 2.0, 6.0),
                                              ((20, 150, 11), 1.0, 9.0), ((40, 24, 256), 2.0, 6.0),
-                                             ((16, 64, 256), 1.0, 3.0)])  # last: x rows through tensor maps
+                                             ((16, 64, 256), 1.0, 3.0),  # x rows through tensor maps
+                                             ((24, 20, 200), 1.0, 6.0)])  # 16-byte y / z copies, ragged group
 def test_tc_structure_tensor_ragged(tc, mask, shape, sigma, rho):
     tc(mask)
     vol = _rand_vol(shape, seed=sum(shape))
@@ -92,14 +93,16 @@ def test_tc_sub_box_matches_oracle_and_whole(tc, mask):
 
 
 @pytest.mark.parametrize("mask", MASKS)
-def test_tc_aligned_sub_box_matches_oracle_and_whole(tc, mask):
-    # boxes on 16-byte boundaries with whole 128-line groups: the 16-byte copy path
+@pytest.mark.parametrize("nx_out", [128, 100])
+def test_tc_aligned_sub_box_matches_oracle_and_whole(tc, mask, nx_out):
+    # boxes on 16-byte boundaries: the 16-byte copy paths (100: a ragged line
+    # group, whose last warps copy line by line)
     tc(mask)
     vol = _rand_vol((48, 60, 192), seed=13)
     sigma, rho = 1.0, 3.0
     h = O.radius(sigma) + O.radius(rho)
     assert h == 16
-    out_lo, out_n = (16, 20, 16), (128, 20, 16)
+    out_lo, out_n = (16, 20, 16), (nx_out, 20, 16)
     in_lo = tuple(a - h for a in out_lo)
     in_n = tuple(n + 2 * h for n in out_n)
     g = G.stages(vol, sigma, rho, (0, 0, 0), (0, 0, 1), in_box=(in_lo, in_n), out_box=(out_lo, out_n))
@@ -212,13 +215,13 @@ def _kernels_and_outputs(vol, sigma, rho, chunk=(0, 0, 0)):
     return names, vec.cpu().numpy(), fa.cpu().numpy()
 
 
-@pytest.mark.parametrize("nx,rho,expect_tc", [(128, 6.0, "xyz"), (256, 8.0, "xyz"), (100, 6.0, "x"),
+@pytest.mark.parametrize("nx,rho,expect_tc", [(128, 6.0, "xyz"), (256, 8.0, "xyz"), (100, 6.0, ""),
                                               (126, 6.0, ""), (128, 3.0, "")])
 def test_default_selection_is_per_volume(nx, rho, expect_tc):
     # with the library's own settings the tensor cores take rho radii >= 24 on
-    # volumes whose x extent suits the 16-byte copies (x: multiples of 4, which
-    # alone keeps the fused x / y stencil; y / z: multiples of 128); chunks of
-    # any shape take the whole volume's passes and match it bit for bit
+    # volumes whose x extent is a multiple of 128 (whole line groups with 16-byte
+    # copies); chunks of any shape take the whole volume's passes and match it
+    # bit for bit
     vol = _rand_vol((40, 36, nx), seed=nx)
     names, v, fa = _kernels_and_outputs(vol, 1.0, rho)
     tc_axes = "".join(a for a in "xyz" if f"rho_{a}_tc" in names)
