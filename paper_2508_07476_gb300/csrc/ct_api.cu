@@ -195,7 +195,8 @@ struct ct_plan_s {
   bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
   int tc_rho = 7;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
   int tc_min_r = 24;        // ... for rho radii of at least this (tuning choice)
-  bool tc_any_box = false;  // ... and volumes of any x extent (tuning choice)
+  int64_t tc_min_vox = int64_t(1) << 25;  // ... on volumes of at least this many voxels (tuning choice)
+  bool tc_any_box = false;  // ... or on every volume (tuning choice)
   bool eig_compact = true;  // masked eigen stage over compacted inside voxels (tuning choice)
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
@@ -366,14 +367,17 @@ Fallback fallback_of(ct_plan P, int slot) {
 // a function of the plan, the volume's extent and the scale, never of the box,
 // so that every chunk and sub-box of a volume takes the same arithmetic as the
 // whole and their results agree bit for bit.  Those passes are bound by HBM at
-// 48 B per voxel on whole 128-line groups with 16-byte copies (x extents that
-// are multiples of 128) and several times slower otherwise; the FP32 stencils cost 6 (2R+1) FMAs per voxel and pass, so
-// below R ~ 17 they are the faster.  Measured on 200 uneven crops (R = 8..32,
-// x extents 64..384, mostly unaligned): all stencils 7.2e9 voxels/s, all
-// tensor cores 6.0e9, tensor cores for R = 32 only 7.0e9.  tc_any_box drops
-// the extent condition (tests drive every copy path with it).
+// 48 B per voxel with 16-byte copies (x extents that are multiples of 4) and
+// several times slower otherwise; the FP32 stencils cost 6 (2R+1) FMAs per
+// voxel and pass, so below R ~ 17 they are the faster, and on small volumes
+// the persistent passes' start-up outweighs them (one step: 200^3 0.87 ms on
+// the tensor cores against 0.72 on the stencils; 384^3 2.70 against 3.34;
+// 400^3 3.91 against 4.23; 200 uneven crops 167 ms against 164).  tc_any_box
+// drops the extent and size conditions (tests drive every copy path with it).
 bool use_tc(const ct_plan P, const Scale& sc, const int dims[3], int axis) {
-  return (P->tc_rho >> axis & 1) && sc.rkr >= P->tc_min_r && (P->tc_any_box || rho_tc_volume_aligned(dims[0], axis));
+  const int64_t vox = (int64_t)dims[0] * dims[1] * dims[2];
+  return (P->tc_rho >> axis & 1) && sc.rkr >= P->tc_min_r &&
+         (P->tc_any_box || (rho_tc_volume_aligned(dims[0], axis) && vox >= P->tc_min_vox));
 }
 
 // Gradient, products and the x, y passes of rho: J over G (first buffer), then
@@ -552,6 +556,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_SPLIT_GRAD")) P->split_grad = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_RHO")) P->tc_rho = std::atoi(e) & 7;
   if (const char* e = std::getenv("CT_TUNE_TC_ANY_BOX")) P->tc_any_box = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_TC_MIN_VOX")) P->tc_min_vox = std::max<int64_t>(0, std::atoll(e));
   if (const char* e = std::getenv("CT_TUNE_EIG_COMPACT")) P->eig_compact = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_MIN_R")) P->tc_min_r = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))

@@ -460,6 +460,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int pos = pg + 4 * i;
             cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + pos * IU.istride);
           }
+        } else if (!IU.lok) {
+          // a line past the box: its products are never stored and every line's
+          // row of the product is its own, so it stages nothing
         } else if (inside) {
           const float* p = IU.src + qs * IU.istride;
 #pragma unroll
@@ -835,11 +838,9 @@ cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], flo
   }
 }
 
-// The tensor cores take volumes whose x extent is a multiple of 128 (whole line
-// groups on the y / z passes): at 400^3 their y / z passes took 2.27 ms each
-// against the z stencil's 0.90 (a mostly empty last group, whose warps copy
-// line by line), and at 200^3 the path took 1.03 ms against 0.71.
-bool rho_tc_volume_aligned(int nx, int axis) { return (void)axis, nx % kTcLines == 0; }
+// The tensor cores take volumes whose x extent is a multiple of 4 (16-byte rows;
+// a ragged last line group copies its lines past the box not at all).
+bool rho_tc_volume_aligned(int nx, int axis) { return (void)axis, nx % 4 == 0; }
 
 unsigned int tc_timeouts(bool reset) {
   unsigned int v = 0;

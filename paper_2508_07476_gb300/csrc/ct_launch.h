@@ -55,7 +55,7 @@ cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], flo
                           const Taps& taps, int rk, cudaStream_t st);
 unsigned int tc_timeouts(bool reset);
 // Whether a volume nx voxels wide suits launch_rho_tc along axis: 16-byte copies
-// of whole 128-line groups (x extent a multiple of 128).
+// of its rows (x extent a multiple of 4).
 bool rho_tc_volume_aligned(int nx, int axis);
 
 struct EigOut {

@@ -215,13 +215,17 @@ def _kernels_and_outputs(vol, sigma, rho, chunk=(0, 0, 0)):
     return names, vec.cpu().numpy(), fa.cpu().numpy()
 
 
-@pytest.mark.parametrize("nx,rho,expect_tc", [(128, 6.0, "xyz"), (256, 8.0, "xyz"), (100, 6.0, ""),
-                                              (126, 6.0, ""), (128, 3.0, "")])
-def test_default_selection_is_per_volume(nx, rho, expect_tc):
-    # with the library's own settings the tensor cores take rho radii >= 24 on
-    # volumes whose x extent is a multiple of 128 (whole line groups with 16-byte
-    # copies); chunks of any shape take the whole volume's passes and match it
-    # bit for bit
+@pytest.mark.parametrize("nx,rho,min_vox,expect_tc", [(128, 6.0, "0", "xyz"), (256, 8.0, "0", "xyz"),
+                                                      (100, 6.0, "0", "xyz"), (126, 6.0, "0", ""),
+                                                      (128, 3.0, "0", ""), (128, 6.0, None, "")])
+def test_default_selection_is_per_volume(monkeypatch, nx, rho, min_vox, expect_tc):
+    # the tensor cores take rho radii >= 24 on volumes whose x extent suits their
+    # 16-byte copies (a multiple of 4) and, with the library's own settings, of
+    # at least 2^25 voxels (None: that default, which sends these small volumes
+    # to the stencils); chunks of any shape take the whole volume's passes and
+    # match it bit for bit
+    if min_vox is not None:
+        monkeypatch.setenv("CT_TUNE_TC_MIN_VOX", min_vox)
     vol = _rand_vol((40, 36, nx), seed=nx)
     names, v, fa = _kernels_and_outputs(vol, 1.0, rho)
     tc_axes = "".join(a for a in "xyz" if f"rho_{a}_tc" in names)
