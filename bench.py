@@ -295,7 +295,7 @@ def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int, inside: float = 
 MEASURED_TRAFFIC = {"rho_x_tc": (45.0, "profiles/kernels_annulus256.md"),
                     "rho_y_tc": (44.8, "profiles/kernels_annulus256.md"),
                     "rho_z_tc": (44.9, "profiles/kernels_annulus256.md"),
-                    "eig_angles": (36.3, "profiles/kernels_annulus256.md")}
+                    "eig_angles": (36.4, "profiles/kernels_annulus256.md")}
 
 
 def run_ours(args):

@@ -195,7 +195,7 @@ struct ct_plan_s {
   bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
   int tc_rho = 7;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
   int tc_min_r = 24;        // ... for rho radii of at least this (tuning choice)
-  int64_t tc_min_vox = int64_t(1) << 25;  // ... on volumes of at least this many voxels (tuning choice)
+  int64_t tc_min_vox = int64_t(1) << 24;  // ... on volumes of at least this many voxels (tuning choice)
   bool tc_any_box = false;  // ... or on every volume (tuning choice)
   bool eig_compact = true;  // masked eigen stage over compacted inside voxels (tuning choice)
   // per-kernel timing (ct_plan_profile)
@@ -371,8 +371,9 @@ Fallback fallback_of(ct_plan P, int slot) {
 // several times slower otherwise; the FP32 stencils cost 6 (2R+1) FMAs per
 // voxel and pass, so below R ~ 17 they are the faster, and on small volumes
 // the persistent passes' start-up outweighs them (one step: 200^3 0.87 ms on
-// the tensor cores against 0.72 on the stencils; 384^3 2.70 against 3.34;
-// 400^3 3.91 against 4.23; 200 uneven crops 167 ms against 164).  tc_any_box
+// the tensor cores against 0.72 on the stencils; 256^3 0.98 against 1.12;
+// 384^3 2.70 against 3.34; 400^3 3.91 against 4.23; 200 uneven crops, all on
+// the tensor cores where the extent allows, 167 ms against 164).  tc_any_box
 // drops the extent and size conditions (tests drive every copy path with it).
 bool use_tc(const ct_plan P, const Scale& sc, const int dims[3], int axis) {
   const int64_t vox = (int64_t)dims[0] * dims[1] * dims[2];

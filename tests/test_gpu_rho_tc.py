@@ -221,7 +221,7 @@ def _kernels_and_outputs(vol, sigma, rho, chunk=(0, 0, 0)):
 def test_default_selection_is_per_volume(monkeypatch, nx, rho, min_vox, expect_tc):
     # the tensor cores take rho radii >= 24 on volumes whose x extent suits their
     # 16-byte copies (a multiple of 4) and, with the library's own settings, of
-    # at least 2^25 voxels (None: that default, which sends these small volumes
+    # at least 2^24 voxels (None: that default, which sends these small volumes
     # to the stencils); chunks of any shape take the whole volume's passes and
     # match it bit for bit
     if min_vox is not None:
