@@ -261,8 +261,8 @@ struct TcUnit {
   const float* src;
   float* dst;
   int64_t istride, ostride;
-  bool lok;    // line m exists
-  bool wfull;  // y / z: all 32 lines of this thread's warp exist (16-byte copies read 4 lines)
+  bool lok;           // line m exists
+  bool wfull = true;  // y / z: all 32 lines of this thread's warp exist (16-byte copies read 4 lines)
 };
 
 // One 1-D pass of the integration-scale Gaussian along `axis` (0, 1 or 2; XAXIS
