@@ -893,10 +893,14 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
   return CT_OK;
 }
 
-// Host-resident item: chunks alternate between the plan's two streams; each
-// chunk's haloed input box is copied straight from the caller's array, and its
-// outputs straight back into the caller's arrays, so copies of one chunk
-// overlap the kernels of the other.  Stream order protects each slot's buffers.
+// Host-resident item.  Chunks that share their y / z extents (a run along x)
+// share one slab of copies: the slab's haloed input box comes over in one 3D
+// copy (rows of the whole run, not of one chunk, and no x halo copied twice),
+// each chunk of the run is computed from it into the slab's output planes,
+// and those go back in one copy per plane.  Slabs alternate between the plan's
+// two streams, so the copies of one overlap the kernels of the other; stream
+// order protects each slot's buffers.  Every chunk's arithmetic is that of a
+// chunk on its own, so the results equal the whole volume's bit for bit.
 ct_status run_host_item(ct_plan P, const ct_item& it) {
   ItemCtx c;
   ct_status rc = item_ctx(P, it, &c);
@@ -907,11 +911,10 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
   for (int k = 0; k < 4; ++k)
     if (op.ptr[k]) out_bytes_per_vox += op.esz[k] * op.planes[k];
   std::vector<Box> chunks = chunk_grid(c.dims, P->p.chunk);
-  // a short first chunk (a quarter of its z extent, at least 8 planes), so that the
-  // first device-to-host copies start early (512^3 in 128-plane slabs: 20.9 -> 19.0
-  // ms; a ramp doubling up to the slab height measured 20.1); chunked results
-  // equal whole-volume ones
-  if (chunks.size() >= 2 && chunks[0].n[2] >= 16) {
+  // z slabs: a short first slab (a quarter of its z extent, at least 8 planes),
+  // so that the first device-to-host copies start early (512^3 in 128-plane
+  // slabs: 20.9 -> 19.0 ms; a ramp doubling up to the slab height measured 20.1)
+  if (chunks.size() >= 2 && chunks[0].n[2] >= 16 && chunks[0].n[0] == c.dims[0] && chunks[0].n[1] == c.dims[1]) {
     Box head = chunks[0], rest = chunks[0];
     head.n[2] = std::max(8, chunks[0].n[2] / 4);
     rest.lo[2] += head.n[2];
@@ -920,10 +923,17 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
     chunks.insert(chunks.begin(), head);
   }
   int64_t nwhole = box_vox(c.whole);
-  for (size_t ci = 0; ci < chunks.size(); ++ci) {
-    int slot = (int)(ci & 1);
+  int slab = 0;
+  for (size_t g0 = 0; g0 < chunks.size(); ++slab) {
+    size_t g1 = g0 + 1;  // the run: consecutive chunks with the same y / z extents, adjacent in x
+    while (g1 < chunks.size() && chunks[g1].lo[1] == chunks[g0].lo[1] && chunks[g1].n[1] == chunks[g0].n[1] &&
+           chunks[g1].lo[2] == chunks[g0].lo[2] && chunks[g1].n[2] == chunks[g0].n[2] &&
+           chunks[g1].lo[0] == chunks[g1 - 1].lo[0] + chunks[g1 - 1].n[0])
+      ++g1;
+    const int slot = slab & 1;
     cudaStream_t st = P->st[slot];
-    const Box& ob = chunks[ci];
+    Box ob = chunks[g0];  // the slab's output box
+    ob.n[0] = chunks[g1 - 1].lo[0] + chunks[g1 - 1].n[0] - ob.lo[0];
     Box ib = grow_clip3(ob, c.sc.halo, c.dims);
     int64_t niv = box_vox(ib), nov = box_vox(ob);
     size_t in_bytes = (sizeof(uint16_t) * niv + 255) / 256 * 256;
@@ -940,7 +950,7 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
       CT_CUDA(copy_box(it.mask, dmask, c.whole, ob, 1, true, st), "host to device copy");
     }
     P->stats.h2d_bytes += (int64_t)(sizeof(uint16_t) * niv + mask_bytes);
-    // device outputs: dense planes over ob, in the order vec(3), ha, ia, fa
+    // device outputs: dense planes over the slab, in the order vec(3), ha, ia, fa
     uint8_t* dptr = (uint8_t*)P->d_out[slot];
     void* dout[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int k = 0; k < 4; ++k) {
@@ -949,7 +959,9 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
       dptr += nov * op.esz[k] * op.planes[k];
     }
     EigOut o{dout[0], dout[1], dout[2], dout[3], P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
-    if ((rc = fused_stages(P, c.sc, c.dims, P->d_in[slot], ib, ob, dmask, ob, c.F, o, slot, mixed, st))) return rc;
+    for (size_t ci = g0; ci < g1; ++ci)
+      if ((rc = fused_stages(P, c.sc, c.dims, P->d_in[slot], ib, chunks[ci], dmask, ob, c.F, o, slot, mixed, st)))
+        return rc;
     for (int k = 0; k < 4; ++k) {
       if (!op.ptr[k]) continue;
       for (int pl = 0; pl < op.planes[k]; ++pl) {
@@ -960,6 +972,7 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
     }
     P->stats.d2h_bytes += (int64_t)out_bytes;
     P->stats.voxels += nov;
+    g0 = g1;
   }
   for (int s = 0; s < 2; ++s) CT_CUDA(cudaStreamSynchronize(P->st[s]), "chunked run");
   return CT_OK;
