@@ -198,6 +198,7 @@ struct ct_plan_s {
   int64_t tc_min_vox = int64_t(1) << 24;  // ... on volumes of at least this many voxels (tuning choice)
   bool tc_any_box = false;  // ... or on every volume (tuning choice)
   bool eig_compact = true;  // masked eigen stage over compacted inside voxels (tuning choice)
+  int64_t slab_bytes = int64_t(4) << 30;  // host streaming: device bytes of one slab's buffers at most
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -559,6 +560,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_TC_ANY_BOX")) P->tc_any_box = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_MIN_VOX")) P->tc_min_vox = std::max<int64_t>(0, std::atoll(e));
   if (const char* e = std::getenv("CT_TUNE_EIG_COMPACT")) P->eig_compact = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_SLAB_BYTES")) P->slab_bytes = std::max<int64_t>(0, std::atoll(e));
   if (const char* e = std::getenv("CT_TUNE_TC_MIN_R")) P->tc_min_r = std::max(0, std::atoi(e));
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
@@ -923,13 +925,23 @@ ct_status run_host_item(ct_plan P, const ct_item& it) {
     chunks.insert(chunks.begin(), head);
   }
   int64_t nwhole = box_vox(c.whole);
+  // device bytes of a slab's buffers (haloed input, mask, outputs), kept under
+  // the plan's slab_bytes per slot by ending a run early
+  auto slab_bytes = [&](const Box& b) {
+    const Box g = grow_clip3(b, c.sc.halo, c.dims);
+    return (int64_t)sizeof(uint16_t) * box_vox(g) + (int64_t)(1 + out_bytes_per_vox) * box_vox(b);
+  };
   int slab = 0;
   for (size_t g0 = 0; g0 < chunks.size(); ++slab) {
     size_t g1 = g0 + 1;  // the run: consecutive chunks with the same y / z extents, adjacent in x
     while (g1 < chunks.size() && chunks[g1].lo[1] == chunks[g0].lo[1] && chunks[g1].n[1] == chunks[g0].n[1] &&
            chunks[g1].lo[2] == chunks[g0].lo[2] && chunks[g1].n[2] == chunks[g0].n[2] &&
-           chunks[g1].lo[0] == chunks[g1 - 1].lo[0] + chunks[g1 - 1].n[0])
+           chunks[g1].lo[0] == chunks[g1 - 1].lo[0] + chunks[g1 - 1].n[0]) {
+      Box wider = chunks[g0];
+      wider.n[0] = chunks[g1].lo[0] + chunks[g1].n[0] - wider.lo[0];
+      if (slab_bytes(wider) > P->slab_bytes) break;
       ++g1;
+    }
     const int slot = slab & 1;
     cudaStream_t st = P->st[slot];
     Box ob = chunks[g0];  // the slab's output box

@@ -203,13 +203,18 @@ def test_fused_ragged_masked(shape, sigma, rho, prec):
     assert np.all(np.isnan(gpu["fa"][out])) and np.all(np.isnan(gpu["ha"][out])) and np.all(np.isnan(gpu["v"][:, out]))
 
 
+@pytest.mark.parametrize("slab_bytes", [None, "1"])
 @pytest.mark.parametrize("prec", [FP32, MIXED])
-def test_chunked_and_host_equal_whole_bit_exact(prec):
+def test_chunked_and_host_equal_whole_bit_exact(monkeypatch, prec, slab_bytes):
+    # host streaming: the chunks of one x run share a slab of copies ("1": every
+    # slab a single chunk); z-slab runs start with a short first slab (8 + 12, 20,
+    # 20, 4 and 10 + 30, 24 planes here)
+    if slab_bytes is not None:
+        monkeypatch.setenv("CT_TUNE_SLAB_BYTES", slab_bytes)
     W, vol, _, cen, ax = _helix64()
     whole = G.fused(vol, W.sigma, W.rho, cen, ax, precision=prec)
-    # host-streamed runs start with a short first chunk (8 + 12, 20, 20, 4 and 10 + 30, 24 planes of z slabs here)
     for chunk, on_host in [((24, 20, 28), False), ((0, 0, 17), False), ((32, 32, 32), True), ((0, 0, 0), True),
-                           ((0, 0, 20), True), ((64, 64, 40), True)]:
+                           ((0, 0, 20), True), ((64, 64, 40), True), ((24, 40, 30), True)]:
         part = G.fused(vol, W.sigma, W.rho, cen, ax, precision=prec, chunk=chunk, on_host=on_host)
         for k in ("v", "ha", "ia", "fa"):
             np.testing.assert_array_equal(part[k], whole[k], err_msg=f"{k} chunk={chunk} host={on_host}")
