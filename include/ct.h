@@ -169,10 +169,13 @@ typedef struct ct_item {
  * Fused hot path: the whole pipeline for each item.  items_on_host = 0: every
  * pointer of the items is a device pointer and the work is enqueued on
  * `stream` (returns without waiting).  items_on_host = 1: pointers are host
- * pointers (pinned or pageable); the volume is processed in chunks of the
- * plan's chunk size with a halo of R(sigma) + R(rho), copied through the
- * plan's pinned staging buffers on two streams; the call returns when every
- * output is in host memory.  Results do not depend on the chunking.
+ * pointers (pinned or pageable; pinned copies run at the link's rate); the
+ * volume is processed in chunks of the plan's chunk size with a halo of
+ * R(sigma) + R(rho).  The chunks of one run along x share a slab of copies
+ * (its haloed input box in, its output box out, straight between the caller's
+ * arrays and the plan's device buffers, up to 4 GiB of them per slab), slabs
+ * alternating between two streams; the call returns when every output is in
+ * host memory.  Results do not depend on the chunking.
  */
 ct_status ct_run_chunks(ct_plan plan, const ct_item* items, int32_t n_items, int32_t items_on_host, void* stream);
 
