@@ -42,7 +42,12 @@
  *   - The caller owns every input and output buffer; the plan owns its scratch
  *     memory, streams and staging buffers and frees them in ct_plan_destroy.
  *   - Asynchronous device errors surface as CT_ERR_CUDA from the next call
- *     that synchronises (ct_run_chunks, ct_plan_sync, ct_plan_stats).
+ *     that synchronises (ct_run_chunks with host items, ct_plan_sync,
+ *     ct_plan_stats).  Every wait of a kernel on another part of itself is
+ *     bounded; a kernel whose wait runs out stops, drains its own copies and
+ *     releases what it holds, leaving the context usable, and the next of
+ *     those calls returns CT_ERR_TIMEOUT (the outputs of the work since the
+ *     previous synchronising call are then invalid).
  *   - There is no CPU fallback: without a usable CUDA device every compute
  *     call returns CT_ERR_NO_DEVICE.
  */
@@ -132,15 +137,21 @@ ct_status ct_structure_tensor(ct_plan plan, const uint16_t* d_vol, const int64_t
                               const int64_t out_lo[3], const int64_t out_n[3], float* d_S, void* stream);
 
 /*
- * Stage: eigen-decomposition of n tensors (6 FP32 planes of n).  d_evals
- * (nullable) receives the 3 eigenvalues ascending; d_evec receives the unit
- * eigenvector of the smallest eigenvalue (3 planes), its sign chosen so that
- * the largest-magnitude component is positive.  Uses the plan's precision.
+ * Stage: eigen-decomposition of n tensors (Figure 1b: the fibre direction is
+ * the structure tensor's third eigenvector, the one of the smallest
+ * eigenvalue; Implementation: eigen-decomposition of the structure tensor).
+ * d_S holds 6 FP32 planes of n tensors; d_evals (nullable) receives the 3
+ * eigenvalues ascending; d_evec receives the unit eigenvector of the smallest
+ * eigenvalue (3 planes), its sign chosen so that the largest-magnitude
+ * component is positive.  Uses the plan's precision.  Plan scratch holds the
+ * list of near-degenerate tensors re-solved after the closed form.
  */
 ct_status ct_eig_smallest(ct_plan plan, const float* d_S, int64_t n, float* d_evals, float* d_evec, void* stream);
 
 /*
- * Stage: HA, IA, FA over the box (out_lo, out_n) from the smallest
+ * Stage: HA, IA, FA (Figure 1c: helix and intrusion angles of the fibre
+ * direction in the left ventricle's cylindrical frame, and fractional
+ * anisotropy; Summary) over the box (out_lo, out_n) from the smallest
  * eigenvectors and the eigenvalues (3 FP32 planes each, box-shaped), in the
  * plan's frame.  d_mask (nullable) is a box-shaped uint8 array; 0 = outside.
  * Outputs (each nullable) use the plan's encodings: d_vec 3 planes of the
@@ -166,7 +177,10 @@ typedef struct ct_item {
 } ct_item;
 
 /*
- * Fused hot path: the whole pipeline for each item.  items_on_host = 0: every
+ * Fused hot path (Implementation: volumes processed chunk by chunk with
+ * padding so that chunks match the whole; independent jobs for many volumes;
+ * Figure 1b, c for the stages): the whole pipeline for each item.
+ * items_on_host = 0: every
  * pointer of the items is a device pointer and the work is enqueued on
  * `stream` (returns without waiting).  items_on_host = 1: pointers are host
  * pointers (pinned or pageable; pinned copies run at the link's rate); the
@@ -193,7 +207,14 @@ ct_status ct_run_box(ct_plan plan, const uint16_t* d_vol, const int64_t in_lo[3]
                      const int64_t out_lo[3], const int64_t out_n[3], const uint8_t* d_mask, void* d_vec, void* d_ha,
                      void* d_ia, void* d_fa, void* stream);
 
-/* Wait for all work of the plan; report asynchronous errors. */
+/*
+ * Wait for the plan's work: its own streams and, on each stream a call of the
+ * plan enqueued work on, that work (other work on those streams or the
+ * device is not waited for).  Reports asynchronous errors (CT_ERR_CUDA) and a
+ * kernel of the plan whose bounded wait ran out since the last sync
+ * (CT_ERR_TIMEOUT; the wait limit is a plan setting, CT_TUNE_TC_WAIT_LIMIT
+ * polls, default 2^20).
+ */
 ct_status ct_plan_sync(ct_plan plan);
 
 typedef struct ct_stats {
@@ -213,12 +234,16 @@ ct_status ct_plan_stats(ct_plan plan, ct_stats* out, int32_t reset);
  * allocation once running (cudaMalloc may synchronise the device), code that
  * must not fail for lack of memory half-way through.  The paper has no
  * counterpart; this is a property of the library, not of the method.
- * Same arguments and results as ct_eig_smallest, without a plan: precision is
- * CT_PREC_FP32 or CT_PREC_MIXED.  The re-solve list lives in a fixed 8 MiB
- * array of the library's device image (resident on every device that loads
- * the library, until exit), so at most 2^20 tensors per call; larger n is
- * CT_ERR_INVALID.  No allocation of any kind is made.  The first call on a
- * device looks the array's address up (make it before any stream capture).
+ * Same arguments and results as ct_eig_smallest (bit for bit: the same kernels),
+ * without a plan: precision is CT_PREC_FP32 or CT_PREC_MIXED.  The re-solve
+ * list lives in a fixed 8 MiB array of the library's device image, so at most
+ * 2^20 tensors per call; larger n is CT_ERR_INVALID, checked before any CUDA
+ * call.  No call allocates.  The array is part of a module that CUDA loads
+ * lazily: the FIRST call on a device loads it (claiming its 8 MiB on that
+ * device, where it stays until exit, and possibly synchronising the device)
+ * and looks its address up.  Make that first call at start-up, before any
+ * stream capture.  The address is kept per device and CUDA context; after a
+ * device reset the next call looks it up again (and loads the module again).
  * All calls share the array: each call clears its counters on `stream`, and
  * calls that overlap on the GPU race on it.
  */
@@ -347,6 +372,16 @@ typedef struct ct_track_params {
 ct_status ct_track(const ct_track_params* params, const int64_t vol_dims[3], const float* d_vec, const float* d_fa,
                    const uint8_t* d_mask, const float* d_seeds, int64_t n_seeds, float* d_points, int32_t* d_count,
                    void* stream);
+
+/*
+ * Measurement support (not part of the method): the device's FP32 FMA rate.
+ * A kernel of independent FMA chains fills every SM of the current device
+ * (the SM count read from the device) for `iterations` steps of 16 FMAs per
+ * thread, timed with CUDA events; *fma_per_s = FMAs / elapsed time, *sm_count
+ * (nullable) the device's SM count, *ms (nullable) the elapsed time.  The
+ * benchmark states the FP32 roofline against this rate.  Synchronous.
+ */
+ct_status ct_fp32_fma_rate(int64_t iterations, double* fma_per_s, int32_t* sm_count, double* ms);
 
 /* Message for the calling thread's last non-OK status ("" if none). */
 const char* ct_last_error(void);

@@ -536,3 +536,14 @@ int cto_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Set the threads later calls use (the benchmark's 1-core figure); no-op
+   without OpenMP. */
+void cto_set_num_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}

@@ -55,6 +55,7 @@ def _bind(path: str):
     lib.cto_pipeline.argtypes = [P, P, P, P, D, D, D, P, P, P, D, P, P, P, P, P, P]
     lib.cto_pipeline3.argtypes = [P, P, P, P, D, D, D, P, P, P, P, P, D, P, P, P, P, P, P]
     lib.cto_num_threads.restype = ctypes.c_int
+    lib.cto_set_num_threads.argtypes = [ctypes.c_int]
     return lib
 
 
@@ -119,6 +120,11 @@ def _check(rc: int, what: str):
 
 def num_threads() -> int:
     return int(_load().cto_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of later calls (OpenMP); the benchmark times a 1-core figure with it."""
+    _load().cto_set_num_threads(int(n))
 
 
 def radius(s: float, truncate: float = 4.0) -> int:

@@ -118,6 +118,9 @@ _SIGNATURES = [
     ("ct_plan_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("ct_plan_kernel_times", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_kernel_time), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    ("ct_fp32_fma_rate", ctypes.c_int32,
+     [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+      ctypes.POINTER(ctypes.c_double)]),
     ("ct_last_error", ctypes.c_char_p, []),
     ("ct_radius", ctypes.c_int32, [ctypes.c_double, ctypes.c_double]),
 ]
@@ -320,6 +323,13 @@ def ct_plan_kernel_times(plan) -> dict:
     n = ctypes.c_int32(0)
     _check(load().ct_plan_kernel_times(plan, buf, 64, ctypes.byref(n)))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+
+def ct_fp32_fma_rate(iterations: int = 200000) -> dict:
+    """Measured FP32 FMA rate of the current device: {fma_per_s, sms, ms}."""
+    rate, sms, ms = ctypes.c_double(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().ct_fp32_fma_rate(int(iterations), ctypes.byref(rate), ctypes.byref(sms), ctypes.byref(ms)))
+    return {"fma_per_s": rate.value, "sms": sms.value, "ms": ms.value}
 
 
 def ct_last_error() -> str:

@@ -83,18 +83,8 @@ Box make_box(const int64_t lo[3], const int64_t n[3]) {
   return b;
 }
 
-Box grow_clip(const Box& b, int r, const int dims[3]) {
-  Box o;
-  for (int a = 0; a < 3; ++a) {
-    int lo = std::max(0, b.lo[a] - r);
-    int hi = std::min(dims[a] - 1, b.lo[a] + b.n[a] - 1 + r);
-    o.lo[a] = lo;
-    o.n[a] = hi - lo + 1;
-  }
-  return o;
-}
-
-// grown by r[a] along axis a (anisotropic voxels give each axis its radius)
+// b grown by r[a] along axis a (anisotropic voxels give each axis its radius),
+// clipped to the volume
 Box grow_clip3(const Box& b, const int r[3], const int dims[3]) {
   Box o;
   for (int a = 0; a < 3; ++a) {
@@ -166,10 +156,13 @@ struct ct_plan_s {
   unsigned long long* fb_total = nullptr;  // running count of re-solved voxels
   int64_t* fb_list[kSlots] = {};
   int64_t fb_cap[kSlots] = {};
-  // re-solve list of the fused z pass (index + tensor per entry)
-  int64_t* fs_idx[kSlots] = {};
-  float* fs_S[kSlots] = {};
-  int64_t fs_cap[kSlots] = {};
+  // device word counting the tensor-core CTAs of this plan that gave up a
+  // bounded wait (read and cleared by ct_plan_sync)
+  unsigned int* d_timeouts = nullptr;
+  uint32_t tc_wait_limit = 1u << 20;  // mbarrier polls before such a CTA gives up
+  // streams that calls of this plan enqueued work on since the last sync,
+  // each with an event recorded after that work (ct_plan_sync waits for these)
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> marks;
   // device staging for host-resident items
   uint16_t* d_in[2] = {nullptr, nullptr};
   uint8_t* d_mask[2] = {nullptr, nullptr};
@@ -190,9 +183,6 @@ struct ct_plan_s {
   ct_stats stats;
   std::mutex mu;
   int stream_block = 16;  // outputs per thread block of the y / z passes (tuning choice)
-  bool fuse_z_eig = false;  // z pass fused with the eigen stage, or split (tuning choice)
-  bool fuse_xy = true;      // x and y passes in one kernel, or two (tuning choice)
-  bool split_grad = true;   // gradient as x/y kernel + z kernel, or one tiled kernel (tuning choice)
   int tc_rho = 7;           // rho passes on the tensor cores: bit a for axis a (tuning choice)
   int tc_min_r = 24;        // ... for rho radii of at least this (tuning choice)
   int64_t tc_min_vox = int64_t(1) << 24;  // ... on volumes of at least this many voxels (tuning choice)
@@ -304,38 +294,6 @@ ct_status ensure_scratch(ct_plan P, int slot, int64_t vox) {
   return ensure_fallback(P, slot, vox);
 }
 
-// List for the fused z pass: 1/16 of the voxels (at least 64 Ki entries); the
-// kernel re-solves in place whatever does not fit.
-ct_status ensure_fused_fallback(ct_plan P, int slot, int64_t vox) {
-  int64_t cap = std::max<int64_t>(65536, vox / 16);
-  if (!P->fb_count[slot]) CT_CUDA(cudaMalloc(&P->fb_count[slot], sizeof(int)), "counter allocation");
-  if (!P->fb_total) {
-    CT_CUDA(cudaMalloc(&P->fb_total, sizeof(unsigned long long)), "counter allocation");
-    CT_CUDA(cudaMemset(P->fb_total, 0, sizeof(unsigned long long)), "counter reset");
-  }
-  if (P->fs_cap[slot] < cap) {
-    if (P->fs_idx[slot]) cudaFree(P->fs_idx[slot]);
-    if (P->fs_S[slot]) cudaFree(P->fs_S[slot]);
-    P->fs_idx[slot] = nullptr;
-    P->fs_S[slot] = nullptr;
-    P->fs_cap[slot] = 0;
-    CT_CUDA(cudaMalloc(&P->fs_idx[slot], sizeof(int64_t) * cap), "re-solve list allocation");
-    CT_CUDA(cudaMalloc(&P->fs_S[slot], sizeof(float) * 6 * cap), "re-solve list allocation");
-    P->fs_cap[slot] = cap;
-  }
-  return CT_OK;
-}
-
-FallbackS fused_fallback_of(ct_plan P, int slot) {
-  FallbackS fb;
-  fb.count = P->fb_count[slot];
-  fb.total = P->fb_total;
-  fb.idx = P->fs_idx[slot];
-  fb.S = P->fs_S[slot];
-  fb.cap = P->fs_cap[slot];
-  return fb;
-}
-
 Fallback fallback_of(ct_plan P, int slot) {
   Fallback fb;
   fb.count = P->fb_count[slot];
@@ -343,6 +301,47 @@ Fallback fallback_of(ct_plan P, int slot) {
   fb.list = P->fb_list[slot];
   fb.cap = P->fb_cap[slot];
   return fb;
+}
+
+// Remember that this plan enqueued work on stream st: an event recorded after
+// it lets ct_plan_sync wait for exactly the plan's work.
+ct_status mark(ct_plan P, cudaStream_t st) {
+  for (auto& m : P->marks)
+    if (m.first == st) {
+      CT_CUDA(cudaEventRecord(m.second, st), "event record");
+      return CT_OK;
+    }
+  cudaEvent_t ev = nullptr;
+  CT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event creation");
+  cudaError_t e = cudaEventRecord(ev, st);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return cuda_fail(e, "event record");
+  }
+  P->marks.push_back({st, ev});
+  return CT_OK;
+}
+
+// Wait for the plan's work (its own streams and those its calls used); then
+// report a tensor-core CTA that gave up a bounded wait as CT_ERR_TIMEOUT.
+ct_status sync_plan(ct_plan P) {
+  cudaError_t e = cudaSuccess;
+  for (auto& m : P->marks)
+    if (e == cudaSuccess) e = cudaEventSynchronize(m.second);
+  for (int k = 0; k < ct_plan_s::kSlots && e == cudaSuccess; ++k)
+    if (P->st[k]) e = cudaStreamSynchronize(P->st[k]);
+  if (e == cudaSuccess && P->gst) e = cudaStreamSynchronize(P->gst);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "device work");
+  unsigned int n = 0;
+  e = cudaMemcpyAsync(&n, P->d_timeouts, sizeof n, cudaMemcpyDeviceToHost, P->st[0]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st[0]);
+  if (e == cudaSuccess && n) e = cudaMemsetAsync(P->d_timeouts, 0, sizeof n, P->st[0]);
+  if (e == cudaSuccess && n) e = cudaStreamSynchronize(P->st[0]);
+  if (e != cudaSuccess) return cuda_fail(e, "timeout word read");
+  if (n)
+    return fail(CT_ERR_TIMEOUT, "%u tensor-core CTAs gave up a bounded wait (their outputs are invalid)", n);
+  return CT_OK;
 }
 
 // Launch `call` (a cudaError_t expression) bracketed by timing events when profiling.
@@ -395,35 +394,31 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
   Bxy.n[0] = ob.n[0];
   Bxy.lo[1] = ob.lo[1];
   Bxy.n[1] = ob.n[1];
-  // the split gradient keeps its 3 partial planes (over G grown in z) in B
+  // the gradient keeps its 3 partial planes (over G grown in z) in B
   const Box Ab = grad_partial_box(G, vb, sc.rks, dims[2]);
-  const int64_t need = P->split_grad ? std::max<int64_t>(box_vox(G), (box_vox(Ab) + 1) / 2) : box_vox(G);
+  const int64_t need = std::max<int64_t>(box_vox(G), (box_vox(Ab) + 1) / 2);
   ct_status rc = ensure_scratch(P, slot, need);
   if (rc) return rc;
   float* A = P->buf[slot][0];
   float* B = P->buf[slot][1];
-  if (P->split_grad) {
-    CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts[0], sc.ts[1], sc.rks, st),
-              "gradient x/y kernel launch");
-    CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts[2], sc.ss, sc.rks, mixed, st),
-              "gradient z kernel launch");
-  } else {
-    if (sc.rs[0] != sc.rs[1] || sc.rs[0] != sc.rs[2] || sc.ss[0] != 1.f || sc.ss[1] != 1.f || sc.ss[2] != 1.f)
-      return fail(CT_ERR_UNSUPPORTED, "the one-kernel gradient takes unit voxels only (CT_TUNE_SPLIT_GRAD=0)");
-    CT_LAUNCH(P, st, "grad_products", launch_grad_products(vol, vb, dims, A, G, sc.ts[0], sc.rks, mixed, st),
-              "gradient kernel launch");
-  }
+  CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts[0], sc.ts[1], sc.rks, st),
+            "gradient x/y kernel launch");
+  CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts[2], sc.ss, sc.rks, mixed, st),
+            "gradient z kernel launch");
   // x and y on the tensor cores together, or as one fused FP32 stencil; a mask
   // that selects one of the two axes (tuning, tests) runs them as separate passes
   const bool tcx = use_tc(P, sc, dims, 0), tcy = use_tc(P, sc, dims, 1);
   const bool one_axis = (P->tc_rho & 3) == 1 || (P->tc_rho & 3) == 2;
-  if ((tcx && tcy) || (one_axis && (tcx || tcy)) || !P->fuse_xy) {
+  const TcCtl ctl{P->d_timeouts, P->tc_wait_limit};
+  if ((tcx && tcy) || (one_axis && (tcx || tcy))) {
     if (tcx)
-      CT_LAUNCH(P, st, "rho_x_tc", launch_rho_tc(A, G, dims, B, Bx, 0, sc.tr[0], sc.rkr, st), "rho x kernel launch");
+      CT_LAUNCH(P, st, "rho_x_tc", launch_rho_tc(A, G, dims, B, Bx, 0, sc.tr[0], sc.rkr, ctl, st),
+                "rho x kernel launch");
     else
       CT_LAUNCH(P, st, "rho_x", launch_rho_x(A, G, dims, B, Bx, sc.tr[0], sc.rkr, st), "rho x kernel launch");
     if (tcy)
-      CT_LAUNCH(P, st, "rho_y_tc", launch_rho_tc(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, st), "rho y kernel launch");
+      CT_LAUNCH(P, st, "rho_y_tc", launch_rho_tc(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, ctl, st),
+                "rho y kernel launch");
     else
       CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
                 "rho y kernel launch");
@@ -440,7 +435,9 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
 ct_status z_pass(ct_plan P, const Scale& sc, const int dims[3], const float* Sxy, const Box& Bxy, float* S,
                  const Box& ob, cudaStream_t st) {
   if (use_tc(P, sc, dims, 2))
-    CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, st), "rho z kernel launch");
+    CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr,
+                                               TcCtl{P->d_timeouts, P->tc_wait_limit}, st),
+              "rho z kernel launch");
   else
     CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
               "rho z kernel launch");
@@ -460,8 +457,9 @@ ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uin
 ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
                     const EigOut& o, int slot, bool mixed, cudaStream_t st);
 
-// The fused hot path: x, y passes, then the z pass fused with eigen + angles,
-// then the re-solve of the listed voxels.  Outputs in arrays covering o.ab.
+// The fused hot path (Figure 1b, c): gradient and products, the three rho
+// passes into the free scratch buffer, then eigen + angles + mask + encode and
+// the re-solve of the listed voxels.  Outputs in arrays covering o.ab.
 ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
                        const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F, const EigOut& o, int slot,
                        bool mixed, cudaStream_t st) {
@@ -469,20 +467,9 @@ ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint
   Box Bxy;
   ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
   if (rc) return rc;
-  if (!P->fuse_z_eig) {  // split: z pass into the free buffer, then the eigen stage
-    float* S = Sxy == P->buf[slot][0] ? P->buf[slot][1] : P->buf[slot][0];
-    if ((rc = z_pass(P, sc, dims, Sxy, Bxy, S, ob, st))) return rc;
-    return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
-  }
-  if ((rc = ensure_fused_fallback(P, slot, box_vox(ob)))) return rc;
-  FallbackS fb = fused_fallback_of(P, slot);
-  CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
-  CT_LAUNCH(P, st, "rho_z_eig",
-            launch_rho_z_eig(Sxy, Bxy, dims, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, sc.tr[2], sc.rkr, st),
-            "rho z + eigen kernel launch");
-  CT_LAUNCH(P, st, "eig_resolve", launch_fallback_s(ob, F, P->p.fill_value, o, mixed, fb, fb.cap, st),
-            "re-solve kernel launch");
-  return CT_OK;
+  float* S = Sxy == P->buf[slot][0] ? P->buf[slot][1] : P->buf[slot][0];
+  if ((rc = z_pass(P, sc, dims, Sxy, Bxy, S, ob, st))) return rc;
+  return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
 }
 
 // Eigen + angles over ob from S (over ob); outputs in arrays covering o.ab.
@@ -522,8 +509,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if ((rc = make_scale(*params, params->sigma, params->rho, &sc))) return rc;
   if (!device_present()) return fail(CT_ERR_NO_DEVICE, "no CUDA device is available");
   {
-    cudaError_t e = prepare_sigma_kernels();
-    if (e == cudaSuccess) e = prepare_rho_xy_kernels();
+    cudaError_t e = prepare_rho_xy_kernels();
     if (e == cudaSuccess) e = prepare_grad_split_kernels();
     if (e == cudaSuccess) e = prepare_rho_tc_kernels();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attribute set-up");
@@ -553,9 +539,6 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   }
   std::memset(&P->stats, 0, sizeof P->stats);
   if (const char* e = std::getenv("CT_TUNE_STREAM_BLOCK")) P->stream_block = std::atoi(e) == 8 ? 8 : 16;
-  if (const char* e = std::getenv("CT_TUNE_FUSE_Z_EIG")) P->fuse_z_eig = std::atoi(e) != 0;
-  if (const char* e = std::getenv("CT_TUNE_FUSE_XY")) P->fuse_xy = std::atoi(e) != 0;
-  if (const char* e = std::getenv("CT_TUNE_SPLIT_GRAD")) P->split_grad = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_RHO")) P->tc_rho = std::atoi(e) & 7;
   if (const char* e = std::getenv("CT_TUNE_TC_ANY_BOX")) P->tc_any_box = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_MIN_VOX")) P->tc_min_vox = std::max<int64_t>(0, std::atoll(e));
@@ -565,7 +548,16 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_TC_WAIT_LIMIT")) P->tc_wait_limit = (uint32_t)std::max(0, std::atoi(e));
   cudaGetDevice(&P->device);
+  {
+    cudaError_t e = cudaMalloc(&P->d_timeouts, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(P->d_timeouts, 0, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+      ct_plan_destroy(P);
+      return cuda_fail(e, "timeout word allocation");
+    }
+  }
   for (int k = 0; k < 2; ++k) {
     cudaError_t e = cudaStreamCreateWithFlags(&P->st[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev[k], cudaEventDisableTiming);
@@ -582,6 +574,8 @@ ct_status ct_plan_destroy(ct_plan P) {
   if (!P) return CT_OK;
   cudaDeviceSynchronize();
   if (P->d_centres) cudaFree(P->d_centres);
+  if (P->d_timeouts) cudaFree(P->d_timeouts);
+  for (auto& m : P->marks) cudaEventDestroy(m.second);
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->gst) cudaStreamDestroy(P->gst);
@@ -592,8 +586,6 @@ ct_status ct_plan_destroy(ct_plan P) {
       if (P->buf[s][k]) cudaFree(P->buf[s][k]);
     if (P->fb_count[s]) cudaFree(P->fb_count[s]);
     if (P->fb_list[s]) cudaFree(P->fb_list[s]);
-    if (P->fs_idx[s]) cudaFree(P->fs_idx[s]);
-    if (P->fs_S[s]) cudaFree(P->fs_S[s]);
     if (s < 2) {
       if (P->d_in[s]) cudaFree(P->d_in[s]);
       if (P->d_mask[s]) cudaFree(P->d_mask[s]);
@@ -631,7 +623,7 @@ ct_status ct_structure_tensor(ct_plan P, const uint16_t* d_vol, const int64_t in
                      (cudaStream_t)stream);
   if (rc) return rc;
   P->stats.voxels += box_vox(ob);
-  return CT_OK;
+  return mark(P, (cudaStream_t)stream);
 }
 
 ct_status ct_eig_smallest(ct_plan P, const float* d_S, int64_t n, float* d_evals, float* d_evec, void* stream) {
@@ -649,7 +641,7 @@ ct_status ct_eig_smallest(ct_plan P, const float* d_S, int64_t n, float* d_evals
   CT_LAUNCH(P, st, "eig_only", launch_eig_only(d_S, n, d_evals, d_evec, mixed, fb, st), "eigen kernel launch");
   CT_LAUNCH(P, st, "eig_only_resolve", launch_eig_only_fallback(d_S, n, d_evals, d_evec, mixed, fb, n, st),
             "re-solve kernel launch");
-  return CT_OK;
+  return mark(P, st);
 }
 
 ct_status ct_angles(ct_plan P, const float* d_evec, const float* d_evals, const int64_t out_lo[3],
@@ -665,7 +657,7 @@ ct_status ct_angles(ct_plan P, const float* d_evec, const float* d_evals, const 
   cudaStream_t st = (cudaStream_t)stream;
   CT_LAUNCH(P, st, "angles_only", launch_angles_only(d_evec, d_evals, ob, d_mask, F, P->p.fill_value, o, st),
             "angles kernel launch");
-  return CT_OK;
+  return mark(P, st);
 }
 
 }  // extern "C"
@@ -817,18 +809,16 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
   }
   const int K = std::max(1, std::min(std::min(P->batch_streams, ct_plan_s::kSlots), n));
   // scratch of every slot sized for its largest item, before any capture
-  std::vector<int64_t> gmax(K, 0), omax(K, 0);
+  std::vector<int64_t> gmax(K, 0);
   int64_t total = 0;
   for (int i = 0; i < n; ++i) {
     const int k = i % K;
     gmax[k] = std::max(gmax[k], box_vox(grow_clip3(ctx[i].whole, ctx[i].sc.rr, ctx[i].dims)));
-    omax[k] = std::max(omax[k], box_vox(ctx[i].whole));
     total += box_vox(ctx[i].whole);
   }
   for (int k = 0; k < K; ++k) {
     if ((rc = ensure_stream(P, k))) return rc;
     if ((rc = ensure_scratch(P, k, gmax[k]))) return rc;
-    if ((rc = ensure_fused_fallback(P, k, omax[k]))) return rc;
   }
   if (!P->gst) {
     CT_CUDA(cudaStreamCreateWithFlags(&P->gst, cudaStreamNonBlocking), "stream creation");
@@ -1012,8 +1002,9 @@ ct_status ct_run_chunks(ct_plan P, const ct_item* items, int32_t n_items, int32_
   if (items_on_host) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "chunked run");
+    return sync_plan(P);  // the outputs are in host memory: report a wait that ran out now
   }
-  return CT_OK;
+  return n_items > 0 ? mark(P, (cudaStream_t)stream) : CT_OK;
 }
 
 ct_status ct_run_box(ct_plan P, const uint16_t* d_vol, const int64_t in_lo[3], const int64_t in_n[3],
@@ -1037,24 +1028,20 @@ ct_status ct_run_box(ct_plan P, const uint16_t* d_vol, const int64_t in_lo[3], c
                     (cudaStream_t)stream);
   if (rc) return rc;
   P->stats.voxels += box_vox(ob);
-  return CT_OK;
+  return mark(P, (cudaStream_t)stream);
 }
 
 ct_status ct_plan_sync(ct_plan P) {
   if (!P) return fail(CT_ERR_INVALID, "plan is NULL");
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "device work");
-  if (const unsigned int n = tc_timeouts(true))
-    return fail(CT_ERR_CUDA, "%u tensor-core CTAs gave up waiting for their MMAs (results are invalid)", n);
-  return CT_OK;
+  std::lock_guard<std::mutex> lk(P->mu);
+  return sync_plan(P);
 }
 
 ct_status ct_plan_stats(ct_plan P, ct_stats* out, int32_t reset) {
   if (!P || !out) return fail(CT_ERR_INVALID, "NULL argument");
-  ct_status rc = ct_plan_sync(P);
-  if (rc) return rc;
   std::lock_guard<std::mutex> lk(P->mu);
+  ct_status rc = sync_plan(P);
+  if (rc) return rc;
   *out = P->stats;
   unsigned long long total = 0;
   if (P->fb_total) CT_CUDA(cudaMemcpy(&total, P->fb_total, sizeof total, cudaMemcpyDeviceToHost), "counter read");

@@ -349,6 +349,13 @@ static cudaError_t prepare_gs() {
   return e;
 }
 
+int sigma_kernel_radius(int r) {
+  static const int radii[] = {2, 3, 4, 6, 8, 12};
+  for (int v : radii)
+    if (r <= v) return v;
+  return -1;
+}
+
 cudaError_t prepare_grad_split_kernels() {
   cudaError_t e = prepare_gs<2>();
   if (e == cudaSuccess) e = prepare_gs<3>();

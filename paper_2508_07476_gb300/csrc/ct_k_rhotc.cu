@@ -59,11 +59,8 @@ constexpr int kTcNB = 4;                       // mbarriers per hand-off, used b
 #ifndef CT_TC_BIG_RING
 #define CT_TC_BIG_RING 1  // tuning: 0 restarts a W + NT ring at every work unit
 #endif
-constexpr uint32_t kTcWaitLimit = 1u << 20;    // mbarrier polls before a CTA gives up
+constexpr uint32_t kTcWaitLimit = 1u << 20;    // mbarrier polls before a CTA gives up (and drain limit)
 constexpr uint32_t kTcSuspendNs = 500;         // a waiting thread sleeps up to this long per poll
-
-// CTAs that gave up waiting (read and cleared by tc_timeouts()).
-__device__ unsigned int g_tc_timeouts = 0;
 
 template <int RR>
 struct TcGeom {
@@ -214,9 +211,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// Bounded wait that also gives up once another thread of the CTA has raised *abort.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int* abort) {
-  for (uint32_t i = 0; i < kTcWaitLimit; ++i) {
+// Bounded wait (at most `limit` polls) that also gives up once another thread
+// of the CTA has raised *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int* abort,
+                                                   uint32_t limit = kTcWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try(mbar, parity)) return true;
     if (*abort) return false;
   }
@@ -279,7 +278,7 @@ template <int RR, bool XAXIS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
              int vec, const __grid_constant__ Taps taps, const __grid_constant__ CUtensorMap tin,
-             const __grid_constant__ CUtensorMap tout) {
+             const __grid_constant__ CUtensorMap tout, const TcCtl ctl) {
   using G = TcGeom<RR>;
   constexpr int NT = G::NT;
   constexpr int S = G::stages(XAXIS);
@@ -299,6 +298,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t bar_dfree[kTcNB];   // the epilogue has read tile g's D
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
+  __shared__ int arrived_max;  // x form: most chunks any producer thread has arrived for
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int role = w < 4 ? 0 : (w < 8 ? 1 : 2);  // producer, epilogue, MMA
   const int m = tid & (kTcLines - 1);            // line / TMEM lane (roles 0 and 1)
@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[a])), "n"(kTcLines));
     }
     abort_flag = 0;
+    arrived_max = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) {
@@ -414,8 +415,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     };
     uint32_t k_issue = 0;
+    int arrived = 0;  // x form: chunks this thread has arrived for on bar_chunk
     auto issue_next = [&]() {
       if (iu < n_units) {
+        ++arrived;
         float* rb = sRaw + (k_issue % S) * RAWF;
         const int qs = iq0 + (ic < G::P ? NT * ic : 2 * G::RA + NT * (ic - G::P));
         const bool inside = qs >= qlo && qs + NT - 1 <= qhi;  // no clamping in this chunk
@@ -492,7 +495,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int c = 0; c < G::P + nt; ++c, ++k) {
         cp_async_wait<S - 1>();  // chunk k has landed
         __syncwarp();            // and so have the other lanes' copies (each warp copies only its own lines)
-        if (XAXIS && !mbar_wait_or_abort(smem_u32(&bar_chunk[k % S]), (k / S) & 1u, &abort_flag)) {
+        // x form: the bulk / tensor copies of chunk k have landed (a copy is never
+        // waited for with the short limit: it depends on no other role)
+        if (XAXIS && !__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bar_chunk[k % S]), (k / S) & 1u,
+                                                                 &abort_flag))) {
           abort_flag = 1;
           go = false;
           break;
@@ -546,14 +552,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             back = 3;
           else if (g >= 4 && ws4 < lim)
             back = 4;
-          if (back) ok = mbar_wait_or_abort(mma_bar(g - back), par(g - back), &abort_flag);
+          if (back) ok = mbar_wait_or_abort(mma_bar(g - back), par(g - back), &abort_flag, ctl.wait_limit);
         } else if (c == 0) {  // the ring restarts: every MMA of the previous unit must have read it
-          if (g >= 1) ok = mbar_wait_or_abort(mma_bar(g - 1), par(g - 1), &abort_flag);
-          if (g >= 2) ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag) && ok;
+          if (g >= 1) ok = mbar_wait_or_abort(mma_bar(g - 1), par(g - 1), &abort_flag, ctl.wait_limit);
+          if (g >= 2) ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag, ctl.wait_limit) && ok;
         } else if (t >= 2) {  // tile t's positions take the slots that only tiles up to t - 2 read
-          ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag);
+          ok = mbar_wait_or_abort(mma_bar(g - 2), par(g - 2), &abort_flag, ctl.wait_limit);
         }
-        if (!ok) {
+        if (!__all_sync(0xffffffffu, ok)) {  // the whole warp gives up together
           abort_flag = 1;
           go = false;
           break;
@@ -585,7 +591,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       gbase += 2 * G::RA + NT * nt;
     }
-    cp_async_wait<0>();  // no copy is left in flight
+    cp_async_wait<0>();  // no cp.async copy is left in flight
+    __syncwarp();
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // nor a store to tensor memory
+    if (XAXIS) {
+      // nor a bulk / tensor copy: a CTA that gave up may have issued up to S
+      // chunks beyond the last one it consumed, and its threads may have stopped
+      // at different chunks (never more than S apart: a thread issues chunk
+      // c + S only after every thread has arrived for chunk c).  Each thread
+      // arrives, without a copy, for the chunks it did not issue, so that every
+      // issued chunk's phase completes once its bytes have landed; then each
+      // stage's last phase is waited for.  On a normal exit every thread has
+      // arrived for every chunk and the waits return at once.
+      atomicMax(&arrived_max, arrived);
+      asm volatile("bar.sync 1, %0;" ::"n"(kTcLines) : "memory");
+      const int amax = arrived_max;
+      for (int j = arrived; j < amax; ++j) mbar_arrive(smem_u32(&bar_chunk[j % S]));
+      for (int j = max(0, amax - S); j < amax; ++j) mbar_wait(smem_u32(&bar_chunk[j % S]), (j / S) & 1u);
+    }
   } else if (role == 2) {
     const uint64_t bhi_d = umma_desc(smem_u32(sBhi), 128, G::KCB * 128);
     const uint64_t blo_d = umma_desc(smem_u32(sBlo), 128, G::KCB * 128);
@@ -597,8 +620,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!G::BIG) gbase = 0;
       for (int t = 0; t < nt; ++t, ++g) {
         // the tile is staged, and D[g % ND] has been read (tile g - ND)
-        bool ok = mbar_wait_or_abort(staged_bar(g), par(g), &abort_flag);
-        if (ok && g >= G::ND) ok = mbar_wait_or_abort(dfree_bar(g - G::ND), par(g - G::ND), &abort_flag);
+        bool ok = mbar_wait_or_abort(staged_bar(g), par(g), &abort_flag, ctl.wait_limit);
+        if (ok && g >= G::ND) ok = mbar_wait_or_abort(dfree_bar(g - G::ND), par(g - G::ND), &abort_flag, ctl.wait_limit);
         if (!__all_sync(0xffffffffu, ok)) {
           abort_flag = 1;
           go = false;
@@ -628,7 +651,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncwarp();
       }
       for (int t = 0; t < U.nt; ++t, ++g) {
-        if (!mbar_wait_or_abort(mma_bar(g), par(g), &abort_flag)) {
+        if (!__all_sync(0xffffffffu, mbar_wait_or_abort(mma_bar(g), par(g), &abort_flag, ctl.wait_limit))) {
           abort_flag = 1;
           go = false;
           break;
@@ -704,7 +727,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   if (abort_flag && w == 8) {
     if (committed >= 1) mbar_wait(mma_bar(committed - 1), par(committed - 1));
-    if (lane == 0) atomicAdd(&g_tc_timeouts, 1u);
+    if (lane == 0 && ctl.timeouts) atomicAdd(ctl.timeouts, 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -755,7 +778,7 @@ struct TcLaunch {
     return cudaSuccess;
   }
   static cudaError_t run(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                         const Taps& taps, cudaStream_t st) {
+                         const Taps& taps, const TcCtl& ctl, cudaStream_t st) {
     using G = TcGeom<RR>;
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
@@ -787,7 +810,7 @@ struct TcLaunch {
       if (vout && rows_map(&tout, out, ob)) flags |= 8;
     }
     k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::smem(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg, flags, taps,
-                                                                  tin, tout);
+                                                                  tin, tout, ctl);
     return cudaGetLastError();
   }
 };
@@ -796,9 +819,9 @@ bool TcLaunch<RR, XAXIS>::ready = false;
 
 template <int RR>
 cudaError_t run_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                   const Taps& taps, cudaStream_t st) {
-  return axis == 0 ? TcLaunch<RR, true>::run(in, ib, dims, out, ob, axis, taps, st)
-                   : TcLaunch<RR, false>::run(in, ib, dims, out, ob, axis, taps, st);
+                   const Taps& taps, const TcCtl& ctl, cudaStream_t st) {
+  return axis == 0 ? TcLaunch<RR, true>::run(in, ib, dims, out, ob, axis, taps, ctl, st)
+                   : TcLaunch<RR, false>::run(in, ib, dims, out, ob, axis, taps, ctl, st);
 }
 
 template <int RR>
@@ -822,18 +845,18 @@ cudaError_t prepare_rho_tc_kernels() {
 }
 
 cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                          const Taps& taps, int rk, cudaStream_t st) {
+                          const Taps& taps, int rk, const TcCtl& ctl, cudaStream_t st) {
   if (box_vox(ob) == 0) return cudaSuccess;
   if (axis < 0 || axis > 2) return cudaErrorInvalidValue;
   switch (rk) {
-    case 4: return run_tc<4>(in, ib, dims, out, ob, axis, taps, st);
-    case 6: return run_tc<6>(in, ib, dims, out, ob, axis, taps, st);
-    case 8: return run_tc<8>(in, ib, dims, out, ob, axis, taps, st);
-    case 12: return run_tc<12>(in, ib, dims, out, ob, axis, taps, st);
-    case 16: return run_tc<16>(in, ib, dims, out, ob, axis, taps, st);
-    case 24: return run_tc<24>(in, ib, dims, out, ob, axis, taps, st);
-    case 32: return run_tc<32>(in, ib, dims, out, ob, axis, taps, st);
-    case 36: return run_tc<36>(in, ib, dims, out, ob, axis, taps, st);
+    case 4: return run_tc<4>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 6: return run_tc<6>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 8: return run_tc<8>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 12: return run_tc<12>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 16: return run_tc<16>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 24: return run_tc<24>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 32: return run_tc<32>(in, ib, dims, out, ob, axis, taps, ctl, st);
+    case 36: return run_tc<36>(in, ib, dims, out, ob, axis, taps, ctl, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -841,15 +864,5 @@ cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], flo
 // The tensor cores take volumes whose x extent is a multiple of 4 (16-byte rows;
 // a ragged last line group copies its lines past the box not at all).
 bool rho_tc_volume_aligned(int nx, int axis) { return (void)axis, nx % 4 == 0; }
-
-unsigned int tc_timeouts(bool reset) {
-  unsigned int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_tc_timeouts, sizeof v) != cudaSuccess) return 0;
-  if (reset && v) {
-    const unsigned int z = 0;
-    cudaMemcpyToSymbol(g_tc_timeouts, &z, sizeof z);
-  }
-  return v;
-}
 
 }  // namespace ct

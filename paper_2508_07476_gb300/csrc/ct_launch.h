@@ -10,7 +10,6 @@ namespace ct {
 
 // Set the shared-memory attributes of every kernel instantiation (once per process,
 // before any launch may be captured into a graph).
-cudaError_t prepare_sigma_kernels();
 cudaError_t prepare_rho_xy_kernels();
 cudaError_t prepare_grad_split_kernels();
 
@@ -18,13 +17,9 @@ cudaError_t prepare_grad_split_kernels();
 int sigma_kernel_radius(int r);
 int rho_kernel_radius(int r);
 
-// J (6 planes over ob) = products of the sigma-gradient of vol (array covering vb).
-cudaError_t launch_grad_products(const uint16_t* vol, const Box& vb, const int dims[3], float* J, const Box& ob,
-                                 const Taps& taps, int rk, bool mixed, cudaStream_t st);
-
-// The split gradient: launch_grad_xy writes the x/y-filtered partial fields
-// (3 planes over ab = grad_partial_box(ob, vb, R, dims[2])) of vol; launch_grad_z
-// takes their z pass and writes J (6 planes over ob), as launch_grad_products does.
+// The gradient and its products: launch_grad_xy writes the x/y-filtered partial
+// fields (3 planes over ab = grad_partial_box(ob, vb, R, dims[2])) of vol;
+// launch_grad_z takes their z pass and writes J (6 planes over ob).
 Box grad_partial_box(const Box& ob, const Box& vb, int rs, int dimz);
 // tx / ty / tz: the taps of each axis (anisotropic voxels); scale: the factor of
 // each product (1 / (spacing_a spacing_b), xx yy zz xy xz yz).
@@ -48,12 +43,17 @@ cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3],
 // rho pass along axis 0, 1 or 2 on the tensor cores (banded Toeplitz product,
 // TF32 split operands, FP32 accumulation): same contract as launch_rho_x /
 // launch_rho_stream.  prepare_rho_tc_kernels sets the shared-memory
-// attributes (call before any capture); tc_timeouts returns how many CTAs
-// gave up waiting for their MMAs since the last reset.
+// attributes (call before any capture).  Every CTA that gives up a bounded
+// wait (ctl.wait_limit polls on another role; copies are waited for up to a
+// fixed limit) stops, drains its copies and products, releases its tensor
+// memory and adds 1 to *ctl.timeouts (a device word of the caller's plan).
+struct TcCtl {
+  unsigned int* timeouts;
+  uint32_t wait_limit;
+};
 cudaError_t prepare_rho_tc_kernels();
 cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                          const Taps& taps, int rk, cudaStream_t st);
-unsigned int tc_timeouts(bool reset);
+                          const Taps& taps, int rk, const TcCtl& ctl, cudaStream_t st);
 // Whether a volume nx voxels wide suits launch_rho_tc along axis: 16-byte copies
 // of its rows (x extent a multiple of 4).
 bool rho_tc_volume_aligned(int nx, int axis);
@@ -73,24 +73,6 @@ struct Fallback {
   int64_t* list;
   int64_t cap;
 };
-
-// Near-degenerate voxels of the fused z pass: ob-linear index and the tensor
-// (6 floats per entry, AoS), since that tensor is stored nowhere else.
-struct FallbackS {
-  int* count;
-  unsigned long long* total;
-  int64_t* idx;
-  float* S;
-  int64_t cap;
-};
-
-// rho pass along z fused with eigen-solve + HA/IA/FA: S_xy (6 planes over ib) ->
-// outputs over ob (arrays covering o.ab); mask (nullable) covers mb.
-cudaError_t launch_rho_z_eig(const float* in, const Box& ib, const int dims[3], const Box& ob, const uint8_t* mask,
-                             const Box& mb, const Frame& F, float fill, const EigOut& o, bool mixed,
-                             const FallbackS& fb, const Taps& taps, int rk, cudaStream_t st);
-cudaError_t launch_fallback_s(const Box& ob, const Frame& F, float fill, const EigOut& o, bool mixed,
-                              const FallbackS& fb, int64_t max_items, cudaStream_t st);
 
 // Per-voxel eigen-solve + HA/IA/FA over ob from S (6 planes over sb); mask
 // array (nullable) covers mb.  Near-degenerate voxels are appended to fb.

@@ -10,13 +10,19 @@
 // fixed-size array that lives in the library's device image, so a call never
 // allocates, frees or asks another library to allocate.
 //
-// The array is loaded with the module on every device that uses the library
-// and stays resident until the process exits.  The first call on a device,
-// with that device current, looks its address up once (cudaGetSymbolAddress);
-// make that first call before any stream capture.  Every call shares the one
-// array and the array keeps the last call's contents: the counters are zeroed
-// on the stream at the start of each call, and calls that overlap on the GPU
-// (on different streams, or different host threads) race on the list.
+// The array belongs to this file's module of the library.  Under CUDA's lazy
+// module loading the module, and with it the array's 8 MiB, is loaded on a
+// device by the first call there, which also looks the array's address up
+// once (cudaGetSymbolAddress, with that device current) and may synchronise
+// the device while loading: make that first call at start-up, before any
+// stream capture.  The array then stays resident until the process exits.
+// The address is kept per device together with the identity of the CUDA
+// context it belongs to; after a device reset the next call looks it up again
+// in the new context.  Every call shares the one array and the array keeps the
+// last call's contents: the counters are zeroed on the stream at the start of
+// each call, and calls that overlap on the GPU (on different streams, or
+// different host threads) race on the list.
+#include <cuda.h>  // CUcontext; the two context queries are fetched from the driver at run time
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,23 +45,61 @@ static __device__ __align__(256) unsigned char g_eig_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices] = {};
+struct Cached {
+  unsigned long long ctx_id;  // identity of the context the address belongs to (0: unknown)
+  unsigned char* addr;
+};
+Cached g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique identity of the calling thread's current context (0 when there is
+// none yet or the driver cannot say).  Context identities are never reused
+// within a process, unlike context handles.
+unsigned long long current_context_id() {
+  static const CtxGetCurrent get_current = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<CtxGetCurrent>(p)
+               : nullptr;
+  }();
+  static const CtxGetId get_id = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? reinterpret_cast<CtxGetId>(p)
+               : nullptr;
+  }();
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device and context.
 ct_status scratch_address(unsigned char** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return ct::set_error(CT_ERR_NO_DEVICE, "no CUDA device is available: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return ct::set_error(CT_ERR_UNSUPPORTED, "device index %d out of range", dev);
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  Cached& c = g_addr[dev];
+  const unsigned long long id = current_context_id();
+  if (!c.addr || id != c.ctx_id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_eig_scratch);
+    e = cudaGetSymbolAddress(&p, g_eig_scratch);  // with no context yet, this creates the primary one
     if (e != cudaSuccess)
       return ct::set_error(CT_ERR_CUDA, "scratch address lookup failed: %s", cudaGetErrorString(e));
-    g_addr[dev] = static_cast<unsigned char*>(p);
+    c.addr = static_cast<unsigned char*>(p);
+    c.ctx_id = id ? id : current_context_id();
   }
-  *out = g_addr[dev];
+  *out = c.addr;
   return CT_OK;
 }
 

@@ -143,14 +143,17 @@ def angle_deg(u, v):
 EPS_S = {_lib.CT_PREC_FP32: 1e-5, _lib.CT_PREC_MIXED: 1e-3}
 
 
-def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32) -> dict:
+def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32, angles: bool = True) -> dict:
     """Per-output errors on the graded voxel sets; returns metrics (no asserts).
 
     "well" voxels are those whose direction the form can fix to 0.5 deg (the
     perturbation bound below 0.5 deg); the literal HA / IA bounds apply there,
     and everywhere else HA and IA are held to what the direction error d
     allows: |dIA| <= d and |dHA| <= d / cos(IA) (plus 0.01 deg of rounding).
+    angles=False leaves HA and IA out (quantised outputs: see compare_u8q).
     """
+    if not angles:
+        gpu = dict(gpu, ha=ora["ha"], ia=ora["ia"])
     inside = np.ones(ora["fa"].shape, bool) if mask is None else mask.astype(bool)
     sel = inside & (ora["fa"] >= FA_MIN) & np.isfinite(ora["ha"])
     out = {"n_graded": int(sel.sum()), "n_inside": int(inside.sum())}
@@ -184,8 +187,23 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32)
     return out
 
 
-def assert_within(m: dict, label: str = "", literal_ha: bool = False):
+# Caps on the share of graded voxels that the perturbation-bound reading
+# exempts from the literal bounds (see the module docstring), per arithmetic
+# form: "literal": voxels whose direction error exceeds 0.5 deg (each still
+# within its own bound); "ill": voxels whose bound exceeds 0.5 deg at all, so
+# that their HA / IA are held to the bound instead of 0.5 deg.  A regression
+# that moved many voxels past 0.5 deg, or inputs whose tensors were mostly
+# ill-conditioned, would fail here rather than pass unseen.
+CAPS = {_lib.CT_PREC_FP32: {"literal": 1e-3, "ill": 3e-1}, _lib.CT_PREC_MIXED: {"literal": 1e-2, "ill": 5e-1}}
+CAP_MIN_GRADED = 2000  # caps apply to samples of at least this many graded voxels
+
+
+def assert_within(m: dict, label: str = "", literal_ha: bool = False, precision: int = None):
     msg = f"{label}: {m}"
+    if precision is not None and m["n_graded"] >= CAP_MIN_GRADED:
+        cap = CAPS[precision]
+        assert m["dir_literal_fail"] <= cap["literal"] * m["n_graded"], msg
+        assert m["n_ill_conditioned"] <= cap["ill"] * m["n_graded"], msg
     assert m["dir_bound_excess"] <= 0.0, msg
     assert m["ha_max"] <= ANG_TOL_DEG, msg
     assert m["ia_max"] <= ANG_TOL_DEG, msg
@@ -194,3 +212,39 @@ def assert_within(m: dict, label: str = "", literal_ha: bool = False):
     if literal_ha:
         assert m["ha_literal_max"] <= ANG_TOL_DEG, msg
     assert m["fa_max"] <= FA_TOL, msg
+
+
+def u8q_code(deg):
+    """The U8Q code of an angle in degrees (the library's encoding, include/ct.h)."""
+    return np.rint((np.asarray(deg, dtype=np.float64) + 90.0) * 256.0 / 180.0).astype(np.int64) % 256
+
+
+def compare_u8q(codes: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32) -> dict:
+    """HA / IA codes against the oracle's own quantisation of its FP64 angles, on
+    the voxels whose direction the form fixes to 0.5 deg (graded as in compare):
+    the largest code distance (mod 256).  IA is compared up to sign where
+    |HA| > 89 deg, where the orientation rule may flip the vector."""
+    inside = np.ones(ora["fa"].shape, bool) if mask is None else mask.astype(bool)
+    sel = inside & (ora["fa"] >= FA_MIN) & np.isfinite(ora["ha"])
+    if "evals" in ora:
+        ev = ora["evals"]
+        gap = np.maximum(ev[1] - ev[0], 1e-300)
+        sel &= np.degrees(EPS_S[precision] * ev.sum(0) / gap) <= DIR_TOL_DEG
+    out = {"n_graded": int(sel.sum())}
+
+    def dist(a, b):
+        d = (a - b) % 256
+        return np.minimum(d, 256 - d)
+
+    for k in ("ha", "ia"):
+        if codes.get(k) is None:
+            continue
+        c = codes[k].astype(np.int64)[sel]
+        d = dist(c, u8q_code(ora[k][sel]))
+        if k == "ia":
+            flip = np.abs(ora["ha"][sel]) > 89.0
+            d = np.where(flip, np.minimum(d, dist(c, u8q_code(-ora[k][sel]))), d)
+        out[f"{k}_code_max"] = int(d.max()) if d.size else 0
+    out["outside_code_nonzero"] = int(sum(int((codes[k][~inside] != 0).sum()) for k in ("ha", "ia")
+                                          if codes.get(k) is not None))
+    return out

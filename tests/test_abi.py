@@ -128,3 +128,29 @@ def test_no_device_is_reported_without_fallback(libpath):
     with pytest.raises(_lib.CTError) as ei:
         _create()
     assert ei.value.status == _lib.CT_ERR_NO_DEVICE
+
+
+def test_noalloc_entry_point_is_exported(libpath):
+    assert "ct_eig_smallest_noalloc" in header_functions()
+    assert hasattr(ctypes.CDLL(libpath), "ct_eig_smallest_noalloc")
+
+
+@pytest.mark.parametrize("args,needle", [
+    ((None, 4, None, 16, 0), "NULL"),          # no tensors
+    ((16, 4, None, None, 0), "NULL"),          # no eigenvector output
+    ((16, 4, None, 16, 7), "precision"),
+    ((16, -1, None, 16, 0), "n must be"),
+    ((16, (1 << 20) + 1, None, 16, 1), "exceeds"),  # above the static scratch's 2^20 tensors
+])
+def test_noalloc_validates_before_any_cuda_call(libpath, args, needle):
+    # the checks run on the host before the device is touched, so they hold
+    # without a GPU (the pointers are never dereferenced)
+    lib = _lib.load()
+    S, n, ev, vec, prec = args
+    st = lib.ct_eig_smallest_noalloc(S, n, ev, vec, prec, None)
+    assert st == _lib.CT_ERR_INVALID
+    assert needle in _lib.ct_last_error()
+
+
+def test_noalloc_zero_tensors_is_a_no_op(libpath):
+    assert _lib.load().ct_eig_smallest_noalloc(16, 0, None, 16, 0, None) == _lib.CT_OK

@@ -30,8 +30,26 @@ def test_launched_sequence_floor():
     assert round(total) == 229
 
 
-def test_stencil_fma_count_and_roofline():
-    # 8 sigma passes, 6 products, 18 rho passes of 2R+1 taps: 1024 at sigma 2, rho 6
+def test_stencil_fma_count():
+    # 8 sigma passes, 6 products, 18 rho passes of 2R+1 taps: 1024 at sigma 2, rho 6;
+    # 1312 at sigma 2, rho 8; 1520 at sigma 3, rho 9
     assert bench._fma_per_voxel(8, 24) == 8 * 17 + 6 + 18 * 49 == 1024
-    fma_peak = 152 * 128 * 2070e6
-    assert fma_peak / 1024 == pytest.approx(3.93e10, rel=1e-3)
+    assert bench._fma_per_voxel(8, 32) == 1312
+    assert bench._fma_per_voxel(12, 36) == 1520
+
+
+def test_grading_exempts_only_ill_conditioned_voxels():
+    # a direction error above 0.5 deg passes only where the voxel's own bound
+    # eps_S tr S / (l2 - l1) is larger, and is counted either way
+    import numpy as np
+    ev = np.array([[1.0, 1.0], [1.0 + 1e-4, 2.0], [3.0, 3.0]])[:, :, None, None]  # [3, 2, 1, 1]
+    ora = {"fa": np.full((2, 1, 1), 0.5), "ha": np.zeros((2, 1, 1)), "ia": np.zeros((2, 1, 1)), "evals": ev,
+           "v": np.zeros((3, 2, 1, 1))}
+    ora["v"][0] = 1.0
+    t = np.radians(1.0)
+    out = {k: ora[k].copy() for k in ("ha", "ia", "fa")}
+    out["v"] = np.zeros((3, 2, 1, 1))
+    out["v"][0], out["v"][1] = np.cos(t), np.sin(t)  # 1 deg off on both voxels
+    r = bench._grade_box(ora, out, np.ones((2, 1, 1), bool), 1)
+    assert r["dir_over_05"] == 2 and r["ill"] == 1
+    assert r["dir_bound_excess"] > 0  # the well-conditioned voxel fails its 0.5 deg bound

@@ -76,7 +76,7 @@ def test_batch_graph_equals_items_alone_and_oracle(prec):
         for k in ("v", "ha", "ia", "fa"):
             np.testing.assert_array_equal(b[k], alone[k], err_msg=f"{w.name} {k} (alone)")
         ora = O.pipeline(h, w.sigma, w.rho, cen, ax)
-        G.assert_within(G.compare(b, ora, precision=prec), w.name)
+        G.assert_within(G.compare(b, ora, precision=prec), w.name, precision=prec)
 
 
 def test_run_box_chunks_equal_whole():

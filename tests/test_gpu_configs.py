@@ -1,0 +1,197 @@
+"""Parity at the scales of the benchmark configurations, on the default path.
+
+The full-size workloads run the integration-scale passes on the tensor cores
+(R(rho) >= 24 on volumes of at least 2^24 voxels whose x extent is a multiple
+of 4) and reach scales the small parity cases do not: R(sigma) = 12 and
+R(rho) = 32 / 36.  Each case below is a 2^24-voxel volume built like the
+configuration it stands for, run through ct_run_chunks with the plan's
+default kernel choice and the configuration's output encodings, and compared
+with the FP64 oracle on sampled boxes:
+
+  stream   sigma 2, rho 8 (R 8, 32): the x4-scaled annulus (radii 480 / 880,
+           period 8, IA field, 5% Poisson-like noise, mask); F16 outputs
+  tera     sigma 3, rho 9 (R 12, 36): radii 1000 / 1800, period 10; U8Q HA /
+           IA codes, F16 FA (and an F16 vector, to grade the direction)
+  crop     sigma 3, rho 8 and sigma 1, rho 2: the two ends of the uneven
+           crops (radii 0.2 / 0.42 of the side, no mask, Gaussian noise);
+           F16 outputs (rho 2 runs on the FP32 stencils)
+
+Boxes straddle the tensor-core tiles' 64-position seams on every axis, the
+x pass's 128-row groups (y = 128), the volume's corners and edges, and seeded
+points of the wall.  A second volume, 1024 x 16 x 1024, puts work-unit seams
+(x = 512 in the x pass, z = 512 in the z pass) inside graded boxes.
+Tolerances and caps: gpu_util.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2508_07476_gb300 import _lib, build, synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import gpu_util as G  # noqa: E402
+
+FP32, MIXED = _lib.CT_PREC_FP32, _lib.CT_PREC_MIXED
+F32, F16, U8Q = _lib.CT_OUT_F32, _lib.CT_OUT_F16, _lib.CT_OUT_U8Q
+TILT = (math.sin(math.radians(10.0)), 0.0, math.cos(math.radians(10.0)))
+
+
+def _spec(name, shape=(256, 256, 256)):
+    nz, ny, nx = shape
+    if name == "stream":  # the inner wall crosses x (256 wide: r from ~400 to ~650; 1024 wide: ~100 to ~1120)
+        return synth.AnnulusSpec(shape=shape, r_in=480.0, r_out=880.0, period=8.0, ha_in_deg=70.0,
+                                 ha_out_deg=-70.0, center=(-400.0 if nx <= 256 else -100.0, (ny - 1) / 2,
+                                                           (nz - 1) / 2), axis=TILT,
+                                 noise=("poisson_like", 0.05), ia_std_deg=5.0, ia_corr=40.0, seed=3)
+    if name == "tera":
+        return synth.AnnulusSpec(shape=shape, r_in=1000.0, r_out=1800.0, period=10.0, ha_in_deg=70.0,
+                                 ha_out_deg=-70.0, center=(-920.0, (ny - 1) / 2, (nz - 1) / 2), axis=TILT,
+                                 noise=("poisson_like", 0.05), ia_std_deg=5.0, ia_corr=40.0, seed=5)
+    if name == "crop":
+        m = min(shape)
+        ax = (math.sin(math.radians(15.0)) * math.cos(1.0), math.sin(math.radians(15.0)) * math.sin(1.0),
+              math.cos(math.radians(15.0)))
+        return synth.AnnulusSpec(shape=shape, r_in=0.2 * m, r_out=0.42 * m, period=6.0, ha_in_deg=55.0,
+                                 ha_out_deg=-55.0, center=(0.42 * (nx - 1), 0.55 * (ny - 1), 0.5 * (nz - 1)),
+                                 axis=ax, noise=("gauss", 60.0), seed=1017)
+    raise ValueError(name)
+
+
+CASES = {
+    "stream_s2_r8": ("stream", 2.0, 8.0, True, (F16, F16, F16)),
+    "tera_s3_r9": ("tera", 3.0, 9.0, True, (F16, U8Q, F16)),
+    "crop_s3_r8": ("crop", 3.0, 8.0, False, (F16, F16, F16)),
+    "crop_s1_r2": ("crop", 1.0, 2.0, False, (F16, F16, F16)),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    _lib.load()
+
+
+_VOLS = {}
+
+
+def _volume(name, shape=(256, 256, 256)):
+    key = (name, shape)
+    if key not in _VOLS:
+        spec = _spec(name, shape)
+        _VOLS[key] = (spec,) + synth.generate(spec)
+    return _VOLS[key]
+
+
+def _seam_boxes(shape, mask, seed, b=16):
+    """Boxes across tile seams, row-group and corner positions, plus wall points."""
+    nz, ny, nx = shape
+    boxes = [(120, 120, 56), (184, 56, 120), (120, 184, 184), (184, 120, 184), (56, 120, 120), (0, 0, 0),
+             (nx - b, ny - b, nz - b), (0, 120, nz - b), (nx - b, 0, 120)]
+    rng = np.random.default_rng(seed)
+    walls = 0
+    for _ in range(100000):
+        if walls == 5:
+            break
+        x, y, z = (int(rng.integers(0, d)) for d in (nx, ny, nz))
+        if mask is None or mask[z, y, x]:
+            boxes.append((x - b // 2, y - b // 2, z - b // 2))
+            walls += 1
+    return [tuple(int(min(max(0, v), d - b)) for v, d in zip(lo, (nx, ny, nz))) for lo in boxes]
+
+
+_ORA = {}
+
+
+def _oracle_box(key, vol, sigma, rho, cen, ax, mask, lo, n):
+    k = (key, lo, n)
+    if k not in _ORA:
+        _ORA[k] = O.pipeline(vol, sigma, rho, cen, ax, mask=mask, lo=lo, n=n)
+    return _ORA[k]
+
+
+def _grade(key, vol, mask, spec, sigma, rho, prec, types, gpu, boxes, b):
+    cen, ax = synth.frame_of(spec)
+    graded = 0
+    for lo in boxes:
+        n = (b, b, b)
+        ora = _oracle_box(key, vol, sigma, rho, cen, ax, mask, lo, n)
+        sl = (slice(lo[2], lo[2] + b), slice(lo[1], lo[1] + b), slice(lo[0], lo[0] + b))
+        sub = {k: (gpu[k][(slice(None),) + sl] if k == "v" else gpu[k][sl]) for k in ("v", "ha", "ia", "fa")}
+        msub = None if mask is None else mask[sl]
+        quant = types[1] == U8Q
+        m = G.compare(sub, ora, msub, precision=prec, angles=not quant)
+        print(key, prec, lo, m)
+        G.assert_within(m, f"{key} box {lo} prec={prec}", precision=prec)
+        if quant:
+            q = G.compare_u8q({"ha": sub["ha"], "ia": sub["ia"]}, ora, msub, precision=prec)
+            print(key, prec, lo, q)
+            assert q["ha_code_max"] <= 1 and q["ia_code_max"] <= 1, (lo, q)
+            assert q["outside_code_nonzero"] == 0, (lo, q)
+        graded += m["n_graded"]
+    return graded
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP32])
+@pytest.mark.parametrize("case", list(CASES))
+def test_config_scale_default_path_matches_oracle(case, prec):
+    name, sigma, rho, use_mask, types = CASES[case]
+    spec, vol, mask = _volume(name)
+    mask = mask if use_mask else None
+    cen, ax = synth.frame_of(spec)
+    gpu = G.fused(vol, sigma, rho, cen, ax, mask=mask, precision=prec, vec_type=types[0], angle_type=types[1],
+                  fa_type=types[2])
+    graded = _grade(case, vol, mask, spec, sigma, rho, prec, types, gpu, _seam_boxes(vol.shape, mask, 31), 16)
+    assert graded > 2000, graded
+    if mask is not None:  # outside the mask every output is the fill (NaN; U8Q code 0)
+        out = ~mask.astype(bool)
+        assert np.all(np.isnan(gpu["fa"][out]))
+        if types[1] == U8Q:
+            assert np.all(gpu["ha"][out] == 0) and np.all(gpu["ia"][out] == 0)
+        else:
+            assert np.all(np.isnan(gpu["ha"][out]))
+
+
+def _kernel_names(vol, sigma, rho, cen, ax, mask):
+    nz, ny, nx = vol.shape
+    plan = _lib.ct_plan_create(_lib.make_params(sigma, rho, cen, ax, MIXED), (nx, ny, nz))
+    try:
+        _lib.ct_plan_profile(plan, True)
+        fa = torch.empty((nz, ny, nx), device="cuda")
+        m = None if mask is None else G.dev_u8(mask)
+        _lib.ct_run_chunks(plan, [_lib.make_item(G.dev_u16(vol), (nx, ny, nz), m, None, None, None, fa)], False)
+        torch.cuda.synchronize()
+        return set(_lib.ct_plan_kernel_times(plan))
+    finally:
+        _lib.ct_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("case,tc", [("stream_s2_r8", True), ("tera_s3_r9", True), ("crop_s3_r8", True),
+                                     ("crop_s1_r2", False)])
+def test_config_scale_takes_the_expected_passes(case, tc):
+    # the cases above grade the tensor-core passes where the benchmark runs them
+    name, sigma, rho, use_mask, _ = CASES[case]
+    spec, vol, mask = _volume(name)
+    cen, ax = synth.frame_of(spec)
+    names = _kernel_names(vol, sigma, rho, cen, ax, mask if use_mask else None)
+    assert all(f"rho_{a}_tc" in names for a in "xyz") == tc, names
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP32])
+def test_work_unit_seams_match_oracle(prec):
+    # 1024 x 16 x 1024: the x pass splits each row into two units (x = 512) and
+    # the z pass each line (z = 512); graded boxes straddle both seams
+    shape = (1024, 16, 1024)
+    spec, vol, mask = _volume("stream", shape)
+    sigma, rho = 2.0, 8.0
+    cen, ax = synth.frame_of(spec)
+    gpu = G.fused(vol, sigma, rho, cen, ax, mask=mask, precision=prec)
+    b = 16
+    boxes = [(504, 0, 504), (504, 0, 0), (504, 0, 1008), (400, 0, 504), (700, 0, 248), (600, 0, 760)]
+    graded = _grade("unit_seams", vol, mask, spec, sigma, rho, prec, (F32, F32, F32), gpu, boxes, b)
+    assert graded > 2000, graded

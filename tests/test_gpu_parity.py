@@ -185,7 +185,7 @@ def test_fused_helix64_matches_oracle(prec):
     m = G.compare(gpu, ora, precision=prec)
     print("helix64", prec, m)
     # the FP32 form meets the HA bound literally on every graded voxel
-    G.assert_within(m, f"helix64 prec={prec}", literal_ha=(prec == FP32))
+    G.assert_within(m, f"helix64 prec={prec}", literal_ha=(prec == FP32), precision=prec)
 
 
 @pytest.mark.parametrize("shape,sigma,rho,prec", [((23, 29, 37), 1.0, 2.0, FP32), ((40, 17, 70), 1.5, 3.0, MIXED),
@@ -313,4 +313,4 @@ def test_full_size_annulus512_sampled(annulus512, prec):
         sl = (slice(lo[2], lo[2] + n[2]), slice(lo[1], lo[1] + n[1]), slice(lo[0], lo[0] + n[0]))
         sub = {k: (gpu[k][(slice(None),) + sl] if k == "v" else gpu[k][sl]) for k in ("v", "ha", "ia", "fa")}
         m = G.compare(sub, ora, mask[sl], precision=prec)
-        G.assert_within(m, f"box {lo} {n} prec={prec}")
+        G.assert_within(m, f"box {lo} {n} prec={prec}", precision=prec)

@@ -137,9 +137,11 @@ def test_tc_agrees_with_stencil(tc):
     assert rel.max() <= 2e-5, rel.max()
 
 
-def test_tc_many_units_aligned_agrees_with_stencil(tc):
+def test_tc_many_units_aligned_matches_oracle(tc):
     # 16-byte copies and many work units per CTA on every axis (the regime of
-    # the full-size runs): the tensor-core tensors agree with the stencil's
+    # the full-size runs), graded against the oracle on boxes across the 64-
+    # position tile seams (x 64 / 128 / 448, y 128, z 64) and the x pass's
+    # 128-row groups (y = 128), and against the FP32 stencils everywhere
     vol = _rand_vol((96, 256, 512), seed=17)
     out = {}
     for mask in (0, 7):
@@ -147,6 +149,11 @@ def test_tc_many_units_aligned_agrees_with_stencil(tc):
         out[mask] = G.stages(vol, 2.0, 6.0, (0, 0, 0), (0, 0, 1))["S"].astype(np.float64)
     rel = np.abs(out[7] - out[0]) / (out[0][0] + out[0][1] + out[0][2])[None]
     assert rel.max() <= 2e-5, rel.max()
+    b = 12
+    for lo in [(58, 122, 58), (122, 250 - b, 0), (442, 0, 90 - b), (500, 122, 40), (0, 122, 84)]:
+        S_o = O.structure_tensor(vol, 2.0, 6.0, lo=lo, n=(b, b, b))
+        sub = out[7][:, lo[2]:lo[2] + b, lo[1]:lo[1] + b, lo[0]:lo[0] + b]
+        assert _rel(sub, S_o) <= 2e-5, lo
 
 
 @pytest.mark.parametrize("prec", [FP32, MIXED])
