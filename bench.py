@@ -390,6 +390,10 @@ def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int, inside: float = 
         return 0, nvox * (2 + 12)
     if name == "grad_z":  # three planes in, six products out
         return 0, nvox * (12 + 24)
+    if name in ("grad_z_g32", "grad_z_g16"):  # three planes in, the gradient out (FP32 / FP16)
+        return 0, nvox * (12 + (12 if name.endswith("32") else 6))
+    if name in ("rho_z_tc_g32", "rho_z_tc_g16"):  # the gradient in (products formed on chip), six planes out
+        return 0, nvox * ((12 if name.endswith("32") else 6) + 24)
     if name == "rho_xy":
         return nvox * 12 * (2 * rr + 1), nvox * 48
     if name == "rho_z_eig":

@@ -187,6 +187,7 @@ struct ct_plan_s {
   int tc_min_r = 24;        // ... for rho radii of at least this (tuning choice)
   int64_t tc_min_vox = int64_t(1) << 24;  // ... on volumes of at least this many voxels (tuning choice)
   bool tc_any_box = false;  // ... or on every volume (tuning choice)
+  bool tc_products = true;  // with all three passes there: products formed in the first (tuning choice)
   bool eig_compact = true;  // masked eigen stage over compacted inside voxels (tuning choice)
   int64_t slab_bytes = int64_t(4) << 30;  // host streaming: device bytes of one slab's buffers at most
   // per-kernel timing (ct_plan_profile)
@@ -381,19 +382,22 @@ bool use_tc(const ct_plan P, const Scale& sc, const int dims[3], int axis) {
          (P->tc_any_box || (rho_tc_volume_aligned(dims[0], axis) && vox >= P->tc_min_vox));
 }
 
-// Gradient, products and the x, y passes of rho: J over G (first buffer), then
-// S_xy over Bxy (returned with its box; the second buffer when x and y are
-// fused, the first otherwise).  vol covers vb.
-ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb, const Box& ob,
-                    int slot, bool mixed, cudaStream_t st, float** Sxy, Box* Bxy_out) {
-  Box G = grow_clip3(ob, sc.rr, dims);
-  Box Bx = G, Bxy = G;
-  Bx.lo[0] = ob.lo[0];
-  Bx.n[0] = ob.n[0];
-  Bxy.lo[0] = ob.lo[0];
-  Bxy.n[0] = ob.n[0];
-  Bxy.lo[1] = ob.lo[1];
-  Bxy.n[1] = ob.n[1];
+// The structure tensor S (6 planes over ob) of vol (covering vb): the gradient
+// at sigma, its products and the three rho passes (Figure 1b).  S goes to
+// S_out when given (the stage API), else to a scratch buffer; *S_res tells
+// which.  Two chains, chosen per plan and volume, never per box, so that
+// chunks and sub-boxes of a volume reproduce it bit for bit:
+//   - every rho pass on the tensor cores (and products in the first pass,
+//     the plan's default): the gradient g (FP16 in the mixed form) goes to
+//     HBM instead of the six products; the z pass forms the products as it
+//     stages them, then the y and x passes follow:
+//       grad_xy -> B, grad_z: g -> A, z: S_z -> B, y: S_zy -> A, x: S -> out;
+//   - otherwise the products J and the x, y passes (tensor cores per axis, or
+//     the fused FP32 stencil), then the z pass:
+//       grad_xy -> B, grad_z: J -> A, x / y -> B or A, z -> out.
+ct_status smooth_chain(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
+                       const Box& ob, int slot, bool mixed, cudaStream_t st, float* S_out, float** S_res) {
+  const Box G = grow_clip3(ob, sc.rr, dims);
   // the gradient keeps its 3 partial planes (over G grown in z) in B
   const Box Ab = grad_partial_box(G, vb, sc.rks, dims[2]);
   const int64_t need = std::max<int64_t>(box_vox(G), (box_vox(Ab) + 1) / 2);
@@ -401,15 +405,40 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
   if (rc) return rc;
   float* A = P->buf[slot][0];
   float* B = P->buf[slot][1];
+  const TcCtl ctl{P->d_timeouts, P->tc_wait_limit};
   CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts[0], sc.ts[1], sc.rks, st),
             "gradient x/y kernel launch");
-  CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts[2], sc.ss, sc.rks, mixed, st),
+  const bool tcx = use_tc(P, sc, dims, 0), tcy = use_tc(P, sc, dims, 1), tcz = use_tc(P, sc, dims, 2);
+  if (tcx && tcy && tcz && P->tc_products) {
+    Box Bz = G, Bzy = G;
+    Bz.lo[2] = Bzy.lo[2] = ob.lo[2];
+    Bz.n[2] = Bzy.n[2] = ob.n[2];
+    Bzy.lo[1] = ob.lo[1];
+    Bzy.n[1] = ob.n[1];
+    float* S = S_out ? S_out : B;
+    CT_LAUNCH(P, st, mixed ? "grad_z_g16" : "grad_z_g32",
+              launch_grad_z(B, Ab, A, G, sc.ts[2], sc.ss, sc.rks, mixed, true, st), "gradient z kernel launch");
+    CT_LAUNCH(P, st, mixed ? "rho_z_tc_g16" : "rho_z_tc_g32",
+              launch_rho_tc_products(A, mixed, G, dims, B, Bz, 2, sc.tr[2], sc.ss, sc.rkr, ctl, st),
+              "rho z kernel launch");
+    CT_LAUNCH(P, st, "rho_y_tc", launch_rho_tc(B, Bz, dims, A, Bzy, 1, sc.tr[1], sc.rkr, ctl, st),
+              "rho y kernel launch");
+    CT_LAUNCH(P, st, "rho_x_tc", launch_rho_tc(A, Bzy, dims, S, ob, 0, sc.tr[0], sc.rkr, ctl, st),
+              "rho x kernel launch");
+    *S_res = S;
+    return CT_OK;
+  }
+  Box Bx = G, Bxy = G;
+  Bx.lo[0] = Bxy.lo[0] = ob.lo[0];
+  Bx.n[0] = Bxy.n[0] = ob.n[0];
+  Bxy.lo[1] = ob.lo[1];
+  Bxy.n[1] = ob.n[1];
+  CT_LAUNCH(P, st, "grad_z", launch_grad_z(B, Ab, A, G, sc.ts[2], sc.ss, sc.rks, mixed, false, st),
             "gradient z kernel launch");
   // x and y on the tensor cores together, or as one fused FP32 stencil; a mask
   // that selects one of the two axes (tuning, tests) runs them as separate passes
-  const bool tcx = use_tc(P, sc, dims, 0), tcy = use_tc(P, sc, dims, 1);
   const bool one_axis = (P->tc_rho & 3) == 1 || (P->tc_rho & 3) == 2;
-  const TcCtl ctl{P->d_timeouts, P->tc_wait_limit};
+  float* Sxy;
   if ((tcx && tcy) || (one_axis && (tcx || tcy))) {
     if (tcx)
       CT_LAUNCH(P, st, "rho_x_tc", launch_rho_tc(A, G, dims, B, Bx, 0, sc.tr[0], sc.rkr, ctl, st),
@@ -422,36 +451,27 @@ ct_status xy_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_
     else
       CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
                 "rho y kernel launch");
-    *Sxy = A;
+    Sxy = A;
   } else {
     CT_LAUNCH(P, st, "rho_xy", launch_rho_xy(A, G, dims, B, Bxy, sc.tr[0], sc.tr[1], sc.rkr, st), "rho xy kernel launch");
-    *Sxy = B;
+    Sxy = B;
   }
-  *Bxy_out = Bxy;
-  return CT_OK;
-}
-
-// The z pass of rho: S (6 planes over ob) from S_xy (6 planes over Bxy).
-ct_status z_pass(ct_plan P, const Scale& sc, const int dims[3], const float* Sxy, const Box& Bxy, float* S,
-                 const Box& ob, cudaStream_t st) {
-  if (use_tc(P, sc, dims, 2))
-    CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr,
-                                               TcCtl{P->d_timeouts, P->tc_wait_limit}, st),
+  float* S = S_out ? S_out : (Sxy == A ? B : A);
+  if (tcz)
+    CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, ctl, st),
               "rho z kernel launch");
   else
     CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
               "rho z kernel launch");
+  *S_res = S;
   return CT_OK;
 }
 
 // The whole smoothing chain into S (6 planes over ob): the stage API.
 ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
                         const Box& ob, float* S_out, int slot, bool mixed, cudaStream_t st) {
-  float* Sxy = nullptr;
-  Box Bxy;
-  ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
-  if (rc) return rc;
-  return z_pass(P, sc, dims, Sxy, Bxy, S_out, ob, st);
+  float* S = nullptr;
+  return smooth_chain(P, sc, dims, vol, vb, ob, slot, mixed, st, S_out, &S);
 }
 
 ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
@@ -463,12 +483,9 @@ ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mas
 ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint16_t* vol, const Box& vb,
                        const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F, const EigOut& o, int slot,
                        bool mixed, cudaStream_t st) {
-  float* Sxy = nullptr;
-  Box Bxy;
-  ct_status rc = xy_stages(P, sc, dims, vol, vb, ob, slot, mixed, st, &Sxy, &Bxy);
+  float* S = nullptr;
+  ct_status rc = smooth_chain(P, sc, dims, vol, vb, ob, slot, mixed, st, nullptr, &S);
   if (rc) return rc;
-  float* S = Sxy == P->buf[slot][0] ? P->buf[slot][1] : P->buf[slot][0];
-  if ((rc = z_pass(P, sc, dims, Sxy, Bxy, S, ob, st))) return rc;
   return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
 }
 
@@ -549,6 +566,7 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_WAIT_LIMIT")) P->tc_wait_limit = (uint32_t)std::max(0, std::atoi(e));
+  if (const char* e = std::getenv("CT_TUNE_TC_PRODUCTS")) P->tc_products = std::atoi(e) != 0;
   cudaGetDevice(&P->device);
   {
     cudaError_t e = cudaMalloc(&P->d_timeouts, sizeof(unsigned int));

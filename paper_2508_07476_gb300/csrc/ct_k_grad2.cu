@@ -229,9 +229,12 @@ constexpr int kGzAhead = CT_GZ_AHEAD;
 // leaving gradients down to 2^-6 intensity units normal.
 constexpr float kGzHalfScale = 1.0f / 256.0f;
 
-template <int RS, bool MIXED>
+// GOUT: write the gradient itself (3 planes: FP16 holding g * 2^-8 in the
+// mixed form, FP32 otherwise) for a consumer that forms the products, instead
+// of the six products.
+template <int RS, bool MIXED, bool GOUT>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
-    k_grad_z(const float* __restrict__ F, Box ab, float* __restrict__ J, Box ob, int seg, const Taps taps,
+    k_grad_z(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg, const Taps taps,
              const ProdScale ps) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
@@ -269,7 +272,10 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
   for (int s = 0; s < AH; ++s) issue(s, s);
 
   const int64_t nob = box_vox(ob);
-  float* obase = J + box_index(ob, xi, y, p0);
+  float* J = static_cast<float*>(Jv);
+  __half* Jh = static_cast<__half*>(Jv);
+  const int64_t obase_i = box_index(ob, xi, y, p0);
+  float* obase = J + obase_i;
   const int ostride = ob.n[0] * ob.n[1];
   float w0[P], w1[P], w2[P];
 #pragma unroll
@@ -294,6 +300,21 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
           gx = fmaf(taps.w[RS + k], w0[sp] + w0[sm], gx);
           gy = fmaf(taps.w[RS + k], w1[sp] + w1[sm], gy);
           gz = fmaf(taps.c[RS + k], w2[sp] - w2[sm], gz);
+        }
+        if (GOUT) {  // the gradient itself, held in FP16 (scaled) in the mixed form
+          if (ok) {
+            const int64_t o = obase_i + (int64_t)(s - 2 * RS) * ostride;
+            if (MIXED) {
+              Jh[o] = __float2half_rn(gx * kGzHalfScale);
+              Jh[o + nob] = __float2half_rn(gy * kGzHalfScale);
+              Jh[o + 2 * nob] = __float2half_rn(gz * kGzHalfScale);
+            } else {
+              J[o] = gx;
+              J[o + nob] = gy;
+              J[o + 2 * nob] = gz;
+            }
+          }
+          continue;
         }
         if (MIXED) {  // gradient held in FP16 (scaled), products formed exactly in FP32
           gx = __half2float(__float2half_rn(gx * kGzHalfScale)) * (1.0f / kGzHalfScale);
@@ -342,10 +363,11 @@ static size_t gz_smem() {
 template <int RS>
 static cudaError_t prepare_gs() {
   cudaError_t e = set_xy_attr<RS, CT_GXY_XT>();
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_grad_z<RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gz_smem<RS>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_grad_z<RS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gz_smem<RS>());
+  const int sm = (int)gz_smem<RS>();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 
@@ -401,8 +423,8 @@ static cudaError_t launch_gxy_r(const uint16_t* vol, const Box& vb, const int di
 }
 
 template <int RS>
-static cudaError_t launch_gz_r(const float* F, const Box& ab, float* J, const Box& ob, const Taps& taps,
-                               const ProdScale& ps, bool mixed, cudaStream_t st) {
+static cudaError_t launch_gz_r(const float* F, const Box& ab, void* J, const Box& ob, const Taps& taps,
+                               const ProdScale& ps, bool mixed, bool gout, cudaStream_t st) {
   // warps along x: the widest that leaves the fewest idle columns
   int wx = 1;
   for (int w = 2; w <= kGzThreads / 32; w *= 2) {
@@ -417,10 +439,16 @@ static cudaError_t launch_gz_r(const float* F, const Box& ab, float* J, const Bo
   const int seg = (ob.n[2] + nseg - 1) / nseg;
   dim3 grid((ob.n[0] + block.x - 1) / block.x, (ob.n[1] + block.y - 1) / block.y, (ob.n[2] + seg - 1) / seg);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
-  if (mixed)
-    k_grad_z<RS, true><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
-  else
-    k_grad_z<RS, false><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
+  if (gout) {
+    if (mixed)
+      k_grad_z<RS, true, true><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
+    else
+      k_grad_z<RS, false, true><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
+  } else if (mixed) {
+    k_grad_z<RS, true, false><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
+  } else {
+    k_grad_z<RS, false, false><<<grid, block, gz_smem<RS>(), st>>>(F, ab, J, ob, seg, taps, ps);
+  }
   return cudaGetLastError();
 }
 
@@ -439,8 +467,8 @@ cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3]
   }
 }
 
-cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& tz,
-                          const float scale[6], int rk, bool mixed, cudaStream_t st) {
+cudaError_t launch_grad_z(const float* F, const Box& ab, void* J, const Box& ob, const Taps& tz,
+                          const float scale[6], int rk, bool mixed, bool gout, cudaStream_t st) {
   if (box_vox(ob) == 0) return cudaSuccess;
   if (box_vox(ab) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
   ProdScale ps;
@@ -450,12 +478,12 @@ cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob
     ps.unit = ps.unit && scale[k] == 1.f;
   }
   switch (rk) {
-    case 2: return launch_gz_r<2>(F, ab, J, ob, tz, ps, mixed, st);
-    case 3: return launch_gz_r<3>(F, ab, J, ob, tz, ps, mixed, st);
-    case 4: return launch_gz_r<4>(F, ab, J, ob, tz, ps, mixed, st);
-    case 6: return launch_gz_r<6>(F, ab, J, ob, tz, ps, mixed, st);
-    case 8: return launch_gz_r<8>(F, ab, J, ob, tz, ps, mixed, st);
-    case 12: return launch_gz_r<12>(F, ab, J, ob, tz, ps, mixed, st);
+    case 2: return launch_gz_r<2>(F, ab, J, ob, tz, ps, mixed, gout, st);
+    case 3: return launch_gz_r<3>(F, ab, J, ob, tz, ps, mixed, gout, st);
+    case 4: return launch_gz_r<4>(F, ab, J, ob, tz, ps, mixed, gout, st);
+    case 6: return launch_gz_r<6>(F, ab, J, ob, tz, ps, mixed, gout, st);
+    case 8: return launch_gz_r<8>(F, ab, J, ob, tz, ps, mixed, gout, st);
+    case 12: return launch_gz_r<12>(F, ab, J, ob, tz, ps, mixed, gout, st);
     default: return cudaErrorInvalidValue;
   }
 }

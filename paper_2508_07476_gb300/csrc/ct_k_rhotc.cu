@@ -92,18 +92,25 @@ struct TcGeom {
   // output buffer, whichever layout a chunk uses (32 padded rows of XS floats, or
   // NT / 32 swizzled 32 x 32 boxes), so that every hand-off stays within the warp
   static constexpr int WS = (32 * XS * 4 + 1023) / 1024 * 1024;
-  // one chunk: y / z [NT positions][128 lines]; x four warp slices
-  static constexpr int raw_floats(bool xaxis) { return xaxis ? 4 * WS / 4 : NT * kTcLines; }
-  static constexpr int stages(bool xaxis) { return xaxis ? 3 : 4; }  // chunks in flight
+  // one chunk: y / z [NT positions][128 lines] (products: two such arrays of
+  // gradient components, FP32 or FP16); x four warp slices
+  static constexpr int raw_floats(bool xaxis, int prod = 0) {
+    return xaxis ? 4 * WS / 4 : (prod == 1 ? 2 * NT * kTcLines : NT * kTcLines);
+  }
+  // chunks in flight (FP32 gradient pairs: two, the most that fit beside B)
+  static constexpr int stages(bool xaxis, int prod = 0) { return xaxis ? 3 : (prod == 1 ? 2 : 4); }
   static_assert((2 * B_BYTES) % 1024 == 0 && NT * 32 * 4 <= WS && TE == XS, "x-form slices");
-  static constexpr int need(bool xaxis) {
-    return 1024 + 2 * B_BYTES + stages(xaxis) * raw_floats(xaxis) * 4 +
+  static constexpr int need(bool xaxis, int prod = 0) {
+    return 1024 + 2 * B_BYTES + stages(xaxis, prod) * raw_floats(xaxis, prod) * 4 +
            (xaxis ? 4 * WS + 2 * ROW_BYTES : 0);  // + slack to align the base to 1024 bytes
   }
   // dynamic shared memory requested: at least half an SM's (233472 bytes,
   // 1 KB reserved per CTA), so that one CTA, holding all the tensor memory,
   // is resident per SM
-  static constexpr int smem(bool xaxis) { return need(xaxis) > 233472 / 2 ? need(xaxis) : 233472 / 2; }
+  static constexpr int smem(bool xaxis, int prod = 0) {
+    return need(xaxis, prod) > 233472 / 2 ? need(xaxis, prod) : 233472 / 2;
+  }
+  static_assert(need(false, 1) <= 232448 && need(false, 2) <= 232448 && need(true) <= 232448, "shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -262,6 +269,33 @@ struct TcUnit {
   int64_t istride, ostride;
   bool lok;           // line m exists
   bool wfull = true;  // y / z: all 32 lines of this thread's warp exist (16-byte copies read 4 lines)
+  // products form: element offsets of the line's relative position 0 in the
+  // planes of gradient components a and b of the unit's component g_a g_b
+  int64_t ga = 0, gb = 0;
+  int comp = 0;
+};
+
+// The products form's inputs: gradient planes (FP32, or FP16 holding g * 2^-8)
+// and the factor of each product (1 / (spacing_a spacing_b); `unit` when all 1).
+struct TcProd {
+  float s[6];
+  int unit;
+};
+
+// component k of the tensor = g_a g_b with a = kProdA[k], b = kProdB[k] (xx yy zz xy xz yz)
+__host__ __device__ constexpr int prod_a(int k) { return k < 3 ? k : (k < 5 ? 0 : 1); }
+__host__ __device__ constexpr int prod_b(int k) { return k < 3 ? k : (k == 3 ? 1 : 2); }
+
+template <int PROD>
+struct GradT {
+  using T = float;
+  static __device__ __forceinline__ float get(float v) { return v; }
+};
+template <>
+struct GradT<2> {
+  using T = __half;
+  // the mixed form's gradient: FP16 holding g * 2^-8, restored exactly
+  static __device__ __forceinline__ float get(__half v) { return __half2float(v) * 256.0f; }
 };
 
 // One 1-D pass of the integration-scale Gaussian along `axis` (0, 1 or 2; XAXIS
@@ -274,15 +308,26 @@ struct TcUnit {
 // allows 16-byte copies; bit 1 (x form), the output rows start on 16-byte
 // boundaries; bits 2 / 3 (x form), tin / tout map the 128-row groups as
 // (x, row, component) boxes of the input / output (all checked on the host).
-template <int RR, bool XAXIS>
+//
+// PROD (y / z form only): the input is not the 6 tensor planes but the 3
+// gradient planes (1: FP32, 2: FP16 holding g * 2^-8), and the producers form
+// each component's product g_a g_b (times its factor) from the two staged
+// gradient chunks before splitting it, with the same FP32 operations the
+// gradient kernel would have used to store it: the product field never
+// crosses HBM.  Work units then take the six components of one line group
+// in turn, so that the group's gradient lines are read from L2 after the
+// first component.
+template <int RR, bool XAXIS, int PROD>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
              int vec, const __grid_constant__ Taps taps, const __grid_constant__ CUtensorMap tin,
-             const __grid_constant__ CUtensorMap tout, const TcCtl ctl) {
+             const __grid_constant__ CUtensorMap tout, const TcCtl ctl, const TcProd pr) {
+  static_assert(!(XAXIS && PROD), "the products form is a y / z form");
   using G = TcGeom<RR>;
+  using GT = typename GradT<PROD>::T;
   constexpr int NT = G::NT;
-  constexpr int S = G::stages(XAXIS);
-  constexpr int RAWF = G::raw_floats(XAXIS);
+  constexpr int S = G::stages(XAXIS, PROD);
+  constexpr int RAWF = G::raw_floats(XAXIS, PROD);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float* sBhi = reinterpret_cast<float*>(smem);
@@ -375,16 +420,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       U.src = in + comp * box_vox(ib) + box_index(ib, ib.lo[0], yy, zz);
       U.dst = out + comp * box_vox(ob) + box_index(ob, a_lo, yy, zz);
     } else {
-      const int xg = (int)(grp % ngx);
-      const int64_t co = grp / ngx;
-      const int comp = (int)(co / ob.n[other]);
-      const int o = ob.lo[other] + (int)(co % ob.n[other]);
+      // plain: groups by (component, other, x group), x group fastest; products:
+      // component fastest (the six components of a line group in turn)
+      const int xg = PROD ? (int)((grp / 6) % ngx) : (int)(grp % ngx);
+      const int64_t co = PROD ? (grp / 6) / ngx : grp / ngx;
+      const int comp = PROD ? (int)(grp % 6) : (int)(co / ob.n[other]);
+      const int o = ob.lo[other] + (int)(PROD ? co : co % ob.n[other]);
       const int x = ob.lo[0] + xg * kTcLines + m;
       U.lok = x < ob.lo[0] + ob.n[0];
       U.wfull = xg * kTcLines + 32 * (m >> 5) + 32 <= ob.n[0];
       const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
       const int yb = axis == 1 ? ib.lo[1] : o, zb = axis == 1 ? o : ib.lo[2];
       U.src = in + comp * box_vox(ib) + box_index(ib, xi, yb, zb);
+      if (PROD) {
+        U.comp = comp;
+        U.ga = prod_a(comp) * box_vox(ib) + box_index(ib, xi, yb, zb);
+        U.gb = prod_b(comp) * box_vox(ib) + box_index(ib, xi, yb, zb);
+      }
       U.istride = axis == 1 ? ib.n[0] : (int64_t)ib.n[0] * ib.n[1];
       const int yo = axis == 1 ? a_lo : o, zo = axis == 1 ? o : a_lo;
       U.dst = out + comp * box_vox(ob) + box_index(ob, xi, yo, zo);
@@ -449,6 +501,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
               for (int i = 0; i < 32; ++i)
                 cp_async4(smem_u32(rb + wq * (G::WS / 4) + i * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
+            }
+          }
+        } else if (PROD) {
+          // the two gradient components of the unit's product (one for xx, yy, zz)
+          const GT* gbase = reinterpret_cast<const GT*>(in);
+          GT* sa = reinterpret_cast<GT*>(rb);
+          GT* sb = sa + NT * kTcLines;
+          const bool two = prod_a(IU.comp) != prod_b(IU.comp);
+          if ((vec & 1) && inside && IU.wfull) {
+            // 16-byte copies of LPC consecutive lines, within the warp's own 32 lines:
+            // lane -> line group qd of the warp, positions pg + PPI i
+            constexpr int LPC = 16 / (int)sizeof(GT), GPW = 32 / LPC, PPI = 32 / GPW;
+            const int qd = lane % GPW, pg = lane / GPW;
+            const GT* pa = gbase + IU.ga + (LPC * qd - lane) + (int64_t)qs * IU.istride;
+            const GT* pb = gbase + IU.gb + (LPC * qd - lane) + (int64_t)qs * IU.istride;
+#pragma unroll
+            for (int i = 0; i < NT / PPI; ++i) {
+              const int pos = pg + PPI * i;
+              const int so = pos * kTcLines + 32 * wq + LPC * qd;
+              cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + pos * IU.istride));
+              if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + pos * IU.istride));
+            }
+          } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
+#pragma unroll 4
+            for (int j = 0; j < NT; ++j) {
+              const int64_t q = (int64_t)min(max(qs + j, qlo), qhi) * IU.istride;
+              if (PROD == 1) {  // FP32: asynchronous 4-byte copies
+                cp_async4(smem_u32(sa + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.ga + q));
+                if (two)
+                  cp_async4(smem_u32(sb + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.gb + q));
+              } else {  // FP16: below the 4-byte copy size, loaded and stored here
+                sa[j * kTcLines + m] = gbase[IU.ga + q];
+                if (two) sb[j * kTcLines + m] = gbase[IU.gb + q];
+              }
             }
           }
         } else if ((vec & 1) && inside && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
@@ -527,6 +613,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
               for (int j = 0; j < NT; ++j) v[j] = j < jlo ? elo : (j > jhi ? ehi : v[j]);
             }
+          }
+        } else if (PROD) {
+          const GT* sa = reinterpret_cast<const GT*>(rb);
+          const GT* sb = prod_a(CU.comp) != prod_b(CU.comp) ? sa + NT * kTcLines : sa;
+          const float f = pr.s[CU.comp];
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const float a = GradT<PROD>::get(sa[j * kTcLines + m]), b = GradT<PROD>::get(sb[j * kTcLines + m]);
+            v[j] = pr.unit ? a * b : (a * b) * f;
           }
         } else {
 #pragma unroll
@@ -764,21 +859,21 @@ bool rows_map(CUtensorMap* map, const float* base, const Box& b) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int RR, bool XAXIS>
+template <int RR, bool XAXIS, int PROD>
 struct TcLaunch {
   static bool ready;
   static cudaError_t prepare() {
     if (ready) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcGeom<RR>::smem(XAXIS));
+    cudaError_t e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS, PROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcGeom<RR>::smem(XAXIS, PROD));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      e = cudaFuncSetAttribute(k_rho_tc<RR, XAXIS, PROD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     ready = true;
     return cudaSuccess;
   }
   static cudaError_t run(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                         const Taps& taps, const TcCtl& ctl, cudaStream_t st) {
+                         const Taps& taps, const TcCtl& ctl, const TcProd& pr, cudaStream_t st) {
     using G = TcGeom<RR>;
     cudaError_t e = prepare();
     if (e != cudaSuccess) return e;
@@ -794,10 +889,11 @@ struct TcLaunch {
     const int64_t units = groups * ((a_n + seg - 1) / seg);
     const int grid = (int)std::min<int64_t>(units, sms);
     // 16-byte copies: the input rows start on 16-byte boundaries, and so do
-    // the copied pieces (y / z: quads of lines, in warps whose 32 lines all
-    // lie in the box; x: the windows)
-    const bool rows16 = ((uintptr_t)in % 16) == 0 && ib.n[0] % 4 == 0;
-    const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0 : rows16 && (ob.lo[0] - ib.lo[0]) % 4 == 0;
+    // the copied pieces (y / z: groups of 4 lines, 8 for FP16 gradients, in
+    // warps whose 32 lines all lie in the box; x: the windows)
+    const int lq = PROD == 2 ? 8 : 4;  // elements per 16 bytes
+    const bool rows16 = ((uintptr_t)in % 16) == 0 && ib.n[0] % lq == 0;
+    const bool vin = axis == 0 ? rows16 && ib.lo[0] % 4 == 0 : rows16 && (ob.lo[0] - ib.lo[0]) % lq == 0;
     const bool vout = axis == 0 && ((uintptr_t)out % 16) == 0 && ob.n[0] % 4 == 0 && ob.lo[0] % 4 == 0;
     int flags = (vin ? 1 : 0) | (vout ? 2 : 0);
     // x form: tensor maps when each 128-row group is 128 consecutive rows of one component,
@@ -809,25 +905,47 @@ struct TcLaunch {
       if (vin && ob.lo[1] == ib.lo[1] && ob.n[1] == ib.n[1] && rows_map(&tin, in, ib)) flags |= 4;
       if (vout && rows_map(&tout, out, ob)) flags |= 8;
     }
-    k_rho_tc<RR, XAXIS><<<grid, kTcThreads, G::smem(XAXIS), st>>>(in, ib, dims[axis], out, ob, axis, seg, flags, taps,
-                                                                  tin, tout, ctl);
+    k_rho_tc<RR, XAXIS, PROD><<<grid, kTcThreads, G::smem(XAXIS, PROD), st>>>(in, ib, dims[axis], out, ob, axis, seg,
+                                                                              flags, taps, tin, tout, ctl, pr);
     return cudaGetLastError();
   }
 };
-template <int RR, bool XAXIS>
-bool TcLaunch<RR, XAXIS>::ready = false;
+template <int RR, bool XAXIS, int PROD>
+bool TcLaunch<RR, XAXIS, PROD>::ready = false;
 
 template <int RR>
 cudaError_t run_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
-                   const Taps& taps, const TcCtl& ctl, cudaStream_t st) {
-  return axis == 0 ? TcLaunch<RR, true>::run(in, ib, dims, out, ob, axis, taps, ctl, st)
-                   : TcLaunch<RR, false>::run(in, ib, dims, out, ob, axis, taps, ctl, st);
+                   const Taps& taps, const TcCtl& ctl, int prod, const TcProd& pr, cudaStream_t st) {
+  if (axis == 0) return TcLaunch<RR, true, 0>::run(in, ib, dims, out, ob, axis, taps, ctl, pr, st);
+  if (prod == 1) return TcLaunch<RR, false, 1>::run(in, ib, dims, out, ob, axis, taps, ctl, pr, st);
+  if (prod == 2) return TcLaunch<RR, false, 2>::run(in, ib, dims, out, ob, axis, taps, ctl, pr, st);
+  return TcLaunch<RR, false, 0>::run(in, ib, dims, out, ob, axis, taps, ctl, pr, st);
 }
 
 template <int RR>
 cudaError_t prepare_tc() {
-  cudaError_t e = TcLaunch<RR, true>::prepare();
-  return e == cudaSuccess ? TcLaunch<RR, false>::prepare() : e;
+  cudaError_t e = TcLaunch<RR, true, 0>::prepare();
+  if (e == cudaSuccess) e = TcLaunch<RR, false, 0>::prepare();
+  if (e == cudaSuccess) e = TcLaunch<RR, false, 1>::prepare();
+  if (e == cudaSuccess) e = TcLaunch<RR, false, 2>::prepare();
+  return e;
+}
+
+cudaError_t dispatch_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
+                        const Taps& taps, int rk, const TcCtl& ctl, int prod, const TcProd& pr, cudaStream_t st) {
+  if (box_vox(ob) == 0) return cudaSuccess;
+  if (axis < 0 || axis > 2 || (prod && axis == 0)) return cudaErrorInvalidValue;
+  switch (rk) {
+    case 4: return run_tc<4>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 6: return run_tc<6>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 8: return run_tc<8>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 12: return run_tc<12>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 16: return run_tc<16>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 24: return run_tc<24>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 32: return run_tc<32>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    case 36: return run_tc<36>(in, ib, dims, out, ob, axis, taps, ctl, prod, pr, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -846,19 +964,21 @@ cudaError_t prepare_rho_tc_kernels() {
 
 cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
                           const Taps& taps, int rk, const TcCtl& ctl, cudaStream_t st) {
-  if (box_vox(ob) == 0) return cudaSuccess;
-  if (axis < 0 || axis > 2) return cudaErrorInvalidValue;
-  switch (rk) {
-    case 4: return run_tc<4>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 6: return run_tc<6>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 8: return run_tc<8>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 12: return run_tc<12>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 16: return run_tc<16>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 24: return run_tc<24>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 32: return run_tc<32>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    case 36: return run_tc<36>(in, ib, dims, out, ob, axis, taps, ctl, st);
-    default: return cudaErrorInvalidValue;
+  TcProd pr;
+  std::memset(&pr, 0, sizeof pr);
+  return dispatch_tc(in, ib, dims, out, ob, axis, taps, rk, ctl, 0, pr, st);
+}
+
+cudaError_t launch_rho_tc_products(const void* g, bool half, const Box& ib, const int dims[3], float* out,
+                                   const Box& ob, int axis, const Taps& taps, const float scale[6], int rk,
+                                   const TcCtl& ctl, cudaStream_t st) {
+  TcProd pr;
+  pr.unit = 1;
+  for (int k = 0; k < 6; ++k) {
+    pr.s[k] = scale[k];
+    pr.unit = pr.unit && scale[k] == 1.f;
   }
+  return dispatch_tc(static_cast<const float*>(g), ib, dims, out, ob, axis, taps, rk, ctl, half ? 2 : 1, pr, st);
 }
 
 // The tensor cores take volumes whose x extent is a multiple of 4 (16-byte rows;

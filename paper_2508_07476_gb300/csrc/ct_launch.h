@@ -19,14 +19,16 @@ int rho_kernel_radius(int r);
 
 // The gradient and its products: launch_grad_xy writes the x/y-filtered partial
 // fields (3 planes over ab = grad_partial_box(ob, vb, R, dims[2])) of vol;
-// launch_grad_z takes their z pass and writes J (6 planes over ob).
+// launch_grad_z takes their z pass and writes J (6 FP32 planes over ob), or
+// with gout the gradient g (3 planes over ob: FP16 holding g * 2^-8 in the
+// mixed form, FP32 otherwise) for launch_rho_tc_products to form J from.
 Box grad_partial_box(const Box& ob, const Box& vb, int rs, int dimz);
 // tx / ty / tz: the taps of each axis (anisotropic voxels); scale: the factor of
 // each product (1 / (spacing_a spacing_b), xx yy zz xy xz yz).
 cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3], float* F, const Box& ab,
                            const Taps& tx, const Taps& ty, int rk, cudaStream_t st);
-cudaError_t launch_grad_z(const float* F, const Box& ab, float* J, const Box& ob, const Taps& tz,
-                          const float scale[6], int rk, bool mixed, cudaStream_t st);
+cudaError_t launch_grad_z(const float* F, const Box& ab, void* J, const Box& ob, const Taps& tz,
+                          const float scale[6], int rk, bool mixed, bool gout, cudaStream_t st);
 
 // rho pass along x: out (6 planes over ob) from in (6 planes over ib).
 cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
@@ -54,6 +56,13 @@ struct TcCtl {
 cudaError_t prepare_rho_tc_kernels();
 cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,
                           const Taps& taps, int rk, const TcCtl& ctl, cudaStream_t st);
+// The same pass along axis 1 or 2 reading the gradient instead of the tensor:
+// g (3 planes over ib: FP16 holding g * 2^-8 when half, else FP32, as
+// launch_grad_z writes them with gout) -> out (6 planes over ob) = the pass of
+// the products g_a g_b * scale[k], each formed as launch_grad_z forms it.
+cudaError_t launch_rho_tc_products(const void* g, bool half, const Box& ib, const int dims[3], float* out,
+                                   const Box& ob, int axis, const Taps& taps, const float scale[6], int rk,
+                                   const TcCtl& ctl, cudaStream_t st);
 // Whether a volume nx voxels wide suits launch_rho_tc along axis: 16-byte copies
 // of its rows (x extent a multiple of 4).
 bool rho_tc_volume_aligned(int nx, int axis);

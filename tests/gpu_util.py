@@ -194,7 +194,7 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
 # that their HA / IA are held to the bound instead of 0.5 deg.  A regression
 # that moved many voxels past 0.5 deg, or inputs whose tensors were mostly
 # ill-conditioned, would fail here rather than pass unseen.
-CAPS = {_lib.CT_PREC_FP32: {"literal": 1e-3, "ill": 3e-1}, _lib.CT_PREC_MIXED: {"literal": 1e-2, "ill": 5e-1}}
+CAPS = {_lib.CT_PREC_FP32: {"literal": 1e-4, "ill": 3e-1}, _lib.CT_PREC_MIXED: {"literal": 2e-3, "ill": 6e-1}}
 CAP_MIN_GRADED = 2000  # caps apply to samples of at least this many graded voxels
 
 

@@ -5,7 +5,10 @@ CT_TUNE_TC_RHO selects, per plan, which axes run on the tensor cores (bit a
 for axis a; the library default is 7, all three, for rho radii of 24 and up
 on volumes whose x extent suits 16-byte copies); the oracle cases run each
 single axis, all three and none (the FP32 stencils), so a wrong ring slot,
-band offset, transpose or clamp on any axis fails.  Tolerances are
+band offset, transpose or clamp on any axis fails.  With all three axes the
+default chain stores the gradient (FP16 in the mixed form) and forms the
+products in the z pass (then y, then x); CT_TUNE_TC_PRODUCTS=0 keeps the
+products in the gradient kernel and runs x, y, z: both are graded.  Tolerances are
 the FP32 stage tolerances of test_gpu_parity.py: the split keeps each product
 within about 2^-20 of its value, below the stencil's own accumulated rounding.
 """
@@ -37,10 +40,11 @@ def tc(monkeypatch):
     # the library picks the tensor cores for R >= 24 and volumes whose x extent
     # suits the 16-byte copies; these tests force them (or the stencils, mask 0)
     # at every radius and extent
-    def use(mask):
+    def use(mask, products=True):
         monkeypatch.setenv("CT_TUNE_TC_RHO", str(mask))
         monkeypatch.setenv("CT_TUNE_TC_MIN_R", "0")
         monkeypatch.setenv("CT_TUNE_TC_ANY_BOX", "1")
+        monkeypatch.setenv("CT_TUNE_TC_PRODUCTS", "1" if products else "0")
     return use
 
 
@@ -72,10 +76,11 @@ def test_tc_structure_tensor_ragged(tc, mask, shape, sigma, rho):
     assert err <= 2e-5, (mask, err)
 
 
-@pytest.mark.parametrize("mask", MASKS)
+@pytest.mark.parametrize("mask", MASKS + ["7j"])
 def test_tc_sub_box_matches_oracle_and_whole(tc, mask):
     # a padded chunk whose line groups, rows and segments are all ragged
-    tc(mask)
+    # ("7j": all three axes with the products in the gradient kernel)
+    tc(7, False) if mask == "7j" else tc(mask)
     vol = _rand_vol((60, 150, 140), seed=11)
     sigma, rho = 1.0, 3.0
     h = O.radius(sigma) + O.radius(rho)
@@ -93,10 +98,12 @@ def test_tc_sub_box_matches_oracle_and_whole(tc, mask):
 
 
 @pytest.mark.parametrize("mask", MASKS)
-@pytest.mark.parametrize("nx_out", [128, 100])
+@pytest.mark.parametrize("nx_out", [128, 100, 124])
 def test_tc_aligned_sub_box_matches_oracle_and_whole(tc, mask, nx_out):
     # boxes on 16-byte boundaries: the 16-byte copy paths (100: a ragged line
-    # group, whose last warps copy line by line)
+    # group, whose last warps copy line by line; 124: x extents that are
+    # multiples of 4 but not 8, where the FP16 gradient rows lose their
+    # 16-byte alignment and go line by line)
     tc(mask)
     vol = _rand_vol((48, 60, 192), seed=13)
     sigma, rho = 1.0, 3.0
@@ -114,9 +121,10 @@ def test_tc_aligned_sub_box_matches_oracle_and_whole(tc, mask, nx_out):
     np.testing.assert_array_equal(g["S"], full["S"][sl])
 
 
+@pytest.mark.parametrize("products", [True, False])
 @pytest.mark.parametrize("prec,tol", [(FP32, 2e-5), (MIXED, 2e-3)])
-def test_tc_helix64(tc, prec, tol):
-    tc(7)
+def test_tc_helix64(tc, prec, tol, products):
+    tc(7, products)
     W = synth.single_chunk_64()
     vol, _ = synth.generate(W.spec)
     cen, ax = synth.frame_of(W.spec)
@@ -156,9 +164,10 @@ def test_tc_many_units_aligned_matches_oracle(tc):
         assert _rel(sub, S_o) <= 2e-5, lo
 
 
+@pytest.mark.parametrize("products", [True, False])
 @pytest.mark.parametrize("prec", [FP32, MIXED])
-def test_tc_fused_and_chunked_match_oracle(tc, prec):
-    tc(7)
+def test_tc_fused_and_chunked_match_oracle(tc, prec, products):
+    tc(7, products)
     W = synth.single_chunk_64()
     vol, mask = synth.generate(W.spec)
     cen, ax = synth.frame_of(W.spec)
@@ -242,3 +251,20 @@ def test_default_selection_is_per_volume(monkeypatch, nx, rho, min_vox, expect_t
     assert {n for n in names_c if n.startswith("rho")} == {n for n in names if n.startswith("rho")}
     np.testing.assert_array_equal(v_c, v)
     np.testing.assert_array_equal(fa_c, fa)
+
+
+@pytest.mark.parametrize("shape", [(40, 24, 256), (24, 20, 204), (20, 30, 61), (16, 40, 128)])
+def test_tc_fp16_gradient_paths(tc, shape):
+    # the mixed form's gradient crosses HBM in FP16 and the z pass forms the
+    # products from it: 16-byte copies of 8 lines (x extent a multiple of 8),
+    # line-by-line loads otherwise (204, 61).  The chain with the products in
+    # the gradient kernel uses the same FP16-rounded gradient and the same FP32
+    # products, so the two differ only by the order of the three passes
+    vol = _rand_vol(shape, seed=sum(shape) + 1)
+    S_o = O.structure_tensor(vol, 1.0, 3.0)
+    out = {}
+    for products in (True, False):
+        tc(7, products)
+        out[products] = G.stages(vol, 1.0, 3.0, (10.0, 10.0, 5.0), (0.0, 0.0, 1.0), precision=MIXED)["S"]
+        assert _rel(out[products], S_o) <= 2e-3, products
+    assert _rel(out[True], out[False].astype(np.float64)) <= 2e-5
