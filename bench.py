@@ -59,6 +59,9 @@ def _args():
                     help="annulus512 (default, the headline line) or one of the other workload shapes")
     ap.add_argument("--crops", type=int, default=200)
     ap.add_argument("--zplanes", type=int, default=0, help="stream2048/tera4096: limit the z extent (0 = full)")
+    ap.add_argument("--split", choices=["replicas", "zslab"], default="replicas",
+                    help="under torchrun: one volume per rank (replicas, weak scaling) or one volume split in "
+                         "z-slabs with their halos (zslab, strong scaling)")
     return ap.parse_args()
 
 
@@ -1000,10 +1003,78 @@ def run_tera(args):
            "accuracy": accuracy})
 
 
+def run_zslab(args):
+    """One annulus volume split across the ranks in z-slabs (strong scaling):
+    rank k generates the input planes of its slab plus the halo and runs the
+    padded-box call on them; no collective on the data path."""
+    import torch
+    from paper_2508_07476_gb300 import _lib, partition, synth
+    import __graft_entry__
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    W = _workload(args.size)
+    n = args.size
+    h = _lib.ct_radius(W.sigma) + _lib.ct_radius(W.rho)
+    sl = partition.z_slabs((n, n, n), world, h)[rank]
+    i0, i1 = sl.in_z
+    z0, z1 = sl.out_z
+    vol, _ = synth.generate(W.spec, (i0, i1))
+    _, mask = synth.generate(W.spec, (z0, z1))
+    cen, ax = synth.frame_of(W.spec)
+    d_vol = torch.from_numpy(vol.view(np.int16)).cuda()
+    d_mask = torch.from_numpy(mask).cuda()
+    nzs = z1 - z0
+    outs = [torch.empty((3, nzs, n, n), device="cuda")] + [torch.empty((nzs, n, n), device="cuda") for _ in range(3)]
+    plan = _lib.ct_plan_create(_lib.make_params(W.sigma, W.rho, cen, ax, _lib.CT_PREC_MIXED), (n, n, n))
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    try:
+        for _ in range(args.warmup):
+            _lib.ct_run_box(plan, d_vol, sl.in_lo, sl.in_n, sl.out_lo, sl.out_n, d_mask, *outs, stream)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            _lib.ct_run_box(plan, d_vol, sl.in_lo, sl.in_n, sl.out_lo, sl.out_n, d_mask, *outs, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+        st = _lib.ct_plan_stats(plan)
+    finally:
+        _lib.ct_plan_destroy(plan)
+    if rank == 0:
+        line = {"metric": METRIC, "value": n ** 3 / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded annulus volume)",
+                "config": {"workload": W.name, "dims": [n, n, n], "sigma": W.sigma, "rho": W.rho, "mask": True,
+                           "precision": "mixed", "parallelism": f"one volume in {world} z-slabs, halo {h} planes",
+                           "slab_planes": [s.out_n[2] for s in partition.z_slabs((n, n, n), world, h)]},
+                "gpu_launches": st["launches"]}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.split == "zslab":
+        run_zslab(args)
     elif args.workload == "crops200":
         run_crops(args)
     elif args.workload == "stream2048":

@@ -509,19 +509,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           GT* sa = reinterpret_cast<GT*>(rb);
           GT* sb = sa + NT * kTcLines;
           const bool two = prod_a(IU.comp) != prod_b(IU.comp);
-          if ((vec & 1) && inside && IU.wfull) {
+          if ((vec & 1) && IU.wfull) {
             // 16-byte copies of LPC consecutive lines, within the warp's own 32 lines:
-            // lane -> line group qd of the warp, positions pg + PPI i
+            // lane -> line group qd of the warp, positions pg + PPI i, each clamped
+            // to the box (a copy holds one position of its lines)
             constexpr int LPC = 16 / (int)sizeof(GT), GPW = 32 / LPC, PPI = 32 / GPW;
             const int qd = lane % GPW, pg = lane / GPW;
-            const GT* pa = gbase + IU.ga + (LPC * qd - lane) + (int64_t)qs * IU.istride;
-            const GT* pb = gbase + IU.gb + (LPC * qd - lane) + (int64_t)qs * IU.istride;
+            const GT* pa = gbase + IU.ga + (LPC * qd - lane);
+            const GT* pb = gbase + IU.gb + (LPC * qd - lane);
 #pragma unroll
             for (int i = 0; i < NT / PPI; ++i) {
               const int pos = pg + PPI * i;
+              const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
               const int so = pos * kTcLines + 32 * wq + LPC * qd;
-              cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + pos * IU.istride));
-              if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + pos * IU.istride));
+              cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + q));
+              if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + q));
             }
           } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
 #pragma unroll 4
@@ -537,17 +539,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               }
             }
           }
-        } else if ((vec & 1) && inside && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
-                                                 // own 32 lines (the stage hand-off is warp-local):
-                                                 // lane -> lines 32 wq + 4 (lane % 8).., positions
-                                                 // lane / 8 + 4 i; a warp with lines past the box
-                                                 // copies its own line, clamped, below
+        } else if ((vec & 1) && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
+                                       // own 32 lines (the stage hand-off is warp-local):
+                                       // lane -> lines 32 wq + 4 (lane % 8).., positions
+                                       // lane / 8 + 4 i, each clamped to the box; a warp
+                                       // with lines past the box copies its own line below
           const int qd = lane & 7, pg = lane >> 3;
-          const float* p = IU.src + (4 * qd - lane) + (int64_t)qs * IU.istride;
+          const float* p = IU.src + (4 * qd - lane);
 #pragma unroll
           for (int i = 0; i < NT / 4; ++i) {
             const int pos = pg + 4 * i;
-            cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + pos * IU.istride);
+            const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
+            cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + q);
           }
         } else if (!IU.lok) {
           // a line past the box: its products are never stored and every line's
@@ -576,6 +579,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
       const TcUnit CU = decode(unit);
       const int nt = CU.nt;
+      const float fprod = PROD ? (CU.comp < 3 ? (CU.comp == 0 ? pr.s[0] : CU.comp == 1 ? pr.s[1] : pr.s[2])
+                                              : (CU.comp == 3 ? pr.s[3] : CU.comp == 4 ? pr.s[4] : pr.s[5]))
+                               : 1.f;  // selected without indexing the parameter (no stack copy)
       if (!G::BIG) gbase = 0;
       const int q0u = CU.p0 - G::RA - alo;  // relative input position of window position 0
       for (int c = 0; c < G::P + nt; ++c, ++k) {
@@ -617,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         } else if (PROD) {
           const GT* sa = reinterpret_cast<const GT*>(rb);
           const GT* sb = prod_a(CU.comp) != prod_b(CU.comp) ? sa + NT * kTcLines : sa;
-          const float f = pr.s[CU.comp];
+          const float f = fprod;
 #pragma unroll
           for (int j = 0; j < NT; ++j) {
             const float a = GradT<PROD>::get(sa[j * kTcLines + m]), b = GradT<PROD>::get(sb[j * kTcLines + m]);

@@ -143,14 +143,17 @@ def angle_deg(u, v):
 EPS_S = {_lib.CT_PREC_FP32: 1e-5, _lib.CT_PREC_MIXED: 1e-3}
 
 
-def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32, angles: bool = True) -> dict:
+def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32, angles: bool = True,
+            f16_angles: bool = False) -> dict:
     """Per-output errors on the graded voxel sets; returns metrics (no asserts).
 
     "well" voxels are those whose direction the form can fix to 0.5 deg (the
     perturbation bound below 0.5 deg); the literal HA / IA bounds apply there,
     and everywhere else HA and IA are held to what the direction error d
     allows: |dIA| <= d and |dHA| <= d / cos(IA) (plus 0.01 deg of rounding).
-    angles=False leaves HA and IA out (quantised outputs: see compare_u8q).
+    angles=False leaves HA and IA out (quantised outputs: see compare_u8q);
+    f16_angles adds the FP16 encoding's rounding (half a unit in the last place
+    of the oracle's angle) to the HA / IA perturbation bounds.
     """
     if not angles:
         gpu = dict(gpu, ha=ora["ha"], ia=ora["ia"])
@@ -171,7 +174,13 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     dha_all = np.abs((gpu["ha"][sel] - ora["ha"][sel] + 90.0) % 180.0 - 90.0)
     cos_ia = np.cos(np.radians(ora["ia"][sel]))
     ha_graded = well & (cos_ia >= math.cos(math.radians(HA_IA_LIMIT_DEG)))
-    out["ha_bound_excess"] = float((dha_all - (d / np.maximum(cos_ia, 1e-12) + 0.01)).max()) if d.size else 0.0
+    def q16(a):  # half a unit in the last place of FP16 at |a| (0 for FP32 outputs)
+        if not f16_angles:
+            return 0.0
+        return np.spacing(np.abs(a).astype(np.float16)).astype(np.float64) / 2
+
+    out["ha_bound_excess"] = float((dha_all - (d / np.maximum(cos_ia, 1e-12) + 0.01 + q16(ora["ha"][sel]))).max()) \
+        if d.size else 0.0
     out["ha_literal_max"] = float(dha_all.max()) if dha_all.size else 0.0
     dia_all = np.abs(gpu["ia"][sel] - ora["ia"][sel])
     flip = np.abs(ora["ha"][sel]) > 89.0
@@ -179,7 +188,7 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     # |IA| is 1-Lipschitz in the direction; its sign follows the orientation rule,
     # which a direction error may flip, so the bound compares magnitudes
     dia_abs = np.abs(np.abs(gpu["ia"][sel]) - np.abs(ora["ia"][sel]))
-    out["ia_bound_excess"] = float((dia_abs - (d + 0.01)).max()) if d.size else 0.0
+    out["ia_bound_excess"] = float((dia_abs - (d + 0.01 + q16(ora["ia"][sel]))).max()) if d.size else 0.0
     dfa = np.abs(gpu["fa"][inside] - ora["fa"][inside])
     for name, e in (("dir", d), ("ha", dha_all[ha_graded]), ("ia", dia_all[well]), ("fa", dfa)):
         out[f"{name}_max"] = float(e.max()) if e.size else 0.0
@@ -187,23 +196,25 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     return out
 
 
-# Caps on the share of graded voxels that the perturbation-bound reading
-# exempts from the literal bounds (see the module docstring), per arithmetic
-# form: "literal": voxels whose direction error exceeds 0.5 deg (each still
-# within its own bound); "ill": voxels whose bound exceeds 0.5 deg at all, so
-# that their HA / IA are held to the bound instead of 0.5 deg.  A regression
-# that moved many voxels past 0.5 deg, or inputs whose tensors were mostly
-# ill-conditioned, would fail here rather than pass unseen.
-CAPS = {_lib.CT_PREC_FP32: {"literal": 1e-4, "ill": 3e-1}, _lib.CT_PREC_MIXED: {"literal": 2e-3, "ill": 6e-1}}
+# Caps on the voxels the perturbation-bound reading exempts (see the module
+# docstring), per arithmetic form.  "literal": the share of graded voxels whose
+# direction error exceeds 0.5 deg (each still within its own bound); a GPU
+# regression that moved many voxels past 0.5 deg fails here rather than pass
+# unseen.  "ill": the share whose bound exceeds 0.5 deg at all (their HA / IA
+# held to the bound instead of 0.5 deg); it depends on the input alone (the
+# oracle's eigenvalue gaps and the form's error bound), so it is capped per
+# workload by the caller (max_ill) where the input is a configuration's.
+CAPS = {_lib.CT_PREC_FP32: {"literal": 1e-4}, _lib.CT_PREC_MIXED: {"literal": 2e-3}}
 CAP_MIN_GRADED = 2000  # caps apply to samples of at least this many graded voxels
 
 
-def assert_within(m: dict, label: str = "", literal_ha: bool = False, precision: int = None):
+def assert_within(m: dict, label: str = "", literal_ha: bool = False, precision: int = None,
+                  max_ill: float = None):
     msg = f"{label}: {m}"
     if precision is not None and m["n_graded"] >= CAP_MIN_GRADED:
-        cap = CAPS[precision]
-        assert m["dir_literal_fail"] <= cap["literal"] * m["n_graded"], msg
-        assert m["n_ill_conditioned"] <= cap["ill"] * m["n_graded"], msg
+        assert m["dir_literal_fail"] <= CAPS[precision]["literal"] * m["n_graded"], msg
+    if max_ill is not None and m["n_graded"] >= CAP_MIN_GRADED:
+        assert m["n_ill_conditioned"] <= max_ill * m["n_graded"], msg
     assert m["dir_bound_excess"] <= 0.0, msg
     assert m["ha_max"] <= ANG_TOL_DEG, msg
     assert m["ia_max"] <= ANG_TOL_DEG, msg

@@ -61,6 +61,11 @@ def _spec(name, shape=(256, 256, 256)):
     raise ValueError(name)
 
 
+# share of graded voxels whose perturbation bound exceeds 0.5 deg, per
+# configuration and form (the input's property; measured shares well below)
+MAX_ILL = {("stream", MIXED): 0.05, ("stream", FP32): 0.01, ("tera", MIXED): 0.05, ("tera", FP32): 0.01,
+           ("crop", MIXED): 0.95, ("crop", FP32): 0.10, ("unit", MIXED): 0.05, ("unit", FP32): 0.01}
+
 CASES = {
     "stream_s2_r8": ("stream", 2.0, 8.0, True, (F16, F16, F16)),
     "tera_s3_r9": ("tera", 3.0, 9.0, True, (F16, U8Q, F16)),
@@ -117,7 +122,7 @@ def _oracle_box(key, vol, sigma, rho, cen, ax, mask, lo, n):
 
 def _grade(key, vol, mask, spec, sigma, rho, prec, types, gpu, boxes, b):
     cen, ax = synth.frame_of(spec)
-    graded = 0
+    tot = {"graded": 0, "ill": 0, "literal": 0}
     for lo in boxes:
         n = (b, b, b)
         ora = _oracle_box(key, vol, sigma, rho, cen, ax, mask, lo, n)
@@ -125,16 +130,23 @@ def _grade(key, vol, mask, spec, sigma, rho, prec, types, gpu, boxes, b):
         sub = {k: (gpu[k][(slice(None),) + sl] if k == "v" else gpu[k][sl]) for k in ("v", "ha", "ia", "fa")}
         msub = None if mask is None else mask[sl]
         quant = types[1] == U8Q
-        m = G.compare(sub, ora, msub, precision=prec, angles=not quant)
+        m = G.compare(sub, ora, msub, precision=prec, angles=not quant, f16_angles=types[1] == F16)
         print(key, prec, lo, m)
         G.assert_within(m, f"{key} box {lo} prec={prec}", precision=prec)
+        tot["graded"] += m["n_graded"]
+        tot["ill"] += m["n_ill_conditioned"]
+        tot["literal"] += m["dir_literal_fail"]
         if quant:
             q = G.compare_u8q({"ha": sub["ha"], "ia": sub["ia"]}, ora, msub, precision=prec)
             print(key, prec, lo, q)
             assert q["ha_code_max"] <= 1 and q["ia_code_max"] <= 1, (lo, q)
             assert q["outside_code_nonzero"] == 0, (lo, q)
-        graded += m["n_graded"]
-    return graded
+    # over the case's boxes: the caps of gpu_util on the direction, and the
+    # share of ill-conditioned voxels this configuration's input gives
+    print(key, prec, "totals", tot)
+    assert tot["literal"] <= G.CAPS[prec]["literal"] * tot["graded"], tot
+    assert tot["ill"] <= MAX_ILL[(key.split("_")[0], prec)] * tot["graded"], tot
+    return tot["graded"]
 
 
 @pytest.mark.parametrize("prec", [MIXED, FP32])
@@ -179,7 +191,7 @@ def test_config_scale_takes_the_expected_passes(case, tc):
     spec, vol, mask = _volume(name)
     cen, ax = synth.frame_of(spec)
     names = _kernel_names(vol, sigma, rho, cen, ax, mask if use_mask else None)
-    assert all(f"rho_{a}_tc" in names for a in "xyz") == tc, names
+    assert all(any(k.startswith(f"rho_{a}_tc") for k in names) for a in "xyz") == tc, names
 
 
 @pytest.mark.parametrize("prec", [MIXED, FP32])
