@@ -374,6 +374,46 @@ ct_status ct_track(const ct_track_params* params, const int64_t vol_dims[3], con
                    void* stream);
 
 /*
+ * Autotuner of the kernel choices (the paper gives none: the integration-scale
+ * smoothing's formulation and schedule are this library's).  For volumes of
+ * size vol_dims at the scales and precision of `params`, it times on the
+ * current device, on a seeded synthetic annulus of that size (with the
+ * annulus mask when `masked`), one padded-box call per candidate over the
+ * whole volume, or over a chunk of size `chunk` (nullable; 0 = whole extent)
+ * at the volume's centre with its halo, as ct_run_chunks processes chunks: the rho passes as FP32 stencils (8 or 16 outputs per y / z thread
+ * block) or on the tensor cores (products formed in the gradient kernel or in
+ * the first pass; work units of at most 512, 256 or 128 outputs), then, when
+ * masked, the eigen stage over compacted voxels or a thread per voxel.  Best
+ * of 3 runs after a warm-up, CUDA events.  *out gets the best choice, its
+ * time and that of the built-in choices.  With cache_file (nullable) the
+ * choice is stored there under the device's name and the key (precision,
+ * instantiated radii R(sigma) and R(rho), x extent class: a multiple of 8, of
+ * 4, or neither; floor(log2(voxels))), replacing an entry of the same key.
+ * Plans read the cache at creation (CT_TUNE_CACHE names it, "" disables it;
+ * default: tuning/tune_cache.json beside the library's package directory)
+ * and apply the entry of their precision, radii and x class whose size class
+ * is nearest to a volume's, within one either way; the choice is made per
+ * volume, so chunks of a volume reproduce it bit for bit.  Any CT_TUNE_*
+ * setting of these choices in the environment disables the cache for a plan.
+ * Synchronous; allocates its own device buffers (the timed box and its halo:
+ * at most 2^30 voxels).
+ */
+typedef struct ct_tune_result {
+  int32_t rho_path;     /* 0 FP32 stencils; 1 tensor cores, products in the gradient kernel;
+                           2 tensor cores, products formed in the first pass */
+  int32_t seg_cap;      /* tensor-core outputs per work unit at most (0: not tuned) */
+  int32_t stream_block; /* stencil outputs per y / z thread block (0: not tuned) */
+  int32_t eig_compact;  /* 1 compacted, 0 a thread per voxel, -1 not tuned (unmasked) */
+  double ms;            /* best time of one run */
+  double default_ms;    /* time with the built-in choices */
+  int32_t candidates;   /* configurations timed */
+  int32_t reserved;
+} ct_tune_result;
+
+ct_status ct_autotune(const ct_params* params, const int64_t vol_dims[3], const int64_t chunk[3], int32_t masked,
+                      const char* cache_file, ct_tune_result* out);
+
+/*
  * Measurement support (not part of the method): the device's FP32 FMA rate.
  * A kernel of independent FMA chains fills every SM of the current device
  * (the SM count read from the device) for `iterations` steps of 16 FMAs per

@@ -74,6 +74,12 @@ class ct_profile_spec(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class ct_tune_result(ctypes.Structure):
+    _fields_ = [("rho_path", ctypes.c_int32), ("seg_cap", ctypes.c_int32), ("stream_block", ctypes.c_int32),
+                ("eig_compact", ctypes.c_int32), ("ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class ct_track_params(ctypes.Structure):
     _fields_ = [("step", ctypes.c_double), ("fa_min", ctypes.c_double), ("max_turn_deg", ctypes.c_double),
                 ("max_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -118,6 +124,9 @@ _SIGNATURES = [
     ("ct_plan_profile", ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32]),
     ("ct_plan_kernel_times", ctypes.c_int32,
      [ctypes.c_void_p, ctypes.POINTER(ct_kernel_time), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    ("ct_autotune", ctypes.c_int32,
+     [ctypes.POINTER(ct_params), _I64x3, ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p,
+      ctypes.POINTER(ct_tune_result)]),
     ("ct_fp32_fma_rate", ctypes.c_int32,
      [ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
       ctypes.POINTER(ctypes.c_double)]),
@@ -323,6 +332,16 @@ def ct_plan_kernel_times(plan) -> dict:
     n = ctypes.c_int32(0)
     _check(load().ct_plan_kernel_times(plan, buf, 64, ctypes.byref(n)))
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+
+def ct_autotune(params: ct_params, vol_dims, masked: bool, cache_file: Optional[str] = None, chunk=None) -> dict:
+    """Time the kernel choices for volumes of this size and scale (on the whole
+    volume, or on one chunk of it); store the best in cache_file."""
+    r = ct_tune_result()
+    path = None if cache_file is None else os.fsencode(cache_file)
+    ch = None if chunk is None else ctypes.cast(_i64x3(chunk), ctypes.c_void_p)
+    _check(load().ct_autotune(ctypes.byref(params), _i64x3(vol_dims), ch, int(bool(masked)), path, ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in ct_tune_result._fields_ if k != "reserved"}
 
 
 def ct_fp32_fma_rate(iterations: int = 200000) -> dict:

@@ -6,6 +6,7 @@
 // handling at the global edges only, a chunked run reproduces the
 // whole-volume result exactly.
 #include <cuda_runtime.h>
+#include <dlfcn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -13,7 +14,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -190,6 +193,22 @@ struct ct_plan_s {
   bool tc_products = true;  // with all three passes there: products formed in the first (tuning choice)
   bool eig_compact = true;  // masked eigen stage over compacted inside voxels (tuning choice)
   int64_t slab_bytes = int64_t(4) << 30;  // host streaming: device bytes of one slab's buffers at most
+  // Autotuned choices (ct_autotune), read from the tuning cache at plan
+  // creation: this GPU's entries, one per (precision, instantiated radii,
+  // x-extent class, size class) of a volume.  A choice applies to every box of
+  // a volume alike (the key is the volume's), so chunks still reproduce it.
+  struct TuneEntry {
+    int precision, rs, rr, xclass, vlog2;
+    int rho_path;      // 0: FP32 stencils; 1: tensor cores, products in the gradient kernel;
+                       // 2: tensor cores, products formed in the first pass
+    int seg_cap;       // tensor-core outputs per work unit at most (0: the default)
+    int stream_block;  // stencil y / z outputs per thread block (0: the default)
+    int eig_compact;   // masked eigen stage over compacted voxels (-1: the default)
+    double ms;
+  };
+  std::vector<TuneEntry> tune;
+  bool tune_forced = false;           // a CT_TUNE_* setting of the rho path set: the cache is not used
+  const TuneEntry* trial = nullptr;   // ct_autotune's candidate under test
   // per-kernel timing (ct_plan_profile)
   bool profile = false;
   struct Rec {
@@ -364,6 +383,31 @@ ct_status sync_plan(ct_plan P) {
     (P)->stats.launches += 1;                                               \
   } while (0)
 
+int x_class(int nx) { return nx % 8 == 0 ? 8 : (nx % 4 == 0 ? 4 : 1); }
+
+int vox_log2(const int dims[3]) {
+  const int64_t v = (int64_t)dims[0] * dims[1] * dims[2];
+  int l = 0;
+  while (l < 62 && (int64_t(1) << (l + 1)) <= v) ++l;
+  return l;
+}
+
+// The autotuned choice for a volume of size dims at scale sc (nullptr: the
+// defaults): the entry of the same precision, radii and x-extent class whose
+// size class is nearest, within a factor of two either way.
+const ct_plan_s::TuneEntry* tuned(const ct_plan P, const Scale& sc, const int dims[3]) {
+  if (P->trial) return P->trial;
+  if (P->tune_forced) return nullptr;
+  const int xc = x_class(dims[0]), vl = vox_log2(dims);
+  const ct_plan_s::TuneEntry* best = nullptr;
+  for (const auto& t : P->tune) {
+    if (t.precision != P->p.precision || t.rs != sc.rks || t.rr != sc.rkr || t.xclass != xc) continue;
+    if (std::abs(t.vlog2 - vl) > 1) continue;
+    if (!best || std::abs(t.vlog2 - vl) < std::abs(best->vlog2 - vl)) best = &t;
+  }
+  return best;
+}
+
 // Whether the rho pass along axis of a volume dims[] runs on the tensor cores:
 // a function of the plan, the volume's extent and the scale, never of the box,
 // so that every chunk and sub-box of a volume takes the same arithmetic as the
@@ -377,6 +421,7 @@ ct_status sync_plan(ct_plan P) {
 // the tensor cores where the extent allows, 167 ms against 164).  tc_any_box
 // drops the extent and size conditions (tests drive every copy path with it).
 bool use_tc(const ct_plan P, const Scale& sc, const int dims[3], int axis) {
+  if (const auto* t = tuned(P, sc, dims)) return t->rho_path > 0;
   const int64_t vox = (int64_t)dims[0] * dims[1] * dims[2];
   return (P->tc_rho >> axis & 1) && sc.rkr >= P->tc_min_r &&
          (P->tc_any_box || (rho_tc_volume_aligned(dims[0], axis) && vox >= P->tc_min_vox));
@@ -405,11 +450,13 @@ ct_status smooth_chain(ct_plan P, const Scale& sc, const int dims[3], const uint
   if (rc) return rc;
   float* A = P->buf[slot][0];
   float* B = P->buf[slot][1];
-  const TcCtl ctl{P->d_timeouts, P->tc_wait_limit};
+  const auto* tuning = tuned(P, sc, dims);
+  const TcCtl ctl{P->d_timeouts, P->tc_wait_limit, tuning ? tuning->seg_cap : 0};
+  const int sblock = tuning && tuning->stream_block ? tuning->stream_block : P->stream_block;
   CT_LAUNCH(P, st, "grad_xy", launch_grad_xy(vol, vb, dims, B, Ab, sc.ts[0], sc.ts[1], sc.rks, st),
             "gradient x/y kernel launch");
   const bool tcx = use_tc(P, sc, dims, 0), tcy = use_tc(P, sc, dims, 1), tcz = use_tc(P, sc, dims, 2);
-  if (tcx && tcy && tcz && P->tc_products) {
+  if (tcx && tcy && tcz && (tuning ? tuning->rho_path == 2 : P->tc_products)) {
     Box Bz = G, Bzy = G;
     Bz.lo[2] = Bzy.lo[2] = ob.lo[2];
     Bz.n[2] = Bzy.n[2] = ob.n[2];
@@ -449,7 +496,7 @@ ct_status smooth_chain(ct_plan P, const Scale& sc, const int dims[3], const uint
       CT_LAUNCH(P, st, "rho_y_tc", launch_rho_tc(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, ctl, st),
                 "rho y kernel launch");
     else
-      CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, P->stream_block, st),
+      CT_LAUNCH(P, st, "rho_y", launch_rho_stream(B, Bx, dims, A, Bxy, 1, sc.tr[1], sc.rkr, sblock, st),
                 "rho y kernel launch");
     Sxy = A;
   } else {
@@ -461,7 +508,7 @@ ct_status smooth_chain(ct_plan P, const Scale& sc, const int dims[3], const uint
     CT_LAUNCH(P, st, "rho_z_tc", launch_rho_tc(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, ctl, st),
               "rho z kernel launch");
   else
-    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, P->stream_block, st),
+    CT_LAUNCH(P, st, "rho_z", launch_rho_stream(Sxy, Bxy, dims, S, ob, 2, sc.tr[2], sc.rkr, sblock, st),
               "rho z kernel launch");
   *S_res = S;
   return CT_OK;
@@ -475,7 +522,7 @@ ct_status tensor_stages(ct_plan P, const Scale& sc, const int dims[3], const uin
 }
 
 ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
-                    const EigOut& o, int slot, bool mixed, cudaStream_t st);
+                    const EigOut& o, int slot, bool mixed, bool compact, cudaStream_t st);
 
 // The fused hot path (Figure 1b, c): gradient and products, the three rho
 // passes into the free scratch buffer, then eigen + angles + mask + encode and
@@ -486,21 +533,126 @@ ct_status fused_stages(ct_plan P, const Scale& sc, const int dims[3], const uint
   float* S = nullptr;
   ct_status rc = smooth_chain(P, sc, dims, vol, vb, ob, slot, mixed, st, nullptr, &S);
   if (rc) return rc;
-  return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, st);
+  const auto* t = tuned(P, sc, dims);
+  return eig_stage(P, S, ob, mask, mb, F, o, slot, mixed, t && t->eig_compact >= 0 ? t->eig_compact != 0 : P->eig_compact,
+                   st);
 }
 
 // Eigen + angles over ob from S (over ob); outputs in arrays covering o.ab.
 ct_status eig_stage(ct_plan P, const float* S, const Box& ob, const uint8_t* mask, const Box& mb, const Frame& F,
-                    const EigOut& o, int slot, bool mixed, cudaStream_t st) {
+                    const EigOut& o, int slot, bool mixed, bool compact, cudaStream_t st) {
   Fallback fb = fallback_of(P, slot);
   CT_CUDA(cudaMemsetAsync(fb.count, 0, sizeof(int), st), "counter reset");
   CT_LAUNCH(P, st, "eig_angles",
-            launch_eig_angles(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, P->eig_compact, st),
+            launch_eig_angles(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, compact, st),
             "eigen kernel launch");
   CT_LAUNCH(P, st, "eig_resolve",
             launch_eig_angles_fallback(S, ob, ob, mask, mb, F, P->p.fill_value, o, mixed, fb, box_vox(ob), st),
             "re-solve kernel launch");
   return CT_OK;
+}
+
+// ------------------------------------------------------------ tuning cache
+// A JSON array, one object per line, written by ct_autotune:
+//   {"gpu": "<device name>", "precision": p, "rs": R_sigma, "rr": R_rho,
+//    "xclass": 8|4|1, "vox_log2": l, "rho_path": 0|1|2, "seg_cap": n,
+//    "stream_block": n, "eig_compact": -1|0|1, "ms": t}
+struct CacheLine {
+  std::string gpu;
+  ct_plan_s::TuneEntry e;
+};
+
+std::string default_cache_path() {
+  Dl_info info;
+  if (dladdr(reinterpret_cast<void*>(&ct_radius), &info) && info.dli_fname) {
+    const std::string so = info.dli_fname;  // <package>/_build/libct_gb300.so
+    const size_t k = so.rfind('/');
+    return (k == std::string::npos ? std::string(".") : so.substr(0, k)) + "/../tuning/tune_cache.json";
+  }
+  return "";
+}
+
+// CT_TUNE_CACHE names the cache ("" disables it); else the package's own.
+std::string cache_path() {
+  if (const char* e = std::getenv("CT_TUNE_CACHE")) return e;
+  return default_cache_path();
+}
+
+std::string gpu_name(int dev) {
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "";
+  }
+  return pr.name;
+}
+
+bool json_num(const std::string& line, const char* key, double* v) {
+  const std::string k = std::string("\"") + key + "\":";
+  const size_t p = line.find(k);
+  if (p == std::string::npos) return false;
+  const char* b = line.c_str() + p + k.size();
+  char* end = nullptr;
+  *v = std::strtod(b, &end);
+  return end != b;
+}
+
+bool json_str(const std::string& line, const char* key, std::string* v) {
+  const std::string k = std::string("\"") + key + "\":";
+  size_t p = line.find(k);
+  if (p == std::string::npos) return false;
+  p = line.find('"', p + k.size());
+  if (p == std::string::npos) return false;
+  const size_t q = line.find('"', p + 1);
+  if (q == std::string::npos) return false;
+  *v = line.substr(p + 1, q - p - 1);
+  return true;
+}
+
+std::vector<CacheLine> read_cache(const std::string& path) {
+  std::vector<CacheLine> out;
+  std::ifstream f(path);
+  std::string line;
+  while (f && std::getline(f, line)) {
+    if (line.find('{') == std::string::npos) continue;
+    CacheLine c;
+    double v[10];
+    static const char* keys[10] = {"precision", "rs", "rr", "xclass", "vox_log2", "rho_path", "seg_cap",
+                                   "stream_block", "eig_compact", "ms"};
+    bool ok = json_str(line, "gpu", &c.gpu);
+    for (int k = 0; k < 10 && ok; ++k) ok = json_num(line, keys[k], &v[k]);
+    if (!ok) continue;
+    c.e = {(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6], (int)v[7], (int)v[8], v[9]};
+    out.push_back(c);
+  }
+  return out;
+}
+
+bool same_key(const ct_plan_s::TuneEntry& a, const ct_plan_s::TuneEntry& b) {
+  return a.precision == b.precision && a.rs == b.rs && a.rr == b.rr && a.xclass == b.xclass && a.vlog2 == b.vlog2;
+}
+
+bool write_cache(const std::string& path, const std::vector<CacheLine>& lines) {
+  const std::string tmp = path + ".tmp";
+  {
+    std::ofstream f(tmp);
+    if (!f) return false;
+    f << "[\n";
+    for (size_t i = 0; i < lines.size(); ++i) {
+      const auto& e = lines[i].e;
+      char buf[512];
+      std::snprintf(buf, sizeof buf,
+                    "{\"gpu\": \"%s\", \"precision\": %d, \"rs\": %d, \"rr\": %d, \"xclass\": %d, "
+                    "\"vox_log2\": %d, \"rho_path\": %d, \"seg_cap\": %d, \"stream_block\": %d, "
+                    "\"eig_compact\": %d, \"ms\": %.4f}",
+                    lines[i].gpu.c_str(), e.precision, e.rs, e.rr, e.xclass, e.vlog2, e.rho_path, e.seg_cap,
+                    e.stream_block, e.eig_compact, e.ms);
+      f << buf << (i + 1 < lines.size() ? ",\n" : "\n");
+    }
+    f << "]\n";
+    if (!f) return false;
+  }
+  return std::rename(tmp.c_str(), path.c_str()) == 0;
 }
 
 }  // namespace
@@ -567,7 +719,16 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;
   if (const char* e = std::getenv("CT_TUNE_TC_WAIT_LIMIT")) P->tc_wait_limit = (uint32_t)std::max(0, std::atoi(e));
   if (const char* e = std::getenv("CT_TUNE_TC_PRODUCTS")) P->tc_products = std::atoi(e) != 0;
+  for (const char* k : {"CT_TUNE_TC_RHO", "CT_TUNE_TC_MIN_R", "CT_TUNE_TC_MIN_VOX", "CT_TUNE_TC_ANY_BOX",
+                        "CT_TUNE_TC_PRODUCTS", "CT_TUNE_STREAM_BLOCK", "CT_TUNE_EIG_COMPACT"})
+    if (std::getenv(k)) P->tune_forced = true;
   cudaGetDevice(&P->device);
+  if (!P->tune_forced) {
+    const std::string path = cache_path(), gpu = gpu_name(P->device);
+    if (!path.empty())
+      for (const auto& c : read_cache(path))
+        if (c.gpu == gpu) P->tune.push_back(c.e);
+  }
   {
     cudaError_t e = cudaMalloc(&P->d_timeouts, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(P->d_timeouts, 0, sizeof(unsigned int));
@@ -1106,6 +1267,172 @@ ct_status ct_plan_kernel_times(ct_plan P, ct_kernel_time* out, int32_t capacity,
   int32_t n = 0;
   for (size_t k = 0; k < acc.size() && n < capacity; ++k) out[n++] = acc[k];
   *count = n;
+  return CT_OK;
+}
+
+namespace {
+
+// Device buffers of one autotuning run, freed on every exit.
+struct TuneBuffers {
+  void* p[6] = {};
+  ~TuneBuffers() {
+    for (void* q : p)
+      if (q) cudaFree(q);
+  }
+};
+
+}  // namespace
+
+ct_status ct_autotune(const ct_params* params, const int64_t vol_dims[3], const int64_t chunk[3], int32_t masked,
+                      const char* cache_file, ct_tune_result* out) {
+  if (!out || !vol_dims) return fail(CT_ERR_INVALID, "NULL argument");
+  ct_status rc = check_params(params);
+  if (rc) return rc;
+  int dims[3];
+  for (int k = 0; k < 3; ++k) {
+    if (vol_dims[k] < 1 || vol_dims[k] > (1 << 20)) return fail(CT_ERR_INVALID, "vol_dims must be in [1, 2^20]");
+    dims[k] = (int)vol_dims[k];
+  }
+  Scale sc;
+  if ((rc = make_scale(*params, params->sigma, params->rho, &sc))) return rc;
+  // the timed box: the whole volume, or a chunk of the given size at its centre
+  // with its halo (the input box), as ct_run_chunks would process it
+  Box ob;
+  for (int k = 0; k < 3; ++k) {
+    const int c = chunk && chunk[k] > 0 ? (int)std::min<int64_t>(chunk[k], dims[k]) : dims[k];
+    ob.lo[k] = (dims[k] - c) / 2;
+    ob.n[k] = c;
+  }
+  const Box ib = grow_clip3(ob, sc.halo, dims);
+  const int64_t vox = box_vox(ib);
+  if (vox > (int64_t(1) << 30)) return fail(CT_ERR_INVALID, "the timed box and its halo hold at most 2^30 voxels");
+  int64_t in_lo[3], in_n[3], out_lo[3], out_n[3];
+  for (int k = 0; k < 3; ++k) {
+    in_lo[k] = ib.lo[k];
+    in_n[k] = ib.n[k];
+    out_lo[k] = ob.lo[k];
+    out_n[k] = ob.n[k];
+  }
+  if (!device_present()) return fail(CT_ERR_NO_DEVICE, "no CUDA device is available");
+  int dev = 0;
+  CT_CUDA(cudaGetDevice(&dev), "device query");
+  // a seeded annulus of the volume's size (the benchmark's construction, scaled)
+  TuneBuffers buf;
+  const size_t esz_v = elem_size(params->vec_type), esz_a = elem_size(params->angle_type),
+               esz_f = elem_size(params->fa_type);
+  const int64_t ovox = box_vox(ob);
+  CT_CUDA(cudaMalloc(&buf.p[0], sizeof(uint16_t) * vox), "volume allocation");
+  if (masked) CT_CUDA(cudaMalloc(&buf.p[1], ovox), "mask allocation");
+  CT_CUDA(cudaMalloc(&buf.p[2], esz_v * 3 * ovox), "output allocation");
+  CT_CUDA(cudaMalloc(&buf.p[3], esz_a * ovox), "output allocation");
+  CT_CUDA(cudaMalloc(&buf.p[4], esz_a * ovox), "output allocation");
+  CT_CUDA(cudaMalloc(&buf.p[5], esz_f * ovox), "output allocation");
+  ct_synth_spec sp;
+  std::memset(&sp, 0, sizeof sp);
+  const double m = std::min(dims[0], std::min(dims[1], dims[2]));
+  for (int k = 0; k < 3; ++k) sp.center[k] = (dims[k] - 1) / 2.0;
+  sp.axis[0] = std::sin(10.0 * M_PI / 180.0);
+  sp.axis[2] = std::cos(10.0 * M_PI / 180.0);
+  sp.r_in = 0.2 * m;
+  sp.r_out = 0.42 * m;
+  sp.period = 6.0;
+  sp.ha_in_deg = 60.0;
+  sp.ha_out_deg = -60.0;
+  sp.background = 1000.0;
+  sp.amplitude = 800.0;
+  sp.noise_kind = 0;
+  sp.noise_level = 50.0;
+  sp.flags = CT_SYNTH_FP32;
+  sp.seed = 11;
+  cudaStream_t st = nullptr;
+  CT_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream creation");
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } sg{st};
+  if ((rc = ct_synth_annulus(&sp, vol_dims, in_lo, in_n, (uint16_t*)buf.p[0], nullptr, st))) return rc;
+  if (masked && (rc = ct_synth_annulus(&sp, vol_dims, out_lo, out_n, nullptr, (uint8_t*)buf.p[1], st))) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CT_CUDA(cudaEventCreate(&e0), "event creation");
+  CT_CUDA(cudaEventCreate(&e1), "event creation");
+  struct EventGuard {
+    cudaEvent_t a, b;
+    ~EventGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } eg{e0, e1};
+  // one candidate: the whole volume as one padded box, best of 3 after a warm-up
+  auto measure = [&](const ct_plan_s::TuneEntry* cand, double* ms) -> ct_status {
+    ct_plan P = nullptr;
+    ct_status r = ct_plan_create(params, vol_dims, &P);
+    if (r) return r;
+    P->tune.clear();
+    P->tune_forced = true;
+    P->trial = cand;
+    double best = 1e30;
+    for (int it = 0; it < 4 && r == CT_OK; ++it) {
+      cudaEventRecord(e0, st);
+      r = ct_run_box(P, (const uint16_t*)buf.p[0], in_lo, in_n, out_lo, out_n, (const uint8_t*)buf.p[1], buf.p[2],
+                     buf.p[3], buf.p[4], buf.p[5], st);
+      cudaEventRecord(e1, st);
+      if (r == CT_OK) r = ct_plan_sync(P);
+      float t = 0.f;
+      if (r == CT_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "timing");
+      if (it > 0) best = std::min(best, (double)t);
+    }
+    ct_plan_destroy(P);
+    *ms = best;
+    return r;
+  };
+  std::memset(out, 0, sizeof *out);
+  if ((rc = measure(nullptr, &out->default_ms))) return rc;
+  const int xc = x_class(dims[0]), vl = vox_log2(dims);
+  std::vector<ct_plan_s::TuneEntry> cands;
+  auto entry = [&](int path, int seg, int sb, int ec) {
+    return ct_plan_s::TuneEntry{params->precision, sc.rks, sc.rkr, xc, vl, path, seg, sb, ec, 0.0};
+  };
+  if (xc >= 4)  // the tensor-core passes' 16-byte copies want x extents that are multiples of 4
+    for (int path : {2, 1})
+      for (int seg : {512, 256, 128}) cands.push_back(entry(path, seg, 0, -1));
+  for (int sb : {16, 8}) cands.push_back(entry(0, 0, sb, -1));
+  ct_plan_s::TuneEntry best = cands[0];
+  best.ms = 1e30;
+  for (auto& c : cands) {
+    if ((rc = measure(&c, &c.ms))) return rc;
+    if (c.ms < best.ms) best = c;
+  }
+  int n_timed = (int)cands.size() + 1;
+  if (masked) {  // the eigen stage's form, on the best path
+    ct_plan_s::TuneEntry pick = best;
+    pick.ms = 1e30;
+    for (int ec : {1, 0}) {
+      ct_plan_s::TuneEntry c = best;
+      c.eig_compact = ec;
+      if ((rc = measure(&c, &c.ms))) return rc;
+      ++n_timed;
+      if (c.ms < pick.ms) pick = c;
+    }
+    best = pick;
+  }
+  out->rho_path = best.rho_path;
+  out->seg_cap = best.seg_cap;
+  out->stream_block = best.stream_block;
+  out->eig_compact = best.eig_compact;
+  out->ms = best.ms;
+  out->candidates = n_timed;
+  if (cache_file && *cache_file) {
+    std::vector<CacheLine> lines = read_cache(cache_file);
+    const std::string gpu = gpu_name(dev);
+    bool replaced = false;
+    for (auto& l : lines)
+      if (l.gpu == gpu && same_key(l.e, best)) {
+        l.e = best;
+        replaced = true;
+      }
+    if (!replaced) lines.push_back(CacheLine{gpu, best});
+    if (!write_cache(cache_file, lines)) return fail(CT_ERR_INVALID, "cannot write the tuning cache %s", cache_file);
+  }
   return CT_OK;
 }
 

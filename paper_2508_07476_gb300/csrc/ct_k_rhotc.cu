@@ -289,13 +289,24 @@ __host__ __device__ constexpr int prod_b(int k) { return k < 3 ? k : (k == 3 ? 1
 template <int PROD>
 struct GradT {
   using T = float;
-  static __device__ __forceinline__ float get(float v) { return v; }
+  static constexpr float kBScale = 1.0f;
+  // the product g_a g_b
+  static __device__ __forceinline__ float prod(float a, float b) { return a * b; }
 };
 template <>
 struct GradT<2> {
   using T = __half;
-  // the mixed form's gradient: FP16 holding g * 2^-8, restored exactly
-  static __device__ __forceinline__ float get(__half v) { return __half2float(v) * 256.0f; }
+  // The mixed form's gradient is FP16 holding g * 2^-8.  The product of two
+  // FP16 values is exact in FP32, so one mixed-precision FMA (FP16 operands,
+  // FP32 result, + 0) gives (g_a 2^-8)(g_b 2^-8) exactly; the missing 2^16 is
+  // carried by the taps (B scaled by 2^16, which scales every product of the
+  // pass exactly), so D is the same as from the restored products.
+  static constexpr float kBScale = 65536.0f;
+  static __device__ __forceinline__ float prod(__half a, __half b) {
+    float r;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(r) : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(b)), "f"(0.0f));
+    return r;
+  }
 };
 
 // One 1-D pass of the integration-scale Gaussian along `axis` (0, 1 or 2; XAXIS
@@ -353,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   for (int e = tid; e < NT * G::W; e += kTcThreads) {
     const int n = e / G::W, k = e % G::W;
     const int j = k - n - (G::RA - RR);
-    const float v = (j >= 0 && j <= 2 * RR) ? taps.w[j] : 0.f;
+    const float v = (j >= 0 && j <= 2 * RR) ? taps.w[j] * GradT<PROD>::kBScale : 0.f;
     const float hi = tf32_round(v);
     const int c = core_index(n, k, G::KCB);
     sBhi[c] = hi;
@@ -626,8 +637,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const float f = fprod;
 #pragma unroll
           for (int j = 0; j < NT; ++j) {
-            const float a = GradT<PROD>::get(sa[j * kTcLines + m]), b = GradT<PROD>::get(sb[j * kTcLines + m]);
-            v[j] = pr.unit ? a * b : (a * b) * f;
+            const float ab = GradT<PROD>::prod(sa[j * kTcLines + m], sb[j * kTcLines + m]);
+            v[j] = pr.unit ? ab : ab * f;
           }
         } else {
 #pragma unroll
@@ -890,7 +901,10 @@ struct TcLaunch {
     const int a_n = ob.lo[axis] + ob.n[axis] - (ob.lo[axis] & ~(G::NT - 1));  // aligned extent
     const int64_t groups = axis == 0 ? (6 * (int64_t)ob.n[1] * ob.n[2] + kTcLines - 1) / kTcLines
                                      : 6 * (int64_t)ob.n[3 - axis] * ((ob.n[0] + kTcLines - 1) / kTcLines);
-    int seg = 512;  // outputs per unit: long enough to amortise the ring fill, short enough to spread
+    // outputs per unit: long enough to amortise the ring fill, short enough to spread
+    // (a power of two from NT to 512, so that units start on tile boundaries)
+    int seg = 512;
+    while (ctl.seg_cap > 0 && seg > ctl.seg_cap && seg > G::NT) seg /= 2;
     while (seg > G::NT && groups * ((a_n + seg - 1) / seg) < 2 * sms) seg /= 2;
     const int64_t units = groups * ((a_n + seg - 1) / seg);
     const int grid = (int)std::min<int64_t>(units, sms);

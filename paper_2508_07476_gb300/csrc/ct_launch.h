@@ -52,6 +52,7 @@ cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3],
 struct TcCtl {
   unsigned int* timeouts;
   uint32_t wait_limit;
+  int seg_cap;  // outputs per work unit at most (0: 512); the work is then spread over the SMs
 };
 cudaError_t prepare_rho_tc_kernels();
 cudaError_t launch_rho_tc(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,

@@ -174,12 +174,13 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     dha_all = np.abs((gpu["ha"][sel] - ora["ha"][sel] + 90.0) % 180.0 - 90.0)
     cos_ia = np.cos(np.radians(ora["ia"][sel]))
     ha_graded = well & (cos_ia >= math.cos(math.radians(HA_IA_LIMIT_DEG)))
-    def q16(a):  # half a unit in the last place of FP16 at |a| (0 for FP32 outputs)
+    def q16(k):  # half a unit in the last place of FP16 at the output's magnitude (0 for FP32 outputs)
         if not f16_angles:
             return 0.0
-        return np.spacing(np.abs(a).astype(np.float16)).astype(np.float64) / 2
+        a = np.maximum(np.abs(gpu[k][sel]), np.abs(ora[k][sel]))
+        return np.spacing(a.astype(np.float16)).astype(np.float64) / 2
 
-    out["ha_bound_excess"] = float((dha_all - (d / np.maximum(cos_ia, 1e-12) + 0.01 + q16(ora["ha"][sel]))).max()) \
+    out["ha_bound_excess"] = float((dha_all - (d / np.maximum(cos_ia, 1e-12) + 0.01 + q16("ha"))).max()) \
         if d.size else 0.0
     out["ha_literal_max"] = float(dha_all.max()) if dha_all.size else 0.0
     dia_all = np.abs(gpu["ia"][sel] - ora["ia"][sel])
@@ -188,7 +189,7 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     # |IA| is 1-Lipschitz in the direction; its sign follows the orientation rule,
     # which a direction error may flip, so the bound compares magnitudes
     dia_abs = np.abs(np.abs(gpu["ia"][sel]) - np.abs(ora["ia"][sel]))
-    out["ia_bound_excess"] = float((dia_abs - (d + 0.01 + q16(ora["ia"][sel]))).max()) if d.size else 0.0
+    out["ia_bound_excess"] = float((dia_abs - (d + 0.01 + q16("ia"))).max()) if d.size else 0.0
     dfa = np.abs(gpu["fa"][inside] - ora["fa"][inside])
     for name, e in (("dir", d), ("ha", dha_all[ha_graded]), ("ia", dia_all[well]), ("fa", dfa)):
         out[f"{name}_max"] = float(e.max()) if e.size else 0.0

@@ -154,3 +154,15 @@ def test_noalloc_validates_before_any_cuda_call(libpath, args, needle):
 
 def test_noalloc_zero_tensors_is_a_no_op(libpath):
     assert _lib.load().ct_eig_smallest_noalloc(16, 0, None, 16, 0, None) == _lib.CT_OK
+
+
+def test_autotune_validates_before_any_cuda_call(libpath):
+    lib = _lib.load()
+    p = _lib.make_params(1.0, 3.0, (0, 0, 0), (0, 0, 1))
+    res = _lib.ct_tune_result()
+    assert lib.ct_autotune(ctypes.byref(p), _lib._i64x3((16, 16, 16)), None, 0, None, None) == _lib.CT_ERR_INVALID
+    assert lib.ct_autotune(ctypes.byref(p), _lib._i64x3((0, 16, 16)), None, 0, None,
+                           ctypes.byref(res)) == _lib.CT_ERR_INVALID
+    bad = _lib.make_params(1.0, 3.0, (0, 0, 0), (0, 0, 0))
+    assert lib.ct_autotune(ctypes.byref(bad), _lib._i64x3((16, 16, 16)), None, 0, None,
+                           ctypes.byref(res)) == _lib.CT_ERR_INVALID
