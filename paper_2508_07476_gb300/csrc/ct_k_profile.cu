@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "ct.h"
@@ -44,7 +45,43 @@ __device__ __forceinline__ float decode_ha(const void* ha, int64_t i, bool& ok) 
   }
 }
 
+// 8 consecutive HA values from one 16- (or 32-) byte aligned load.
 template <int TYPE>
+__device__ __forceinline__ void load8(const void* ha, int64_t i, float h[8], bool ok[8]) {
+  if (TYPE == CT_OUT_F32) {
+    const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(ha) + i);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w; h[4] = b.x; h[5] = b.y; h[6] = b.z; h[7] = b.w;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ok[k] = isfinite(h[k]);
+  } else if (TYPE == CT_OUT_F16) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const __half*>(ha) + i));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+      h[2 * k] = f.x;
+      h[2 * k + 1] = f.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ok[k] = isfinite(h[k]);
+  } else {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint8_t*>(ha) + i));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int code = ((k < 4 ? q.x : q.y) >> (8 * (k & 3))) & 0xff;
+      ok[k] = code != 0;
+      h[k] = (float)code * (180.f / 256.f) - 90.f;
+    }
+  }
+}
+
+// Each thread takes 8 consecutive voxels of a row (one vector load of HA and
+// of the mask when the rows allow it: VEC), counts runs of equal bins itself
+// and adds a run to the CTA's shared histogram when its bin changes; at the
+// end of the 8 the warp's lanes that end in the same bin add their runs with
+// one atomic.  Grid-stride over the 8-voxel segments.
+template <int TYPE, bool VEC>
 __global__ void __launch_bounds__(kProfThreads) k_transmural(const void* __restrict__ ha,
                                                              const uint8_t* __restrict__ mask, ProfDev P,
                                                              unsigned long long* __restrict__ hist) {
@@ -52,35 +89,87 @@ __global__ void __launch_bounds__(kProfThreads) k_transmural(const void* __restr
   const int nb = P.nd * P.nh;
   for (int k = threadIdx.x; k < nb; k += kProfThreads) sh[k] = 0u;
   __syncthreads();
-  const int64_t rows = (int64_t)P.n1 * P.n2;
-  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-    const int yr = (int)(row % P.n1), zr = (int)(row / P.n1);
-    const float dy = (float)(P.lo[1] + yr) - P.c[1], dz = (float)(P.lo[2] + zr) - P.c[2];
-    const int64_t base = row * P.n0;
-    for (int xr = threadIdx.x; xr < P.n0; xr += kProfThreads) {
-      const int64_t i = base + xr;
-      int bin = -1;
-      bool ok = mask == nullptr || __ldg(mask + i) != 0;
-      if (ok) {
-        const float h = decode_ha<TYPE>(ha, i, ok);
-        const float dx = (float)(P.lo[0] + xr) - P.c[0];
-        const float t = dx * P.a[0] + dy * P.a[1] + dz * P.a[2];
-        const float rx = dx - t * P.a[0], ry = dy - t * P.a[1], rz = dz - t * P.a[2];
-        const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - P.r_in) * P.inv_w;
-        if (ok && d >= 0.f && d < 1.f) {
-          const int kd = min((int)(d * (float)P.nd), P.nd - 1);
-          const int kh = min(max((int)((h + 90.f) * ((float)P.nh / 180.f)), 0), P.nh - 1);
-          bin = kd * P.nh + kh;
+  const int segs_row = (P.n0 + 7) / 8;
+  const int64_t nseg = (int64_t)segs_row * P.n1 * P.n2;
+  for (int64_t b = (int64_t)blockIdx.x * kProfThreads; b < nseg; b += (int64_t)gridDim.x * kProfThreads) {
+    const int64_t s = b + threadIdx.x;
+    int cur = -1;
+    uint32_t cnt = 0;
+    if (s < nseg) {
+      const int64_t row = s / segs_row;
+      const int x0 = (int)(s - row * segs_row) * 8;
+      const int yr = (int)(row % P.n1), zr = (int)(row / P.n1);
+      const float dy = (float)(P.lo[1] + yr) - P.c[1], dz = (float)(P.lo[2] + zr) - P.c[2];
+      const int64_t i0 = row * P.n0 + x0;
+      const int nk = min(8, P.n0 - x0);
+      float h[8];
+      bool ok[8];
+      uint8_t m8[8];
+      if (VEC) {  // whole 8-voxel segments on aligned rows
+        load8<TYPE>(ha, i0, h, ok);
+        if (mask) {
+          const uint2 q = __ldg(reinterpret_cast<const uint2*>(mask + i0));
+#pragma unroll
+          for (int k = 0; k < 8; ++k) m8[k] = ((k < 4 ? q.x : q.y) >> (8 * (k & 3))) & 0xff;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          ok[k] = false;
+          h[k] = 0.f;
+          m8[k] = 0;
+          if (k < nk) {
+            h[k] = decode_ha<TYPE>(ha, i0 + k, ok[k]);
+            if (mask) m8[k] = __ldg(mask + i0 + k);
+          }
         }
       }
-      // neighbouring voxels mostly share a bin: one shared-memory atomic per distinct bin of the warp
-      const unsigned same = __match_any_sync(__activemask(), bin);
-      if (bin >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&sh[bin], (uint32_t)__popc(same));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k >= nk) break;
+        int bin = -1;
+        if (ok[k] && (mask == nullptr || m8[k] != 0)) {
+          const float dx = (float)(P.lo[0] + x0 + k) - P.c[0];
+          const float t = dx * P.a[0] + dy * P.a[1] + dz * P.a[2];
+          const float rx = dx - t * P.a[0], ry = dy - t * P.a[1], rz = dz - t * P.a[2];
+          const float d = (sqrtf(rx * rx + ry * ry + rz * rz) - P.r_in) * P.inv_w;
+          if (d >= 0.f && d < 1.f) {
+            const int kd = min((int)(d * (float)P.nd), P.nd - 1);
+            const int kh = min(max((int)((h[k] + 90.f) * ((float)P.nh / 180.f)), 0), P.nh - 1);
+            bin = kd * P.nh + kh;
+          }
+        }
+        if (bin == cur) {
+          ++cnt;
+        } else {
+          if (cur >= 0) atomicAdd(&sh[cur], cnt);
+          cur = bin;
+          cnt = 1;
+        }
+      }
     }
+    // the last runs: lanes ending in the same bin add them with one atomic
+    const unsigned same = __match_any_sync(0xffffffffu, cur);
+    const uint32_t total = __reduce_add_sync(same, cnt);
+    if (cur >= 0 && (int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&sh[cur], total);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < nb; k += kProfThreads)
     if (sh[k]) atomicAdd(hist + k, (unsigned long long)sh[k]);
+}
+
+template <int TYPE>
+cudaError_t launch_profile(const void* ha, const uint8_t* mask, const ProfDev& P, unsigned long long* hist, int grid,
+                           size_t smem, bool vec, cudaStream_t st) {
+  cudaError_t e;
+  if (vec) {
+    e = cudaFuncSetAttribute(k_transmural<TYPE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_transmural<TYPE, true><<<grid, kProfThreads, smem, st>>>(ha, mask, P, hist);
+  } else {
+    e = cudaFuncSetAttribute(k_transmural<TYPE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) k_transmural<TYPE, false><<<grid, kProfThreads, smem, st>>>(ha, mask, P, hist);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace
@@ -116,25 +205,22 @@ extern "C" ct_status ct_transmural_profile(const ct_profile_spec* spec, const in
   P.n0 = (int)n[0];
   P.n1 = (int)n[1];
   P.n2 = (int)n[2];
-  const int64_t rows = n[1] * n[2];
-  const int grid = (int)(rows < 152 * 4 ? rows : 152 * 4);
+  const int64_t segs = (n[0] + 7) / 8 * n[1] * n[2];
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  const int64_t want = (int64_t)sms * 4;  // four CTAs of 256 threads per SM
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (segs + kProfThreads - 1) / kProfThreads));
   const size_t smem = sizeof(uint32_t) * (size_t)P.nd * P.nh;
+  // vector loads: rows of whole 8-voxel segments on 16-byte aligned arrays
+  const bool vec = n[0] % 8 == 0 && (uintptr_t)d_ha % 16 == 0 && (d_mask == nullptr || (uintptr_t)d_mask % 8 == 0);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   unsigned long long* h = reinterpret_cast<unsigned long long*>(d_hist);
   switch (spec->ha_type) {
-    case CT_OUT_F32:
-      e = cudaFuncSetAttribute(k_transmural<CT_OUT_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_transmural<CT_OUT_F32><<<grid, kProfThreads, smem, st>>>(d_ha, d_mask, P, h);
-      break;
-    case CT_OUT_F16:
-      e = cudaFuncSetAttribute(k_transmural<CT_OUT_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_transmural<CT_OUT_F16><<<grid, kProfThreads, smem, st>>>(d_ha, d_mask, P, h);
-      break;
-    default:
-      e = cudaFuncSetAttribute(k_transmural<CT_OUT_U8Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_transmural<CT_OUT_U8Q><<<grid, kProfThreads, smem, st>>>(d_ha, d_mask, P, h);
-      break;
+    case CT_OUT_F32: e = launch_profile<CT_OUT_F32>(d_ha, d_mask, P, h, grid, smem, vec, st); break;
+    case CT_OUT_F16: e = launch_profile<CT_OUT_F16>(d_ha, d_mask, P, h, grid, smem, vec, st); break;
+    default: e = launch_profile<CT_OUT_U8Q>(d_ha, d_mask, P, h, grid, smem, vec, st); break;
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return ct::set_error(CT_ERR_CUDA, "profile launch failed: %s", cudaGetErrorString(e));

@@ -48,10 +48,13 @@ def _assert_close(gpu, ora, slack):
     assert abs(int(gpu.sum()) - int(ora.sum())) <= slack
 
 
+@pytest.mark.parametrize("nx", [301, 304])
 @pytest.mark.parametrize("ha_type", [_lib.CT_OUT_F32, _lib.CT_OUT_F16, _lib.CT_OUT_U8Q])
-def test_histogram_of_a_given_field(ha_type):
+def test_histogram_of_a_given_field(ha_type, nx):
     rng = np.random.default_rng(5)
-    shape = (23, 70, 301)  # ragged: several CTAs' rows, a partial 256-thread row
+    # 301: rows of ragged 8-voxel segments, loaded voxel by voxel; 304: whole
+    # segments, one vector load each
+    shape = (23, 70, nx)
     lo, dims = (40, 3, 7), (400, 80, 40)
     center, axis = (190.3, 40.7, 12.0), (0.15, -0.2, 1.0)
     r_in, r_out, nd, nh = 10.0, 60.0, 16, 90
