@@ -144,7 +144,7 @@ EPS_S = {_lib.CT_PREC_FP32: 1e-5, _lib.CT_PREC_MIXED: 1e-3}
 
 
 def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32, angles: bool = True,
-            f16_angles: bool = False) -> dict:
+            f16_angles: bool = False, f16_vec: bool = False) -> dict:
     """Per-output errors on the graded voxel sets; returns metrics (no asserts).
 
     "well" voxels are those whose direction the form can fix to 0.5 deg (the
@@ -153,7 +153,10 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     allows: |dIA| <= d and |dHA| <= d / cos(IA) (plus 0.01 deg of rounding).
     angles=False leaves HA and IA out (quantised outputs: see compare_u8q);
     f16_angles adds the FP16 encoding's rounding (half a unit in the last place
-    of the oracle's angle) to the HA / IA perturbation bounds.
+    of the output angle) to the HA / IA perturbation bounds; f16_vec adds the
+    FP16 vector's own rounding (at most 0.025 deg: components below 1 rounded
+    to 2^-12) to the direction error d those bounds use, since HA and IA are
+    computed from the FP32 vector before it is encoded.
     """
     if not angles:
         gpu = dict(gpu, ha=ora["ha"], ia=ora["ia"])
@@ -180,7 +183,8 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
         a = np.maximum(np.abs(gpu[k][sel]), np.abs(ora[k][sel]))
         return np.spacing(a.astype(np.float16)).astype(np.float64) / 2
 
-    out["ha_bound_excess"] = float((dha_all - (d / np.maximum(cos_ia, 1e-12) + 0.01 + q16("ha"))).max()) \
+    dv = d + (0.025 if f16_vec else 0.0)
+    out["ha_bound_excess"] = float((dha_all - (dv / np.maximum(cos_ia, 1e-12) + 0.01 + q16("ha"))).max()) \
         if d.size else 0.0
     out["ha_literal_max"] = float(dha_all.max()) if dha_all.size else 0.0
     dia_all = np.abs(gpu["ia"][sel] - ora["ia"][sel])
@@ -189,7 +193,7 @@ def compare(gpu: dict, ora: dict, mask=None, precision: int = _lib.CT_PREC_FP32,
     # |IA| is 1-Lipschitz in the direction; its sign follows the orientation rule,
     # which a direction error may flip, so the bound compares magnitudes
     dia_abs = np.abs(np.abs(gpu["ia"][sel]) - np.abs(ora["ia"][sel]))
-    out["ia_bound_excess"] = float((dia_abs - (d + 0.01 + q16("ia"))).max()) if d.size else 0.0
+    out["ia_bound_excess"] = float((dia_abs - (dv + 0.01 + q16("ia"))).max()) if d.size else 0.0
     dfa = np.abs(gpu["fa"][inside] - ora["fa"][inside])
     for name, e in (("dir", d), ("ha", dha_all[ha_graded]), ("ia", dia_all[well]), ("fa", dfa)):
         out[f"{name}_max"] = float(e.max()) if e.size else 0.0

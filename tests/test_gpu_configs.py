@@ -130,7 +130,8 @@ def _grade(key, vol, mask, spec, sigma, rho, prec, types, gpu, boxes, b):
         sub = {k: (gpu[k][(slice(None),) + sl] if k == "v" else gpu[k][sl]) for k in ("v", "ha", "ia", "fa")}
         msub = None if mask is None else mask[sl]
         quant = types[1] == U8Q
-        m = G.compare(sub, ora, msub, precision=prec, angles=not quant, f16_angles=types[1] == F16)
+        m = G.compare(sub, ora, msub, precision=prec, angles=not quant, f16_angles=types[1] == F16,
+                      f16_vec=types[0] == F16)
         print(key, prec, lo, m)
         G.assert_within(m, f"{key} box {lo} prec={prec}", precision=prec)
         tot["graded"] += m["n_graded"]
@@ -185,8 +186,10 @@ def _kernel_names(vol, sigma, rho, cen, ax, mask):
 
 @pytest.mark.parametrize("case,tc", [("stream_s2_r8", True), ("tera_s3_r9", True), ("crop_s3_r8", True),
                                      ("crop_s1_r2", False)])
-def test_config_scale_takes_the_expected_passes(case, tc):
-    # the cases above grade the tensor-core passes where the benchmark runs them
+def test_config_scale_takes_the_expected_passes(monkeypatch, case, tc):
+    # with the built-in choices (the tuning cache set aside) the cases above run
+    # the tensor-core passes at R(rho) >= 24 and the stencils below
+    monkeypatch.setenv("CT_TUNE_CACHE", "")
     name, sigma, rho, use_mask, _ = CASES[case]
     spec, vol, mask = _volume(name)
     cen, ax = synth.frame_of(spec)

@@ -235,6 +235,7 @@ def _kernels_and_outputs(vol, sigma, rho, chunk=(0, 0, 0)):
                                                       (100, 6.0, "0", "xyz"), (126, 6.0, "0", ""),
                                                       (128, 3.0, "0", ""), (128, 6.0, None, "")])
 def test_default_selection_is_per_volume(monkeypatch, nx, rho, min_vox, expect_tc):
+    monkeypatch.setenv("CT_TUNE_CACHE", "")  # the built-in choices
     # the tensor cores take rho radii >= 24 on volumes whose x extent suits their
     # 16-byte copies (a multiple of 4) and, with the library's own settings, of
     # at least 2^24 voxels (None: that default, which sends these small volumes
