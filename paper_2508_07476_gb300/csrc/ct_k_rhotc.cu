@@ -26,11 +26,13 @@
 // 4 positions).
 //
 // The CTA is warp-specialised, one CTA per SM holding all 512 tensor-memory
-// columns.  Four producer warps own the 128 lines: they copy NT-position
-// chunks of their lines into shared memory with cp.async (16-byte copies when
-// the boxes are 16-byte aligned), several chunks ahead in one stream that runs
-// on across work units, then split a landed chunk, write both rings and arrive
-// on the tile's "staged" mbarrier.  An MMA warp waits on it, issues the
+// columns.  Producer warps own the 128 lines (x form: four warps, one line per
+// thread; y / z forms: eight warps, two per lane quadrant, each with half of
+// every chunk's positions): they copy NT-position chunks of their lines into
+// shared memory with cp.async (16-byte copies when the boxes are 16-byte
+// aligned), several chunks ahead in one stream that runs on across work units,
+// then split a landed chunk, write both rings and arrive on the tile's
+// "staged" mbarrier.  An MMA warp waits on it, issues the
 // 3 W / 8 MMAs (one elected lane, the loop in warp-uniform control flow) into
 // one of two accumulators and commits them to that accumulator's mbarrier.
 // Four epilogue warps wait on it, read their 32 lanes of D, free the
@@ -53,8 +55,18 @@ namespace ct {
 
 namespace {
 
-constexpr int kTcLines = 128;                  // = M: producer thread / TMEM lane m owns line m
-constexpr int kTcThreads = 2 * kTcLines + 32;  // producer warps 0-3, epilogue warps 4-7, MMA warp 8
+constexpr int kTcLines = 128;  // = M: TMEM lane m holds line m
+// Warp roles: producer warps 0 .. NP-1, epilogue warps NP .. NP+3, the MMA warp
+// NP+4.  The x form has one producer thread per line (NP = 4); the y / z forms
+// split each chunk's positions between two producer warps per lane quadrant
+// (NP = 8: warp w stages positions [(w / 4) NT / 2, + NT / 2) of the lines
+// 32 (w % 4) ..), which halves each producer thread's work per tile.
+template <bool XAXIS>
+struct TcRoles {
+  static constexpr int NP = XAXIS ? 4 : 8;
+  static constexpr int THREADS = 32 * (NP + 5);
+  static constexpr int MMA_WARP = NP + 4;
+};
 constexpr int kTcNB = 4;                       // mbarriers per hand-off, used by tiles g mod 4 in turn
 #ifndef CT_TC_BIG_RING
 #define CT_TC_BIG_RING 1  // tuning: 0 restarts a W + NT ring at every work unit
@@ -329,7 +341,7 @@ struct GradT<2> {
 // in turn, so that the group's gradient lines are read from L2 after the
 // first component.
 template <int RR, bool XAXIS, int PROD>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
              int vec, const __grid_constant__ Taps taps, const __grid_constant__ CUtensorMap tin,
              const __grid_constant__ CUtensorMap tout, const TcCtl ctl, const TcProd pr) {
@@ -356,12 +368,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ volatile int abort_flag;
   __shared__ int arrived_max;  // x form: most chunks any producer thread has arrived for
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int role = w < 4 ? 0 : (w < 8 ? 1 : 2);  // producer, epilogue, MMA
+  using RL = TcRoles<XAXIS>;
+  const int role = w < RL::NP ? 0 : (w < RL::NP + 4 ? 1 : 2);  // producer, epilogue, MMA
   const int m = tid & (kTcLines - 1);            // line / TMEM lane (roles 0 and 1)
   const int wq = w & 3;                          // lane quadrant of this warp
 
   // B = the banded Toeplitz matrix of the taps, split into TF32 head and remainder
-  for (int e = tid; e < NT * G::W; e += kTcThreads) {
+  for (int e = tid; e < NT * G::W; e += RL::THREADS) {
     const int n = e / G::W, k = e % G::W;
     const int j = k - n - (G::RA - RR);
     const float v = (j >= 0 && j <= 2 * RR) ? taps.w[j] * GradT<PROD>::kBScale : 0.f;
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int a = 0; a < S; ++a)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_chunk[a])), "n"(kTcLines));
     for (int a = 0; a < kTcNB; ++a) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(kTcLines));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(32 * RL::NP));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma[a])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[a])), "n"(kTcLines));
     }
@@ -458,6 +471,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   uint32_t g = 0;          // tiles this thread's role has handled (every role counts the same sequence)
   uint32_t committed = 0;  // MMA warp: tiles whose MMAs it has committed
+  // a producer warp's positions of each chunk: [p_lo, p_lo + NTP)
+  constexpr int NTP = XAXIS ? NT : NT / 2;
+  const int p_lo = XAXIS ? 0 : (w >> 2) * NTP;
   if (role == 0) {
     // the copy stream: chunk ic of unit iu (window positions NT ic for ic < P,
     // then tile ic - P's NT), one cp.async group per chunk, stage k mod S
@@ -529,8 +545,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const GT* pa = gbase + IU.ga + (LPC * qd - lane);
             const GT* pb = gbase + IU.gb + (LPC * qd - lane);
 #pragma unroll
-            for (int i = 0; i < NT / PPI; ++i) {
-              const int pos = pg + PPI * i;
+            for (int i = 0; i < NTP / PPI; ++i) {
+              const int pos = p_lo + pg + PPI * i;
               const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
               const int so = pos * kTcLines + 32 * wq + LPC * qd;
               cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + q));
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
           } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
 #pragma unroll 4
-            for (int j = 0; j < NT; ++j) {
+            for (int j = p_lo; j < p_lo + NTP; ++j) {
               const int64_t q = (int64_t)min(max(qs + j, qlo), qhi) * IU.istride;
               if (PROD == 1) {  // FP32: asynchronous 4-byte copies
                 cp_async4(smem_u32(sa + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.ga + q));
@@ -558,8 +574,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int qd = lane & 7, pg = lane >> 3;
           const float* p = IU.src + (4 * qd - lane);
 #pragma unroll
-          for (int i = 0; i < NT / 4; ++i) {
-            const int pos = pg + 4 * i;
+          for (int i = 0; i < NTP / 4; ++i) {
+            const int pos = p_lo + pg + 4 * i;
             const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
             cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + q);
           }
@@ -569,10 +585,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         } else if (inside) {
           const float* p = IU.src + qs * IU.istride;
 #pragma unroll
-          for (int j = 0; j < NT; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
+          for (int j = p_lo; j < p_lo + NTP; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
         } else {
 #pragma unroll
-          for (int j = 0; j < NT; ++j)
+          for (int j = p_lo; j < p_lo + NTP; ++j)
             cp_async4(smem_u32(rb + j * kTcLines + m), IU.src + min(max(qs + j, qlo), qhi) * IU.istride);
         }
         if (++ic == iC) enter(iu + gridDim.x);
@@ -607,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           break;
         }
         const float* rb = sRaw + (k % S) * RAWF;
-        float v[NT];
+        float v[NTP];
         if (XAXIS) {
           const int qs = q0u + (c < G::P ? NT * c : 2 * G::RA + NT * (c - G::P));
           const int jlo = max(0, qlo - qs), jhi = min(NT - 1, qhi - qs);
@@ -636,13 +652,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const GT* sb = prod_a(CU.comp) != prod_b(CU.comp) ? sa + NT * kTcLines : sa;
           const float f = fprod;
 #pragma unroll
-          for (int j = 0; j < NT; ++j) {
-            const float ab = GradT<PROD>::prod(sa[j * kTcLines + m], sb[j * kTcLines + m]);
+          for (int j = 0; j < NTP; ++j) {
+            const float ab = GradT<PROD>::prod(sa[(p_lo + j) * kTcLines + m], sb[(p_lo + j) * kTcLines + m]);
             v[j] = pr.unit ? ab : ab * f;
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < NT; ++j) v[j] = rb[j * kTcLines + m];
+          for (int j = 0; j < NTP; ++j) v[j] = rb[(p_lo + j) * kTcLines + m];
         }
         __syncwarp();  // every lane has read the stage before it is refilled
         issue_next();
@@ -679,9 +695,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // split and write both rings (slots mod WR)
 #pragma unroll
-        for (int cc = 0; cc < NT / 8; ++cc) {
-          if (8 * cc >= nw) break;  // uniform across the warp
-          const int slot = (gbase + q + 8 * cc) % G::WR;
+        for (int cc = 0; cc < NTP / 8; ++cc) {
+          if (p_lo + 8 * cc >= nw) break;  // uniform across the warp
+          const int slot = (gbase + q + p_lo + 8 * cc) % G::WR;
           float hi[8], lo[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -837,7 +853,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // a CTA that gave up waits once more (bounded) for the last product it
   // committed before it releases the tensor memory, and reports itself
   __syncthreads();
-  if (abort_flag && w == 8) {
+  if (abort_flag && w == RL::MMA_WARP) {
     if (committed >= 1) mbar_wait(mma_bar(committed - 1), par(committed - 1));
     if (lane == 0 && ctl.timeouts) atomicAdd(ctl.timeouts, 1u);
   }
@@ -925,7 +941,8 @@ struct TcLaunch {
       if (vin && ob.lo[1] == ib.lo[1] && ob.n[1] == ib.n[1] && rows_map(&tin, in, ib)) flags |= 4;
       if (vout && rows_map(&tout, out, ob)) flags |= 8;
     }
-    k_rho_tc<RR, XAXIS, PROD><<<grid, kTcThreads, G::smem(XAXIS, PROD), st>>>(in, ib, dims[axis], out, ob, axis, seg,
+    k_rho_tc<RR, XAXIS, PROD><<<grid, TcRoles<XAXIS>::THREADS, G::smem(XAXIS, PROD), st>>>(in, ib, dims[axis], out, ob,
+                                                                                           axis, seg,
                                                                               flags, taps, tin, tout, ctl, pr);
     return cudaGetLastError();
   }
