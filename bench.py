@@ -411,7 +411,9 @@ def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int, inside: float = 
 # capture); valid only for the kernel version summarised in the named file.
 MEASURED_TRAFFIC = {"rho_x_tc": (45.0, "profiles/kernels_annulus256.md"),
                     "rho_y_tc": (44.8, "profiles/kernels_annulus256.md"),
-                    "rho_z_tc": (44.9, "profiles/kernels_annulus256.md"),
+                    "rho_z_tc_g16": (26.6, "profiles/kernels_annulus256.md"),
+                    "grad_z_g16": (16.4, "profiles/kernels_annulus256.md"),
+                    "grad_xy": (10.4, "profiles/kernels_annulus256.md"),
                     "eig_angles": (36.4, "profiles/kernels_annulus256.md")}
 
 

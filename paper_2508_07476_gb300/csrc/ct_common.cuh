@@ -48,6 +48,64 @@ __device__ __forceinline__ int clamp_to(int p, int dim, int lo, int n) {
   return clampi(clampi(p, 0, dim - 1), lo, lo + n - 1);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent multi-item launches.  A stage kernel's body reads its block index
+// and grid size from a VBlock instead of blockIdx / gridDim: the single-item
+// kernel passes its own, and a persistent launch over a batch of items (the
+// blocks of item i numbered first[i] .. first[i+1] - 1 in one sequence, its
+// grid grids[i]) runs the body once per block it takes from a device counter,
+// so that all items of the batch share one launch and the SMs stay busy
+// across items of any size.  The counter is zeroed before the launch; every
+// CTA stops once the counter passes the last block (no CTA waits on another).
+struct VBlock {
+  uint3 idx;
+  uint3 dim;
+};
+
+__device__ __forceinline__ VBlock hw_block() {
+  VBlock b;
+  b.idx = blockIdx;
+  b.dim = make_uint3(gridDim.x, gridDim.y, gridDim.z);
+  return b;
+}
+
+// Per-launch table of a multi-item launch (device pointers).
+struct MultiTable {
+  const int64_t* first;  // n + 1 block offsets
+  const uint3* grids;    // n grids
+  int n;
+  unsigned long long* counter;
+};
+
+template <typename F>
+__device__ __forceinline__ void for_each_vblock(const MultiTable& T, F&& f) {
+  __shared__ long long s_next;
+  const int64_t total = T.first[T.n];
+  for (;;) {
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_next = (long long)atomicAdd(T.counter, 1ull);
+    __syncthreads();
+    const int64_t b = s_next;
+    __syncthreads();  // every thread has read it before it is overwritten
+    if (b >= total) break;
+    int lo = 0, hi = T.n - 1;  // the item whose blocks hold b: the last with first <= b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (T.first[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint3 g = T.grids[lo];
+    int64_t r = b - T.first[lo];
+    VBlock v;
+    v.dim = g;
+    v.idx.x = (unsigned)(r % g.x);
+    r /= g.x;
+    v.idx.y = (unsigned)(r % g.y);
+    v.idx.z = (unsigned)(r / g.y);
+    f(lo, v);
+    __syncthreads();  // the block's shared memory is free for the next one
+  }
+}
+
 // Asynchronous 4-byte global -> shared copies (cp.async), grouped per commit.
 __device__ __forceinline__ void cp_async4(uint32_t smem_dst, const float* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");

@@ -66,19 +66,19 @@ __device__ __forceinline__ void u16x8_to_f32(const uint4 q, float* f) {
 }
 
 template <int RS, int XT>
-__global__ void __launch_bounds__(XT, 512 / XT)
-    k_grad_xy(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, float* __restrict__ F, Box ab, int seg,
-              const Taps tx, const Taps ty) {
+__device__ __forceinline__ void grad_xy_body(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy,
+                                             float* __restrict__ F, Box ab, int seg, const Taps& tx, const Taps& ty,
+                                             const VBlock blk) {
   using G = GXYGeom<RS, XT>;
   constexpr int TB = G::TB;
   extern __shared__ __align__(16) float gsm[];
   float* stage = gsm;                  // [TB][XS] staged rows, (v, v) per voxel
   float* sx = gsm + TB * G::XS;        // [TB][SXS] x-pass rows, (c_x I, w_x I) per voxel
   const int t = threadIdx.x;
-  const int x0 = ab.lo[0] + blockIdx.x * XT;
+  const int x0 = ab.lo[0] + blk.idx.x * XT;
   const int xend = ab.lo[0] + ab.n[0];
-  const int z = ab.lo[2] + blockIdx.y;
-  const int p0 = ab.lo[1] + blockIdx.z * seg;
+  const int z = ab.lo[2] + blk.idx.y;
+  const int p0 = ab.lo[1] + blk.idx.z * seg;
   const int L = min(seg, ab.lo[1] + ab.n[1] - p0);
   if (L <= 0) return;
   const uint16_t* plane = vol + (int64_t)(z - vb.lo[2]) * vb.n[0] * vb.n[1];
@@ -204,6 +204,24 @@ __global__ void __launch_bounds__(XT, 512 / XT)
   }
 }
 
+template <int RS, int XT>
+__global__ void __launch_bounds__(XT, 512 / XT)
+    k_grad_xy(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, float* __restrict__ F, Box ab, int seg,
+              const __grid_constant__ Taps tx, const __grid_constant__ Taps ty) {
+  grad_xy_body<RS, XT>(vol, vb, dimx, dimy, F, ab, seg, tx, ty, hw_block());
+}
+
+// The same over a batch of volumes in one persistent launch (MultiTable).
+template <int RS, int XT>
+__global__ void __launch_bounds__(XT, 512 / XT)
+    k_grad_xy_multi(const GxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
+                    const __grid_constant__ Taps ty) {
+  for_each_vblock(T, [&](int i, const VBlock& v) {
+    const GxyItem& it = items[i];
+    grad_xy_body<RS, XT>(it.vol, it.vb, it.dimx, it.dimy, it.F, it.ab, it.seg, tx, ty, v);
+  });
+}
+
 // ---------------------------------------------------------------- z pass
 // One thread per (x, y) column of the output box walks z.  The three partial
 // fields arrive by 4-byte cp.async into a shared ring of P = 2R+1 steps
@@ -233,19 +251,18 @@ constexpr float kGzHalfScale = 1.0f / 256.0f;
 // mixed form, FP32 otherwise) for a consumer that forms the products, instead
 // of the six products.
 template <int RS, bool MIXED, bool GOUT>
-__global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
-    k_grad_z(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg, const Taps taps,
-             const ProdScale ps) {
+__device__ __forceinline__ void grad_z_body(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg,
+                                            const Taps& taps, const ProdScale& ps, const VBlock blk) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
   extern __shared__ __align__(16) float gz_ring[];  // [P][3][kGzThreads]
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
-  const int yr = blockIdx.y * blockDim.y + threadIdx.y;
+  const int x = ob.lo[0] + blk.idx.x * blockDim.x + threadIdx.x;
+  const int yr = blk.idx.y * blockDim.y + threadIdx.y;
   const bool ok = x < ob.lo[0] + ob.n[0] && yr < ob.n[1];
   const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
   const int y = ob.lo[1] + min(yr, ob.n[1] - 1);
-  const int p0 = ob.lo[2] + blockIdx.z * seg;  // first output plane
+  const int p0 = ob.lo[2] + blk.idx.z * seg;  // first output plane
   const int L = min(seg, ob.lo[2] + ob.n[2] - p0);
   if (L <= 0) return;
   const int nsteps = L + 2 * RS;
@@ -345,6 +362,26 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
   cp_async_wait<0>();
 }
 
+template <int RS, bool MIXED, bool GOUT>
+__global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
+    k_grad_z(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg,
+             const __grid_constant__ Taps taps, const __grid_constant__ ProdScale ps) {
+  grad_z_body<RS, MIXED, GOUT>(F, ab, Jv, ob, seg, taps, ps, hw_block());
+}
+
+// The same (the six products) over a batch of volumes in one persistent launch,
+// blocks of kGzMultiX x (kGzThreads / kGzMultiX) threads.
+constexpr int kGzMultiX = 128;
+template <int RS, bool MIXED>
+__global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
+    k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps,
+                   const __grid_constant__ ProdScale ps) {
+  for_each_vblock(T, [&](int i, const VBlock& v) {
+    const GzItem& it = items[i];
+    grad_z_body<RS, MIXED, false>(it.F, it.ab, it.J, it.ob, it.seg, taps, ps, v);
+  });
+}
+
 // ---------------------------------------------------------------- launch
 #ifndef CT_GXY_XT
 #define CT_GXY_XT 128  // columns (threads) per gradient x/y CTA (tuning choice)
@@ -364,6 +401,11 @@ template <int RS>
 static cudaError_t prepare_gs() {
   cudaError_t e = set_xy_attr<RS, CT_GXY_XT>();
   const int sm = (int)gz_smem<RS>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_grad_xy_multi<RS, CT_GXY_XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GXYGeom<RS, CT_GXY_XT>::SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z_multi<RS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z_multi<RS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_grad_z<RS, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -463,6 +505,108 @@ cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3]
     case 6: return launch_gxy_r<6>(vol, vb, dims, F, ab, tx, ty, st);
     case 8: return launch_gxy_r<8>(vol, vb, dims, F, ab, tx, ty, st);
     case 12: return launch_gxy_r<12>(vol, vb, dims, F, ab, tx, ty, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------- batches
+template <int RS>
+static uint3 gxy_item(GxyItem& it) {
+  using G = GXYGeom<RS, CT_GXY_XT>;
+  constexpr int XT = CT_GXY_XT;
+  const Box& ab = it.ab;
+  const int64_t ctas = (int64_t)((ab.n[0] + XT - 1) / XT) * ab.n[2];
+  int nseg = 1;
+  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ab.n[1] / (nseg * 2) >= 8 * G::TB) nseg *= 2;
+  it.seg = (ab.n[1] + nseg - 1) / nseg;
+  return make_uint3((ab.n[0] + XT - 1) / XT, ab.n[2], (ab.n[1] + it.seg - 1) / it.seg);
+}
+
+uint3 grad_xy_item(int rk, GxyItem& it) {
+  switch (rk) {
+    case 2: return gxy_item<2>(it);
+    case 3: return gxy_item<3>(it);
+    case 4: return gxy_item<4>(it);
+    case 6: return gxy_item<6>(it);
+    case 8: return gxy_item<8>(it);
+    default: return gxy_item<12>(it);
+  }
+}
+
+template <int RS>
+static cudaError_t gxy_multi(const GxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                             const Taps& ty, cudaStream_t st) {
+  using G = GXYGeom<RS, CT_GXY_XT>;
+  const int grid = persistent_grid(k_grad_xy_multi<RS, CT_GXY_XT>, CT_GXY_XT, G::SMEM, blocks);
+  k_grad_xy_multi<RS, CT_GXY_XT><<<grid, CT_GXY_XT, G::SMEM, st>>>(items, T, tx, ty);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_xy_multi(const GxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                                 const Taps& ty, int rk, cudaStream_t st) {
+  switch (rk) {
+    case 2: return gxy_multi<2>(items, T, blocks, tx, ty, st);
+    case 3: return gxy_multi<3>(items, T, blocks, tx, ty, st);
+    case 4: return gxy_multi<4>(items, T, blocks, tx, ty, st);
+    case 6: return gxy_multi<6>(items, T, blocks, tx, ty, st);
+    case 8: return gxy_multi<8>(items, T, blocks, tx, ty, st);
+    case 12: return gxy_multi<12>(items, T, blocks, tx, ty, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int RS>
+static uint3 gz_item(GzItem& it) {
+  const Box& ob = it.ob;
+  const dim3 block(kGzMultiX, kGzThreads / kGzMultiX);
+  const int64_t cols = (int64_t)((ob.n[0] + block.x - 1) / block.x) * ((ob.n[1] + block.y - 1) / block.y);
+  int nseg = 1;
+  while (nseg < 16 && cols * nseg < (int64_t)152 * 2 * 4 && ob.n[2] / (nseg * 2) >= 4 * (2 * RS + 1)) nseg *= 2;
+  it.seg = (ob.n[2] + nseg - 1) / nseg;
+  return make_uint3((ob.n[0] + block.x - 1) / block.x, (ob.n[1] + block.y - 1) / block.y,
+                    (ob.n[2] + it.seg - 1) / it.seg);
+}
+
+uint3 grad_z_item(int rk, GzItem& it) {
+  switch (rk) {
+    case 2: return gz_item<2>(it);
+    case 3: return gz_item<3>(it);
+    case 4: return gz_item<4>(it);
+    case 6: return gz_item<6>(it);
+    case 8: return gz_item<8>(it);
+    default: return gz_item<12>(it);
+  }
+}
+
+template <int RS>
+static cudaError_t gz_multi(const GzItem* items, const MultiTable& T, int64_t blocks, const Taps& tz,
+                            const ProdScale& ps, bool mixed, cudaStream_t st) {
+  const dim3 block(kGzMultiX, kGzThreads / kGzMultiX);
+  if (mixed) {
+    const int grid = persistent_grid(k_grad_z_multi<RS, true>, kGzThreads, gz_smem<RS>(), blocks);
+    k_grad_z_multi<RS, true><<<grid, block, gz_smem<RS>(), st>>>(items, T, tz, ps);
+  } else {
+    const int grid = persistent_grid(k_grad_z_multi<RS, false>, kGzThreads, gz_smem<RS>(), blocks);
+    k_grad_z_multi<RS, false><<<grid, block, gz_smem<RS>(), st>>>(items, T, tz, ps);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_z_multi(const GzItem* items, const MultiTable& T, int64_t blocks, const Taps& tz,
+                                const float scale[6], int rk, bool mixed, cudaStream_t st) {
+  ProdScale ps;
+  ps.unit = 1;
+  for (int k = 0; k < 6; ++k) {
+    ps.s[k] = scale[k];
+    ps.unit = ps.unit && scale[k] == 1.f;
+  }
+  switch (rk) {
+    case 2: return gz_multi<2>(items, T, blocks, tz, ps, mixed, st);
+    case 3: return gz_multi<3>(items, T, blocks, tz, ps, mixed, st);
+    case 4: return gz_multi<4>(items, T, blocks, tz, ps, mixed, st);
+    case 6: return gz_multi<6>(items, T, blocks, tz, ps, mixed, st);
+    case 8: return gz_multi<8>(items, T, blocks, tz, ps, mixed, st);
+    case 12: return gz_multi<12>(items, T, blocks, tz, ps, mixed, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -68,6 +68,73 @@ cudaError_t launch_rho_tc_products(const void* g, bool half, const Box& ib, cons
 // of its rows (x extent a multiple of 4).
 bool rho_tc_volume_aligned(int nx, int axis);
 
+// ---------------------------------------------------------------- batches
+// One persistent launch per stage over a batch of volumes (MultiTable, in
+// ct_common.cuh): the item's arguments as the single-item launch takes them;
+// *_item fills the item's launch shape (seg) and returns its grid exactly as
+// the single launch would choose them, so that a batch reproduces every
+// item's results bit for bit; launch_*_multi runs the stage over a device
+// table of items (grid: the SMs times the blocks each holds, at most `blocks`).
+struct GxyItem {
+  const uint16_t* vol;
+  Box vb;
+  int dimx, dimy;
+  float* F;
+  Box ab;
+  int seg;
+};
+struct GzItem {
+  const float* F;
+  Box ab;
+  float* J;
+  Box ob;
+  int seg;
+};
+struct RxyItem {
+  const float* in;
+  Box ib;
+  int dimx, dimy;
+  float* out;
+  Box ob;
+  int seg;
+};
+struct RzItem {
+  const float* in;
+  Box ib;
+  int dim_axis;
+  float* out;
+  Box ob;
+  int seg;
+};
+uint3 grad_xy_item(int rk, GxyItem& it);
+cudaError_t launch_grad_xy_multi(const GxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                                 const Taps& ty, int rk, cudaStream_t st);
+uint3 grad_z_item(int rk, GzItem& it);
+cudaError_t launch_grad_z_multi(const GzItem* items, const MultiTable& T, int64_t blocks, const Taps& tz,
+                                const float scale[6], int rk, bool mixed, cudaStream_t st);
+// the fused x / y stencil at the CTA width `xt` (128 or 256; rho_xy_width picks it as the single launch does)
+int rho_xy_width(int n0);
+uint3 rho_xy_item(int rk, int xt, RxyItem& it);
+cudaError_t launch_rho_xy_multi(const RxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                                const Taps& ty, int rk, int xt, cudaStream_t st);
+// the z stencil (axis 2), block_t outputs per thread block; the block shape
+// of an item: rho_stream_block (the single launch's), fixed per batch launch
+uint3 rho_z_item(int rk, int block_t, dim3 block, RzItem& it);
+dim3 rho_stream_block(const Box& ob, int axis);
+cudaError_t launch_rho_z_multi(const RzItem* items, const MultiTable& T, int64_t blocks, dim3 block,
+                               const Taps& taps, int rk, int block_t, cudaStream_t st);
+
+// Persistent grid of a multi-item launch: the SMs times the CTAs each holds.
+template <typename K>
+int persistent_grid(K kernel, int threads, size_t smem, int64_t blocks) {
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+  const int64_t g = (int64_t)per * sms;
+  return (int)(blocks < g ? (blocks > 0 ? blocks : 1) : g);
+}
+
 struct EigOut {
   void* vec;
   void* ha;
