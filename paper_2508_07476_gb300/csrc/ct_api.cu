@@ -176,6 +176,15 @@ struct ct_plan_s {
   // batches: graph of the multi-stream launch sequence, keyed by the item list
   int batch_streams = 4;
   bool batch_graph = true;
+  // persistent batches (run_persistent_waves): device items on the FP32
+  // stencil chain run as one persistent launch per stage and tap set, in waves
+  // whose scratch fits batch_bytes of the arena
+  bool batch_persistent = true;
+  int64_t batch_bytes = int64_t(16) << 30;
+  void* arena = nullptr;
+  size_t arena_cap = 0;
+  void* tables = nullptr;
+  size_t tables_cap = 0;
   cudaStream_t gst = nullptr;   // origin stream of the captured graph
   cudaEvent_t gev[2] = {nullptr, nullptr};
   cudaGraph_t graph = nullptr;
@@ -717,6 +726,8 @@ ct_status ct_plan_create(const ct_params* params, const int64_t vol_dims[3], ct_
   if (const char* e = std::getenv("CT_TUNE_BATCH_STREAMS"))
     P->batch_streams = std::max(1, std::min(ct_plan_s::kSlots, std::atoi(e)));
   if (const char* e = std::getenv("CT_TUNE_BATCH_GRAPH")) P->batch_graph = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_BATCH_PERSISTENT")) P->batch_persistent = std::atoi(e) != 0;
+  if (const char* e = std::getenv("CT_TUNE_BATCH_BYTES")) P->batch_bytes = std::max<int64_t>(1, std::atoll(e));
   if (const char* e = std::getenv("CT_TUNE_TC_WAIT_LIMIT")) P->tc_wait_limit = (uint32_t)std::max(0, std::atoi(e));
   if (const char* e = std::getenv("CT_TUNE_TC_PRODUCTS")) P->tc_products = std::atoi(e) != 0;
   for (const char* k : {"CT_TUNE_TC_RHO", "CT_TUNE_TC_MIN_R", "CT_TUNE_TC_MIN_VOX", "CT_TUNE_TC_ANY_BOX",
@@ -758,6 +769,8 @@ ct_status ct_plan_destroy(ct_plan P) {
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->graph) cudaGraphDestroy(P->graph);
   if (P->gst) cudaStreamDestroy(P->gst);
+  if (P->arena) cudaFree(P->arena);
+  if (P->tables) cudaFree(P->tables);
   for (int k = 0; k < 2; ++k)
     if (P->gev[k]) cudaEventDestroy(P->gev[k]);
   for (int s = 0; s < ct_plan_s::kSlots; ++s) {
@@ -961,6 +974,367 @@ uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
   return h;
 }
 
+// ---------------------------------------------------------- persistent batches
+// The stencil-chain items of a batch run stage by stage, each stage as one
+// persistent launch per tap set (template radius and taps) over every item of
+// a wave: the CTAs take (item, block) work from a device counter, so items of
+// any size share the SMs.  A wave holds the items whose scratch (the two tensor
+// buffers and the re-solve list) fits the plan's batch_bytes; waves reuse the
+// arena in stream order.  Every item's blocks, launch shape and arithmetic are
+// those of its single launch, so a batch reproduces each item alone bit for
+// bit.  The launch records (tables in device memory, uploaded before any
+// capture) are built here; run_persistent_waves enqueues them.
+struct MultiRec {
+  int kind;          // 0 grad_xy, 1 grad_z, 2 rho_xy, 3 rho_z, 4 eigen (compact), 5 eigen (per voxel)
+  int rk, xt, block_t;
+  bool plain;
+  dim3 block;
+  Taps t0, t1;
+  float ss[6];
+  size_t items_off, first_off, grids_off, counter_off;
+  int n;
+  int64_t blocks;
+};
+
+struct WaveRec {
+  std::vector<MultiRec> launches;
+  size_t counters_off = 0, n_counters = 0;  // per-launch work counters, zeroed per wave
+  size_t fbc_off = 0, n_fbc = 0;            // re-solve list counters
+  size_t eig_items_off = 0;                 // every eigen item of the wave, contiguous
+  int n_eig = 0;
+  int64_t max_vox = 0;
+};
+
+struct HostTable {
+  std::vector<unsigned char> bytes;
+  template <typename T>
+  size_t put(const T* p, size_t n) {
+    const size_t off = (bytes.size() + 15) / 16 * 16;
+    bytes.resize(off + sizeof(T) * n);
+    if (n) std::memcpy(bytes.data() + off, p, sizeof(T) * n);
+    return off;
+  }
+  size_t zeros(size_t nbytes) {
+    const size_t off = (bytes.size() + 15) / 16 * 16;
+    bytes.resize(off + nbytes, 0);
+    return off;
+  }
+};
+
+// Group the wave's items of one stage by a key and append one launch record per group.
+template <typename Item, typename KeyEq, typename Fill>
+void add_groups(HostTable& H, WaveRec& W, std::vector<Item>& items, std::vector<uint3>& grids,
+                std::vector<MultiRec>& proto, KeyEq same, Fill fill) {
+  std::vector<bool> done(items.size(), false);
+  for (size_t i = 0; i < items.size(); ++i) {
+    if (done[i]) continue;
+    std::vector<Item> gi;
+    std::vector<uint3> gg;
+    std::vector<int64_t> first(1, 0);
+    for (size_t j = i; j < items.size(); ++j) {
+      if (done[j] || !same(proto[i], proto[j])) continue;
+      done[j] = true;
+      gi.push_back(items[j]);
+      gg.push_back(grids[j]);
+      first.push_back(first.back() + (int64_t)grids[j].x * grids[j].y * grids[j].z);
+    }
+    MultiRec r = proto[i];
+    r.n = (int)gi.size();
+    r.blocks = first.back();
+    r.items_off = H.put(gi.data(), gi.size());
+    r.first_off = H.put(first.data(), first.size());
+    r.grids_off = H.put(gg.data(), gg.size());
+    r.counter_off = 0;  // set when the wave's counters are laid out
+    fill(r);
+    W.launches.push_back(r);
+  }
+}
+
+bool same_taps(const Taps& a, const Taps& b) { return std::memcmp(&a, &b, sizeof(Taps)) == 0; }
+
+// Scratch of one item in a persistent wave: A, B (6 planes each of need voxels) and its re-solve list.
+int64_t item_scratch_bytes(const ItemCtx& c) {
+  const Box G = grow_clip3(c.whole, c.sc.rr, c.dims);
+  const Box Ab = grad_partial_box(G, c.whole, c.sc.rks, c.dims[2]);
+  const int64_t need = std::max<int64_t>(box_vox(G), (box_vox(Ab) + 1) / 2);
+  return 2 * (int64_t)sizeof(float) * 6 * need + (int64_t)sizeof(int64_t) * box_vox(c.whole) + 1024;
+}
+
+// Build the waves of the items listed in `which` (indices into items / ctx).
+ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vector<ItemCtx>& ctx,
+                                 const std::vector<int>& which, std::vector<WaveRec>* waves, HostTable* H,
+                                 size_t* arena_need) {
+  const bool mixed = P->p.precision == CT_PREC_MIXED;
+  *arena_need = 0;
+  size_t k = 0;
+  while (k < which.size()) {
+    // the wave: items in order while their scratch fits the budget (one at least)
+    std::vector<int> wv;
+    int64_t bytes = 0;
+    while (k < which.size()) {
+      const int64_t b = item_scratch_bytes(ctx[which[k]]);
+      if (!wv.empty() && bytes + b > P->batch_bytes) break;
+      wv.push_back(which[k]);
+      bytes += b;
+      ++k;
+    }
+    *arena_need = std::max(*arena_need, (size_t)bytes);
+    WaveRec W;
+    std::vector<GxyItem> gxy;
+    std::vector<GzItem> gz;
+    std::vector<RxyItem> rxy;
+    std::vector<RzItem> rz;
+    std::vector<EigItem> eig;
+    std::vector<uint3> g_gxy, g_gz, g_rxy, g_rz, g_eig;
+    std::vector<MultiRec> p_gxy, p_gz, p_rxy, p_rz, p_eig;
+    std::vector<size_t> fb_count_slot;
+    size_t off = 0;  // arena offset of the next item's scratch
+    for (int idx : wv) {
+      const ItemCtx& c = ctx[idx];
+      const ct_item& it = items[idx];
+      const Box ob = c.whole;
+      const Box G = grow_clip3(ob, c.sc.rr, c.dims);
+      const Box Ab = grad_partial_box(G, ob, c.sc.rks, c.dims[2]);
+      Box Bxy = G;
+      Bxy.lo[0] = ob.lo[0];
+      Bxy.n[0] = ob.n[0];
+      Bxy.lo[1] = ob.lo[1];
+      Bxy.n[1] = ob.n[1];
+      const int64_t need = std::max<int64_t>(box_vox(G), (box_vox(Ab) + 1) / 2);
+      // arena pointers are offsets until the arena exists: stored relative, fixed up below
+      const size_t a_off = off, b_off = a_off + sizeof(float) * 6 * need, l_off = b_off + sizeof(float) * 6 * need;
+      off = (l_off + sizeof(int64_t) * box_vox(ob) + 255) / 256 * 256;
+      float* A = reinterpret_cast<float*>(a_off);
+      float* B = reinterpret_cast<float*>(b_off);
+      MultiRec base;
+      std::memset(&base, 0, sizeof base);
+      base.block = dim3(1, 1, 1);
+      {
+        GxyItem x{it.vol, ob, c.dims[0], c.dims[1], B, Ab, 0};
+        g_gxy.push_back(grad_xy_item(c.sc.rks, x));
+        gxy.push_back(x);
+        MultiRec r = base;
+        r.kind = 0;
+        r.rk = c.sc.rks;
+        r.t0 = c.sc.ts[0];
+        r.t1 = c.sc.ts[1];
+        p_gxy.push_back(r);
+      }
+      {
+        GzItem x{B, Ab, A, G, 0};
+        g_gz.push_back(grad_z_item(c.sc.rks, x));
+        gz.push_back(x);
+        MultiRec r = base;
+        r.kind = 1;
+        r.rk = c.sc.rks;
+        r.t0 = c.sc.ts[2];
+        std::memcpy(r.ss, c.sc.ss, sizeof r.ss);
+        p_gz.push_back(r);
+      }
+      {
+        RxyItem x{A, G, c.dims[0], c.dims[1], B, Bxy, 0};
+        const int xt = rho_xy_width(Bxy.n[0]);
+        g_rxy.push_back(rho_xy_item(c.sc.rkr, xt, x));
+        rxy.push_back(x);
+        MultiRec r = base;
+        r.kind = 2;
+        r.rk = c.sc.rkr;
+        r.xt = xt;
+        r.t0 = c.sc.tr[0];
+        r.t1 = c.sc.tr[1];
+        p_rxy.push_back(r);
+      }
+      const auto* t = tuned(P, c.sc, c.dims);
+      {
+        RzItem x{B, Bxy, c.dims[2], A, ob, 0};
+        MultiRec r = base;
+        r.kind = 3;
+        r.rk = c.sc.rkr;
+        r.block_t = t && t->stream_block ? t->stream_block : P->stream_block;
+        r.block = rho_stream_block(ob, 2);
+        r.t0 = c.sc.tr[2];
+        g_rz.push_back(rho_z_item(c.sc.rkr, r.block_t, r.block, x));
+        rz.push_back(x);
+        p_rz.push_back(r);
+      }
+      {
+        Fallback fb;
+        fb.count = nullptr;  // set below to the wave's counter slot
+        fb.total = P->fb_total;
+        fb.list = reinterpret_cast<int64_t*>(l_off);
+        fb.cap = box_vox(ob);
+        EigOut o{it.vec, it.ha, it.ia, it.fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
+        EigItem x{A, ob, ob, it.mask, ob, c.F, o, fb};
+        const bool compact = it.mask && (t && t->eig_compact >= 0 ? t->eig_compact != 0 : P->eig_compact);
+        MultiRec r = base;
+        r.kind = compact ? 4 : 5;
+        r.plain = c.F.sp[0] == 1.f && c.F.sp[1] == 1.f && c.F.sp[2] == 1.f && c.F.centres == nullptr;
+        g_eig.push_back(eig_item_grid(compact, x));
+        eig.push_back(x);
+        p_eig.push_back(r);
+      }
+      W.max_vox = std::max(W.max_vox, box_vox(ob));
+    }
+    // re-solve counters: one int per eigen item, in the table (zeroed per wave)
+    W.n_fbc = eig.size();
+    W.fbc_off = H->zeros(sizeof(int) * W.n_fbc);
+    for (size_t i = 0; i < eig.size(); ++i)
+      eig[i].fb.count = reinterpret_cast<int*>(W.fbc_off + sizeof(int) * i);  // table offset, fixed up below
+    // order the eigen items by kernel form so that the re-solve can take them all contiguously
+    std::vector<size_t> order(eig.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return p_eig[a].kind < p_eig[b].kind || (p_eig[a].kind == p_eig[b].kind && p_eig[a].plain > p_eig[b].plain); });
+    {
+      std::vector<EigItem> e2;
+      std::vector<uint3> g2;
+      std::vector<MultiRec> p2;
+      for (size_t i : order) {
+        e2.push_back(eig[i]);
+        g2.push_back(g_eig[i]);
+        p2.push_back(p_eig[i]);
+      }
+      eig.swap(e2);
+      g_eig.swap(g2);
+      p_eig.swap(p2);
+    }
+    add_groups(*H, W, gxy, g_gxy, p_gxy,
+               [](const MultiRec& a, const MultiRec& b) { return a.rk == b.rk && same_taps(a.t0, b.t0) && same_taps(a.t1, b.t1); },
+               [](MultiRec&) {});
+    add_groups(*H, W, gz, g_gz, p_gz,
+               [](const MultiRec& a, const MultiRec& b) {
+                 return a.rk == b.rk && same_taps(a.t0, b.t0) && std::memcmp(a.ss, b.ss, sizeof a.ss) == 0;
+               },
+               [](MultiRec&) {});
+    add_groups(*H, W, rxy, g_rxy, p_rxy,
+               [](const MultiRec& a, const MultiRec& b) {
+                 return a.rk == b.rk && a.xt == b.xt && same_taps(a.t0, b.t0) && same_taps(a.t1, b.t1);
+               },
+               [](MultiRec&) {});
+    add_groups(*H, W, rz, g_rz, p_rz,
+               [](const MultiRec& a, const MultiRec& b) {
+                 return a.rk == b.rk && a.block_t == b.block_t && same_taps(a.t0, b.t0);
+               },
+               [](MultiRec&) {});
+    // the eigen items in groups of equal kernel form, and all of them once more,
+    // contiguous, for the wave's re-solve
+    W.n_eig = (int)eig.size();
+    W.eig_items_off = H->put(eig.data(), eig.size());
+    add_groups(*H, W, eig, g_eig, p_eig,
+               [](const MultiRec& a, const MultiRec& b) { return a.kind == b.kind && a.plain == b.plain; },
+               [](MultiRec&) {});
+    W.n_counters = W.launches.size();
+    W.counters_off = H->zeros(sizeof(unsigned long long) * W.n_counters);
+    for (size_t g = 0; g < W.launches.size(); ++g)
+      W.launches[g].counter_off = W.counters_off + sizeof(unsigned long long) * g;
+    waves->push_back(W);
+  }
+  (void)mixed;
+  return CT_OK;
+}
+
+// Replace the arena and table offsets stored in the table's item records by
+// device addresses (the records hold offsets until the buffers exist).
+void fix_up_eig(EigItem* x, uintptr_t arena, uintptr_t tables) {
+  x->S = reinterpret_cast<const float*>(arena + reinterpret_cast<uintptr_t>(x->S));
+  x->fb.list = reinterpret_cast<int64_t*>(arena + reinterpret_cast<uintptr_t>(x->fb.list));
+  x->fb.count = reinterpret_cast<int*>(tables + reinterpret_cast<uintptr_t>(x->fb.count));
+}
+
+void fix_up_tables(HostTable& H, const std::vector<WaveRec>& waves, uintptr_t arena, uintptr_t tables) {
+  for (const WaveRec& W : waves) {
+    for (int i = 0; i < W.n_eig; ++i)
+      fix_up_eig(reinterpret_cast<EigItem*>(H.bytes.data() + W.eig_items_off) + i, arena, tables);
+    for (const MultiRec& r : W.launches) {
+      unsigned char* p = H.bytes.data() + r.items_off;
+      for (int i = 0; i < r.n; ++i) {
+        switch (r.kind) {
+          case 0: {
+            GxyItem* x = reinterpret_cast<GxyItem*>(p) + i;
+            x->F = reinterpret_cast<float*>(arena + reinterpret_cast<uintptr_t>(x->F));
+            break;
+          }
+          case 1: {
+            GzItem* x = reinterpret_cast<GzItem*>(p) + i;
+            x->F = reinterpret_cast<const float*>(arena + reinterpret_cast<uintptr_t>(x->F));
+            x->J = reinterpret_cast<float*>(arena + reinterpret_cast<uintptr_t>(x->J));
+            break;
+          }
+          case 2: {
+            RxyItem* x = reinterpret_cast<RxyItem*>(p) + i;
+            x->in = reinterpret_cast<const float*>(arena + reinterpret_cast<uintptr_t>(x->in));
+            x->out = reinterpret_cast<float*>(arena + reinterpret_cast<uintptr_t>(x->out));
+            break;
+          }
+          case 3: {
+            RzItem* x = reinterpret_cast<RzItem*>(p) + i;
+            x->in = reinterpret_cast<const float*>(arena + reinterpret_cast<uintptr_t>(x->in));
+            x->out = reinterpret_cast<float*>(arena + reinterpret_cast<uintptr_t>(x->out));
+            break;
+          }
+          default:
+            fix_up_eig(reinterpret_cast<EigItem*>(p) + i, arena, tables);
+            break;
+        }
+      }
+    }
+  }
+}
+
+// Enqueue the waves on st (the tables and arena are in place).
+ct_status run_persistent_waves(ct_plan P, const std::vector<WaveRec>& waves, cudaStream_t st) {
+  const bool mixed = P->p.precision == CT_PREC_MIXED;
+  const uintptr_t tb = reinterpret_cast<uintptr_t>(P->tables);
+  for (const WaveRec& W : waves) {
+    CT_CUDA(cudaMemsetAsync(reinterpret_cast<void*>(tb + W.counters_off), 0, sizeof(unsigned long long) * W.n_counters,
+                            st),
+            "counter reset");
+    CT_CUDA(cudaMemsetAsync(reinterpret_cast<void*>(tb + W.fbc_off), 0, sizeof(int) * W.n_fbc, st), "counter reset");
+    for (const MultiRec& r : W.launches) {
+      MultiTable T;
+      T.first = reinterpret_cast<const int64_t*>(tb + r.first_off);
+      T.grids = reinterpret_cast<const uint3*>(tb + r.grids_off);
+      T.n = r.n;
+      T.counter = reinterpret_cast<unsigned long long*>(tb + r.counter_off);
+      const void* items = reinterpret_cast<const void*>(tb + r.items_off);
+      switch (r.kind) {
+        case 0:
+          CT_LAUNCH(P, st, "grad_xy_batch",
+                    launch_grad_xy_multi(static_cast<const GxyItem*>(items), T, r.blocks, r.t0, r.t1, r.rk, st),
+                    "batched gradient x/y launch");
+          break;
+        case 1:
+          CT_LAUNCH(P, st, "grad_z_batch",
+                    launch_grad_z_multi(static_cast<const GzItem*>(items), T, r.blocks, r.t0, r.ss, r.rk, mixed, st),
+                    "batched gradient z launch");
+          break;
+        case 2:
+          CT_LAUNCH(P, st, "rho_xy_batch",
+                    launch_rho_xy_multi(static_cast<const RxyItem*>(items), T, r.blocks, r.t0, r.t1, r.rk, r.xt, st),
+                    "batched rho xy launch");
+          break;
+        case 3:
+          CT_LAUNCH(P, st, "rho_z_batch",
+                    launch_rho_z_multi(static_cast<const RzItem*>(items), T, r.blocks, r.block, r.t0, r.rk, r.block_t,
+                                       st),
+                    "batched rho z launch");
+          break;
+        default:
+          CT_LAUNCH(P, st, "eig_batch",
+                    launch_eig_multi(static_cast<const EigItem*>(items), T, r.blocks, r.kind == 4, P->p.vec_type,
+                                     P->p.angle_type, P->p.fa_type, r.plain, P->p.fill_value, st),
+                    "batched eigen launch");
+          break;
+      }
+    }
+    CT_LAUNCH(P, st, "eig_resolve_batch",
+              launch_eig_fallback_multi(reinterpret_cast<const EigItem*>(tb + W.eig_items_off), W.n_eig, W.max_vox,
+                                        P->p.fill_value, mixed, st),
+              "batched re-solve launch");
+  }
+  return CT_OK;
+}
+
 // A batch of device-resident volumes (uneven sizes, per-item scales and
 // frames): items go round-robin onto up to kSlots streams, each with its own
 // scratch slot, so that small volumes run side by side.  The whole
@@ -987,17 +1361,41 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
     return CT_OK;
   }
   const int K = std::max(1, std::min(std::min(P->batch_streams, ct_plan_s::kSlots), n));
+  // persistent batches: the items on the stencil chain (the tensor-core chain
+  // keeps its own per-item launches) go through run_persistent_waves on
+  // stream 0; the others round-robin over the remaining streams
+  std::vector<int> pers, rest;
+  for (int i = 0; i < n; ++i) {
+    const ItemCtx& c = ctx[i];
+    bool ok = P->batch_persistent && !use_tc(P, c.sc, c.dims, 0) && !use_tc(P, c.sc, c.dims, 1) &&
+              !use_tc(P, c.sc, c.dims, 2);
+    if (ok) {
+      EigOut o{items[i].vec, items[i].ha, items[i].ia, items[i].fa, P->p.vec_type, P->p.angle_type, P->p.fa_type,
+               c.whole};
+      EigItem e{nullptr, c.whole, c.whole, items[i].mask, c.whole, c.F, o, Fallback{}};
+      const Box G = grow_clip3(c.whole, c.sc.rr, c.dims);
+      ok = eig_item_ok(e) && box_vox(grad_partial_box(G, c.whole, c.sc.rks, c.dims[2])) < (int64_t(1) << 31) &&
+           6 * box_vox(G) < (int64_t(1) << 31) && c.whole.n[2] <= 65535 && 6 * c.whole.n[2] <= 65535;
+    }
+    (ok ? pers : rest).push_back(i);
+  }
+  const int k0 = pers.empty() || K == 1 ? 0 : 1;  // first stream of the per-item launches
+  const int kn = std::max(1, K - k0);
   // scratch of every slot sized for its largest item, before any capture
   std::vector<int64_t> gmax(K, 0);
   int64_t total = 0;
-  for (int i = 0; i < n; ++i) {
-    const int k = i % K;
+  for (int i = 0; i < n; ++i) total += box_vox(ctx[i].whole);
+  for (size_t r = 0; r < rest.size(); ++r) {
+    const int i = rest[r], k = k0 + (int)(r % kn);
     gmax[k] = std::max(gmax[k], box_vox(grow_clip3(ctx[i].whole, ctx[i].sc.rr, ctx[i].dims)));
-    total += box_vox(ctx[i].whole);
   }
   for (int k = 0; k < K; ++k) {
     if ((rc = ensure_stream(P, k))) return rc;
-    if ((rc = ensure_scratch(P, k, gmax[k]))) return rc;
+    if (gmax[k] > 0 && (rc = ensure_scratch(P, k, gmax[k]))) return rc;
+  }
+  if (!pers.empty() && !P->fb_total) {
+    CT_CUDA(cudaMalloc(&P->fb_total, sizeof(unsigned long long)), "counter allocation");
+    CT_CUDA(cudaMemset(P->fb_total, 0, sizeof(unsigned long long)), "counter reset");
   }
   if (!P->gst) {
     CT_CUDA(cudaStreamCreateWithFlags(&P->gst, cudaStreamNonBlocking), "stream creation");
@@ -1007,19 +1405,33 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
   key = fnv1a(key, items, sizeof(ct_item) * (size_t)n);
   key = fnv1a(key, &P->p, sizeof(ct_params));
   key = fnv1a(key, &K, sizeof K);
+  key = fnv1a(key, &P->batch_persistent, sizeof P->batch_persistent);
+  key = fnv1a(key, &P->batch_bytes, sizeof P->batch_bytes);
   if (!P->graph_exec || P->graph_key != key) {
     if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
     if (P->graph) cudaGraphDestroy(P->graph);
     P->graph_exec = nullptr;
     P->graph = nullptr;
+    // the persistent waves' tables and scratch arena, in place before the capture
+    std::vector<WaveRec> waves;
+    if (!pers.empty()) {
+      HostTable H;
+      size_t arena_need = 0;
+      if ((rc = build_persistent_waves(P, items, ctx, pers, &waves, &H, &arena_need))) return rc;
+      if ((rc = ensure_device(&P->arena, &P->arena_cap, arena_need, "batch scratch"))) return rc;
+      if ((rc = ensure_device(&P->tables, &P->tables_cap, H.bytes.size(), "batch tables"))) return rc;
+      fix_up_tables(H, waves, reinterpret_cast<uintptr_t>(P->arena), reinterpret_cast<uintptr_t>(P->tables));
+      CT_CUDA(cudaMemcpy(P->tables, H.bytes.data(), H.bytes.size(), cudaMemcpyHostToDevice), "batch table upload");
+    }
     const int64_t launches0 = P->stats.launches;
     CT_CUDA(cudaStreamBeginCapture(P->gst, cudaStreamCaptureModeRelaxed), "graph capture");
     P->capturing = true;
     cudaError_t e = cudaEventRecord(P->gev[0], P->gst);
     for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(P->st[k], P->gev[0], 0);
     rc = CT_OK;
-    for (int i = 0; i < n && e == cudaSuccess && rc == CT_OK; ++i) {
-      const int k = i % K;
+    if (e == cudaSuccess && !waves.empty()) rc = run_persistent_waves(P, waves, P->st[0]);
+    for (size_t r = 0; r < rest.size() && e == cudaSuccess && rc == CT_OK; ++r) {
+      const int i = rest[r], k = k0 + (int)(r % kn);
       const ItemCtx& c = ctx[i];
       EigOut o{items[i].vec, items[i].ha, items[i].ia, items[i].fa, P->p.vec_type, P->p.angle_type, P->p.fa_type,
                c.whole};

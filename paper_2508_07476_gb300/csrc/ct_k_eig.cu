@@ -10,6 +10,8 @@
 // FP32 cyclic Jacobi in the FP32 form, FP64 closed form (FP64 Jacobi if that
 // too is near-degenerate) in the mixed form.  The list keeps the re-solve off
 // the common path, so no warp diverges into it.
+#include <algorithm>
+
 #include "ct.h"
 #include "ct_common.cuh"
 #include "ct_launch.h"
@@ -114,12 +116,12 @@ __device__ __forceinline__ int box_index32(const Box& b, int x, int y, int z) {
 }
 
 template <int VT, int AT, int FT, bool PLAIN>
-__global__ void __launch_bounds__(256, CT_EIG_MINB)
-    k_eig_angles32(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
-                   float fill, EigOut o, bool mixed, Fallback fb) {
-  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void eig32_body(const float* __restrict__ S, Box sb, Box ob,
+                                           const uint8_t* __restrict__ mask, Box mb, const Frame& F, float fill,
+                                           const EigOut& o, const Fallback& fb, const VBlock blk) {
+  const int x = ob.lo[0] + blk.idx.x * blockDim.x + threadIdx.x;
   if (x >= ob.lo[0] + ob.n[0]) return;
-  const int y = ob.lo[1] + blockIdx.y, z = ob.lo[2] + blockIdx.z;
+  const int y = ob.lo[1] + blk.idx.y, z = ob.lo[2] + blk.idx.z;
   const bool inside = mask == nullptr || __ldg(mask + box_index32(mb, x, y, z)) != 0;
   float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
   if (inside) {
@@ -133,9 +135,17 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
     s.e = __ldg(S + 4 * ns + si);
     s.f = __ldg(S + 5 * ns + si);
     if (!eig_closed<float>(s, l, v))
-      push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
+      push_fallback(fb, ((int64_t)blk.idx.z * ob.n[1] + blk.idx.y) * ob.n[0] + (x - ob.lo[0]));
   }
   write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
+}
+
+template <int VT, int AT, int FT, bool PLAIN>
+__global__ void __launch_bounds__(256, CT_EIG_MINB)
+    k_eig_angles32(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
+                   float fill, EigOut o, bool mixed, Fallback fb) {
+  (void)mixed;
+  eig32_body<VT, AT, FT, PLAIN>(S, sb, ob, mask, mb, F, fill, o, fb, hw_block());
 }
 
 // The masked form: a CTA of kEigThreads threads takes kEigSpan consecutive
@@ -168,16 +178,16 @@ static_assert(kEigWarps * kEigSpanK <= 32, "one warp scans the per-warp counts")
 static_assert(kEigSpan <= 65536, "list entries are 16-bit");
 
 template <int VT, int AT, int FT, bool PLAIN>
-__global__ void __launch_bounds__(kEigThreads, CT_EIG_MINB * 256 / kEigThreads)
-    k_eig_angles_compact(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
-                         Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
+__device__ __forceinline__ void eig_compact_body(const float* __restrict__ S, Box sb, Box ob,
+                                                 const uint8_t* __restrict__ mask, Box mb, const Frame& F, float fill,
+                                                 const EigOut& o, const Fallback& fb, const VBlock blk) {
   constexpr int NC = kEigWarps * kEigSpanK;
   __shared__ uint16_t list[kEigSpan];
   __shared__ int cnt[NC];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int x0 = ob.lo[0] + blockIdx.x * kEigSpan;
+  const int x0 = ob.lo[0] + blk.idx.x * kEigSpan;
   const int xend = ob.lo[0] + ob.n[0];
-  const int y = ob.lo[1] + blockIdx.y, z = ob.lo[2] + blockIdx.z;
+  const int y = ob.lo[1] + blk.idx.y, z = ob.lo[2] + blk.idx.z;
   unsigned in_bits[kEigSpanK];
 #pragma unroll
   for (int k = 0; k < kEigSpanK; ++k) {
@@ -230,10 +240,36 @@ __global__ void __launch_bounds__(kEigThreads, CT_EIG_MINB * 256 / kEigThreads)
       const int x = xs[u];
       float l[3], v[3];
       if (!eig_closed<float>(s[u], l, v))
-        push_fallback(fb, ((int64_t)blockIdx.z * ob.n[1] + blockIdx.y) * ob.n[0] + (x - ob.lo[0]));
+        push_fallback(fb, ((int64_t)blk.idx.z * ob.n[1] + blk.idx.y) * ob.n[0] + (x - ob.lo[0]));
       write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
     }
   }
+}
+
+template <int VT, int AT, int FT, bool PLAIN>
+__global__ void __launch_bounds__(kEigThreads, CT_EIG_MINB * 256 / kEigThreads)
+    k_eig_angles_compact(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
+                         Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
+  (void)mixed;
+  eig_compact_body<VT, AT, FT, PLAIN>(S, sb, ob, mask, mb, F, fill, o, fb, hw_block());
+}
+
+// The eigen stage over a batch of volumes in one persistent launch: masked
+// items through the compacted form (kEigThreads per CTA), unmasked ones one
+// voxel per thread (kEigMultiThreads per CTA); the encodings and the plain
+// frame are the batch's (the plan's).
+constexpr int kEigMultiThreads = 256;
+template <int VT, int AT, int FT, bool PLAIN, bool COMPACT>
+__global__ void __launch_bounds__(COMPACT ? kEigThreads : kEigMultiThreads,
+                                  COMPACT ? CT_EIG_MINB * 256 / kEigThreads : CT_EIG_MINB)
+    k_eig_multi(const EigItem* __restrict__ items, const MultiTable T, float fill) {
+  for_each_vblock(T, [&](int i, const VBlock& v) {
+    const EigItem& it = items[i];
+    if (COMPACT)
+      eig_compact_body<VT, AT, FT, PLAIN>(it.S, it.sb, it.ob, it.mask, it.mb, it.F, fill, it.o, it.fb, v);
+    else
+      eig32_body<VT, AT, FT, PLAIN>(it.S, it.sb, it.ob, it.mask, it.mb, it.F, fill, it.o, it.fb, v);
+  });
 }
 
 __global__ void __launch_bounds__(128)
@@ -250,6 +286,25 @@ __global__ void __launch_bounds__(128)
     float l[3], v[3];
     resolve(s, mixed, l, v);
     write_voxel(o, box_index(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
+  }
+}
+
+// The re-solve of a batch: blockIdx.y = item, each item's listed voxels grid-strided.
+__global__ void __launch_bounds__(128)
+    k_eig_fallback_multi(const EigItem* __restrict__ items, float fill, bool mixed) {
+  const EigItem& it = items[blockIdx.y];
+  const int64_t cnt = min((int64_t)*it.fb.count, it.fb.cap);
+  const int64_t ns = box_vox(it.sb);
+  const Box ob = it.ob;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = it.fb.list[j];
+    const int x = ob.lo[0] + (int)(i % ob.n[0]);
+    const int y = ob.lo[1] + (int)((i / ob.n[0]) % ob.n[1]);
+    const int z = ob.lo[2] + (int)(i / ((int64_t)ob.n[0] * ob.n[1]));
+    Sym3<float> s = load_sym(it.S, ns, box_index(it.sb, x, y, z));
+    float l[3], v[3];
+    resolve(s, mixed, l, v);
+    write_voxel(it.o, box_index(it.o.ab, x, y, z), true, it.F, x, y, z, l, v, fill);
   }
 }
 
@@ -329,6 +384,55 @@ cudaError_t launch_eig_angles_fallback(const float* S, const Box& sb, const Box&
                                        const Fallback& fb, int64_t max_items, cudaStream_t st) {
   if (max_items <= 0) return cudaSuccess;
   k_eig_angles_fallback<<<grid_for(max_items, 128), 128, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ batches
+bool eig_item_ok(const EigItem& it) {
+  const int64_t lim = ((int64_t)1 << 31) - 1;
+  return it.ob.n[1] <= 65535 && it.ob.n[2] <= 65535 && 6 * box_vox(it.sb) <= lim && 3 * box_vox(it.o.ab) <= lim &&
+         box_vox(it.mb) <= lim;
+}
+
+uint3 eig_item_grid(bool compact, const EigItem& it) {
+  const Box& ob = it.ob;
+  return compact ? make_uint3((ob.n[0] + kEigSpan - 1) / kEigSpan, ob.n[1], ob.n[2])
+                 : make_uint3((ob.n[0] + kEigMultiThreads - 1) / kEigMultiThreads, ob.n[1], ob.n[2]);
+}
+
+template <int VT, int AT, int FT, bool PLAIN, bool COMPACT>
+static cudaError_t eig_multi_t(const EigItem* items, const MultiTable& T, int64_t blocks, float fill,
+                               cudaStream_t st) {
+  constexpr int threads = COMPACT ? kEigThreads : kEigMultiThreads;
+  const int grid = persistent_grid(k_eig_multi<VT, AT, FT, PLAIN, COMPACT>, threads, 0, blocks);
+  k_eig_multi<VT, AT, FT, PLAIN, COMPACT><<<grid, threads, 0, st>>>(items, T, fill);
+  return cudaGetLastError();
+}
+
+template <bool COMPACT>
+static cudaError_t eig_multi_c(const EigItem* items, const MultiTable& T, int64_t blocks, int vt, int at, int ft,
+                               bool plain, float fill, cudaStream_t st) {
+  if (vt == CT_OUT_F32 && at == CT_OUT_F32 && ft == CT_OUT_F32)
+    return plain ? eig_multi_t<0, 0, 0, true, COMPACT>(items, T, blocks, fill, st)
+                 : eig_multi_t<0, 0, 0, false, COMPACT>(items, T, blocks, fill, st);
+  if (vt == CT_OUT_F16 && at == CT_OUT_F16 && ft == CT_OUT_F16)
+    return plain ? eig_multi_t<1, 1, 1, true, COMPACT>(items, T, blocks, fill, st)
+                 : eig_multi_t<1, 1, 1, false, COMPACT>(items, T, blocks, fill, st);
+  if (at == CT_OUT_U8Q && ft == CT_OUT_F16) return eig_multi_t<-1, 2, 1, false, COMPACT>(items, T, blocks, fill, st);
+  return eig_multi_t<-1, -1, -1, false, COMPACT>(items, T, blocks, fill, st);
+}
+
+cudaError_t launch_eig_multi(const EigItem* items, const MultiTable& T, int64_t blocks, bool compact, int vt, int at,
+                             int ft, bool plain, float fill, cudaStream_t st) {
+  return compact ? eig_multi_c<true>(items, T, blocks, vt, at, ft, plain, fill, st)
+                 : eig_multi_c<false>(items, T, blocks, vt, at, ft, plain, fill, st);
+}
+
+cudaError_t launch_eig_fallback_multi(const EigItem* items, int n_items, int64_t max_per_item, float fill, bool mixed,
+                                      cudaStream_t st) {
+  if (n_items <= 0 || max_per_item <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::min<int64_t>((max_per_item + 127) / 128, 64), (unsigned)n_items);
+  k_eig_fallback_multi<<<grid, 128, 0, st>>>(items, fill, mixed);
   return cudaGetLastError();
 }
 

@@ -158,22 +158,22 @@ constexpr int kStreamThreads = 256;
 #define CT_RZ_MINB 1
 #endif
 template <int RR, int kT>
-__global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
-    k_rho_stream(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis,
-                 int seg, const Taps taps) {
+__device__ __forceinline__ void rho_stream_body(const float* __restrict__ in, Box ib, int dim_axis,
+                                                float* __restrict__ out, Box ob, int axis, int seg, const Taps& taps,
+                                                const VBlock blk) {
   constexpr int P = 2 * RR + 1;
   constexpr int WN = kT + 2 * RR;
   __shared__ float ring[2 * kT][kStreamThreads];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int other = 3 - axis;  // the non-x cross axis
-  const int x = ob.lo[0] + blockIdx.x * blockDim.x + threadIdx.x;
+  const int x = ob.lo[0] + blk.idx.x * blockDim.x + threadIdx.x;
   const int n_other = other == 1 ? ob.n[1] : ob.n[2];
-  const bool cok = blockIdx.y * blockDim.y + threadIdx.y < 6 * n_other;
-  const int cross = min(blockIdx.y * blockDim.y + threadIdx.y, 6 * n_other - 1);  // (comp, other) pair
+  const bool cok = blk.idx.y * blockDim.y + threadIdx.y < 6 * n_other;
+  const int cross = min(blk.idx.y * blockDim.y + threadIdx.y, 6 * n_other - 1);  // (comp, other) pair
   const int comp = cross / n_other;
   const int o = (other == 1 ? ob.lo[1] : ob.lo[2]) + cross % n_other;
   const int a_lo = axis == 1 ? ob.lo[1] : ob.lo[2], a_n = axis == 1 ? ob.n[1] : ob.n[2];
-  const int p0 = a_lo + blockIdx.z * seg;  // first output position on the axis
+  const int p0 = a_lo + blk.idx.z * seg;  // first output position on the axis
   const int L = min(seg, a_lo + a_n - p0);
   if (L <= 0) return;
   const bool xok = x < ob.lo[0] + ob.n[0] && cok;
@@ -258,6 +258,23 @@ __global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
   cp_async_wait<0>();
 }
 
+template <int RR, int kT>
+__global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
+    k_rho_stream(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis,
+                 int seg, const __grid_constant__ Taps taps) {
+  rho_stream_body<RR, kT>(in, ib, dim_axis, out, ob, axis, seg, taps, hw_block());
+}
+
+// The z pass over a batch of volumes in one persistent launch (MultiTable).
+template <int RR, int kT>
+__global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
+    k_rho_z_multi(const RzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps) {
+  for_each_vblock(T, [&](int i, const VBlock& v) {
+    const RzItem& it = items[i];
+    rho_stream_body<RR, kT>(it.in, it.ib, it.dim_axis, it.out, it.ob, 2, it.seg, taps, v);
+  });
+}
+
 template <int RR>
 static cudaError_t launch_rho_x_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                                   const Taps& taps, cudaStream_t st) {
@@ -283,25 +300,36 @@ cudaError_t launch_rho_x(const float* in, const Box& ib, const int dims[3], floa
   }
 }
 
-template <int RR>
-static cudaError_t launch_stream_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
-                                   int axis, const Taps& taps, int block_t, cudaStream_t st) {
+// The walk's segment length (enough CTAs to fill the GPU) and the CTA shape
+// (warps along x: the widest that leaves the fewest idle columns).
+static int stream_seg(const Box& ob, int axis, int RR) {
   const int other = 3 - axis;
   const int n_axis = ob.n[axis];
-  if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-  // segment the walk so that the grid has enough CTAs to fill the GPU
   int64_t cols = (int64_t)((ob.n[0] + 31) / 32) * 32 * 6 * ob.n[other];
   int nseg = 1;
   while (nseg < 16 && cols * nseg < (int64_t)152 * 1024 * 8 && n_axis / (nseg * 2) >= 4 * (2 * RR + 1)) nseg *= 2;
-  int seg = (n_axis + nseg - 1) / nseg;
-  // warps along x per CTA: the widest that leaves the fewest idle columns
+  return (n_axis + nseg - 1) / nseg;
+}
+
+dim3 rho_stream_block(const Box& ob, int axis) {
+  (void)axis;
   int wx = 1;
   for (int w = 2; w <= kStreamThreads / 32; w *= 2) {
     const int span = 32 * w, best = 32 * wx;
     if (32 * (w / 2) >= ob.n[0]) break;  // a narrower CTA already covers the row
     if ((ob.n[0] + span - 1) / span * span <= (ob.n[0] + best - 1) / best * best) wx = w;
   }
-  dim3 block(32 * wx, kStreamThreads / (32 * wx));
+  return dim3(32 * wx, kStreamThreads / (32 * wx));
+}
+
+template <int RR>
+static cudaError_t launch_stream_r(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
+                                   int axis, const Taps& taps, int block_t, cudaStream_t st) {
+  const int other = 3 - axis;
+  const int n_axis = ob.n[axis];
+  if (box_vox(ib) >= ((int64_t)1 << 31) || box_vox(ob) >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const int seg = stream_seg(ob, axis, RR);
+  const dim3 block = rho_stream_block(ob, axis);
   dim3 grid((ob.n[0] + block.x - 1) / block.x, (6 * ob.n[other] + block.y - 1) / block.y, (n_axis + seg - 1) / seg);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
   if (block_t == 8)
@@ -309,6 +337,42 @@ static cudaError_t launch_stream_r(const float* in, const Box& ib, const int dim
   else
     k_rho_stream<RR, 16><<<grid, block, 0, st>>>(in, ib, dims[axis], out, ob, axis, seg, taps);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batches
+uint3 rho_z_item(int rk, int block_t, dim3 block, RzItem& it) {
+  (void)block_t;
+  it.seg = stream_seg(it.ob, 2, rk);
+  return make_uint3((it.ob.n[0] + block.x - 1) / block.x, (6 * it.ob.n[1] + block.y - 1) / block.y,
+                    (it.ob.n[2] + it.seg - 1) / it.seg);
+}
+
+template <int RR>
+static cudaError_t z_multi_r(const RzItem* items, const MultiTable& T, int64_t blocks, dim3 block, const Taps& taps,
+                             int block_t, cudaStream_t st) {
+  if (block_t == 8) {
+    const int grid = persistent_grid(k_rho_z_multi<RR, 8>, kStreamThreads, 0, blocks);
+    k_rho_z_multi<RR, 8><<<grid, block, 0, st>>>(items, T, taps);
+  } else {
+    const int grid = persistent_grid(k_rho_z_multi<RR, 16>, kStreamThreads, 0, blocks);
+    k_rho_z_multi<RR, 16><<<grid, block, 0, st>>>(items, T, taps);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_z_multi(const RzItem* items, const MultiTable& T, int64_t blocks, dim3 block,
+                               const Taps& taps, int rk, int block_t, cudaStream_t st) {
+  switch (rk) {
+    case 4: return z_multi_r<4>(items, T, blocks, block, taps, block_t, st);
+    case 6: return z_multi_r<6>(items, T, blocks, block, taps, block_t, st);
+    case 8: return z_multi_r<8>(items, T, blocks, block, taps, block_t, st);
+    case 12: return z_multi_r<12>(items, T, blocks, block, taps, block_t, st);
+    case 16: return z_multi_r<16>(items, T, blocks, block, taps, block_t, st);
+    case 24: return z_multi_r<24>(items, T, blocks, block, taps, block_t, st);
+    case 32: return z_multi_r<32>(items, T, blocks, block, taps, block_t, st);
+    case 36: return z_multi_r<36>(items, T, blocks, block, taps, block_t, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_rho_stream(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob, int axis,

@@ -51,9 +51,9 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc)
 }
 
 template <int RR, int XT, bool SAMEXY>
-__global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
-    k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
-             const Taps tx, const Taps ty) {
+__device__ __forceinline__ void rho_xy_body(const float* __restrict__ in, Box ib, int dimx, int dimy,
+                                            float* __restrict__ out, Box ob, int seg, const Taps& tx, const Taps& ty,
+                                            const VBlock blk) {
   using G = XYGeom<RR, XT>;
   constexpr int kTB = G::TB;
   constexpr int kXT = XT;
@@ -63,11 +63,11 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
   float* sx = smem + kStages * kTB * G::XS;         // [kTB][SXS]
 
   const int t = threadIdx.x;
-  const int x0 = ob.lo[0] + blockIdx.x * kXT;
+  const int x0 = ob.lo[0] + blk.idx.x * kXT;
   const int xend = ob.lo[0] + ob.n[0];
-  const int comp = blockIdx.y / ob.n[2];
-  const int z = ob.lo[2] + blockIdx.y % ob.n[2];
-  const int p0 = ob.lo[1] + blockIdx.z * seg;
+  const int comp = blk.idx.y / ob.n[2];
+  const int z = ob.lo[2] + blk.idx.y % ob.n[2];
+  const int p0 = ob.lo[1] + blk.idx.z * seg;
   const int L = min(seg, ob.lo[1] + ob.n[1] - p0);
   if (L <= 0) return;
 
@@ -208,6 +208,24 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
   cp_async_wait<0>();
 }
 
+template <int RR, int XT, bool SAMEXY>
+__global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
+    k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
+             const __grid_constant__ Taps tx, const __grid_constant__ Taps ty) {
+  rho_xy_body<RR, XT, SAMEXY>(in, ib, dimx, dimy, out, ob, seg, tx, ty, hw_block());
+}
+
+// The same over a batch of volumes in one persistent launch (MultiTable).
+template <int RR, int XT, bool SAMEXY>
+__global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
+    k_rho_xy_multi(const RxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
+                   const __grid_constant__ Taps ty) {
+  for_each_vblock(T, [&](int i, const VBlock& v) {
+    const RxyItem& it = items[i];
+    rho_xy_body<RR, XT, SAMEXY>(it.in, it.ib, it.dimx, it.dimy, it.out, it.ob, it.seg, tx, ty, v);
+  });
+}
+
 template <int RR, int XT>
 static cudaError_t launch_xy_rt(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,
                                 const Taps& tx, const Taps& ty, cudaStream_t st) {
@@ -249,6 +267,10 @@ static cudaError_t prepare_xy_rt() {
   cudaError_t e = cudaFuncSetAttribute(k_rho_xy<RR, XT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_rho_xy<RR, XT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rho_xy_multi<RR, XT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rho_xy_multi<RR, XT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   return e;
 }
 
@@ -269,6 +291,76 @@ cudaError_t prepare_rho_xy_kernels() {
   if (e == cudaSuccess) e = prepare_xy_r<32>();
   if (e == cudaSuccess) e = prepare_xy_r<36>();
   return e;
+}
+
+// ---------------------------------------------------------------- batches
+int rho_xy_width(int n0) { return narrow_xy(n0) ? 128 : 256; }
+
+template <int RR, int XT>
+static uint3 xy_item(RxyItem& it) {
+  using G = XYGeom<RR, XT>;
+  constexpr int kTB = G::TB;
+  const Box& ob = it.ob;
+  const int64_t rows = (int64_t)6 * ob.n[2];
+  const int64_t ctas = (int64_t)((ob.n[0] + XT - 1) / XT) * rows;
+  int nseg = 1;
+  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ob.n[1] / (nseg * 2) >= 8 * kTB) nseg *= 2;
+  it.seg = (ob.n[1] + nseg - 1) / nseg;
+  return make_uint3((ob.n[0] + XT - 1) / XT, (unsigned)rows, (ob.n[1] + it.seg - 1) / it.seg);
+}
+
+template <int RR>
+static uint3 xy_item_r(int xt, RxyItem& it) {
+  return xt == 128 ? xy_item<RR, 128>(it) : xy_item<RR, 256>(it);
+}
+
+uint3 rho_xy_item(int rk, int xt, RxyItem& it) {
+  switch (rk) {
+    case 4: return xy_item_r<4>(xt, it);
+    case 6: return xy_item_r<6>(xt, it);
+    case 8: return xy_item_r<8>(xt, it);
+    case 12: return xy_item_r<12>(xt, it);
+    case 16: return xy_item_r<16>(xt, it);
+    case 24: return xy_item_r<24>(xt, it);
+    case 32: return xy_item_r<32>(xt, it);
+    default: return xy_item_r<36>(xt, it);
+  }
+}
+
+template <int RR, int XT>
+static cudaError_t xy_multi_t(const RxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                              const Taps& ty, cudaStream_t st) {
+  using G = XYGeom<RR, XT>;
+  const size_t smem = sizeof(float) * (kStages * G::TB * G::XS + G::TB * G::SXS);
+  if (std::memcmp(&tx, &ty, sizeof(Taps)) == 0) {
+    const int grid = persistent_grid(k_rho_xy_multi<RR, XT, true>, XT, smem, blocks);
+    k_rho_xy_multi<RR, XT, true><<<grid, XT, smem, st>>>(items, T, tx, ty);
+  } else {
+    const int grid = persistent_grid(k_rho_xy_multi<RR, XT, false>, XT, smem, blocks);
+    k_rho_xy_multi<RR, XT, false><<<grid, XT, smem, st>>>(items, T, tx, ty);
+  }
+  return cudaGetLastError();
+}
+
+template <int RR>
+static cudaError_t xy_multi_r(const RxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                              const Taps& ty, int xt, cudaStream_t st) {
+  return xt == 128 ? xy_multi_t<RR, 128>(items, T, blocks, tx, ty, st) : xy_multi_t<RR, 256>(items, T, blocks, tx, ty, st);
+}
+
+cudaError_t launch_rho_xy_multi(const RxyItem* items, const MultiTable& T, int64_t blocks, const Taps& tx,
+                                const Taps& ty, int rk, int xt, cudaStream_t st) {
+  switch (rk) {
+    case 4: return xy_multi_r<4>(items, T, blocks, tx, ty, xt, st);
+    case 6: return xy_multi_r<6>(items, T, blocks, tx, ty, xt, st);
+    case 8: return xy_multi_r<8>(items, T, blocks, tx, ty, xt, st);
+    case 12: return xy_multi_r<12>(items, T, blocks, tx, ty, xt, st);
+    case 16: return xy_multi_r<16>(items, T, blocks, tx, ty, xt, st);
+    case 24: return xy_multi_r<24>(items, T, blocks, tx, ty, xt, st);
+    case 32: return xy_multi_r<32>(items, T, blocks, tx, ty, xt, st);
+    case 36: return xy_multi_r<36>(items, T, blocks, tx, ty, xt, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_rho_xy(const float* in, const Box& ib, const int dims[3], float* out, const Box& ob,

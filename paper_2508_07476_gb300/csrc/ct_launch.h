@@ -151,6 +151,25 @@ struct Fallback {
   int64_t cap;
 };
 
+// One item of a batched eigen stage (the arguments of launch_eig_angles).
+struct EigItem {
+  const float* S;
+  Box sb, ob;
+  const uint8_t* mask;
+  Box mb;
+  Frame F;
+  EigOut o;
+  Fallback fb;
+};
+// Whether an item suits the batched eigen kernels (32-bit indices, rows in the grid).
+bool eig_item_ok(const EigItem& it);
+uint3 eig_item_grid(bool compact, const EigItem& it);
+cudaError_t launch_eig_multi(const EigItem* items, const MultiTable& T, int64_t blocks, bool compact, int vt, int at,
+                             int ft, bool plain, float fill, cudaStream_t st);
+// The re-solve of every item's listed voxels (at most max_per_item each) in one launch.
+cudaError_t launch_eig_fallback_multi(const EigItem* items, int n_items, int64_t max_per_item, float fill, bool mixed,
+                                      cudaStream_t st);
+
 // Per-voxel eigen-solve + HA/IA/FA over ob from S (6 planes over sb); mask
 // array (nullable) covers mb.  Near-degenerate voxels are appended to fb.
 // compact: with a mask, each row segment lists its inside voxels first and

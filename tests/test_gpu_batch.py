@@ -1,9 +1,12 @@
 """Batches of uneven volumes and caller-chunked boxes through the C ABI.
 
-A batch (ct_run_chunks with several device items) runs its items side by side
-on several streams inside one captured CUDA graph; each item's outputs must
-equal, bit for bit, those of running the item alone, and match the oracle.
-ct_run_box on padded chunks must reproduce the whole-volume run bit for bit.
+A batch (ct_run_chunks with several device items) runs inside one captured
+CUDA graph: the items on the FP32 stencil chain as one persistent launch per
+stage and tap set (CTAs taking (item, block) work from a device counter, in
+waves that fit the plan's scratch budget), the others as their own launch
+sequences on side streams.  Each item's outputs must equal, bit for bit,
+those of running the item alone, and match the oracle.  ct_run_box on padded
+chunks must reproduce the whole-volume run bit for bit.
 """
 import os
 
@@ -112,3 +115,79 @@ def test_run_box_chunks_equal_whole():
         _lib.ct_plan_destroy(plan)
     for k in ("v", "ha", "ia", "fa"):
         np.testing.assert_array_equal(got[k], whole[k], err_msg=k)
+
+
+def _items(crops, vols, outs, with_mask):
+    items = []
+    for w, v, o in zip(crops, vols, outs):
+        nz, ny, nx = w.spec.shape
+        cen, ax = synth.frame_of(w.spec)
+        m = G.dev_u8(synth.generate(w.spec)[1]) if with_mask else None
+        items.append((_lib.make_item(v, (nx, ny, nz), m, *o, sigma=w.sigma, rho=w.rho, lv_center=cen, lv_axis=ax), m))
+    return items
+
+
+def _batch_outputs(monkeypatch, crops, vols, prec, env, types, with_mask=False):
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    vt, at, ft = types
+    plan = _lib.ct_plan_create(_lib.make_params(1.0, 2.0, (0, 0, 0), (0, 0, 1), prec, vt, at, ft), (1, 1, 1))
+    for k in env:
+        monkeypatch.delenv(k)
+    dt = {_lib.CT_OUT_F32: torch.float32, _lib.CT_OUT_F16: torch.float16, _lib.CT_OUT_U8Q: torch.uint8}
+    outs = []
+    for w in crops:
+        nz, ny, nx = w.spec.shape
+        outs.append((torch.full((3, nz, ny, nx), -7, dtype=dt[vt], device="cuda"),
+                     torch.full((nz, ny, nx), 7, dtype=dt[at], device="cuda"),
+                     torch.full((nz, ny, nx), 7, dtype=dt[at], device="cuda"),
+                     torch.full((nz, ny, nx), -7, dtype=dt[ft], device="cuda")))
+    pairs = _items(crops, vols, outs, with_mask)
+    try:
+        _lib.ct_run_chunks(plan, [p[0] for p in pairs], False)
+        torch.cuda.synchronize()
+        st = _lib.ct_plan_stats(plan, reset=True)
+    finally:
+        _lib.ct_plan_destroy(plan)
+    return [[t.cpu().numpy() for t in o] for o in outs], st
+
+
+@pytest.mark.parametrize("types", [(_lib.CT_OUT_F32,) * 3, (_lib.CT_OUT_F16,) * 3,
+                                   (_lib.CT_OUT_F32, _lib.CT_OUT_U8Q, _lib.CT_OUT_F16)])
+@pytest.mark.parametrize("with_mask", [False, True])
+def test_persistent_batch_equals_per_item_launches(monkeypatch, types, with_mask):
+    # every sigma and rho of the uneven crops (R_sigma 4..12, R_rho 8..32), masks
+    # (compacted eigen stage) or none, the three output encodings; waves of
+    # several items and of one item each; and, with the tensor cores forced
+    # for R_rho >= 24, a batch mixing persistent items with per-item launches
+    crops = synth.crop_batch(count=10, seed=21, size_range=(24, 72))
+    host = [synth.generate(w.spec)[0] for w in crops]
+    vols = [G.dev_u16(h) for h in host]
+    prec = _lib.CT_PREC_MIXED
+    ref, st_ref = _batch_outputs(monkeypatch, crops, vols, prec, {"CT_TUNE_BATCH_PERSISTENT": "0"}, types, with_mask)
+    for env in ({}, {"CT_TUNE_BATCH_BYTES": "1"},
+                {"CT_TUNE_TC_ANY_BOX": "1", "CT_TUNE_TC_MIN_R": "24", "CT_TUNE_BATCH_BYTES": "20000000"}):
+        if "CT_TUNE_TC_ANY_BOX" in env:
+            ref_env = dict(env, CT_TUNE_BATCH_PERSISTENT="0")
+            ref, _ = _batch_outputs(monkeypatch, crops, vols, prec, ref_env, types, with_mask)
+        got, st = _batch_outputs(monkeypatch, crops, vols, prec, env, types, with_mask)
+        assert st["voxels"] == st_ref["voxels"]
+        for w, a, b in zip(crops, got, ref):
+            for k, x, y in zip(("v", "ha", "ia", "fa"), a, b):
+                np.testing.assert_array_equal(x, y, err_msg=f"{w.name} {k} {env}")
+    # the persistent form takes far fewer launches than a launch sequence per crop
+    _, st_p = _batch_outputs(monkeypatch, crops, vols, prec, {}, types, with_mask)
+    assert st_p["launches"] < st_ref["launches"] / 2, (st_p, st_ref)
+
+
+def test_persistent_batch_matches_oracle(monkeypatch):
+    crops = synth.crop_batch(count=6, seed=33, size_range=(24, 64), sigmas=(1.0, 3.0), rhos=(2.0, 8.0))
+    host = [synth.generate(w.spec)[0] for w in crops]
+    vols = [G.dev_u16(h) for h in host]
+    for prec in (_lib.CT_PREC_FP32, _lib.CT_PREC_MIXED):
+        got, _ = _batch_outputs(monkeypatch, crops, vols, prec, {}, (_lib.CT_OUT_F32,) * 3)
+        for w, h, o in zip(crops, host, got):
+            cen, ax = synth.frame_of(w.spec)
+            ora = O.pipeline(h, w.sigma, w.rho, cen, ax)
+            gpu = dict(zip(("v", "ha", "ia", "fa"), o))
+            G.assert_within(G.compare(gpu, ora, precision=prec), f"persistent {w.name} prec={prec}", precision=prec)
