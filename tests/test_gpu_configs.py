@@ -62,9 +62,12 @@ def _spec(name, shape=(256, 256, 256)):
 
 
 # share of graded voxels whose perturbation bound exceeds 0.5 deg, per
-# configuration and form (the input's property; measured shares well below)
-MAX_ILL = {("stream", MIXED): 0.05, ("stream", FP32): 0.01, ("tera", MIXED): 0.05, ("tera", FP32): 0.01,
-           ("crop", MIXED): 0.95, ("crop", FP32): 0.10, ("unit", MIXED): 0.05, ("unit", FP32): 0.01}
+# configuration and form (the input's property).  Measured on GB300: 0 on the
+# stream, tera and unit-seam walls in both forms; on the unmasked crops (noisy
+# background, period 6) 1.2e-4 in the FP32 form and 0.48 in the mixed form,
+# whose bound uses eps_S = 1e-3
+MAX_ILL = {("stream", MIXED): 0.01, ("stream", FP32): 0.01, ("tera", MIXED): 0.01, ("tera", FP32): 0.01,
+           ("crop", MIXED): 0.6, ("crop", FP32): 0.005, ("unit", MIXED): 0.01, ("unit", FP32): 0.01}
 
 CASES = {
     "stream_s2_r8": ("stream", 2.0, 8.0, True, (F16, F16, F16)),
