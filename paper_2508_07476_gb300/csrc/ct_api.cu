@@ -1212,8 +1212,9 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
                },
                [](MultiRec&) {});
     add_groups(*H, W, rz, g_rz, p_rz,
-               [](const MultiRec& a, const MultiRec& b) {
-                 return a.rk == b.rk && a.block_t == b.block_t && same_taps(a.t0, b.t0);
+               [](const MultiRec& a, const MultiRec& b) {  // the CTA shape too: each item's grid assumes its own
+                 return a.rk == b.rk && a.block_t == b.block_t && a.block.x == b.block.x && a.block.y == b.block.y &&
+                        same_taps(a.t0, b.t0);
                },
                [](MultiRec&) {});
     // the eigen items in groups of equal kernel form, and all of them once more,
