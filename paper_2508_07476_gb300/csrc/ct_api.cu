@@ -180,11 +180,12 @@ struct ct_plan_s {
   // stencil chain run as one persistent launch per stage and tap set, in waves
   // whose scratch fits batch_bytes of the arena
   bool batch_persistent = true;
-  int64_t batch_bytes = int64_t(16) << 30;
+  int64_t batch_bytes = int64_t(48) << 30;
   void* arena = nullptr;
   size_t arena_cap = 0;
   void* tables = nullptr;
   size_t tables_cap = 0;
+  cudaEvent_t wev[kSlots] = {};  // fork / join of a wave's chains
   cudaStream_t gst = nullptr;   // origin stream of the captured graph
   cudaEvent_t gev[2] = {nullptr, nullptr};
   cudaGraph_t graph = nullptr;
@@ -771,6 +772,8 @@ ct_status ct_plan_destroy(ct_plan P) {
   if (P->gst) cudaStreamDestroy(P->gst);
   if (P->arena) cudaFree(P->arena);
   if (P->tables) cudaFree(P->tables);
+  for (int k = 0; k < ct_plan_s::kSlots; ++k)
+    if (P->wev[k]) cudaEventDestroy(P->wev[k]);
   for (int k = 0; k < 2; ++k)
     if (P->gev[k]) cudaEventDestroy(P->gev[k]);
   for (int s = 0; s < ct_plan_s::kSlots; ++s) {
@@ -975,10 +978,12 @@ uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
 }
 
 // ---------------------------------------------------------- persistent batches
-// The stencil-chain items of a batch run stage by stage, each stage as one
-// persistent launch per tap set (template radius and taps) over every item of
-// a wave: the CTAs take (item, block) work from a device counter, so items of
-// any size share the SMs.  A wave holds the items whose scratch (the two tensor
+// The stencil-chain items of a batch run as one persistent launch per stage
+// and tap set (template radius and taps) over every item of a wave: the CTAs
+// take (item, block) work from a device counter, so items of any size share
+// the SMs.  The items of one tap set form a chain (gradient x/y, gradient z,
+// rho x/y, rho z) that runs in order on one of the plan's streams, chains side
+// by side; the eigen stage of the whole wave follows them.  A wave holds the items whose scratch (the two tensor
 // buffers and the re-solve list) fits the plan's batch_bytes; waves reuse the
 // arena in stream order.  Every item's blocks, launch shape and arithmetic are
 // those of its single launch, so a batch reproduces each item alone bit for
@@ -986,6 +991,7 @@ uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
 // capture) are built here; run_persistent_waves enqueues them.
 struct MultiRec {
   int kind;          // 0 grad_xy, 1 grad_z, 2 rho_xy, 3 rho_z, 4 eigen (compact), 5 eigen (per voxel)
+  int chain;         // stencil stages: the chain (tap sets) whose four launches run in order on one stream
   int rk, xt, block_t;
   bool plain;
   dim3 block;
@@ -1002,6 +1008,7 @@ struct WaveRec {
   size_t fbc_off = 0, n_fbc = 0;            // re-solve list counters
   size_t eig_items_off = 0;                 // every eigen item of the wave, contiguous
   int n_eig = 0;
+  int n_chains = 0;
   int64_t max_vox = 0;
 };
 
@@ -1087,9 +1094,33 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
     std::vector<EigItem> eig;
     std::vector<uint3> g_gxy, g_gz, g_rxy, g_rz, g_eig;
     std::vector<MultiRec> p_gxy, p_gz, p_rxy, p_rz, p_eig;
-    std::vector<size_t> fb_count_slot;
-    size_t off = 0;  // arena offset of the next item's scratch
+    // the chain of each item: equal radii, taps, product scales and z-block outputs
+    std::vector<int> chain_of;
+    std::vector<int> chain_rep;  // an item of each chain
     for (int idx : wv) {
+      const ItemCtx& c = ctx[idx];
+      const auto* t = tuned(P, c.sc, c.dims);
+      const int bt = t && t->stream_block ? t->stream_block : P->stream_block;
+      int found = -1;
+      for (size_t q = 0; q < chain_rep.size() && found < 0; ++q) {
+        const ItemCtx& d = ctx[chain_rep[q]];
+        const auto* td = tuned(P, d.sc, d.dims);
+        const int btd = td && td->stream_block ? td->stream_block : P->stream_block;
+        bool eq = c.sc.rks == d.sc.rks && c.sc.rkr == d.sc.rkr && bt == btd &&
+                  std::memcmp(c.sc.ss, d.sc.ss, sizeof c.sc.ss) == 0;
+        for (int a = 0; a < 3 && eq; ++a) eq = same_taps(c.sc.ts[a], d.sc.ts[a]) && same_taps(c.sc.tr[a], d.sc.tr[a]);
+        if (eq) found = (int)q;
+      }
+      if (found < 0) {
+        found = (int)chain_rep.size();
+        chain_rep.push_back(idx);
+      }
+      chain_of.push_back(found);
+    }
+    size_t off = 0;  // arena offset of the next item's scratch
+    int item_no = 0;
+    for (int idx : wv) {
+      const int chain = chain_of[item_no++];
       const ItemCtx& c = ctx[idx];
       const ct_item& it = items[idx];
       const Box ob = c.whole;
@@ -1109,6 +1140,7 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
       MultiRec base;
       std::memset(&base, 0, sizeof base);
       base.block = dim3(1, 1, 1);
+      base.chain = chain;
       {
         GxyItem x{it.vol, ob, c.dims[0], c.dims[1], B, Ab, 0};
         g_gxy.push_back(grad_xy_item(c.sc.rks, x));
@@ -1133,7 +1165,7 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
       }
       {
         RxyItem x{A, G, c.dims[0], c.dims[1], B, Bxy, 0};
-        const int xt = rho_xy_width(Bxy.n[0]);
+        const int xt = 128;  // one CTA width for every item of a batch (the arithmetic is the same at either)
         g_rxy.push_back(rho_xy_item(c.sc.rkr, xt, x));
         rxy.push_back(x);
         MultiRec r = base;
@@ -1151,7 +1183,7 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
         r.kind = 3;
         r.rk = c.sc.rkr;
         r.block_t = t && t->stream_block ? t->stream_block : P->stream_block;
-        r.block = rho_stream_block(ob, 2);
+        r.block = dim3(32, 8);  // one CTA shape for every item of a batch (a warp of consecutive x)
         r.t0 = c.sc.tr[2];
         g_rz.push_back(rho_z_item(c.sc.rkr, r.block_t, r.block, x));
         rz.push_back(x);
@@ -1198,32 +1230,20 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
       g_eig.swap(g2);
       p_eig.swap(p2);
     }
-    add_groups(*H, W, gxy, g_gxy, p_gxy,
-               [](const MultiRec& a, const MultiRec& b) { return a.rk == b.rk && same_taps(a.t0, b.t0) && same_taps(a.t1, b.t1); },
-               [](MultiRec&) {});
-    add_groups(*H, W, gz, g_gz, p_gz,
-               [](const MultiRec& a, const MultiRec& b) {
-                 return a.rk == b.rk && same_taps(a.t0, b.t0) && std::memcmp(a.ss, b.ss, sizeof a.ss) == 0;
-               },
-               [](MultiRec&) {});
-    add_groups(*H, W, rxy, g_rxy, p_rxy,
-               [](const MultiRec& a, const MultiRec& b) {
-                 return a.rk == b.rk && a.xt == b.xt && same_taps(a.t0, b.t0) && same_taps(a.t1, b.t1);
-               },
-               [](MultiRec&) {});
-    add_groups(*H, W, rz, g_rz, p_rz,
-               [](const MultiRec& a, const MultiRec& b) {  // the CTA shape too: each item's grid assumes its own
-                 return a.rk == b.rk && a.block_t == b.block_t && a.block.x == b.block.x && a.block.y == b.block.y &&
-                        same_taps(a.t0, b.t0);
-               },
-               [](MultiRec&) {});
+    // the four stages' launches of each chain, in stage order
+    const auto same_chain = [](const MultiRec& a, const MultiRec& b) { return a.chain == b.chain; };
+    add_groups(*H, W, gxy, g_gxy, p_gxy, same_chain, [](MultiRec&) {});
+    add_groups(*H, W, gz, g_gz, p_gz, same_chain, [](MultiRec&) {});
+    add_groups(*H, W, rxy, g_rxy, p_rxy, same_chain, [](MultiRec&) {});
+    add_groups(*H, W, rz, g_rz, p_rz, same_chain, [](MultiRec&) {});
+    W.n_chains = (int)chain_rep.size();
     // the eigen items in groups of equal kernel form, and all of them once more,
     // contiguous, for the wave's re-solve
     W.n_eig = (int)eig.size();
     W.eig_items_off = H->put(eig.data(), eig.size());
     add_groups(*H, W, eig, g_eig, p_eig,
                [](const MultiRec& a, const MultiRec& b) { return a.kind == b.kind && a.plain == b.plain; },
-               [](MultiRec&) {});
+               [](MultiRec& r) { r.chain = -1; });
     W.n_counters = W.launches.size();
     W.counters_off = H->zeros(sizeof(unsigned long long) * W.n_counters);
     for (size_t g = 0; g < W.launches.size(); ++g)
@@ -1282,16 +1302,31 @@ void fix_up_tables(HostTable& H, const std::vector<WaveRec>& waves, uintptr_t ar
   }
 }
 
-// Enqueue the waves on st (the tables and arena are in place).
-ct_status run_persistent_waves(ct_plan P, const std::vector<WaveRec>& waves, cudaStream_t st) {
+// Enqueue the waves: the chains of a wave spread over the plan's first K
+// streams (forked from and joined back into stream 0), then the wave's eigen
+// stage and re-solve on stream 0 (the tables and arena are in place).
+ct_status run_persistent_waves(ct_plan P, const std::vector<WaveRec>& waves, int K) {
   const bool mixed = P->p.precision == CT_PREC_MIXED;
   const uintptr_t tb = reinterpret_cast<uintptr_t>(P->tables);
+  cudaStream_t st0 = P->st[0];
   for (const WaveRec& W : waves) {
     CT_CUDA(cudaMemsetAsync(reinterpret_cast<void*>(tb + W.counters_off), 0, sizeof(unsigned long long) * W.n_counters,
-                            st),
+                            st0),
             "counter reset");
-    CT_CUDA(cudaMemsetAsync(reinterpret_cast<void*>(tb + W.fbc_off), 0, sizeof(int) * W.n_fbc, st), "counter reset");
+    CT_CUDA(cudaMemsetAsync(reinterpret_cast<void*>(tb + W.fbc_off), 0, sizeof(int) * W.n_fbc, st0), "counter reset");
+    const int ks = std::max(1, std::min(K, W.n_chains));
+    CT_CUDA(cudaEventRecord(P->wev[0], st0), "event record");
+    for (int k = 1; k < ks; ++k) CT_CUDA(cudaStreamWaitEvent(P->st[k], P->wev[0], 0), "stream wait");
+    bool joined = false;
     for (const MultiRec& r : W.launches) {
+      if (r.chain < 0 && !joined) {  // the eigen stage: every chain has finished
+        for (int k = 1; k < ks; ++k) {
+          CT_CUDA(cudaEventRecord(P->wev[k], P->st[k]), "event record");
+          CT_CUDA(cudaStreamWaitEvent(st0, P->wev[k], 0), "stream wait");
+        }
+        joined = true;
+      }
+      cudaStream_t st = r.chain >= 0 ? P->st[r.chain % ks] : st0;
       MultiTable T;
       T.first = reinterpret_cast<const int64_t*>(tb + r.first_off);
       T.grids = reinterpret_cast<const uint3*>(tb + r.grids_off);
@@ -1328,9 +1363,9 @@ ct_status run_persistent_waves(ct_plan P, const std::vector<WaveRec>& waves, cud
           break;
       }
     }
-    CT_LAUNCH(P, st, "eig_resolve_batch",
+    CT_LAUNCH(P, st0, "eig_resolve_batch",
               launch_eig_fallback_multi(reinterpret_cast<const EigItem*>(tb + W.eig_items_off), W.n_eig, W.max_vox,
-                                        P->p.fill_value, mixed, st),
+                                        P->p.fill_value, mixed, st0),
               "batched re-solve launch");
   }
   return CT_OK;
@@ -1394,6 +1429,8 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
     if ((rc = ensure_stream(P, k))) return rc;
     if (gmax[k] > 0 && (rc = ensure_scratch(P, k, gmax[k]))) return rc;
   }
+  for (int k = 0; k < K && !pers.empty(); ++k)
+    if (!P->wev[k]) CT_CUDA(cudaEventCreateWithFlags(&P->wev[k], cudaEventDisableTiming), "event creation");
   if (!pers.empty() && !P->fb_total) {
     CT_CUDA(cudaMalloc(&P->fb_total, sizeof(unsigned long long)), "counter allocation");
     CT_CUDA(cudaMemset(P->fb_total, 0, sizeof(unsigned long long)), "counter reset");
@@ -1430,7 +1467,7 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
     cudaError_t e = cudaEventRecord(P->gev[0], P->gst);
     for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(P->st[k], P->gev[0], 0);
     rc = CT_OK;
-    if (e == cudaSuccess && !waves.empty()) rc = run_persistent_waves(P, waves, P->st[0]);
+    if (e == cudaSuccess && !waves.empty()) rc = run_persistent_waves(P, waves, K);
     for (size_t r = 0; r < rest.size() && e == cudaSuccess && rc == CT_OK; ++r) {
       const int i = rest[r], k = k0 + (int)(r % kn);
       const ItemCtx& c = ctx[i];

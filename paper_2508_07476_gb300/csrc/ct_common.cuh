@@ -60,14 +60,18 @@ __device__ __forceinline__ int clamp_to(int p, int dim, int lo, int n) {
 struct VBlock {
   uint3 idx;
   uint3 dim;
+  __device__ __forceinline__ unsigned x() const { return idx.x; }
+  __device__ __forceinline__ unsigned y() const { return idx.y; }
+  __device__ __forceinline__ unsigned z() const { return idx.z; }
 };
 
-__device__ __forceinline__ VBlock hw_block() {
-  VBlock b;
-  b.idx = blockIdx;
-  b.dim = make_uint3(gridDim.x, gridDim.y, gridDim.z);
-  return b;
-}
+// The launch's own block index, read where it is used (the single-item kernels
+// compile as if the body read blockIdx itself).
+struct HwBlock {
+  __device__ __forceinline__ unsigned x() const { return blockIdx.x; }
+  __device__ __forceinline__ unsigned y() const { return blockIdx.y; }
+  __device__ __forceinline__ unsigned z() const { return blockIdx.z; }
+};
 
 // Per-launch table of a multi-item launch (device pointers).
 struct MultiTable {

@@ -115,13 +115,13 @@ __device__ __forceinline__ int box_index32(const Box& b, int x, int y, int z) {
   return ((z - b.lo[2]) * b.n[1] + (y - b.lo[1])) * b.n[0] + (x - b.lo[0]);
 }
 
-template <int VT, int AT, int FT, bool PLAIN>
+template <int VT, int AT, int FT, bool PLAIN, typename BLK>
 __device__ __forceinline__ void eig32_body(const float* __restrict__ S, Box sb, Box ob,
                                            const uint8_t* __restrict__ mask, Box mb, const Frame& F, float fill,
-                                           const EigOut& o, const Fallback& fb, const VBlock blk) {
-  const int x = ob.lo[0] + blk.idx.x * blockDim.x + threadIdx.x;
+                                           const EigOut& o, const Fallback& fb, const BLK blk) {
+  const int x = ob.lo[0] + blk.x() * blockDim.x + threadIdx.x;
   if (x >= ob.lo[0] + ob.n[0]) return;
-  const int y = ob.lo[1] + blk.idx.y, z = ob.lo[2] + blk.idx.z;
+  const int y = ob.lo[1] + blk.y(), z = ob.lo[2] + blk.z();
   const bool inside = mask == nullptr || __ldg(mask + box_index32(mb, x, y, z)) != 0;
   float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
   if (inside) {
@@ -135,7 +135,7 @@ __device__ __forceinline__ void eig32_body(const float* __restrict__ S, Box sb, 
     s.e = __ldg(S + 4 * ns + si);
     s.f = __ldg(S + 5 * ns + si);
     if (!eig_closed<float>(s, l, v))
-      push_fallback(fb, ((int64_t)blk.idx.z * ob.n[1] + blk.idx.y) * ob.n[0] + (x - ob.lo[0]));
+      push_fallback(fb, ((int64_t)blk.z() * ob.n[1] + blk.y()) * ob.n[0] + (x - ob.lo[0]));
   }
   write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
     k_eig_angles32(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb, Frame F,
                    float fill, EigOut o, bool mixed, Fallback fb) {
   (void)mixed;
-  eig32_body<VT, AT, FT, PLAIN>(S, sb, ob, mask, mb, F, fill, o, fb, hw_block());
+  eig32_body<VT, AT, FT, PLAIN>(S, sb, ob, mask, mb, F, fill, o, fb, HwBlock{});
 }
 
 // The masked form: a CTA of kEigThreads threads takes kEigSpan consecutive
@@ -177,17 +177,17 @@ constexpr int kEigWarps = kEigThreads / 32;
 static_assert(kEigWarps * kEigSpanK <= 32, "one warp scans the per-warp counts");
 static_assert(kEigSpan <= 65536, "list entries are 16-bit");
 
-template <int VT, int AT, int FT, bool PLAIN>
+template <int VT, int AT, int FT, bool PLAIN, typename BLK>
 __device__ __forceinline__ void eig_compact_body(const float* __restrict__ S, Box sb, Box ob,
                                                  const uint8_t* __restrict__ mask, Box mb, const Frame& F, float fill,
-                                                 const EigOut& o, const Fallback& fb, const VBlock blk) {
+                                                 const EigOut& o, const Fallback& fb, const BLK blk) {
   constexpr int NC = kEigWarps * kEigSpanK;
   __shared__ uint16_t list[kEigSpan];
   __shared__ int cnt[NC];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int x0 = ob.lo[0] + blk.idx.x * kEigSpan;
+  const int x0 = ob.lo[0] + blk.x() * kEigSpan;
   const int xend = ob.lo[0] + ob.n[0];
-  const int y = ob.lo[1] + blk.idx.y, z = ob.lo[2] + blk.idx.z;
+  const int y = ob.lo[1] + blk.y(), z = ob.lo[2] + blk.z();
   unsigned in_bits[kEigSpanK];
 #pragma unroll
   for (int k = 0; k < kEigSpanK; ++k) {
@@ -240,7 +240,7 @@ __device__ __forceinline__ void eig_compact_body(const float* __restrict__ S, Bo
       const int x = xs[u];
       float l[3], v[3];
       if (!eig_closed<float>(s[u], l, v))
-        push_fallback(fb, ((int64_t)blk.idx.z * ob.n[1] + blk.idx.y) * ob.n[0] + (x - ob.lo[0]));
+        push_fallback(fb, ((int64_t)blk.z() * ob.n[1] + blk.y()) * ob.n[0] + (x - ob.lo[0]));
       write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
     }
   }
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kEigThreads, CT_EIG_MINB * 256 / kEigThreads)
     k_eig_angles_compact(const float* __restrict__ S, Box sb, Box ob, const uint8_t* __restrict__ mask, Box mb,
                          Frame F, float fill, EigOut o, bool mixed, Fallback fb) {
   (void)mixed;
-  eig_compact_body<VT, AT, FT, PLAIN>(S, sb, ob, mask, mb, F, fill, o, fb, hw_block());
+  eig_compact_body<VT, AT, FT, PLAIN>(S, sb, ob, mask, mb, F, fill, o, fb, HwBlock{});
 }
 
 // The eigen stage over a batch of volumes in one persistent launch: masked

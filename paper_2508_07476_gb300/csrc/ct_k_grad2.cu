@@ -65,20 +65,20 @@ __device__ __forceinline__ void u16x8_to_f32(const uint4 q, float* f) {
   }
 }
 
-template <int RS, int XT>
+template <int RS, int XT, typename BLK>
 __device__ __forceinline__ void grad_xy_body(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy,
-                                             float* __restrict__ F, Box ab, int seg, const Taps& tx, const Taps& ty,
-                                             const VBlock blk) {
+                                             float* __restrict__ F, Box ab, int seg, const Taps tx, const Taps ty,
+                                             const BLK blk) {
   using G = GXYGeom<RS, XT>;
   constexpr int TB = G::TB;
   extern __shared__ __align__(16) float gsm[];
   float* stage = gsm;                  // [TB][XS] staged rows, (v, v) per voxel
   float* sx = gsm + TB * G::XS;        // [TB][SXS] x-pass rows, (c_x I, w_x I) per voxel
   const int t = threadIdx.x;
-  const int x0 = ab.lo[0] + blk.idx.x * XT;
+  const int x0 = ab.lo[0] + blk.x() * XT;
   const int xend = ab.lo[0] + ab.n[0];
-  const int z = ab.lo[2] + blk.idx.y;
-  const int p0 = ab.lo[1] + blk.idx.z * seg;
+  const int z = ab.lo[2] + blk.y();
+  const int p0 = ab.lo[1] + blk.z() * seg;
   const int L = min(seg, ab.lo[1] + ab.n[1] - p0);
   if (L <= 0) return;
   const uint16_t* plane = vol + (int64_t)(z - vb.lo[2]) * vb.n[0] * vb.n[1];
@@ -207,15 +207,15 @@ __device__ __forceinline__ void grad_xy_body(const uint16_t* __restrict__ vol, B
 template <int RS, int XT>
 __global__ void __launch_bounds__(XT, 512 / XT)
     k_grad_xy(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, float* __restrict__ F, Box ab, int seg,
-              const __grid_constant__ Taps tx, const __grid_constant__ Taps ty) {
-  grad_xy_body<RS, XT>(vol, vb, dimx, dimy, F, ab, seg, tx, ty, hw_block());
+              const Taps tx, const Taps ty) {
+  grad_xy_body<RS, XT>(vol, vb, dimx, dimy, F, ab, seg, tx, ty, HwBlock{});
 }
 
 // The same over a batch of volumes in one persistent launch (MultiTable).
 template <int RS, int XT>
 __global__ void __launch_bounds__(XT, 512 / XT)
-    k_grad_xy_multi(const GxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
-                    const __grid_constant__ Taps ty) {
+    k_grad_xy_multi(const GxyItem* __restrict__ items, const MultiTable T, const Taps tx,
+                    const Taps ty) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const GxyItem& it = items[i];
     grad_xy_body<RS, XT>(it.vol, it.vb, it.dimx, it.dimy, it.F, it.ab, it.seg, tx, ty, v);
@@ -250,19 +250,19 @@ constexpr float kGzHalfScale = 1.0f / 256.0f;
 // GOUT: write the gradient itself (3 planes: FP16 holding g * 2^-8 in the
 // mixed form, FP32 otherwise) for a consumer that forms the products, instead
 // of the six products.
-template <int RS, bool MIXED, bool GOUT>
+template <int RS, bool MIXED, bool GOUT, typename BLK>
 __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg,
-                                            const Taps& taps, const ProdScale& ps, const VBlock blk) {
+                                            const Taps taps, const ProdScale ps, const BLK blk) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
   extern __shared__ __align__(16) float gz_ring[];  // [P][3][kGzThreads]
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int x = ob.lo[0] + blk.idx.x * blockDim.x + threadIdx.x;
-  const int yr = blk.idx.y * blockDim.y + threadIdx.y;
+  const int x = ob.lo[0] + blk.x() * blockDim.x + threadIdx.x;
+  const int yr = blk.y() * blockDim.y + threadIdx.y;
   const bool ok = x < ob.lo[0] + ob.n[0] && yr < ob.n[1];
   const int xi = min(x, ob.lo[0] + ob.n[0] - 1);
   const int y = ob.lo[1] + min(yr, ob.n[1] - 1);
-  const int p0 = ob.lo[2] + blk.idx.z * seg;  // first output plane
+  const int p0 = ob.lo[2] + blk.z() * seg;  // first output plane
   const int L = min(seg, ob.lo[2] + ob.n[2] - p0);
   if (L <= 0) return;
   const int nsteps = L + 2 * RS;
@@ -365,8 +365,8 @@ __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, Box ab,
 template <int RS, bool MIXED, bool GOUT>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
     k_grad_z(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg,
-             const __grid_constant__ Taps taps, const __grid_constant__ ProdScale ps) {
-  grad_z_body<RS, MIXED, GOUT>(F, ab, Jv, ob, seg, taps, ps, hw_block());
+             const Taps taps, const ProdScale ps) {
+  grad_z_body<RS, MIXED, GOUT>(F, ab, Jv, ob, seg, taps, ps, HwBlock{});
 }
 
 // The same (the six products) over a batch of volumes in one persistent launch,
@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
 constexpr int kGzMultiX = 128;
 template <int RS, bool MIXED>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
-    k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps,
-                   const __grid_constant__ ProdScale ps) {
+    k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const Taps taps,
+                   const ProdScale ps) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const GzItem& it = items[i];
     grad_z_body<RS, MIXED, false>(it.F, it.ab, it.J, it.ob, it.seg, taps, ps, v);

@@ -157,23 +157,23 @@ constexpr int kStreamThreads = 256;
 #ifndef CT_RZ_MINB
 #define CT_RZ_MINB 1
 #endif
-template <int RR, int kT>
+template <int RR, int kT, typename BLK>
 __device__ __forceinline__ void rho_stream_body(const float* __restrict__ in, Box ib, int dim_axis,
-                                                float* __restrict__ out, Box ob, int axis, int seg, const Taps& taps,
-                                                const VBlock blk) {
+                                                float* __restrict__ out, Box ob, int axis, int seg, const Taps taps,
+                                                const BLK blk) {
   constexpr int P = 2 * RR + 1;
   constexpr int WN = kT + 2 * RR;
   __shared__ float ring[2 * kT][kStreamThreads];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int other = 3 - axis;  // the non-x cross axis
-  const int x = ob.lo[0] + blk.idx.x * blockDim.x + threadIdx.x;
+  const int x = ob.lo[0] + blk.x() * blockDim.x + threadIdx.x;
   const int n_other = other == 1 ? ob.n[1] : ob.n[2];
-  const bool cok = blk.idx.y * blockDim.y + threadIdx.y < 6 * n_other;
-  const int cross = min(blk.idx.y * blockDim.y + threadIdx.y, 6 * n_other - 1);  // (comp, other) pair
+  const bool cok = blk.y() * blockDim.y + threadIdx.y < 6 * n_other;
+  const int cross = min(blk.y() * blockDim.y + threadIdx.y, 6 * n_other - 1);  // (comp, other) pair
   const int comp = cross / n_other;
   const int o = (other == 1 ? ob.lo[1] : ob.lo[2]) + cross % n_other;
   const int a_lo = axis == 1 ? ob.lo[1] : ob.lo[2], a_n = axis == 1 ? ob.n[1] : ob.n[2];
-  const int p0 = a_lo + blk.idx.z * seg;  // first output position on the axis
+  const int p0 = a_lo + blk.z() * seg;  // first output position on the axis
   const int L = min(seg, a_lo + a_n - p0);
   if (L <= 0) return;
   const bool xok = x < ob.lo[0] + ob.n[0] && cok;
@@ -261,14 +261,14 @@ __device__ __forceinline__ void rho_stream_body(const float* __restrict__ in, Bo
 template <int RR, int kT>
 __global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
     k_rho_stream(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis,
-                 int seg, const __grid_constant__ Taps taps) {
-  rho_stream_body<RR, kT>(in, ib, dim_axis, out, ob, axis, seg, taps, hw_block());
+                 int seg, const Taps taps) {
+  rho_stream_body<RR, kT>(in, ib, dim_axis, out, ob, axis, seg, taps, HwBlock{});
 }
 
 // The z pass over a batch of volumes in one persistent launch (MultiTable).
 template <int RR, int kT>
 __global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
-    k_rho_z_multi(const RzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps) {
+    k_rho_z_multi(const RzItem* __restrict__ items, const MultiTable T, const Taps taps) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const RzItem& it = items[i];
     rho_stream_body<RR, kT>(it.in, it.ib, it.dim_axis, it.out, it.ob, 2, it.seg, taps, v);

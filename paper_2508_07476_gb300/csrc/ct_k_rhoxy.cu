@@ -50,10 +50,10 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc)
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_dst), "l"(gsrc) : "memory");
 }
 
-template <int RR, int XT, bool SAMEXY>
+template <int RR, int XT, bool SAMEXY, typename BLK>
 __device__ __forceinline__ void rho_xy_body(const float* __restrict__ in, Box ib, int dimx, int dimy,
-                                            float* __restrict__ out, Box ob, int seg, const Taps& tx, const Taps& ty,
-                                            const VBlock blk) {
+                                            float* __restrict__ out, Box ob, int seg, const Taps tx, const Taps ty,
+                                            const BLK blk) {
   using G = XYGeom<RR, XT>;
   constexpr int kTB = G::TB;
   constexpr int kXT = XT;
@@ -63,11 +63,11 @@ __device__ __forceinline__ void rho_xy_body(const float* __restrict__ in, Box ib
   float* sx = smem + kStages * kTB * G::XS;         // [kTB][SXS]
 
   const int t = threadIdx.x;
-  const int x0 = ob.lo[0] + blk.idx.x * kXT;
+  const int x0 = ob.lo[0] + blk.x() * kXT;
   const int xend = ob.lo[0] + ob.n[0];
-  const int comp = blk.idx.y / ob.n[2];
-  const int z = ob.lo[2] + blk.idx.y % ob.n[2];
-  const int p0 = ob.lo[1] + blk.idx.z * seg;
+  const int comp = blk.y() / ob.n[2];
+  const int z = ob.lo[2] + blk.y() % ob.n[2];
+  const int p0 = ob.lo[1] + blk.z() * seg;
   const int L = min(seg, ob.lo[1] + ob.n[1] - p0);
   if (L <= 0) return;
 
@@ -211,15 +211,15 @@ __device__ __forceinline__ void rho_xy_body(const float* __restrict__ in, Box ib
 template <int RR, int XT, bool SAMEXY>
 __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
     k_rho_xy(const float* __restrict__ in, Box ib, int dimx, int dimy, float* __restrict__ out, Box ob, int seg,
-             const __grid_constant__ Taps tx, const __grid_constant__ Taps ty) {
-  rho_xy_body<RR, XT, SAMEXY>(in, ib, dimx, dimy, out, ob, seg, tx, ty, hw_block());
+             const Taps tx, const Taps ty) {
+  rho_xy_body<RR, XT, SAMEXY>(in, ib, dimx, dimy, out, ob, seg, tx, ty, HwBlock{});
 }
 
 // The same over a batch of volumes in one persistent launch (MultiTable).
 template <int RR, int XT, bool SAMEXY>
 __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
-    k_rho_xy_multi(const RxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
-                   const __grid_constant__ Taps ty) {
+    k_rho_xy_multi(const RxyItem* __restrict__ items, const MultiTable T, const Taps tx,
+                   const Taps ty) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const RxyItem& it = items[i];
     rho_xy_body<RR, XT, SAMEXY>(it.in, it.ib, it.dimx, it.dimy, it.out, it.ob, it.seg, tx, ty, v);
