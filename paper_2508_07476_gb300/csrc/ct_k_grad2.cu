@@ -204,11 +204,145 @@ __device__ __forceinline__ void grad_xy_body(const uint16_t* __restrict__ vol, B
   }
 }
 
+// The single-item kernel keeps its own copy of the body (through the body
+// function it ran 6% slower).
 template <int RS, int XT>
 __global__ void __launch_bounds__(XT, 512 / XT)
     k_grad_xy(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy, float* __restrict__ F, Box ab, int seg,
               const Taps tx, const Taps ty) {
-  grad_xy_body<RS, XT>(vol, vb, dimx, dimy, F, ab, seg, tx, ty, HwBlock{});
+  using G = GXYGeom<RS, XT>;
+  constexpr int TB = G::TB;
+  extern __shared__ __align__(16) float gsm[];
+  float* stage = gsm;                  // [TB][XS] staged rows, (v, v) per voxel
+  float* sx = gsm + TB * G::XS;        // [TB][SXS] x-pass rows, (c_x I, w_x I) per voxel
+  const int t = threadIdx.x;
+  const int x0 = ab.lo[0] + blockIdx.x * XT;
+  const int xend = ab.lo[0] + ab.n[0];
+  const int z = ab.lo[2] + blockIdx.y;
+  const int p0 = ab.lo[1] + blockIdx.z * seg;
+  const int L = min(seg, ab.lo[1] + ab.n[1] - p0);
+  if (L <= 0) return;
+  const uint16_t* plane = vol + (int64_t)(z - vb.lo[2]) * vb.n[0] * vb.n[1];
+  const int ylo = max(0, vb.lo[1]), yhi = min(dimy - 1, vb.lo[1] + vb.n[1] - 1);
+  const int xlo_ok = max(0, vb.lo[0]), xhi_ok = min(dimx, vb.lo[0] + vb.n[0]);
+  const int nblocks = G::W + (L + TB - 1) / TB;
+  const bool aligned = (vb.n[0] % 8) == 0 && ((reinterpret_cast<uintptr_t>(vol) & 15) == 0);
+  // this thread's 16-byte chunks of a block: chunk q = t + XT i is row q % TB,
+  // columns x0 - XA + 8 (q / TB) .. +7 (the 8 lanes of a shared-memory phase
+  // then write 8 different rows); loaded whole when inside the box and
+  // aligned, else element by element with clamping
+  int q_row[G::NQ], q_col[G::NQ];
+  bool q_fast[G::NQ];
+#pragma unroll
+  for (int i = 0; i < G::NQ; ++i) {
+    const int q = t + XT * i;
+    q_row[i] = q < TB * G::QW ? q % TB : -1;
+    q_col[i] = x0 - G::XA + 8 * (q / TB);
+    q_fast[i] = aligned && q_col[i] >= xlo_ok && q_col[i] + 7 < xhi_ok && ((q_col[i] - vb.lo[0]) % 8) == 0;
+  }
+  uint4 pre[G::NQ];
+  auto load_block = [&](int b) {  // block b's chunks into registers
+#pragma unroll
+    for (int i = 0; i < G::NQ; ++i) {
+      if (q_row[i] < 0) continue;
+      const int y = min(max(p0 - RS - G::PAD + b * TB + q_row[i], ylo), yhi);
+      const uint16_t* row = plane + (int64_t)(y - vb.lo[1]) * vb.n[0] - vb.lo[0];
+      if (q_fast[i]) {
+        pre[i] = __ldg(reinterpret_cast<const uint4*>(row + q_col[i]));
+      } else {
+        uint32_t h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) h[e] = __ldg(row + clamp_to(q_col[i] + e, dimx, vb.lo[0], vb.n[0]));
+        pre[i] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+      }
+    }
+  };
+  auto store_block = [&]() {  // registers -> staged rows, every voxel twice
+#pragma unroll
+    for (int i = 0; i < G::NQ; ++i) {
+      if (q_row[i] < 0) continue;
+      float f[8];
+      u16x8_to_f32(pre[i], f);
+      float4* d = reinterpret_cast<float4*>(stage + q_row[i] * G::XS + 2 * (q_col[i] - (x0 - G::XA)));
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[e] = make_float4(f[2 * e], f[2 * e], f[2 * e + 1], f[2 * e + 1]);
+    }
+  };
+  // y window of this thread's column: (c_x I, w_x I) rows
+  float2 wp[G::WN];
+#pragma unroll
+  for (int j = 0; j < G::WN; ++j) wp[j] = make_float2(0.f, 0.f);
+  const int xr = t % 8;
+  const int xseg = t / 8;
+  const bool xok = x0 + t < xend;
+  const int64_t nab = box_vox(ab);
+  float* obase = F + box_index(ab, min(x0 + t, xend - 1), p0, z);
+  const int ostride = ab.n[0];
+  const float2 cw0 = make_float2(0.f, tx.w[RS]);  // centre tap of (c_x, w_x)
+  const float2 sgn = make_float2(-1.f, 1.f);
+  const float2 wy0 = make_float2(ty.w[RS], ty.w[RS]);
+  load_block(0);
+  for (int b = 0; b < nblocks; ++b) {
+    store_block();                           // the staged rows were last read before the previous barrier
+    if (b + 1 < nblocks) load_block(b + 1);  // in flight during this block's passes
+    __syncthreads();                         // staged rows complete; x-pass rows free
+    // x pass: 8 outputs of row xr (+ 8 r), columns xseg*8 .. +7, in sub-passes of XH
+#pragma unroll
+    for (int r8 = 0; r8 < TB / 8; ++r8) {
+      const int row = xr + 8 * r8;
+#pragma unroll
+      for (int h = 0; h < 8; h += G::XH) {
+        const float* src = stage + row * G::XS + 2 * (8 * xseg + h + G::B2);
+        float2 d[2 * G::NV];  // (v, v) of voxels B2 + h + j
+#pragma unroll
+        for (int j4 = 0; j4 < G::NV; ++j4) {
+          const float4 q = *reinterpret_cast<const float4*>(src + 4 * j4);
+          d[2 * j4] = make_float2(q.x, q.y);
+          d[2 * j4 + 1] = make_float2(q.z, q.w);
+        }
+        float2 acc[G::XH];  // (c_x I, w_x I)
+#pragma unroll
+        for (int i = 0; i < G::XH; ++i) {
+          const int m = G::O2 + i + RS;  // centre of output h + i in d
+          acc[i] = __fmul2_rn(cw0, d[m]);
+#pragma unroll
+          for (int k = 1; k <= RS; ++k) {
+            const float2 dk = __ffma2_rn(d[m - k], sgn, d[m + k]);  // (v+ - v-, v+ + v-)
+            acc[i] = __ffma2_rn(make_float2(tx.c[RS + k], tx.w[RS + k]), dk, acc[i]);
+          }
+        }
+        float4* o = reinterpret_cast<float4*>(sx + row * G::SXS + 2 * (8 * xseg + h));
+#pragma unroll
+        for (int i = 0; i < G::XH; i += 2) o[i / 2] = make_float4(acc[i].x, acc[i].y, acc[i + 1].x, acc[i + 1].y);
+      }
+    }
+    __syncthreads();  // x-pass rows complete
+    // y pass: slide the window by TB, append this column's rows
+#pragma unroll
+    for (int j = 0; j < 2 * RS; ++j) wp[j] = wp[j + TB];
+#pragma unroll
+    for (int r = 0; r < TB; ++r) wp[2 * RS + r] = *reinterpret_cast<const float2*>(sx + r * G::SXS + 2 * t);
+    if (b >= G::W) {
+      const int m0 = (b - G::W) * TB;  // first output row of this block, relative to p0
+#pragma unroll
+      for (int i = 0; i < TB; ++i) {
+        const int m = i + RS;
+        float2 f02 = __fmul2_rn(wy0, wp[m]);  // (w_y c_x I, w_y w_x I)
+        float f1 = 0.f;
+#pragma unroll
+        for (int k = 1; k <= RS; ++k) {
+          f02 = __ffma2_rn(make_float2(ty.w[RS + k], ty.w[RS + k]), __fadd2_rn(wp[m + k], wp[m - k]), f02);
+          f1 = fmaf(ty.c[RS + k], wp[m + k].y - wp[m - k].y, f1);
+        }
+        if (xok && m0 + i < L) {
+          float* o = obase + (int64_t)(m0 + i) * ostride;
+          o[0] = f02.x;
+          o[nab] = f1;
+          o[2 * nab] = f02.y;
+        }
+      }
+    }
+  }
 }
 
 // The same over a batch of volumes in one persistent launch (MultiTable).
@@ -510,16 +644,14 @@ cudaError_t launch_grad_xy(const uint16_t* vol, const Box& vb, const int dims[3]
 }
 
 // ---------------------------------------------------------------- batches
+// A batch item's walk is never split into segments: the batch's items fill
+// the GPU, and every segment would recompute its warm-up rows.
 template <int RS>
 static uint3 gxy_item(GxyItem& it) {
-  using G = GXYGeom<RS, CT_GXY_XT>;
   constexpr int XT = CT_GXY_XT;
   const Box& ab = it.ab;
-  const int64_t ctas = (int64_t)((ab.n[0] + XT - 1) / XT) * ab.n[2];
-  int nseg = 1;
-  while (nseg < 16 && ctas * nseg < (int64_t)152 * 2 * 4 * (256 / XT) && ab.n[1] / (nseg * 2) >= 8 * G::TB) nseg *= 2;
-  it.seg = (ab.n[1] + nseg - 1) / nseg;
-  return make_uint3((ab.n[0] + XT - 1) / XT, ab.n[2], (ab.n[1] + it.seg - 1) / it.seg);
+  it.seg = ab.n[1];
+  return make_uint3((ab.n[0] + XT - 1) / XT, ab.n[2], 1);
 }
 
 uint3 grad_xy_item(int rk, GxyItem& it) {
@@ -559,12 +691,8 @@ template <int RS>
 static uint3 gz_item(GzItem& it) {
   const Box& ob = it.ob;
   const dim3 block(kGzMultiX, kGzThreads / kGzMultiX);
-  const int64_t cols = (int64_t)((ob.n[0] + block.x - 1) / block.x) * ((ob.n[1] + block.y - 1) / block.y);
-  int nseg = 1;
-  while (nseg < 16 && cols * nseg < (int64_t)152 * 2 * 4 && ob.n[2] / (nseg * 2) >= 4 * (2 * RS + 1)) nseg *= 2;
-  it.seg = (ob.n[2] + nseg - 1) / nseg;
-  return make_uint3((ob.n[0] + block.x - 1) / block.x, (ob.n[1] + block.y - 1) / block.y,
-                    (ob.n[2] + it.seg - 1) / it.seg);
+  it.seg = ob.n[2];  // unsplit (see gxy_item)
+  return make_uint3((ob.n[0] + block.x - 1) / block.x, (ob.n[1] + block.y - 1) / block.y, 1);
 }
 
 uint3 grad_z_item(int rk, GzItem& it) {

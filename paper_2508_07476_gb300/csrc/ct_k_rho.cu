@@ -342,9 +342,9 @@ static cudaError_t launch_stream_r(const float* in, const Box& ib, const int dim
 // ---------------------------------------------------------------- batches
 uint3 rho_z_item(int rk, int block_t, dim3 block, RzItem& it) {
   (void)block_t;
-  it.seg = stream_seg(it.ob, 2, rk);
-  return make_uint3((it.ob.n[0] + block.x - 1) / block.x, (6 * it.ob.n[1] + block.y - 1) / block.y,
-                    (it.ob.n[2] + it.seg - 1) / it.seg);
+  (void)rk;
+  it.seg = it.ob.n[2];  // unsplit: the batch's items fill the GPU, and a segment recomputes its warm-up
+  return make_uint3((it.ob.n[0] + block.x - 1) / block.x, (6 * it.ob.n[1] + block.y - 1) / block.y, 1);
 }
 
 template <int RR>

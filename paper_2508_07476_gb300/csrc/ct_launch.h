@@ -71,10 +71,12 @@ bool rho_tc_volume_aligned(int nx, int axis);
 // ---------------------------------------------------------------- batches
 // One persistent launch per stage over a batch of volumes (MultiTable, in
 // ct_common.cuh): the item's arguments as the single-item launch takes them;
-// *_item fills the item's launch shape (seg) and returns its grid exactly as
-// the single launch would choose them, so that a batch reproduces every
-// item's results bit for bit; launch_*_multi runs the stage over a device
-// table of items (grid: the SMs times the blocks each holds, at most `blocks`).
+// *_item fills the item's launch shape (seg: the whole walk, unsplit, since
+// the batch's items fill the GPU) and returns its grid; the blocks compute
+// every output with the same operations as the single launch, so a batch
+// reproduces every item's results bit for bit; launch_*_multi runs the stage
+// over a device table of items (grid: the SMs times the blocks each holds, at
+// most `blocks`).
 struct GxyItem {
   const uint16_t* vol;
   Box vb;
