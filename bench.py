@@ -694,7 +694,7 @@ def run_crops(args):
     ora_cache = {}
     mode_env = {"persistent": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "1"},
                 "graph": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "0"},
-                "per_crop": {"CT_TUNE_BATCH_GRAPH": "0"}}
+                "per_crop": {"CT_TUNE_BATCH_GRAPH": "0", "CT_TUNE_BATCH_PERSISTENT": "0"}}
     for mode in ("persistent", "graph", "per_crop"):
         os.environ.update(mode_env[mode])
         plan = _lib.ct_plan_create(_lib.make_params(2.0, 6.0, (0, 0, 0), (0, 0, 1), _lib.CT_PREC_MIXED,

@@ -1384,7 +1384,7 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
   ct_status rc;
   for (int i = 0; i < n; ++i)
     if ((rc = item_ctx(P, items[i], &ctx[i]))) return rc;
-  if (!P->batch_graph) {
+  if (!P->batch_graph && !P->batch_persistent) {
     for (int i = 0; i < n; ++i) {
       const ItemCtx& c = ctx[i];
       EigOut o{items[i].vec, items[i].ha, items[i].ia, items[i].fa, P->p.vec_type, P->p.angle_type, P->p.fa_type,
@@ -1438,6 +1438,46 @@ ct_status run_device_batch(ct_plan P, const ct_item* items, int n, cudaStream_t 
   if (!P->gst) {
     CT_CUDA(cudaStreamCreateWithFlags(&P->gst, cudaStreamNonBlocking), "stream creation");
     for (int k = 0; k < 2; ++k) CT_CUDA(cudaEventCreateWithFlags(&P->gev[k], cudaEventDisableTiming), "event creation");
+  }
+  if (!P->batch_graph) {
+    // persistent launches without a graph (their kernels then carry the plan's
+    // timing events): tables built and uploaded on every call, the waves and the
+    // per-item sequences forked from and joined back into the caller's stream
+    std::vector<WaveRec> waves;
+    if (!pers.empty()) {
+      HostTable H;
+      size_t arena_need = 0;
+      CT_CUDA(cudaStreamSynchronize(user), "stream sync");  // the arena and tables may be in use
+      for (int k = 0; k < K; ++k) CT_CUDA(cudaStreamSynchronize(P->st[k]), "stream sync");
+      if ((rc = build_persistent_waves(P, items, ctx, pers, &waves, &H, &arena_need))) return rc;
+      if ((rc = ensure_device(&P->arena, &P->arena_cap, arena_need, "batch scratch"))) return rc;
+      if ((rc = ensure_device(&P->tables, &P->tables_cap, H.bytes.size(), "batch tables"))) return rc;
+      fix_up_tables(H, waves, reinterpret_cast<uintptr_t>(P->arena), reinterpret_cast<uintptr_t>(P->tables));
+      CT_CUDA(cudaMemcpy(P->tables, H.bytes.data(), H.bytes.size(), cudaMemcpyHostToDevice), "batch table upload");
+    }
+    if (!P->gst) {
+      CT_CUDA(cudaStreamCreateWithFlags(&P->gst, cudaStreamNonBlocking), "stream creation");
+      for (int k = 0; k < 2; ++k)
+        CT_CUDA(cudaEventCreateWithFlags(&P->gev[k], cudaEventDisableTiming), "event creation");
+    }
+    CT_CUDA(cudaEventRecord(P->gev[0], user), "event record");
+    for (int k = 0; k < K; ++k) CT_CUDA(cudaStreamWaitEvent(P->st[k], P->gev[0], 0), "stream wait");
+    if (!waves.empty() && (rc = run_persistent_waves(P, waves, K))) return rc;
+    for (size_t r = 0; r < rest.size(); ++r) {
+      const int i = rest[r], k = k0 + (int)(r % kn);
+      const ItemCtx& c = ctx[i];
+      EigOut o{items[i].vec, items[i].ha, items[i].ia, items[i].fa, P->p.vec_type, P->p.angle_type, P->p.fa_type,
+               c.whole};
+      if ((rc = fused_stages(P, c.sc, c.dims, items[i].vol, c.whole, c.whole, items[i].mask, c.whole, c.F, o, k, mixed,
+                             P->st[k])))
+        return rc;
+    }
+    for (int k = 0; k < K; ++k) {
+      CT_CUDA(cudaEventRecord(P->ev[k], P->st[k]), "event record");
+      CT_CUDA(cudaStreamWaitEvent(user, P->ev[k], 0), "stream wait");
+    }
+    P->stats.voxels += total;
+    return CT_OK;
   }
   uint64_t key = 1469598103934665603ull;
   key = fnv1a(key, items, sizeof(ct_item) * (size_t)n);

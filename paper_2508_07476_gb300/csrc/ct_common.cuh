@@ -81,32 +81,40 @@ struct MultiTable {
   unsigned long long* counter;
 };
 
-template <typename F>
+// CLAIM: blocks taken per counter increment (consecutive ones), so that the
+// counter's round trip is paid once per CLAIM blocks of short-lived kernels.
+template <int CLAIM = 1, typename F>
 __device__ __forceinline__ void for_each_vblock(const MultiTable& T, F&& f) {
   __shared__ long long s_next;
   const int64_t total = T.first[T.n];
   for (;;) {
-    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) s_next = (long long)atomicAdd(T.counter, 1ull);
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0)
+      s_next = (long long)atomicAdd(T.counter, (unsigned long long)CLAIM) ;
     __syncthreads();
-    const int64_t b = s_next;
+    const int64_t b0 = s_next;
     __syncthreads();  // every thread has read it before it is overwritten
-    if (b >= total) break;
-    int lo = 0, hi = T.n - 1;  // the item whose blocks hold b: the last with first <= b
+    if (b0 >= total) break;
+    int lo = 0, hi = T.n - 1;  // the item whose blocks hold b0: the last with first <= b0
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (T.first[mid] <= b) lo = mid;
+      if (T.first[mid] <= b0) lo = mid;
       else hi = mid - 1;
     }
-    const uint3 g = T.grids[lo];
-    int64_t r = b - T.first[lo];
-    VBlock v;
-    v.dim = g;
-    v.idx.x = (unsigned)(r % g.x);
-    r /= g.x;
-    v.idx.y = (unsigned)(r % g.y);
-    v.idx.z = (unsigned)(r / g.y);
-    f(lo, v);
-    __syncthreads();  // the block's shared memory is free for the next one
+    for (int c = 0; c < CLAIM; ++c) {
+      const int64_t b = b0 + c;
+      if (b >= total) break;
+      while (lo + 1 < T.n && T.first[lo + 1] <= b) ++lo;  // the claim may run into the next item
+      const uint3 g = T.grids[lo];
+      int64_t r = b - T.first[lo];
+      VBlock v;
+      v.dim = g;
+      v.idx.x = (unsigned)(r % g.x);
+      r /= g.x;
+      v.idx.y = (unsigned)(r % g.y);
+      v.idx.z = (unsigned)(r / g.y);
+      f(lo, v);
+      __syncthreads();  // the block's shared memory is free for the next one
+    }
   }
 }
 

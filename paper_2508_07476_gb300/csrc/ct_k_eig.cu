@@ -263,7 +263,7 @@ template <int VT, int AT, int FT, bool PLAIN, bool COMPACT>
 __global__ void __launch_bounds__(COMPACT ? kEigThreads : kEigMultiThreads,
                                   COMPACT ? CT_EIG_MINB * 256 / kEigThreads : CT_EIG_MINB)
     k_eig_multi(const EigItem* __restrict__ items, const MultiTable T, float fill) {
-  for_each_vblock(T, [&](int i, const VBlock& v) {
+  for_each_vblock<COMPACT ? 4 : 16>(T, [&](int i, const VBlock& v) {
     const EigItem& it = items[i];
     if (COMPACT)
       eig_compact_body<VT, AT, FT, PLAIN>(it.S, it.sb, it.ob, it.mask, it.mb, it.F, fill, it.o, it.fb, v);

@@ -66,9 +66,9 @@ __device__ __forceinline__ void u16x8_to_f32(const uint4 q, float* f) {
 }
 
 template <int RS, int XT, typename BLK>
-__device__ __forceinline__ void grad_xy_body(const uint16_t* __restrict__ vol, Box vb, int dimx, int dimy,
-                                             float* __restrict__ F, Box ab, int seg, const Taps tx, const Taps ty,
-                                             const BLK blk) {
+__device__ __forceinline__ void grad_xy_body(const uint16_t* __restrict__ vol, const Box& vb, int dimx, int dimy,
+                                             float* __restrict__ F, const Box& ab, int seg, const Taps& tx,
+                                             const Taps& ty, const BLK blk) {
   using G = GXYGeom<RS, XT>;
   constexpr int TB = G::TB;
   extern __shared__ __align__(16) float gsm[];
@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(XT, 512 / XT)
 // The same over a batch of volumes in one persistent launch (MultiTable).
 template <int RS, int XT>
 __global__ void __launch_bounds__(XT, 512 / XT)
-    k_grad_xy_multi(const GxyItem* __restrict__ items, const MultiTable T, const Taps tx,
-                    const Taps ty) {
+    k_grad_xy_multi(const GxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
+                    const __grid_constant__ Taps ty) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const GxyItem& it = items[i];
     grad_xy_body<RS, XT>(it.vol, it.vb, it.dimx, it.dimy, it.F, it.ab, it.seg, tx, ty, v);
@@ -385,8 +385,9 @@ constexpr float kGzHalfScale = 1.0f / 256.0f;
 // mixed form, FP32 otherwise) for a consumer that forms the products, instead
 // of the six products.
 template <int RS, bool MIXED, bool GOUT, typename BLK>
-__device__ __forceinline__ void grad_z_body(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg,
-                                            const Taps taps, const ProdScale ps, const BLK blk) {
+__device__ __forceinline__ void grad_z_body(const float* __restrict__ F, const Box& ab, void* __restrict__ Jv,
+                                            const Box& ob, int seg, const Taps& taps, const ProdScale& ps,
+                                            const BLK blk) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
   extern __shared__ __align__(16) float gz_ring[];  // [P][3][kGzThreads]
@@ -498,8 +499,9 @@ __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, Box ab,
 
 template <int RS, bool MIXED, bool GOUT>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
-    k_grad_z(const float* __restrict__ F, Box ab, void* __restrict__ Jv, Box ob, int seg,
-             const Taps taps, const ProdScale ps) {
+    k_grad_z(const float* __restrict__ F, const __grid_constant__ Box ab, void* __restrict__ Jv,
+             const __grid_constant__ Box ob, int seg,
+             const __grid_constant__ Taps taps, const __grid_constant__ ProdScale ps) {
   grad_z_body<RS, MIXED, GOUT>(F, ab, Jv, ob, seg, taps, ps, HwBlock{});
 }
 
@@ -508,8 +510,8 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
 constexpr int kGzMultiX = 128;
 template <int RS, bool MIXED>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
-    k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const Taps taps,
-                   const ProdScale ps) {
+    k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps,
+                   const __grid_constant__ ProdScale ps) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const GzItem& it = items[i];
     grad_z_body<RS, MIXED, false>(it.F, it.ab, it.J, it.ob, it.seg, taps, ps, v);

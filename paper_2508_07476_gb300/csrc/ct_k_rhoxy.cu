@@ -51,9 +51,9 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_dst, const float* gsrc)
 }
 
 template <int RR, int XT, bool SAMEXY, typename BLK>
-__device__ __forceinline__ void rho_xy_body(const float* __restrict__ in, Box ib, int dimx, int dimy,
-                                            float* __restrict__ out, Box ob, int seg, const Taps tx, const Taps ty,
-                                            const BLK blk) {
+__device__ __forceinline__ void rho_xy_body(const float* __restrict__ in, const Box& ib, int dimx, int dimy,
+                                            float* __restrict__ out, const Box& ob, int seg, const Taps& tx,
+                                            const Taps& ty, const BLK blk) {
   using G = XYGeom<RR, XT>;
   constexpr int kTB = G::TB;
   constexpr int kXT = XT;
@@ -372,8 +372,8 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
 // The same over a batch of volumes in one persistent launch (MultiTable).
 template <int RR, int XT, bool SAMEXY>
 __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
-    k_rho_xy_multi(const RxyItem* __restrict__ items, const MultiTable T, const Taps tx,
-                   const Taps ty) {
+    k_rho_xy_multi(const RxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
+                   const __grid_constant__ Taps ty) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
     const RxyItem& it = items[i];
     rho_xy_body<RR, XT, SAMEXY>(it.in, it.ib, it.dimx, it.dimy, it.out, it.ob, it.seg, tx, ty, v);

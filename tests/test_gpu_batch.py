@@ -38,10 +38,12 @@ def _alloc(shape):
 
 def _run_batch(crops, vols, precision, graph: bool):
     os.environ["CT_TUNE_BATCH_GRAPH"] = "1" if graph else "0"
+    os.environ["CT_TUNE_BATCH_PERSISTENT"] = "1" if graph else "0"
     try:
         plan = _lib.ct_plan_create(_lib.make_params(1.0, 2.0, (0, 0, 0), (0, 0, 1), precision), (1, 1, 1))
     finally:
         del os.environ["CT_TUNE_BATCH_GRAPH"]
+        del os.environ["CT_TUNE_BATCH_PERSISTENT"]
     outs, items = [], []
     for w, v in zip(crops, vols):
         nz, ny, nx = w.spec.shape
@@ -165,7 +167,7 @@ def test_persistent_batch_equals_per_item_launches(monkeypatch, types, with_mask
     vols = [G.dev_u16(h) for h in host]
     prec = _lib.CT_PREC_MIXED
     ref, st_ref = _batch_outputs(monkeypatch, crops, vols, prec, {"CT_TUNE_BATCH_PERSISTENT": "0"}, types, with_mask)
-    for env in ({}, {"CT_TUNE_BATCH_BYTES": "1"},
+    for env in ({}, {"CT_TUNE_BATCH_BYTES": "1"}, {"CT_TUNE_BATCH_GRAPH": "0"},
                 {"CT_TUNE_TC_ANY_BOX": "1", "CT_TUNE_TC_MIN_R": "24", "CT_TUNE_BATCH_BYTES": "20000000"}):
         if "CT_TUNE_TC_ANY_BOX" in env:
             ref_env = dict(env, CT_TUNE_BATCH_PERSISTENT="0")
