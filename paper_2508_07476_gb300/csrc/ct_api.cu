@@ -178,8 +178,10 @@ struct ct_plan_s {
   bool batch_graph = true;
   // persistent batches (run_persistent_waves): device items on the FP32
   // stencil chain run as one persistent launch per stage and tap set, in waves
-  // whose scratch fits batch_bytes of the arena
-  bool batch_persistent = true;
+  // whose scratch fits batch_bytes of the arena.  Off by default: on the
+  // 200-crop workload the graph of per-item launches is faster (the batched
+  // bodies index through an item table and lose the per-shape constants)
+  bool batch_persistent = false;
   int64_t batch_bytes = int64_t(48) << 30;
   void* arena = nullptr;
   size_t arena_cap = 0;

@@ -36,9 +36,11 @@ def _alloc(shape):
             torch.empty((nz, ny, nx), device="cuda"), torch.empty((nz, ny, nx), device="cuda"))
 
 
-def _run_batch(crops, vols, precision, graph: bool):
-    os.environ["CT_TUNE_BATCH_GRAPH"] = "1" if graph else "0"
-    os.environ["CT_TUNE_BATCH_PERSISTENT"] = "1" if graph else "0"
+_MODES = {"graph": ("1", "0"), "persistent": ("1", "1"), "per_item": ("0", "0")}  # (graph, persistent)
+
+
+def _run_batch(crops, vols, precision, mode: str):
+    os.environ["CT_TUNE_BATCH_GRAPH"], os.environ["CT_TUNE_BATCH_PERSISTENT"] = _MODES[mode]
     try:
         plan = _lib.ct_plan_create(_lib.make_params(1.0, 2.0, (0, 0, 0), (0, 0, 1), precision), (1, 1, 1))
     finally:
@@ -69,13 +71,17 @@ def test_batch_graph_equals_items_alone_and_oracle(prec):
     crops = synth.crop_batch(count=6, seed=9, size_range=(20, 56), sigmas=(1.0, 1.5), rhos=(2.0, 3.0, 4.0))
     host = [synth.generate(w.spec)[0] for w in crops]
     vols = [G.dev_u16(h) for h in host]
-    batched, s1, s2 = _run_batch(crops, vols, prec, graph=True)
-    seq, _, _ = _run_batch(crops, vols, prec, graph=False)
-    assert s1["voxels"] == s2["voxels"] == sum(h.size for h in host)
-    assert s2["launches"] == s1["launches"] > 0
-    for w, h, b, q in zip(crops, host, batched, seq):
+    batched, s1, s2 = _run_batch(crops, vols, prec, "graph")
+    pers, p1, p2 = _run_batch(crops, vols, prec, "persistent")
+    seq, _, _ = _run_batch(crops, vols, prec, "per_item")
+    for a, b in ((s1, s2), (p1, p2)):
+        assert a["voxels"] == b["voxels"] == sum(h.size for h in host)
+        assert b["launches"] == a["launches"] > 0
+    assert p1["launches"] < s1["launches"]
+    for w, h, b, p, q in zip(crops, host, batched, pers, seq):
         for k in ("v", "ha", "ia", "fa"):
             np.testing.assert_array_equal(b[k], q[k], err_msg=f"{w.name} {k}")
+            np.testing.assert_array_equal(p[k], q[k], err_msg=f"{w.name} {k} (persistent)")
         cen, ax = synth.frame_of(w.spec)
         alone = G.fused(h, w.sigma, w.rho, cen, ax, precision=prec)
         for k in ("v", "ha", "ia", "fa"):
@@ -129,6 +135,9 @@ def _items(crops, vols, outs, with_mask):
     return items
 
 
+PERSISTENT = {"CT_TUNE_BATCH_PERSISTENT": "1"}  # the persistent form is opt-in
+
+
 def _batch_outputs(monkeypatch, crops, vols, prec, env, types, with_mask=False):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
@@ -169,6 +178,7 @@ def test_persistent_batch_equals_per_item_launches(monkeypatch, types, with_mask
     ref, st_ref = _batch_outputs(monkeypatch, crops, vols, prec, {"CT_TUNE_BATCH_PERSISTENT": "0"}, types, with_mask)
     for env in ({}, {"CT_TUNE_BATCH_BYTES": "1"}, {"CT_TUNE_BATCH_GRAPH": "0"},
                 {"CT_TUNE_TC_ANY_BOX": "1", "CT_TUNE_TC_MIN_R": "24", "CT_TUNE_BATCH_BYTES": "20000000"}):
+        env = dict(env, **PERSISTENT)
         if "CT_TUNE_TC_ANY_BOX" in env:
             ref_env = dict(env, CT_TUNE_BATCH_PERSISTENT="0")
             ref, _ = _batch_outputs(monkeypatch, crops, vols, prec, ref_env, types, with_mask)
@@ -179,7 +189,7 @@ def test_persistent_batch_equals_per_item_launches(monkeypatch, types, with_mask
                 np.testing.assert_array_equal(x, y, err_msg=f"{w.name} {k} {env}")
     # the persistent form launches once per stage and tap set (and once per wave for
     # the eigen stage and the re-solve), fewer than a launch sequence per crop
-    _, st_p = _batch_outputs(monkeypatch, crops, vols, prec, {}, types, with_mask)
+    _, st_p = _batch_outputs(monkeypatch, crops, vols, prec, PERSISTENT, types, with_mask)
     n_sets = len({(w.sigma, w.rho) for w in crops})
     assert st_p["launches"] <= 4 * n_sets + 3 < st_ref["launches"], (st_p, st_ref, n_sets)
 
@@ -189,7 +199,7 @@ def test_persistent_batch_matches_oracle(monkeypatch):
     host = [synth.generate(w.spec)[0] for w in crops]
     vols = [G.dev_u16(h) for h in host]
     for prec in (_lib.CT_PREC_FP32, _lib.CT_PREC_MIXED):
-        got, _ = _batch_outputs(monkeypatch, crops, vols, prec, {}, (_lib.CT_OUT_F32,) * 3)
+        got, _ = _batch_outputs(monkeypatch, crops, vols, prec, PERSISTENT, (_lib.CT_OUT_F32,) * 3)
         for w, h, o in zip(crops, host, got):
             cen, ax = synth.frame_of(w.spec)
             ora = O.pipeline(h, w.sigma, w.rho, cen, ax)
