@@ -660,6 +660,10 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
 #pragma unroll
           for (int j = 0; j < NTP; ++j) v[j] = rb[(p_lo + j) * kTcLines + m];
         }
+        // x form: the stage is refilled by bulk / tensor copies (the async proxy),
+        // so this thread's reads of it are ordered before them by a proxy fence
+        // (without it a refill overtook the reads of a work unit's first chunk)
+        if (XAXIS) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();  // every lane has read the stage before it is refilled
         issue_next();
         const int t = c - G::P;  // tile of this chunk (< 0: ring fill)
