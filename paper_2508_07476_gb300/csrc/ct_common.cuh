@@ -81,43 +81,31 @@ struct MultiTable {
   unsigned long long* counter;
 };
 
-// CLAIM: blocks taken per counter increment (consecutive ones).  The next
-// claim's increment is issued before the current blocks run, so its round
-// trip overlaps them; the block offsets and grids of up to kVbCached items are
-// read from shared memory.
-constexpr int kVbCached = 256;
+// CLAIM: blocks taken per counter increment (consecutive ones), so that the
+// counter's round trip is paid once per CLAIM blocks of short-lived kernels.
 template <int CLAIM = 1, typename F>
 __device__ __forceinline__ void for_each_vblock(const MultiTable& T, F&& f) {
   __shared__ long long s_next;
-  __shared__ long long s_first[kVbCached + 1];
-  __shared__ uint3 s_grid[kVbCached];
-  const bool cached = T.n <= kVbCached;
-  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-  const int nthr = blockDim.x * blockDim.y * blockDim.z;
-  if (cached) {
-    for (int k = tid; k <= T.n; k += nthr) s_first[k] = T.first[k];
-    for (int k = tid; k < T.n; k += nthr) s_grid[k] = T.grids[k];
-  }
   const int64_t total = T.first[T.n];
-  if (tid == 0) s_next = (long long)atomicAdd(T.counter, (unsigned long long)CLAIM);
-  __syncthreads();
-  int64_t b0 = s_next;
-  __syncthreads();  // every thread has read it before it is overwritten
-  while (b0 < total) {
-    unsigned long long nxt = 0;
-    if (tid == 0) nxt = atomicAdd(T.counter, (unsigned long long)CLAIM);  // in flight during the blocks
+  for (;;) {
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0)
+      s_next = (long long)atomicAdd(T.counter, (unsigned long long)CLAIM) ;
+    __syncthreads();
+    const int64_t b0 = s_next;
+    __syncthreads();  // every thread has read it before it is overwritten
+    if (b0 >= total) break;
     int lo = 0, hi = T.n - 1;  // the item whose blocks hold b0: the last with first <= b0
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if ((cached ? s_first[mid] : T.first[mid]) <= b0) lo = mid;
+      if (T.first[mid] <= b0) lo = mid;
       else hi = mid - 1;
     }
     for (int c = 0; c < CLAIM; ++c) {
       const int64_t b = b0 + c;
       if (b >= total) break;
-      while (lo + 1 < T.n && (cached ? s_first[lo + 1] : T.first[lo + 1]) <= b) ++lo;  // into the next item
-      const uint3 g = cached ? s_grid[lo] : T.grids[lo];
-      int64_t r = b - (cached ? s_first[lo] : T.first[lo]);
+      while (lo + 1 < T.n && T.first[lo + 1] <= b) ++lo;  // the claim may run into the next item
+      const uint3 g = T.grids[lo];
+      int64_t r = b - T.first[lo];
       VBlock v;
       v.dim = g;
       v.idx.x = (unsigned)(r % g.x);
@@ -127,10 +115,6 @@ __device__ __forceinline__ void for_each_vblock(const MultiTable& T, F&& f) {
       f(lo, v);
       __syncthreads();  // the block's shared memory is free for the next one
     }
-    if (tid == 0) s_next = (long long)nxt;
-    __syncthreads();
-    b0 = s_next;
-    __syncthreads();
   }
 }
 

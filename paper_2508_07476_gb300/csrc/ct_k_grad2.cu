@@ -512,7 +512,7 @@ template <int RS, bool MIXED>
 __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS <= 8 ? 3 : 2))
     k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps,
                    const __grid_constant__ ProdScale ps) {
-  for_each_vblock<2>(T, [&](int i, const VBlock& v) {
+  for_each_vblock(T, [&](int i, const VBlock& v) {
     const GzItem& it = items[i];
     grad_z_body<RS, MIXED, false>(it.F, it.ab, it.J, it.ob, it.seg, taps, ps, v);
   });
