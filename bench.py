@@ -696,6 +696,7 @@ def run_crops(args):
     mode_env = {"persistent": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "1"},
                 "graph": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "0"},
                 "per_crop": {"CT_TUNE_BATCH_GRAPH": "0", "CT_TUNE_BATCH_PERSISTENT": "0"}}
+    clocks = None
     for mode in ("persistent", "graph", "per_crop"):
         os.environ.update(mode_env[mode])
         plan = _lib.ct_plan_create(_lib.make_params(2.0, 6.0, (0, 0, 0), (0, 0, 1), _lib.CT_PREC_MIXED,
@@ -707,12 +708,18 @@ def run_crops(args):
                 _lib.ct_run_chunks(plan, items, False)
             torch.cuda.synchronize()
             _lib.ct_plan_stats(plan, reset=True)
+            sampler = ClockSampler(0) if mode == "graph" else None
+            if sampler:
+                sampler.start()
+                time.sleep(0.3)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(args.steps):
                 _lib.ct_run_chunks(plan, items, False)
             e1.record()
             torch.cuda.synchronize()
+            if sampler:
+                clocks = sampler.stop()
             st = _lib.ct_plan_stats(plan, reset=True)
             ms = e0.elapsed_time(e1) / args.steps
             res[mode] = {"ms_per_step": ms, "voxels_per_s": total / (ms * 1e-3),
@@ -754,7 +761,8 @@ def run_crops(args):
           {"workload": f"crops{args.crops}", "voxels": total, "sizes": "each axis U[64,384]",
            "sigma": "per crop from {1,1.5,2,3}", "rho": "per crop from {2,4,6,8}", "outputs": "f16 v, HA, IA, FA",
            "precision": "mixed"},
-          {"modes": res, "gpu_launches": res["graph"]["launches_per_step"] * args.steps, "accuracy": accuracy})
+          {"modes": res, "gpu_launches": res["graph"]["launches_per_step"] * args.steps, "clocks": clocks,
+           "accuracy": accuracy})
 
 
 def run_stream(args):
@@ -797,10 +805,13 @@ def run_stream(args):
         for _ in range(args.warmup):
             _lib.ct_run_chunks(plan, [item], True)
         _lib.ct_plan_stats(plan, reset=True)
+        sampler = ClockSampler(0)
+        sampler.start()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             _lib.ct_run_chunks(plan, [item], True)
         el = (time.perf_counter() - t0) / args.steps
+        clocks = sampler.stop()
         st = _lib.ct_plan_stats(plan, reset=True)
     finally:
         _lib.ct_plan_destroy(plan)
@@ -836,7 +847,7 @@ def run_stream(args):
            "host_link_bound": {"voxels_per_s": vox / ((h2d + d2h) / (_HOST_LINK_GBS * 1e9)),
                                "note": f"the step's copies at {_HOST_LINK_GBS:.0f} GB/s (H2D and D2H together, "
                                        f"measured on this box)"},
-           "gpu_launches": st["launches"], "setup_s": t_alloc, "accuracy": accuracy})
+           "gpu_launches": st["launches"], "setup_s": t_alloc, "clocks": clocks, "accuracy": accuracy})
 
 
 _HOST_LINK_GBS = 312.0  # host <-> device copies in both directions at once, pinned (measured here)
@@ -939,11 +950,14 @@ def run_tera(args):
         run_chunks(chunks[:max(3, args.warmup)])
         sink.update({"sum": 0, "voxels": 0, "wait_s": 0.0, "read_s": 0.0})
         torch.cuda.synchronize()
+        sampler = ClockSampler(0)
+        sampler.start()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             run_chunks(chunks, timed=True)
         torch.cuda.synchronize()
         el = (time.perf_counter() - t0) / args.steps
+        clocks = sampler.stop()
         pipe_ms = sum(a.elapsed_time(b) for sl in slots for a, b in sl["spans"]) / args.steps
         # the generator alone over the same chunks (timed apart, as the stream's input cost)
         t0 = time.perf_counter()
@@ -1017,7 +1031,7 @@ def run_tera(args):
            "sink_voxels": sink["voxels"], "sink_checksum": sink["sum"],
            "host_s_per_step": {"waiting_for_gpu": sink["wait_s"] / args.steps, "sink_read": sink["read_s"] / args.steps},
            "e2e": {"value": vox / el, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * vox},
-           "accuracy": accuracy})
+           "clocks": clocks, "accuracy": accuracy})
 
 
 def run_zslab(args):
