@@ -1167,7 +1167,7 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
       }
       {
         RxyItem x{A, G, c.dims[0], c.dims[1], B, Bxy, 0};
-        const int xt = 128;  // one CTA width for every item of a batch (the arithmetic is the same at either)
+        const int xt = rho_xy_width(Bxy.n[0]);  // the single launch's CTA width (items of each width in one launch)
         g_rxy.push_back(rho_xy_item(c.sc.rkr, xt, x));
         rxy.push_back(x);
         MultiRec r = base;
@@ -1185,7 +1185,7 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
         r.kind = 3;
         r.rk = c.sc.rkr;
         r.block_t = t && t->stream_block ? t->stream_block : P->stream_block;
-        r.block = dim3(32, 8);  // one CTA shape for every item of a batch (a warp of consecutive x)
+        r.block = rho_stream_block(ob, 2);  // the single launch's CTA shape (items of each shape in one launch)
         r.t0 = c.sc.tr[2];
         g_rz.push_back(rho_z_item(c.sc.rkr, r.block_t, r.block, x));
         rz.push_back(x);
@@ -1236,8 +1236,14 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
     const auto same_chain = [](const MultiRec& a, const MultiRec& b) { return a.chain == b.chain; };
     add_groups(*H, W, gxy, g_gxy, p_gxy, same_chain, [](MultiRec&) {});
     add_groups(*H, W, gz, g_gz, p_gz, same_chain, [](MultiRec&) {});
-    add_groups(*H, W, rxy, g_rxy, p_rxy, same_chain, [](MultiRec&) {});
-    add_groups(*H, W, rz, g_rz, p_rz, same_chain, [](MultiRec&) {});
+    add_groups(*H, W, rxy, g_rxy, p_rxy, [](const MultiRec& a, const MultiRec& b) { return a.chain == b.chain && a.xt == b.xt; },
+               [](MultiRec&) {});
+    add_groups(*H, W, rz, g_rz, p_rz,
+               [](const MultiRec& a, const MultiRec& b) {
+                 return a.chain == b.chain && a.block.x == b.block.x && a.block.y == b.block.y &&
+                        a.block_t == b.block_t;
+               },
+               [](MultiRec&) {});
     W.n_chains = (int)chain_rep.size();
     // the eigen items in groups of equal kernel form, and all of them once more,
     // contiguous, for the wave's re-solve

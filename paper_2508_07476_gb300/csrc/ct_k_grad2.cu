@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(XT, 512 / XT)
     k_grad_xy_multi(const GxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
                     const __grid_constant__ Taps ty) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
-    const GxyItem& it = items[i];
+    const GxyItem it = items[i];  // a local copy: the body keeps its fields in registers
     grad_xy_body<RS, XT>(it.vol, it.vb, it.dimx, it.dimy, it.F, it.ab, it.seg, tx, ty, v);
   });
 }
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kGzThreads, CT_GZ_MINB > 0 ? CT_GZ_MINB : (RS 
     k_grad_z_multi(const GzItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps taps,
                    const __grid_constant__ ProdScale ps) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
-    const GzItem& it = items[i];
+    const GzItem it = items[i];  // a local copy: the body keeps its fields in registers
     grad_z_body<RS, MIXED, false>(it.F, it.ab, it.J, it.ob, it.seg, taps, ps, v);
   });
 }

@@ -270,7 +270,7 @@ template <int RR, int kT>
 __global__ void __launch_bounds__(kStreamThreads, CT_RZ_MINB)
     k_rho_z_multi(const RzItem* __restrict__ items, const MultiTable T, const Taps taps) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
-    const RzItem& it = items[i];
+    const RzItem it = items[i];  // a local copy: the body keeps its fields in registers
     rho_stream_body<RR, kT>(it.in, it.ib, it.dim_axis, it.out, it.ob, 2, it.seg, taps, v);
   });
 }

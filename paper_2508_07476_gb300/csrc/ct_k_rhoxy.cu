@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(XT, CT_XY_MINB * 256 / XT)
     k_rho_xy_multi(const RxyItem* __restrict__ items, const MultiTable T, const __grid_constant__ Taps tx,
                    const __grid_constant__ Taps ty) {
   for_each_vblock(T, [&](int i, const VBlock& v) {
-    const RxyItem& it = items[i];
+    const RxyItem it = items[i];  // a local copy: the body keeps its fields in registers
     rho_xy_body<RR, XT, SAMEXY>(it.in, it.ib, it.dimx, it.dimy, it.out, it.ob, it.seg, tx, ty, v);
   });
 }

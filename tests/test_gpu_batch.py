@@ -187,11 +187,12 @@ def test_persistent_batch_equals_per_item_launches(monkeypatch, types, with_mask
         for w, a, b in zip(crops, got, ref):
             for k, x, y in zip(("v", "ha", "ia", "fa"), a, b):
                 np.testing.assert_array_equal(x, y, err_msg=f"{w.name} {k} {env}")
-    # the persistent form launches once per stage and tap set (and once per wave for
-    # the eigen stage and the re-solve), fewer than a launch sequence per crop
+    # the persistent form launches once per stage, tap set and CTA shape (the x / y
+    # pass at two widths, the z pass at up to four shapes) and once per wave for the
+    # eigen stage and the re-solve: fewer than a launch sequence per crop
     _, st_p = _batch_outputs(monkeypatch, crops, vols, prec, PERSISTENT, types, with_mask)
     n_sets = len({(w.sigma, w.rho) for w in crops})
-    assert st_p["launches"] <= 4 * n_sets + 3 < st_ref["launches"], (st_p, st_ref, n_sets)
+    assert st_p["launches"] <= 8 * n_sets + 3 and st_p["launches"] < st_ref["launches"], (st_p, st_ref, n_sets)
 
 
 def test_persistent_batch_matches_oracle(monkeypatch):
