@@ -68,6 +68,9 @@ struct TcRoles {
   static constexpr int MMA_WARP = NP + 4;
 };
 constexpr int kTcNB = 4;                       // mbarriers per hand-off, used by tiles g mod 4 in turn
+#ifndef CT_TC_NT64_MAX_R
+#define CT_TC_NT64_MAX_R 36  // tuning: largest radius instance with 64-output tiles
+#endif
 #ifndef CT_TC_BIG_RING
 #define CT_TC_BIG_RING 1  // tuning: 0 restarts a W + NT ring at every work unit
 #endif
@@ -77,7 +80,9 @@ constexpr uint32_t kTcSuspendNs = 500;         // a waiting thread sleeps up to 
 template <int RR>
 struct TcGeom {
   static constexpr int RA = (RR + 3) / 4 * 4;    // window margin: W is a multiple of 8
-  static constexpr int NT = RR <= 32 ? 64 : 32;  // outputs per tile (MMA N)
+  // outputs per tile (MMA N): 64, which at R = 36 leaves room for one
+  // accumulator only (CT_TC_NT64_MAX_R = 32 keeps two there with 32-output tiles)
+  static constexpr int NT = RR <= CT_TC_NT64_MAX_R ? 64 : 32;
   static constexpr int W = NT + 2 * RA;          // window positions of a tile
   static constexpr int KCB = W / 4;              // core-matrix columns of B
   static constexpr int KS = W / 8;               // k-steps per tile
