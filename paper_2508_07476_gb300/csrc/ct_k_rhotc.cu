@@ -71,6 +71,15 @@ constexpr int kTcNB = 4;                       // mbarriers per hand-off, used b
 #ifndef CT_TC_NT64_MAX_R
 #define CT_TC_NT64_MAX_R 36  // tuning: largest radius instance with 64-output tiles
 #endif
+#ifndef CT_TC_XSTAGES
+#define CT_TC_XSTAGES 2  // tuning: x form, chunk stages in flight (2 measured faster than 3)
+#endif
+#ifndef CT_TC_YZSTAGES
+#define CT_TC_YZSTAGES 4  // tuning: y / z forms (plain and FP16 products), chunk stages in flight
+#endif
+#ifndef CT_TC_XEPI
+#define CT_TC_XEPI 1  // tuning: x form, output buffers per epilogue warp (2: a tile's store overlaps the next)
+#endif
 #ifndef CT_TC_BIG_RING
 #define CT_TC_BIG_RING 1  // tuning: 0 restarts a W + NT ring at every work unit
 #endif
@@ -115,11 +124,13 @@ struct TcGeom {
     return xaxis ? 4 * WS / 4 : (prod == 1 ? 2 * NT * kTcLines : NT * kTcLines);
   }
   // chunks in flight (FP32 gradient pairs: two, the most that fit beside B)
-  static constexpr int stages(bool xaxis, int prod = 0) { return xaxis ? 3 : (prod == 1 ? 2 : 4); }
+  static constexpr int stages(bool xaxis, int prod = 0) {
+    return xaxis ? CT_TC_XSTAGES : (prod == 1 ? 2 : CT_TC_YZSTAGES);
+  }
   static_assert((2 * B_BYTES) % 1024 == 0 && NT * 32 * 4 <= WS && TE == XS, "x-form slices");
   static constexpr int need(bool xaxis, int prod = 0) {
     return 1024 + 2 * B_BYTES + stages(xaxis, prod) * raw_floats(xaxis, prod) * 4 +
-           (xaxis ? 4 * WS + 2 * ROW_BYTES : 0);  // + slack to align the base to 1024 bytes
+           (xaxis ? 4 * CT_TC_XEPI * WS + 2 * ROW_BYTES : 0);  // + slack to align the base to 1024 bytes
   }
   // dynamic shared memory requested: at least half an SM's (233472 bytes,
   // 1 KB reserved per CTA), so that one CTA, holding all the tensor memory,
@@ -151,8 +162,6 @@ __device__ __forceinline__ void bulk_s2g(float* gdst, uint32_t smem_src, uint32_
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// This thread's bulk stores have read their shared-memory source.
-__device__ __forceinline__ void bulk_s2g_read_done() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
 // Tensor (TMA) copies of a 3-D box (x, row, component), completing on an mbarrier / bulk group.
 __device__ __forceinline__ void tma_load3(uint32_t smem_dst, const CUtensorMap* map, int x, int y, int z,
@@ -363,8 +372,8 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
   float* sRaw = reinterpret_cast<float*>(smem + 2 * G::B_BYTES);
   unsigned char* xs = smem + 2 * G::B_BYTES + S * RAWF * 4;  // x form only
   float* sTe = reinterpret_cast<float*>(xs);
-  const float** sSrc = reinterpret_cast<const float**>(xs + 4 * G::WS);
-  float** sDst = reinterpret_cast<float**>(xs + 4 * G::WS + G::ROW_BYTES);
+  const float** sSrc = reinterpret_cast<const float**>(xs + 4 * CT_TC_XEPI * G::WS);
+  float** sDst = reinterpret_cast<float**>(xs + 4 * CT_TC_XEPI * G::WS + G::ROW_BYTES);
   __shared__ __align__(8) uint64_t bar_chunk[4];        // x form: chunk stage s has landed
   __shared__ __align__(8) uint64_t bar_staged[kTcNB];  // the producers have staged tile g
   __shared__ __align__(8) uint64_t bar_mma[kTcNB];     // tile g's product is in D[g % ND]
@@ -803,10 +812,13 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
         const int nlo = max(0, a_lo - pt), nhi = min(NT, a_end - pt);  // stored outputs [nlo, nhi)
         const int64_t off = pt - a_lo;
         if (XAXIS) {
-          bulk_s2g_read_done();  // this thread's previous bulk stores have read their source
-          __syncwarp();          // and the warp's transposed stores have read theirs
+          // this thread's bulk stores of the tile that used this buffer last have read
+          // their source (with two buffers, the previous tile's may still be reading)
+          asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(CT_TC_XEPI - 1) : "memory");
+          __syncwarp();  // and the warp's transposed stores have read theirs
+          const int eslice = wq * CT_TC_XEPI + (CT_TC_XEPI == 2 ? (int)(g & 1) : 0);
           if ((vec & 8) && nlo == 0 && nhi == NT) {  // a whole tile: two swizzled box stores per warp
-            unsigned char* eb = reinterpret_cast<unsigned char*>(sTe) + wq * G::WS;
+            unsigned char* eb = reinterpret_cast<unsigned char*>(sTe) + eslice * G::WS;
 #pragma unroll
             for (int n = 0; n < NT; n += 4)
               *reinterpret_cast<float4*>(eb + (n / 32) * 4096 + swz(lane, n & 31)) =
@@ -823,7 +835,7 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
             }
             continue;
           }
-          float* er = sTe + wq * (G::WS / 4);  // this warp's slice: its 32 rows at stride TE
+          float* er = sTe + eslice * (G::WS / 4);  // this warp's slice: its 32 rows at stride TE
 #pragma unroll
           for (int n = 0; n < NT; n += 4)
             *reinterpret_cast<float4*>(er + lane * G::TE + n) = make_float4(r[n], r[n + 1], r[n + 2], r[n + 3]);
