@@ -870,7 +870,10 @@ def run_tera(args):
                              noise=("poisson_like", 0.05), ia_std_deg=5.0, ia_corr=40.0, seed=5)
     cen, ax = synth.frame_of(spec)
     sigma, rho, C = 3.0, 9.0, 384
-    halo = _lib.ct_radius(sigma) + _lib.ct_radius(rho)
+    rs, rr = _lib.ct_radius(sigma), _lib.ct_radius(rho)
+    halo = rs + rr
+    fma_meas = _fma_rate_measured(0)
+    fma_rate = fma_meas["fma_per_s"]
     chunks = [(x, y, z) for z in range(0, nz, C) for y in range(0, ny, C) for x in range(0, nx, C)]
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     plans = [_lib.ct_plan_create(_lib.make_params(sigma, rho, cen, ax, _lib.CT_PREC_MIXED, _lib.CT_OUT_F32,
@@ -911,9 +914,11 @@ def run_tera(args):
         ihi = tuple(min(d, a + b + halo) for a, b, d in zip(lo, n, (nx, ny, nzf)))
         return lo, n, ilo, tuple(b - a for a, b in zip(ilo, ihi))
 
-    def run_chunks(todo, timed=False, keep=None):
+    def run_chunks(todo, timed=False, keep=None, serial=False):
+        # serial: every chunk's generator, pipeline and copies on one stream, so
+        # that no kernel runs beside a timed pipeline span
         for i, (x0, y0, z0) in enumerate(todo):
-            sl, st, plan = slots[i & 1], streams[i & 1], plans[i & 1]
+            sl, st, plan = slots[i & 1], streams[0 if serial else i & 1], plans[i & 1]
             drain(sl)
             lo, n, ilo, ino = boxes_of(x0, y0, z0)
             nv = n[0] * n[1] * n[2]
@@ -957,6 +962,16 @@ def run_tera(args):
             run_chunks(chunks, timed=True)
         torch.cuda.synchronize()
         el = (time.perf_counter() - t0) / args.steps
+        overlap_ms = sum(a.elapsed_time(b) for sl in slots for a, b in sl["spans"]) / args.steps
+        # the pipeline alone: the same chunks with the generator serialised before
+        # each chunk's ct_run_box, so that each span times the pipeline only
+        for sl in slots:
+            sl["spans"] = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            run_chunks(chunks, timed=True, serial=True)
+        torch.cuda.synchronize()
+        serial_s = (time.perf_counter() - t0) / args.steps
         clocks = sampler.stop()
         pipe_ms = sum(a.elapsed_time(b) for sl in slots for a, b in sl["spans"]) / args.steps
         # the generator alone over the same chunks (timed apart, as the stream's input cost)
@@ -1023,9 +1038,16 @@ def run_tera(args):
            "mask": True, "outputs": "u8 HA, u8 IA (180/256 deg bins), f16 FA", "precision": "mixed",
            "resident_chunks": 2, "generator": "device, FP32 form, padded chunk + output-box mask per chunk",
            "sink": "two pinned host slots, every byte read by a 64-bit host checksum", "warmup": "first chunks"},
-          {"timing": "value: CUDA events around each chunk's ct_run_box on its stream, summed (an upper bound on "
-                     "the pipeline's time: a span can include the other stream's generator running beside it)",
-           "stream_with_generator": {"s_per_step": el, "voxels_per_s": vox / el},
+          {"timing": "value: CUDA events around each chunk's ct_run_box, summed, with each chunk's generator run "
+                     "before it on the same stream (no other kernel beside a span); clocks sampled over both passes",
+           "roofline": {"bound": "alu", "voxels_per_s_roofline": fma_rate / _fma_per_voxel(rs, rr),
+                        "fma_per_voxel": _fma_per_voxel(rs, rr), "fma_peak": fma_meas,
+                        "frac": vox / (pipe_ms * 1e-3) / (fma_rate / _fma_per_voxel(rs, rr)),
+                        "note": "output voxels; the halo of each chunk (R_sigma + R_rho per side) is extra work"},
+           "stream_with_generator": {"s_per_step": el, "voxels_per_s": vox / el,
+                                     "pipeline_spans_ms": overlap_ms,
+                                     "note": "generator of the next chunk on the other stream, beside the pipeline"},
+           "serial_pass_s_per_step": serial_s,
            "generator_only": {"s_per_step": gen_s, "voxels_per_s": vox / gen_s,
                               "note": "padded chunks + output-box masks generated alone, same streams"},
            "sink_voxels": sink["voxels"], "sink_checksum": sink["sum"],

@@ -10,11 +10,13 @@
 //   D[m][n] = sum_k A[m][k] B[n][k],   A[m][k] = in(line m, first - RA + k),
 //   B[n][k] = w[k - n - (RA - R)] (zero off the band of 2R + 1 taps),
 // one M x N x W product.  Each operand is split into a TF32 head and the FP32
-// remainder (a = a_hi + a_lo, a_hi = a rounded to TF32), and
+// remainder (a = a_hi + a_lo): the taps' heads are rounded to TF32, the data's
+// heads truncated (the low 13 mantissa bits cleared: one logic operation instead
+// of a conversion, on the producers' path), and
 //   D = A_hi B_hi + A_hi B_lo + A_lo B_hi
-// keeps every product within about 2^-20 of its value (the MMA reads the
-// remainders to 11 significant bits; the dropped A_lo B_lo is below 2^-22),
-// comparable with the FP32 stencil's own rounding.
+// keeps every product within about 2^-19 of its value (|A_lo| < 2^-10 |A|,
+// read by the MMA to 11 significant bits; the dropped A_lo B_lo is below
+// 2^-21), far inside the FP32 stage tolerances.
 //
 // A_hi and A_lo live in tensor memory (lane m = line m, one column per
 // position), each a ring of WR = W + NT columns indexed by position mod WR.
@@ -196,6 +198,10 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The TF32 head of a data value: x with its low 13 mantissa bits cleared (an
+// exact TF32 value; x - head is exact in FP32).
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -299,6 +305,9 @@ struct TcUnit {
   // planes of gradient components a and b of the unit's component g_a g_b
   int64_t ga = 0, gb = 0;
   int comp = 0;
+  // x form with tensor maps: the warp's first row as (row, component) of the
+  // output view (computed once per unit: 64-bit divisions are long)
+  int orow = 0, ocomp = 0;
 };
 
 // The products form's inputs: gradient planes (FP32, or FP16 holding g * 2^-8)
@@ -457,6 +466,11 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       const int comp = (int)(t2 / ob.n[2]);
       U.src = in + comp * box_vox(ib) + box_index(ib, ib.lo[0], yy, zz);
       U.dst = out + comp * box_vox(ob) + box_index(ob, a_lo, yy, zz);
+      if (vec & 12) {
+        const int64_t r0 = grp * kTcLines + 32 * (m >> 5);  // the warp's first row
+        U.orow = (int)(r0 % rows_pc);
+        U.ocomp = (int)(r0 / rows_pc);
+      }
     } else {
       // plain: groups by (component, other, x group), x group fastest; products:
       // component fastest (the six components of a line group in turn)
@@ -520,13 +534,11 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
           const int a = max(qs, qlo), b = min(qs + NT - 1, qhi);  // the chunk's part inside the box
           if ((vec & 4) && inside) {  // two swizzled 32 x 32 boxes per warp, issued by one lane
             if (lane == 0) {
-              const int64_t r0 = (iu % n_groups) * kTcLines + 32 * wq;  // the warp's first output row
-              const int row = (int)(row_off + r0 % rows_pc), comp = (int)(r0 / rows_pc);
               mbar_arrive_tx(cb, NT * 32 * 4);
 #pragma unroll
               for (int h = 0; h < NT / 32; ++h)
                 tma_load3(smem_u32(reinterpret_cast<unsigned char*>(rb) + wq * G::WS + h * 4096), &tin,
-                          qs + 32 * h, row, comp, cb);
+                          qs + 32 * h, (int)row_off + IU.orow, IU.ocomp, cb);
             } else {
               mbar_arrive(cb);
             }
@@ -719,7 +731,7 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
           float hi[8], lo[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            hi[j] = tf32_round(v[8 * cc + j]);
+            hi[j] = tf32_head(v[8 * cc + j]);
             lo[j] = v[8 * cc + j] - hi[j];
           }
           tmem_st8(tlane + slot, hi);
@@ -826,11 +838,9 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
-              const int64_t r0 = (unit % n_groups) * kTcLines + 32 * wq;
 #pragma unroll
               for (int h = 0; h < NT / 32; ++h)
-                tma_store3(&tout, pt - ob.lo[0] + 32 * h, (int)(r0 % rows_pc), (int)(r0 / rows_pc),
-                           smem_u32(eb + h * 4096));
+                tma_store3(&tout, pt - ob.lo[0] + 32 * h, U.orow, U.ocomp, smem_u32(eb + h * 4096));
               asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
             continue;
