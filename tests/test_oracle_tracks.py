@@ -120,3 +120,47 @@ def test_parabola_fourth_order():
         p = np.array(fwd)
         errs.append(np.abs(p[:, 1] - (y0 + a * (p[:, 0] - x0) ** 2 / 2)).max())
     assert errs[0] < 1e-6 and errs[0] / errs[1] > 12.0, errs
+
+
+def test_step_margins_at_each_stopping_rule():
+    """The margin of the step that stops a track is its distance from the
+    threshold, worked out by hand: a volume face, a mask edge at a half-integer,
+    an FA threshold, a turn limit; steps far from every threshold keep large
+    margins; and asking for margins leaves the points unchanged."""
+    # straight along +x from x = 2.1 in steps of 0.5 through a volume 12 long
+    # (faces at 0 and 11; y = z = 3.0 lie 3 from theirs): 17 steps reach 10.6,
+    # 0.4 from the face; the next step's stage points 10.85 and 11.1 lie 0.15
+    # inside and 0.1 beyond it (max_turn 90 degrees: turn margin cos 0 - 0 = 1)
+    f = _const_field((8, 8, 12), (1.0, 0.0, 0.0))
+    m = []
+    (fwd, _), = tracks.tracks(f, [(2.1, 3.0, 3.0)], 0.5, 100, margins=m)
+    mf = m[0][0]
+    assert len(fwd) == 18 and fwd[-1][0] == pytest.approx(10.6)
+    assert len(mf) == 18 and mf[-1] == pytest.approx(0.1) and mf[-2] == pytest.approx(0.4)
+    assert mf[0] == pytest.approx(1.0)  # far from every face: the turn margin
+    assert tracks.tracks(f, [(2.1, 3.0, 3.0)], 0.5, 100) == tracks.tracks(f, [(2.1, 3.0, 3.0)], 0.5, 100, margins=[])
+    # a mask ending at voxel 7 (x < 7.5 inside): steps of 0.3 from x = 5.05 land on
+    # 5.35, ..., 7.45 (0.05 inside the edge), then 7.75 stops, 0.25 beyond it
+    mask = np.ones((8, 8, 12), np.uint8)
+    mask[:, :, 8:] = 0
+    m = []
+    (fwd, _), = tracks.tracks(f, [(5.05, 3.0, 3.0)], 0.3, 100, mask=mask, margins=m)
+    mf = m[0][0]
+    assert fwd[-1][0] == pytest.approx(7.45) and mf[-2] == pytest.approx(0.05) and mf[-1] == pytest.approx(0.25)
+    # FA falling linearly along x, fa = 1 - x / 10, threshold 0.5 (x <= 5): steps of
+    # 0.4 from 1.1 end at 4.7 (FA 0.53); the stopping step lands on 5.1 (FA 0.49)
+    fa = np.broadcast_to(1.0 - np.arange(12) / 10.0, (8, 8, 12)).copy()
+    m = []
+    (fwd, _), = tracks.tracks(f, [(1.1, 3.0, 3.0)], 0.4, 100, fa=fa, fa_min=0.5, margins=m)
+    mf = m[0][0]
+    assert fwd[-1][0] == pytest.approx(4.7) and mf[-1] == pytest.approx(0.01) and mf[-2] == pytest.approx(0.03)
+    # a right-angle turn: the field turns from +x to +y at x = 6; with a 30 degree
+    # limit the step that crosses the bend turns by more, and its margin is
+    # cos(30 deg) - cos(turn) for the turn that step computes
+    g = np.zeros((3, 8, 12, 12))
+    g[0, :, :, :6] = 1.0
+    g[1, :, :, 6:] = 1.0
+    m = []
+    (fwd, _), = tracks.tracks(g, [(2.0, 3.0, 3.0)], 0.5, 100, max_turn_deg=30.0, margins=m)
+    mf = m[0][0]
+    assert mf[-1] > 0.0 and mf[-1] < math.cos(math.radians(30.0))
