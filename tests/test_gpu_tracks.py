@@ -4,7 +4,8 @@ Fields are written by numpy (analytic), so no oracle input comes from the
 CUDA path; the pipeline-driven case feeds each side its own pipeline's
 output.  The kernel integrates in FP32: points agree to a small fraction of a
 voxel, and a track's length may differ by one step only where a point lands
-within rounding of a stopping boundary.
+within rounding of a stopping boundary (checked against the oracle's step
+margins).
 """
 import math
 
@@ -43,7 +44,11 @@ def _gpu_tracks(vec, seeds, h, max_steps, fa=None, mask=None, fa_min=0.0, max_tu
     return pts.cpu().numpy(), cnt.cpu().numpy()
 
 
-def _compare(gpu, ora, atol):
+def _compare(gpu, ora, atol, margins=None):
+    """Share of tracks whose lengths agree; every common point within atol.  A
+    track may be one step longer on either side only where the oracle's step
+    at that point lies within rounding of a stopping threshold: its margin
+    (oracle.tracks, in voxels, cosine or FA units) must be below 10 atol."""
     pts, cnt = gpu
     same, worst, n = 0, 0.0, 0
     for i, (fwd, bwd) in enumerate(ora):
@@ -55,6 +60,9 @@ def _compare(gpu, ora, atol):
             if m:
                 worst = max(worst, float(np.abs(pts[i, k, :m] - np.array(tr[:m], dtype=np.float64)).max()))
             same += c == len(tr)
+            if margins is not None and c != len(tr):
+                mg = margins[i][k][m - 1]  # the step attempted from the last common point
+                assert mg < 10 * atol, (i, k, c, len(tr), mg)
     assert worst < atol, worst
     return same / n
 
@@ -75,9 +83,10 @@ def test_tracks_match_oracle_on_a_helix_field():
     f = _helix_field(n, 23.5, 4.0)
     rng = np.random.default_rng(3)
     seeds = np.column_stack([rng.uniform(8, 40, 60), rng.uniform(8, 40, 60), rng.uniform(4, 44, 60)])
-    ora = tracks.tracks(f, seeds, 0.5, 80)
+    mg = []
+    ora = tracks.tracks(f, seeds, 0.5, 80, margins=mg)
     gpu = _gpu_tracks(f, seeds, 0.5, 80)
-    assert _compare(gpu, ora, 2e-3) >= 0.98
+    assert _compare(gpu, ora, 2e-3, mg) >= 0.98
 
 
 def test_stopping_rules_match_oracle():
@@ -93,9 +102,10 @@ def test_stopping_rules_match_oracle():
     rng = np.random.default_rng(4)
     seeds = np.column_stack([rng.uniform(1, 38, 50), rng.uniform(5, 35, 50), rng.uniform(1, 4, 50)])
     for turn, fa_min in ((20.0, 0.5), (90.0, 0.5), (90.0, 0.0)):
-        ora = tracks.tracks(f, seeds, 0.4, 120, fa=fa, mask=mask, fa_min=fa_min, max_turn_deg=turn)
+        mg = []
+        ora = tracks.tracks(f, seeds, 0.4, 120, fa=fa, mask=mask, fa_min=fa_min, max_turn_deg=turn, margins=mg)
         gpu = _gpu_tracks(f, seeds, 0.4, 120, fa=fa, mask=mask, fa_min=fa_min, max_turn_deg=turn)
-        assert _compare(gpu, ora, 1e-3) >= 0.98
+        assert _compare(gpu, ora, 1e-3, mg) >= 0.98
 
 
 def test_orientation_sign_is_ignored_exactly():
