@@ -390,7 +390,9 @@ __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, const B
                                             const BLK blk) {
   constexpr int P = 2 * RS + 1;
   constexpr int AH = kGzAhead < P ? kGzAhead : P - 1;  // steps in flight (the ring holds P)
-  extern __shared__ __align__(16) float gz_ring[];  // [P][3][kGzThreads]
+  // [P] steps of (F0, F1) pairs [kGzThreads][2], then F2 [kGzThreads]: the x and y
+  // components run as FP32 pairs (one packed add and fma per tap for both)
+  extern __shared__ __align__(16) float gz_ring[];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int x = ob.lo[0] + blk.x() * blockDim.x + threadIdx.x;
   const int yr = blk.y() * blockDim.y + threadIdx.y;
@@ -409,14 +411,15 @@ __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, const B
   const int plane = ab.n[0] * ab.n[1];
   const int q0 = p0 - RS - ab.lo[2];
   auto src = [&](int s) -> const float* { return base + (int64_t)min(max(q0 + s, 0), ab.n[2] - 1) * plane; };
-  const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(gz_ring + tid);
-  constexpr uint32_t kField = kGzThreads * sizeof(float), kStep = 3 * kField;
+  const uint32_t ring01 = (uint32_t)__cvta_generic_to_shared(gz_ring + 2 * tid);
+  const uint32_t ring2 = (uint32_t)__cvta_generic_to_shared(gz_ring + 2 * kGzThreads + tid);
+  constexpr uint32_t kStep = 3 * kGzThreads * sizeof(float);
   auto issue = [&](int s, int slot) {
     if (s < nsteps) {
       const float* p = src(s);
-      cp_async4(ring0 + slot * kStep, p);
-      cp_async4(ring0 + slot * kStep + kField, p + nab);
-      cp_async4(ring0 + slot * kStep + 2 * kField, p + 2 * nab);
+      cp_async4(ring01 + slot * kStep, p);
+      cp_async4(ring01 + slot * kStep + 4, p + nab);
+      cp_async4(ring2 + slot * kStep, p + 2 * nab);
     }
     cp_async_commit();
   };
@@ -429,9 +432,13 @@ __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, const B
   const int64_t obase_i = box_index(ob, xi, y, p0);
   float* obase = J + obase_i;
   const int ostride = ob.n[0] * ob.n[1];
-  float w0[P], w1[P], w2[P];
+  float2 w01[P];
+  float w2[P];
 #pragma unroll
-  for (int i = 0; i < P; ++i) { w0[i] = 0.f; w1[i] = 0.f; w2[i] = 0.f; }
+  for (int i = 0; i < P; ++i) {
+    w01[i] = make_float2(0.f, 0.f);
+    w2[i] = 0.f;
+  }
 
   for (int base_s = 0; base_s < nsteps; base_s += P) {
 #pragma unroll
@@ -439,20 +446,21 @@ __device__ __forceinline__ void grad_z_body(const float* __restrict__ F, const B
       const int s = base_s + u;
       if (s >= nsteps) continue;
       cp_async_wait<AH - 1>();  // step s has landed (this thread's own copies)
-      w0[u] = gz_ring[(3 * u) * kGzThreads + tid];
-      w1[u] = gz_ring[(3 * u + 1) * kGzThreads + tid];
+      w01[u] = *reinterpret_cast<const float2*>(gz_ring + 3 * u * kGzThreads + 2 * tid);
       w2[u] = gz_ring[(3 * u + 2) * kGzThreads + tid];
       issue(s + AH, (u + AH) % P);  // into the slot of step s + AH - P, consumed already
       if (s >= 2 * RS) {
         const int c = (u + P - RS) % P;  // window slot of the output plane
-        float gx = taps.w[RS] * w0[c], gy = taps.w[RS] * w1[c], gz = 0.f;
+        // (gx, gy) as a pair: each lane rounds as the scalar fmaf / add would
+        float2 gxy = __fmul2_rn(make_float2(taps.w[RS], taps.w[RS]), w01[c]);
+        float gz = 0.f;
 #pragma unroll
         for (int k = 1; k <= RS; ++k) {
           const int sp = (u + P - RS + k) % P, sm = (u + P - RS - k) % P;
-          gx = fmaf(taps.w[RS + k], w0[sp] + w0[sm], gx);
-          gy = fmaf(taps.w[RS + k], w1[sp] + w1[sm], gy);
+          gxy = __ffma2_rn(make_float2(taps.w[RS + k], taps.w[RS + k]), __fadd2_rn(w01[sp], w01[sm]), gxy);
           gz = fmaf(taps.c[RS + k], w2[sp] - w2[sm], gz);
         }
+        float gx = gxy.x, gy = gxy.y;
         if (GOUT) {  // the gradient itself, held in FP16 (scaled) in the mixed form
           if (ok) {
             const int64_t o = obase_i + (int64_t)(s - 2 * RS) * ostride;
