@@ -59,14 +59,17 @@ namespace {
 
 constexpr int kTcLines = 128;  // = M: TMEM lane m holds line m
 // Warp roles: producer warps 0 .. NP-1, epilogue warps NP .. NP+3, the MMA warp
-// NP+4.  The x form has one producer thread per line (NP = 4); the y / z forms
-// split each chunk's positions between two producer warps per lane quadrant
-// (NP = 8: warp w stages positions [(w / 4) NT / 2, + NT / 2) of the lines
-// 32 (w % 4) ..), which halves each producer thread's work per tile.
+// NP+4.  The x form has one producer thread per line (NP = 4), and four copy
+// warps NP+5 .. NP+8: copy warp w fills the chunk slices of producer warp
+// w % 4 (its 32 rows), so that no producer waits for a copy to be issued and
+// each producer / copy pair runs on its own.  The y / z forms split each
+// chunk's positions between two producer warps per lane quadrant (NP = 8: warp
+// w stages positions [(w / 4) NT / 2, + NT / 2) of the lines 32 (w % 4) ..),
+// which halves each producer thread's work per tile, and copy their own parts.
 template <bool XAXIS>
 struct TcRoles {
   static constexpr int NP = XAXIS ? 4 : 8;
-  static constexpr int THREADS = 32 * (NP + 5);
+  static constexpr int THREADS = 32 * (NP + 5 + (XAXIS ? 4 : 0));
   static constexpr int MMA_WARP = NP + 4;
 };
 constexpr int kTcNB = 4;                       // mbarriers per hand-off, used by tiles g mod 4 in turn
@@ -383,16 +386,17 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
   float* sTe = reinterpret_cast<float*>(xs);
   const float** sSrc = reinterpret_cast<const float**>(xs + 4 * CT_TC_XEPI * G::WS);
   float** sDst = reinterpret_cast<float**>(xs + 4 * CT_TC_XEPI * G::WS + G::ROW_BYTES);
-  __shared__ __align__(8) uint64_t bar_chunk[4];        // x form: chunk stage s has landed
+  __shared__ __align__(8) uint64_t bar_xfull[4][4];    // x form: slice q of chunk stage s has landed
+  __shared__ __align__(8) uint64_t bar_xempty[4][4];   // x form: producer warp q has read slice q of stage s
   __shared__ __align__(8) uint64_t bar_staged[kTcNB];  // the producers have staged tile g
   __shared__ __align__(8) uint64_t bar_mma[kTcNB];     // tile g's product is in D[g % ND]
   __shared__ __align__(8) uint64_t bar_dfree[kTcNB];   // the epilogue has read tile g's D
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
-  __shared__ int arrived_max;  // x form: most chunks any producer thread has arrived for
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   using RL = TcRoles<XAXIS>;
-  const int role = w < RL::NP ? 0 : (w < RL::NP + 4 ? 1 : 2);  // producer, epilogue, MMA
+  const int role = w < RL::NP ? 0 : (w < RL::NP + 4 ? 1 : (w == RL::MMA_WARP ? 2 : 3));  // producer, epilogue,
+                                                                                          // MMA, copy (x form)
   const int m = tid & (kTcLines - 1);            // line / TMEM lane (roles 0 and 1)
   const int wq = w & 3;                          // lane quadrant of this warp
 
@@ -408,14 +412,16 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
   }
   if (tid == 0) {
     for (int a = 0; a < S; ++a)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_chunk[a])), "n"(kTcLines));
+      for (int q = 0; q < 4; ++q) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(smem_u32(&bar_xfull[a][q])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_xempty[a][q])));
+      }
     for (int a = 0; a < kTcNB; ++a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(32 * RL::NP));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma[a])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_dfree[a])), "n"(kTcLines));
     }
     abort_flag = 0;
-    arrived_max = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) {
@@ -502,129 +508,131 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
   // a producer warp's positions of each chunk: [p_lo, p_lo + NTP)
   constexpr int NTP = XAXIS ? NT : NT / 2;
   const int p_lo = XAXIS ? 0 : (w >> 2) * NTP;
-  if (role == 0) {
-    // the copy stream: chunk ic of unit iu (window positions NT ic for ic < P,
-    // then tile ic - P's NT), one cp.async group per chunk, stage k mod S
-    int64_t iu = blockIdx.x;
-    int ic = 0, iC = 0, iq0 = 0;
-    TcUnit IU;
-    auto enter = [&](int64_t u) {
-      iu = u;
-      ic = 0;
-      if (u >= n_units) return;
-      IU = decode(u);
-      iC = G::P + IU.nt;
-      iq0 = IU.p0 - G::RA - alo;
+  // The copy stream (y / z producers, x copy warps): chunk ic of unit iu (window
+  // positions NT ic for ic < P, then tile ic - P's NT), one cp.async group per
+  // chunk, stage k mod S
+  int64_t iu = blockIdx.x;
+  int ic = 0, iC = 0, iq0 = 0;
+  TcUnit IU;
+  auto enter = [&](int64_t u) {
+    iu = u;
+    ic = 0;
+    if (u >= n_units) return;
+    IU = decode(u);
+    iC = G::P + IU.nt;
+    iq0 = IU.p0 - G::RA - alo;
+    if (XAXIS) {
+      __syncwarp();  // the warp's copies of the previous unit have been issued
+      sSrc[m] = IU.src;
+      __syncwarp();
+    }
+  };
+  uint32_t k_issue = 0;
+  auto issue_next = [&]() {
+    if (iu < n_units) {
+      float* rb = sRaw + (k_issue % S) * RAWF;
+      const int qs = iq0 + (ic < G::P ? NT * ic : 2 * G::RA + NT * (ic - G::P));
+      const bool inside = qs >= qlo && qs + NT - 1 <= qhi;  // no clamping in this chunk
       if (XAXIS) {
-        __syncwarp();  // the warp's copies of the previous unit have been issued
-        sSrc[m] = IU.src;
-        __syncwarp();
-      }
-    };
-    uint32_t k_issue = 0;
-    int arrived = 0;  // x form: chunks this thread has arrived for on bar_chunk
-    auto issue_next = [&]() {
-      if (iu < n_units) {
-        ++arrived;
-        float* rb = sRaw + (k_issue % S) * RAWF;
-        const int qs = iq0 + (ic < G::P ? NT * ic : 2 * G::RA + NT * (ic - G::P));
-        const bool inside = qs >= qlo && qs + NT - 1 <= qhi;  // no clamping in this chunk
-        if (XAXIS) {
-          const uint32_t cb = smem_u32(&bar_chunk[k_issue % S]);
-          const int a = max(qs, qlo), b = min(qs + NT - 1, qhi);  // the chunk's part inside the box
-          if ((vec & 4) && inside) {  // two swizzled 32 x 32 boxes per warp, issued by one lane
-            if (lane == 0) {
-              mbar_arrive_tx(cb, NT * 32 * 4);
+        const uint32_t cb = smem_u32(&bar_xfull[k_issue % S][wq]);
+        const int a = max(qs, qlo), b = min(qs + NT - 1, qhi);  // the chunk's part inside the box
+        if ((vec & 4) && inside) {  // two swizzled 32 x 32 boxes per warp, issued by one lane
+          if (lane == 0) {
+            mbar_arrive_tx(cb, NT * 32 * 4);
 #pragma unroll
-              for (int h = 0; h < NT / 32; ++h)
-                tma_load3(smem_u32(reinterpret_cast<unsigned char*>(rb) + wq * G::WS + h * 4096), &tin,
-                          qs + 32 * h, (int)row_off + IU.orow, IU.ocomp, cb);
-            } else {
-              mbar_arrive(cb);
-            }
-          } else if ((vec & 1) && b >= a) {  // one bulk copy of that part of this thread's own row; the reader
-                                      // replicates the edge (start and length stay multiples of 4)
-            mbar_arrive_tx(cb, (b - a + 1) * 4);
-            bulk_g2s(smem_u32(rb + wq * (G::WS / 4) + lane * G::XS + (a - qs)), IU.src + a, (b - a + 1) * 4, cb);
+            for (int h = 0; h < NT / 32; ++h)
+              tma_load3(smem_u32(reinterpret_cast<unsigned char*>(rb) + wq * G::WS + h * 4096), &tin,
+                        qs + 32 * h, (int)row_off + IU.orow, IU.ocomp, cb);
           } else {
             mbar_arrive(cb);
-#pragma unroll
-            for (int h = 0; h < NT / 32; ++h) {
-              const int rel = min(max(qs + 32 * h + lane, qlo), qhi);
-#pragma unroll
-              for (int i = 0; i < 32; ++i)
-                cp_async4(smem_u32(rb + wq * (G::WS / 4) + i * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
-            }
           }
-        } else if (PROD) {
-          // the two gradient components of the unit's product (one for xx, yy, zz)
-          const GT* gbase = reinterpret_cast<const GT*>(in);
-          GT* sa = reinterpret_cast<GT*>(rb);
-          GT* sb = sa + NT * kTcLines;
-          const bool two = prod_a(IU.comp) != prod_b(IU.comp);
-          if ((vec & 1) && IU.wfull) {
-            // 16-byte copies of LPC consecutive lines, within the warp's own 32 lines:
-            // lane -> line group qd of the warp, positions pg + PPI i, each clamped
-            // to the box (a copy holds one position of its lines)
-            constexpr int LPC = 16 / (int)sizeof(GT), GPW = 32 / LPC, PPI = 32 / GPW;
-            const int qd = lane % GPW, pg = lane / GPW;
-            const GT* pa = gbase + IU.ga + (LPC * qd - lane);
-            const GT* pb = gbase + IU.gb + (LPC * qd - lane);
-#pragma unroll
-            for (int i = 0; i < NTP / PPI; ++i) {
-              const int pos = p_lo + pg + PPI * i;
-              const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
-              const int so = pos * kTcLines + 32 * wq + LPC * qd;
-              cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + q));
-              if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + q));
-            }
-          } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
-#pragma unroll 4
-            for (int j = p_lo; j < p_lo + NTP; ++j) {
-              const int64_t q = (int64_t)min(max(qs + j, qlo), qhi) * IU.istride;
-              if (PROD == 1) {  // FP32: asynchronous 4-byte copies
-                cp_async4(smem_u32(sa + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.ga + q));
-                if (two)
-                  cp_async4(smem_u32(sb + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.gb + q));
-              } else {  // FP16: below the 4-byte copy size, loaded and stored here
-                sa[j * kTcLines + m] = gbase[IU.ga + q];
-                if (two) sb[j * kTcLines + m] = gbase[IU.gb + q];
-              }
-            }
-          }
-        } else if ((vec & 1) && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
-                                       // own 32 lines (the stage hand-off is warp-local):
-                                       // lane -> lines 32 wq + 4 (lane % 8).., positions
-                                       // lane / 8 + 4 i, each clamped to the box; a warp
-                                       // with lines past the box copies its own line below
-          const int qd = lane & 7, pg = lane >> 3;
-          const float* p = IU.src + (4 * qd - lane);
-#pragma unroll
-          for (int i = 0; i < NTP / 4; ++i) {
-            const int pos = p_lo + pg + 4 * i;
-            const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
-            cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + q);
-          }
-        } else if (!IU.lok) {
-          // a line past the box: its products are never stored and every line's
-          // row of the product is its own, so it stages nothing
-        } else if (inside) {
-          const float* p = IU.src + qs * IU.istride;
-#pragma unroll
-          for (int j = p_lo; j < p_lo + NTP; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
+        } else if ((vec & 1) && b >= a) {  // one bulk copy of that part of this thread's own row; the reader
+                                    // replicates the edge (start and length stay multiples of 4)
+          mbar_arrive_tx(cb, (b - a + 1) * 4);
+          bulk_g2s(smem_u32(rb + wq * (G::WS / 4) + lane * G::XS + (a - qs)), IU.src + a, (b - a + 1) * 4, cb);
         } else {
 #pragma unroll
-          for (int j = p_lo; j < p_lo + NTP; ++j)
-            cp_async4(smem_u32(rb + j * kTcLines + m), IU.src + min(max(qs + j, qlo), qhi) * IU.istride);
+          for (int h = 0; h < NT / 32; ++h) {
+            const int rel = min(max(qs + 32 * h + lane, qlo), qhi);
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              cp_async4(smem_u32(rb + wq * (G::WS / 4) + i * G::XS + 32 * h + lane), sSrc[32 * wq + i] + rel);
+          }
+          // this thread's arrival once its copies have landed
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(cb) : "memory");
         }
-        if (++ic == iC) enter(iu + gridDim.x);
+      } else if (PROD) {
+        // the two gradient components of the unit's product (one for xx, yy, zz)
+        const GT* gbase = reinterpret_cast<const GT*>(in);
+        GT* sa = reinterpret_cast<GT*>(rb);
+        GT* sb = sa + NT * kTcLines;
+        const bool two = prod_a(IU.comp) != prod_b(IU.comp);
+        if ((vec & 1) && IU.wfull) {
+          // 16-byte copies of LPC consecutive lines, within the warp's own 32 lines:
+          // lane -> line group qd of the warp, positions pg + PPI i, each clamped
+          // to the box (a copy holds one position of its lines)
+          constexpr int LPC = 16 / (int)sizeof(GT), GPW = 32 / LPC, PPI = 32 / GPW;
+          const int qd = lane % GPW, pg = lane / GPW;
+          const GT* pa = gbase + IU.ga + (LPC * qd - lane);
+          const GT* pb = gbase + IU.gb + (LPC * qd - lane);
+#pragma unroll
+          for (int i = 0; i < NTP / PPI; ++i) {
+            const int pos = p_lo + pg + PPI * i;
+            const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
+            const int so = pos * kTcLines + 32 * wq + LPC * qd;
+            cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + q));
+            if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + q));
+          }
+        } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
+#pragma unroll 4
+          for (int j = p_lo; j < p_lo + NTP; ++j) {
+            const int64_t q = (int64_t)min(max(qs + j, qlo), qhi) * IU.istride;
+            if (PROD == 1) {  // FP32: asynchronous 4-byte copies
+              cp_async4(smem_u32(sa + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.ga + q));
+              if (two)
+                cp_async4(smem_u32(sb + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.gb + q));
+            } else {  // FP16: below the 4-byte copy size, loaded and stored here
+              sa[j * kTcLines + m] = gbase[IU.ga + q];
+              if (two) sb[j * kTcLines + m] = gbase[IU.gb + q];
+            }
+          }
+        }
+      } else if ((vec & 1) && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
+                                     // own 32 lines (the stage hand-off is warp-local):
+                                     // lane -> lines 32 wq + 4 (lane % 8).., positions
+                                     // lane / 8 + 4 i, each clamped to the box; a warp
+                                     // with lines past the box copies its own line below
+        const int qd = lane & 7, pg = lane >> 3;
+        const float* p = IU.src + (4 * qd - lane);
+#pragma unroll
+        for (int i = 0; i < NTP / 4; ++i) {
+          const int pos = p_lo + pg + 4 * i;
+          const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
+          cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + q);
+        }
+      } else if (!IU.lok) {
+        // a line past the box: its products are never stored and every line's
+        // row of the product is its own, so it stages nothing
+      } else if (inside) {
+        const float* p = IU.src + qs * IU.istride;
+#pragma unroll
+        for (int j = p_lo; j < p_lo + NTP; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
+      } else {
+#pragma unroll
+        for (int j = p_lo; j < p_lo + NTP; ++j)
+          cp_async4(smem_u32(rb + j * kTcLines + m), IU.src + min(max(qs + j, qlo), qhi) * IU.istride);
       }
-      cp_async_commit();
-      ++k_issue;
-    };
-    enter(blockIdx.x);
+      if (++ic == iC) enter(iu + gridDim.x);
+    }
+    cp_async_commit();
+    ++k_issue;
+  };
+  if (role == 0) {
+    if (!XAXIS) {
+      enter(blockIdx.x);
 #pragma unroll 1
-    for (int i = 0; i < S; ++i) issue_next();
+      for (int i = 0; i < S; ++i) issue_next();
+    }
     uint32_t k = 0;  // chunks consumed
     bool go = true;
     int gbase = 0;  // ring position of this unit's window position 0 (continuous ring: runs on)
@@ -638,11 +646,14 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       if (!G::BIG) gbase = 0;
       const int q0u = CU.p0 - G::RA - alo;  // relative input position of window position 0
       for (int c = 0; c < G::P + nt; ++c, ++k) {
-        cp_async_wait<S - 1>();  // chunk k has landed
-        __syncwarp();            // and so have the other lanes' copies (each warp copies only its own lines)
-        // x form: the bulk / tensor copies of chunk k have landed (a copy is never
-        // waited for with the short limit: it depends on no other role)
-        if (XAXIS && !__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bar_chunk[k % S]), (k / S) & 1u,
+        if (!XAXIS) {
+          cp_async_wait<S - 1>();  // chunk k has landed
+          __syncwarp();            // and so have the other lanes' copies (each warp copies only its own lines)
+        }
+        // x form: the copy warp's copies of this warp's slice of chunk k have
+        // landed (never waited for with the short limit: a copy warp that gives
+        // up raises the abort flag)
+        if (XAXIS && !__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bar_xfull[k % S][wq]), (k / S) & 1u,
                                                                  &abort_flag))) {
           abort_flag = 1;
           go = false;
@@ -686,12 +697,18 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
 #pragma unroll
           for (int j = 0; j < NTP; ++j) v[j] = rb[(p_lo + j) * kTcLines + m];
         }
-        // x form: the stage is refilled by bulk / tensor copies (the async proxy),
-        // so this thread's reads of it are ordered before them by a proxy fence
-        // (without it a refill overtook the reads of a work unit's first chunk)
-        if (XAXIS) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();  // every lane has read the stage before it is refilled
-        issue_next();
+        if (XAXIS) {
+          // the copy warp refills the slice with bulk / tensor copies (the async
+          // proxy): this warp's reads are ordered before them by a proxy fence
+          // (without it a refill overtook the reads of a work unit's first
+          // chunk), then the warp releases the slice
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bar_xempty[k % S][wq]));
+        } else {
+          __syncwarp();  // every lane has read the stage before it is refilled
+          issue_next();
+        }
         const int t = c - G::P;  // tile of this chunk (< 0: ring fill)
         const int q = c < G::P ? NT * c : 2 * G::RA + NT * t;
         const int nw = c < G::P ? min(NT, 2 * G::RA - q) : NT;  // positions written (a fill chunk: its halo part)
@@ -749,24 +766,11 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       }
       gbase += 2 * G::RA + NT * nt;
     }
-    cp_async_wait<0>();  // no cp.async copy is left in flight
-    __syncwarp();
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // nor a store to tensor memory
-    if (XAXIS) {
-      // nor a bulk / tensor copy: a CTA that gave up may have issued up to S
-      // chunks beyond the last one it consumed, and its threads may have stopped
-      // at different chunks (never more than S apart: a thread issues chunk
-      // c + S only after every thread has arrived for chunk c).  Each thread
-      // arrives, without a copy, for the chunks it did not issue, so that every
-      // issued chunk's phase completes once its bytes have landed; then each
-      // stage's last phase is waited for.  On a normal exit every thread has
-      // arrived for every chunk and the waits return at once.
-      atomicMax(&arrived_max, arrived);
-      asm volatile("bar.sync 1, %0;" ::"n"(kTcLines) : "memory");
-      const int amax = arrived_max;
-      for (int j = arrived; j < amax; ++j) mbar_arrive(smem_u32(&bar_chunk[j % S]));
-      for (int j = max(0, amax - S); j < amax; ++j) mbar_wait(smem_u32(&bar_chunk[j % S]), (j / S) & 1u);
+    if (!XAXIS) {
+      cp_async_wait<0>();  // no cp.async copy is left in flight
+      __syncwarp();
     }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // nor a store to tensor memory
   } else if (role == 2) {
     const uint64_t bhi_d = umma_desc(smem_u32(sBhi), 128, G::KCB * 128);
     const uint64_t blo_d = umma_desc(smem_u32(sBlo), 128, G::KCB * 128);
@@ -799,6 +803,26 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       }
       gbase += 2 * G::RA + NT * nt;
     }
+  } else if (XAXIS && role == 3) {
+    // A copy warp (x form): slice wq of chunk k (its producer warp's 32 rows)
+    // into stage k mod S once that producer warp has read the slice's previous
+    // chunk there
+    enter(blockIdx.x);
+    while (iu < n_units) {
+      const uint32_t k = k_issue;
+      if (k >= (uint32_t)S &&
+          !__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bar_xempty[k % S][wq]), ((k / S) - 1) & 1u,
+                                                      &abort_flag, ctl.wait_limit))) {
+        abort_flag = 1;
+        break;
+      }
+      issue_next();
+    }
+    // every issued chunk's copies have landed before the CTA releases its memory
+    // (a slice is refilled only after its previous chunk was read, so at most
+    // the last S chunks can still be in flight)
+    for (uint32_t j = k_issue > (uint32_t)S ? k_issue - S : 0; j < k_issue; ++j)
+      mbar_wait(smem_u32(&bar_xfull[j % S][wq]), (j / S) & 1u);
   } else {
     bool go = true;
     for (int64_t unit = blockIdx.x; unit < n_units && go; unit += gridDim.x) {
