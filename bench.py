@@ -695,11 +695,14 @@ def run_crops(args):
     ora_cache = {}
     mode_env = {"persistent": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "1"},
                 "graph": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "0"},
-                "per_crop": {"CT_TUNE_BATCH_GRAPH": "0", "CT_TUNE_BATCH_PERSISTENT": "0"}}
+                "per_crop": {"CT_TUNE_BATCH_GRAPH": "0", "CT_TUNE_BATCH_PERSISTENT": "0"},
+                "graph_fp32": {"CT_TUNE_BATCH_GRAPH": "1", "CT_TUNE_BATCH_PERSISTENT": "0"}}
     clocks = None
-    for mode in ("persistent", "graph", "per_crop"):
+    for mode in ("persistent", "graph", "per_crop", "graph_fp32"):
+        # graph_fp32: the default batch form with the plain FP32 arithmetic, for the mixed / FP32 comparison
+        prec = _lib.CT_PREC_FP32 if mode == "graph_fp32" else _lib.CT_PREC_MIXED
         os.environ.update(mode_env[mode])
-        plan = _lib.ct_plan_create(_lib.make_params(2.0, 6.0, (0, 0, 0), (0, 0, 1), _lib.CT_PREC_MIXED,
+        plan = _lib.ct_plan_create(_lib.make_params(2.0, 6.0, (0, 0, 0), (0, 0, 1), prec,
                                                     _lib.CT_OUT_F16, _lib.CT_OUT_F16, _lib.CT_OUT_F16), (1, 1, 1))
         for k in mode_env[mode]:
             del os.environ[k]
@@ -725,7 +728,7 @@ def run_crops(args):
             res[mode] = {"ms_per_step": ms, "voxels_per_s": total / (ms * 1e-3),
                          "launches_per_step": st["launches"] / args.steps,
                          "fallback_voxels_per_step": st["fallback_voxels"] / args.steps}
-            if mode != "graph":  # where the time goes: one more step with per-kernel events
+            if mode not in ("graph", "graph_fp32"):  # where the time goes: one more step with per-kernel events
                 _lib.ct_plan_profile(plan, True)
                 _lib.ct_run_chunks(plan, items, False)
                 torch.cuda.synchronize()
@@ -751,7 +754,7 @@ def run_crops(args):
             o = [_decode(t) for t in outs[j]]
             sl = (slice(lo[2], lo[2] + b), slice(lo[1], lo[1] + b), slice(lo[0], lo[0] + b))
             out = {"v": o[0][(slice(None),) + sl], "ha": o[1][sl], "ia": o[2][sl], "fa": o[3][sl]}
-            _merge(worst, _grade_box(ora, out, inside, _lib.CT_PREC_MIXED))
+            _merge(worst, _grade_box(ora, out, inside, prec))
         res[mode]["accuracy"] = _verdict(worst)
     accuracy = dict(res["graph"]["accuracy"])
     accuracy["sample"] = "one 12^3 box in each of 8 seed-chosen crops, F16 outputs decoded (every mode graded the " \
@@ -762,7 +765,8 @@ def run_crops(args):
            "sigma": "per crop from {1,1.5,2,3}", "rho": "per crop from {2,4,6,8}", "outputs": "f16 v, HA, IA, FA",
            "precision": "mixed"},
           {"modes": res, "gpu_launches": res["graph"]["launches_per_step"] * args.steps, "clocks": clocks,
-           "accuracy": accuracy})
+           "accuracy": accuracy,
+           "mixed_vs_fp32": res["graph"]["voxels_per_s"] / res["graph_fp32"]["voxels_per_s"]})
 
 
 def run_stream(args):

@@ -71,10 +71,11 @@ typedef int32_t ct_status;
 
 /* Arithmetic of the path. */
 #define CT_PREC_FP32 0  /* FP32 gradient, tensor and eigen-solve (FP32 Jacobi re-solve
-                           for near-degenerate voxels) */
+                           for near-degenerate voxels: l2 - l1 < 2e-2 (l3 - l1)) */
 #define CT_PREC_MIXED 1 /* gradient held in FP16 (scaled by 2^-8), products and sums in
                            FP32, FP32 closed-form eigen-solve with an FP64 re-solve for
-                           near-degenerate voxels */
+                           near-degenerate voxels (l2 - l1 < 1e-2 (l3 - l1): beyond that
+                           the FP16-held gradient, not the solver, bounds the direction) */
 
 /* Output encodings. */
 #define CT_OUT_F32 0

@@ -332,6 +332,7 @@ Fallback fallback_of(ct_plan P, int slot) {
   fb.total = P->fb_total;
   fb.list = P->fb_list[slot];
   fb.cap = P->fb_cap[slot];
+  fb.gap = degenerate_gap(P->p.precision == CT_PREC_MIXED);
   return fb;
 }
 
@@ -1197,6 +1198,7 @@ ct_status build_persistent_waves(ct_plan P, const ct_item* items, const std::vec
         fb.total = P->fb_total;
         fb.list = reinterpret_cast<int64_t*>(l_off);
         fb.cap = box_vox(ob);
+        fb.gap = degenerate_gap(P->p.precision == CT_PREC_MIXED);
         EigOut o{it.vec, it.ha, it.ia, it.fa, P->p.vec_type, P->p.angle_type, P->p.fa_type, ob};
         EigItem x{A, ob, ob, it.mask, ob, c.F, o, fb};
         const bool compact = it.mask && (t && t->eig_compact >= 0 ? t->eig_compact != 0 : P->eig_compact);

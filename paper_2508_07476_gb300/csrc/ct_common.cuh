@@ -161,6 +161,12 @@ __device__ __forceinline__ float atan2_right(float y, float x) {
 // FP32 input its direction error is at its floor (~0.03 deg) from a gap of
 // 2e-2 of the spread up, 0.044 deg at 1e-2, 0.5 deg at 3e-3.
 constexpr float kDegenerateGap = 2e-2f;
+// The mixed form lists from 1e-2: its tensor already carries the FP16-held
+// gradient's error (about 1e-3 of the trace), which at such gaps turns the
+// direction by far more than the FP32 closed form's own 0.044 deg, so an FP64
+// re-solve there would not change the result's accuracy, only its cost (FP64
+// runs at a small fraction of the FP32 rate).
+constexpr float kDegenerateGapMixed = 1e-2f;
 // The same for the FP64 closed form (the mixed form's re-solve).  Near a double
 // root an error eps in det(B) / 2 moves l1 by about eps p^2 / gap and the null
 // vector by that over the gap, eps (p / gap)^2: at a gap of 1e-4 of the spread
@@ -209,11 +215,12 @@ __device__ __forceinline__ T null_vector(const Sym3<T>& s, T lam, T v[3]) {
 // sin/cos of phi (in [0, pi/3]) from the hardware approximations and the
 // reciprocal square roots from rsqrt; the errors they add, a few 1e-7 of p,
 // are far below what the re-solve threshold leaves between l1 and l2.
+// The FP32 form lists the voxel for a re-solve when l2 - l1 < gap (l3 - l1).
 template <typename T>
-__device__ __forceinline__ bool eig_closed(const Sym3<T>& s, T l[3], T v[3]);
+__device__ __forceinline__ bool eig_closed(const Sym3<T>& s, T l[3], T v[3], T gap);
 
 template <>
-__device__ __forceinline__ bool eig_closed<float>(const Sym3<float>& s, float l[3], float v[3]) {
+__device__ __forceinline__ bool eig_closed<float>(const Sym3<float>& s, float l[3], float v[3], float gap) {
   const float q = (s.a + s.b + s.c) * (1.f / 3.f);
   const float aq = s.a - q, bq = s.b - q, cq = s.c - q;
   const float p1 = s.d * s.d + s.e * s.e + s.f * s.f;
@@ -257,12 +264,13 @@ __device__ __forceinline__ bool eig_closed<float>(const Sym3<float>& s, float l[
   } else {
     v[0] = 1.f; v[1] = 0.f; v[2] = 0.f;
   }
-  return (l2 - l1) >= kDegenerateGap * (l3 - l1) && bn > 0.f;
+  return (l2 - l1) >= gap * (l3 - l1) && bn > 0.f;
 }
 
-// FP64 version (the re-solve of the mixed form): library acos / cos / sqrt.
+// FP64 version (the re-solve of the mixed form): library acos / sincos / sqrt,
+// l1 from the same sin and cos as l3 (one sincos instead of two cos).
 template <>
-__device__ __forceinline__ bool eig_closed<double>(const Sym3<double>& s, double l[3], double v[3]) {
+__device__ __forceinline__ bool eig_closed<double>(const Sym3<double>& s, double l[3], double v[3], double gap) {
   const double q = (s.a + s.b + s.c) / 3.0;
   const double aq = s.a - q, bq = s.b - q, cq = s.c - q;
   const double p1 = s.d * s.d + s.e * s.e + s.f * s.f;
@@ -278,14 +286,16 @@ __device__ __forceinline__ bool eig_closed<double>(const Sym3<double>& s, double
   const double det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) + B02 * (B01 * B12 - B11 * B02);
   const double r = fmin(fmax(0.5 * det, -1.0), 1.0);
   const double phi = acos(r) / 3.0;
-  double l3 = q + 2.0 * p * cos(phi);
-  double l1 = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  double l3 = q + 2.0 * p * cp;
+  double l1 = q - p * (cp + 1.7320508075688772935 * sp);
   double l2 = 3.0 * q - l1 - l3;
   if (l2 < l1) { double t = l1; l1 = l2; l2 = t; }
   if (l3 < l2) { double t = l2; l2 = l3; l3 = t; }
   l[0] = l1; l[1] = l2; l[2] = l3;
   const double bn = null_vector(s, l1, v);
-  return (l2 - l1) >= kDegenerateGap64 * (l3 - l1) && bn > 0.0;
+  return (l2 - l1) >= gap * (l3 - l1) && bn > 0.0;
 }
 
 // Cyclic Jacobi (Golub & Van Loan, Matrix Computations, section 8.5) on a

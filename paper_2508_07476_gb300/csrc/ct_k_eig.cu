@@ -34,7 +34,7 @@ __device__ __forceinline__ void resolve(const Sym3<float>& s, bool mixed, float 
   if (mixed) {
     Sym3<double> sd{(double)s.a, (double)s.b, (double)s.c, (double)s.d, (double)s.e, (double)s.f};
     double ld[3], vd[3];
-    if (!eig_closed<double>(sd, ld, vd)) eig_jacobi<double>(sd, ld, vd);
+    if (!eig_closed<double>(sd, ld, vd, kDegenerateGap64)) eig_jacobi<double>(sd, ld, vd);
     for (int k = 0; k < 3; ++k) {
       l[k] = (float)ld[k];
       v[k] = (float)vd[k];
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256, CT_EIG_MINB)
   float l[3] = {0.f, 0.f, 0.f}, v[3] = {1.f, 0.f, 0.f};
   if (inside) {
     const Sym3<float> s = load_sym(S, box_vox(sb), box_index(sb, x, y, z));
-    if (!eig_closed<float>(s, l, v)) push_fallback(fb, ((int64_t)zr * ob.n[1] + yr) * ob.n[0] + (x - ob.lo[0]));
+    if (!eig_closed<float>(s, l, v, fb.gap)) push_fallback(fb, ((int64_t)zr * ob.n[1] + yr) * ob.n[0] + (x - ob.lo[0]));
   }
   write_voxel<VT, AT, FT>(o, box_index(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
 }
@@ -134,7 +134,7 @@ __device__ __forceinline__ void eig32_body(const float* __restrict__ S, Box sb, 
     s.d = __ldg(S + 3 * ns + si);
     s.e = __ldg(S + 4 * ns + si);
     s.f = __ldg(S + 5 * ns + si);
-    if (!eig_closed<float>(s, l, v))
+    if (!eig_closed<float>(s, l, v, fb.gap))
       push_fallback(fb, ((int64_t)blk.z() * ob.n[1] + blk.y()) * ob.n[0] + (x - ob.lo[0]));
   }
   write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), inside, F, x, y, z, l, v, fill);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void eig_compact_body(const float* __restrict__ S, Bo
       if (i0 + kEigThreads * u >= total) break;
       const int x = xs[u];
       float l[3], v[3];
-      if (!eig_closed<float>(s[u], l, v))
+      if (!eig_closed<float>(s[u], l, v, fb.gap))
         push_fallback(fb, ((int64_t)blk.z() * ob.n[1] + blk.y()) * ob.n[0] + (x - ob.lo[0]));
       write_voxel<VT, AT, FT, int, PLAIN>(o, box_index32(o.ab, x, y, z), true, F, x, y, z, l, v, fill);
     }
@@ -306,6 +306,19 @@ __global__ void __launch_bounds__(128)
     resolve(s, mixed, l, v);
     write_voxel(it.o, box_index(it.o.ab, x, y, z), true, it.F, x, y, z, l, v, fill);
   }
+}
+
+// The re-solve launches: the listed voxels are few (the list's length is read
+// on the device), so a few CTAs per SM stride over it; a grid sized by the box
+// would mostly start CTAs that find nothing (batches launch one per item).
+static int fallback_grid(int64_t max_items) {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 152;
+  }();
+  const int64_t b = (max_items + 127) / 128;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4 * sms));
 }
 
 static int grid_for(int64_t n, int threads) {
@@ -383,7 +396,7 @@ cudaError_t launch_eig_angles_fallback(const float* S, const Box& sb, const Box&
                                        const Box& mb, const Frame& F, float fill, const EigOut& o, bool mixed,
                                        const Fallback& fb, int64_t max_items, cudaStream_t st) {
   if (max_items <= 0) return cudaSuccess;
-  k_eig_angles_fallback<<<grid_for(max_items, 128), 128, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
+  k_eig_angles_fallback<<<fallback_grid(max_items), 128, 0, st>>>(S, sb, ob, mask, mb, F, fill, o, mixed, fb);
   return cudaGetLastError();
 }
 
@@ -443,7 +456,7 @@ __global__ void __launch_bounds__(256)
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     Sym3<float> s = load_sym(S, n, i);
     float l[3], v[3];
-    if (!eig_closed<float>(s, l, v)) push_fallback(fb, i);
+    if (!eig_closed<float>(s, l, v, fb.gap)) push_fallback(fb, i);
     orient_largest(v);
     if (evals) {
       evals[i] = l[0];
@@ -502,7 +515,7 @@ cudaError_t launch_eig_only(const float* S, int64_t n, float* evals, float* evec
 cudaError_t launch_eig_only_fallback(const float* S, int64_t n, float* evals, float* evec, bool mixed,
                                      const Fallback& fb, int64_t max_items, cudaStream_t st) {
   if (max_items <= 0) return cudaSuccess;
-  k_eig_only_fallback<<<grid_for(max_items, 128), 128, 0, st>>>(S, n, evals, evec, mixed, fb);
+  k_eig_only_fallback<<<fallback_grid(max_items), 128, 0, st>>>(S, n, evals, evec, mixed, fb);
   return cudaGetLastError();
 }
 

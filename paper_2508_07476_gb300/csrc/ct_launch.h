@@ -147,11 +147,15 @@ struct EigOut {
 };
 
 struct Fallback {
+  float gap = kDegenerateGap;  // listing threshold of the arithmetic form (degenerate_gap)
   int* count;                 // device counter of listed voxels (reset per launch)
   unsigned long long* total;  // device running total (for statistics)
   int64_t* list;
   int64_t cap;
 };
+
+// The near-degeneracy listing threshold of an arithmetic form (FP32 / mixed).
+inline float degenerate_gap(bool mixed) { return mixed ? kDegenerateGapMixed : kDegenerateGap; }
 
 // One item of a batched eigen stage (the arguments of launch_eig_angles).
 struct EigItem {

@@ -128,8 +128,9 @@ extern "C" ct_status ct_eig_smallest_noalloc(const float* d_S, int64_t n, float*
   fb.total = reinterpret_cast<unsigned long long*>(base + kTotalOffset);
   fb.list = reinterpret_cast<int64_t*>(base + kListOffset);
   fb.cap = kMaxVoxels;
-  cudaError_t e = cudaMemsetAsync(base, 0, kListOffset, st);
   bool mixed = precision == CT_PREC_MIXED;
+  fb.gap = ct::degenerate_gap(mixed);
+  cudaError_t e = cudaMemsetAsync(base, 0, kListOffset, st);
   if (e == cudaSuccess) e = ct::launch_eig_only(d_S, n, d_evals, d_evec, mixed, fb, st);
   if (e == cudaSuccess) e = ct::launch_eig_only_fallback(d_S, n, d_evals, d_evec, mixed, fb, n, st);
   if (e != cudaSuccess) return ct::set_error(CT_ERR_CUDA, "eigen launch failed: %s", cudaGetErrorString(e));

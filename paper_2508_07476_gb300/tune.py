@@ -10,7 +10,7 @@ cache that plans read at creation, keyed by the GPU's name:
   stream2048   2048 x 2048 x 1024 in 256^3 chunks, sigma 2 / rho 8, masked, mixed, F16
   tera4096     4096 x 4096 x 2048 in 384^3 chunks, sigma 3 / rho 9, masked, mixed, U8Q / F16
   crops        the uneven crops' sizes (2^19 .. 2^25 voxels, x extents a multiple
-               of 8, of 4 or neither) at every sigma / rho pair, mixed, F16
+               of 8, of 4 or neither) at every sigma / rho pair, both forms, F16
 
 Usage: python -m paper_2508_07476_gb300.tune [--out PATH] [--only NAME]
 """
@@ -43,15 +43,16 @@ def _jobs(only=None):
         jobs.append(("tera4096", _lib.make_params(3.0, 9.0, (2047.5, 2047.5, 1023.5), tilt, _lib.CT_PREC_MIXED,
                                                   F32, U8Q, F16), (4096, 4096, 2048), (384, 384, 384), True))
     if only in (None, "crops"):
-        # one cube-like volume per size class l (2^l voxels, +-1 class each) and x class
-        for l in (19, 21, 23, 25):
-            e = round((2 ** l) ** (1 / 3))
-            for nx in (e - e % 8, e - e % 8 + 4, e - e % 8 + 1):
-                for sigma in (1.0, 1.5, 2.0, 3.0):
-                    for rho in (2.0, 4.0, 6.0, 8.0):
-                        p = _lib.make_params(sigma, rho, (nx / 2, e / 2, e / 2), (0.0, 0.0, 1.0), _lib.CT_PREC_MIXED,
-                                             F16, F16, F16)
-                        jobs.append((f"crop{nx}x{e}x{e}_s{sigma}_r{rho}", p, (nx, e, e), None, False))
+        # one cube-like volume per size class l (2^l voxels, +-1 class each) and x class, both forms
+        for prec in (_lib.CT_PREC_MIXED, _lib.CT_PREC_FP32):
+            for l in (19, 21, 23, 25):
+                e = round((2 ** l) ** (1 / 3))
+                for nx in (e - e % 8, e - e % 8 + 4, e - e % 8 + 1):
+                    for sigma in (1.0, 1.5, 2.0, 3.0):
+                        for rho in (2.0, 4.0, 6.0, 8.0):
+                            p = _lib.make_params(sigma, rho, (nx / 2, e / 2, e / 2), (0.0, 0.0, 1.0), prec,
+                                                 F16, F16, F16)
+                            jobs.append((f"crop{nx}x{e}x{e}_s{sigma}_r{rho}_p{prec}", p, (nx, e, e), None, False))
     return jobs
 
 

@@ -138,19 +138,25 @@ def test_eig_stage_matches_oracle(prec):
     ang = G.angle_deg(vec[:, graded], v_o[:, graded])
     assert ang.max() <= 0.5, (ang.max(), np.argmax(ang))
     assert stats["fallback_voxels"] > 0  # the near-degenerate quarter went through the re-solve
-    # above the listing threshold (2e-2 of the spread) the FP32 closed form itself
-    # is at its floor on the same FP32 input: a few hundredths of a degree
+    # above the listing threshold the FP32 closed form itself decides the direction
+    # on the same FP32 input: the FP32 form lists below 2e-2 of the spread, where
+    # the closed form is at its floor (a few hundredths of a degree); the mixed
+    # form lists below 1e-2 (its FP16-held gradient already bounds such voxels'
+    # directions only to eps_S tr S / (l2 - l1) >= 5.7 deg), and just above that
+    # the closed form reaches 0.12 deg on these tensors, still well inside 0.5
+    gap_list, bound = (2e-2, 0.06) if prec == FP32 else (1e-2, 0.15)
     spread_ = np.maximum(ev_o[2] - ev_o[0], 1e-300)
     rel_ = (ev_o[1] - ev_o[0]) / spread_
-    fp32 = rel_ > 2.5e-2
-    assert G.angle_deg(vec[:, fp32], v_o[:, fp32]).max() <= 0.06
+    fp32 = rel_ > 1.25 * gap_list
+    assert fp32.sum() > 1000
+    assert G.angle_deg(vec[:, fp32], v_o[:, fp32]).max() <= bound
     if prec == MIXED:
         # the listed voxels are re-solved in FP64 (closed form down to a gap of 1e-4 of
         # the spread, Jacobi below): on the same FP32 input as the oracle their
         # directions agree to far better than the FP32 outputs resolve
         spread = np.maximum(ev_o[2] - ev_o[0], 1e-300)
         rel = (ev_o[1] - ev_o[0]) / spread
-        fp64 = (rel < 1.6e-2) & (rel > 1e-6)  # inside the FP32 listing threshold (2e-2) with margin
+        fp64 = (rel < 0.8 * gap_list) & (rel > 1e-6)  # inside the listing threshold with margin
         assert fp64.sum() > 1000
         ang64 = G.angle_deg(vec[:, fp64], v_o[:, fp64])
         assert ang64.max() <= 1e-3, (ang64.max(), rel[fp64][np.argmax(ang64)])

@@ -33,8 +33,9 @@ def _tensors(n, seed, degenerate_fraction):
     l3 = rng.uniform(2.0, 10.0, size=n) * scale
     l2 = rng.uniform(0.3, 0.7, size=n) * (l3 - l1) + l1
     k = int(n * degenerate_fraction)
-    # the smallest pair closer than 1e-2 of the spread: listed for the re-solve
-    l2[:k] = l1[:k] + (l3[:k] - l1[:k]) * 10 ** rng.uniform(-6, -2, size=k)
+    # the smallest pair closer than 5e-3 of the spread: listed for the re-solve in
+    # either arithmetic form (thresholds 2e-2 and 1e-2)
+    l2[:k] = l1[:k] + (l3[:k] - l1[:k]) * 10 ** rng.uniform(-6, -2.3, size=k)
     lam = np.stack([l1, l2, l3], axis=1)
     A = np.einsum("nij,nj,nkj->nik", Q, lam, Q)
     S = np.stack([A[:, 0, 0], A[:, 1, 1], A[:, 2, 2], A[:, 0, 1], A[:, 0, 2], A[:, 1, 2]])
