@@ -30,19 +30,21 @@
 // The CTA is warp-specialised, one CTA per SM holding all 512 tensor-memory
 // columns.  Producer warps own the 128 lines (x form: four warps, one line per
 // thread; y / z forms: eight warps, two per lane quadrant, each with half of
-// every chunk's positions): they copy NT-position chunks of their lines into
-// shared memory with cp.async (16-byte copies when the boxes are 16-byte
-// aligned), several chunks ahead in one stream that runs on across work units,
-// then split a landed chunk, write both rings and arrive on the tile's
-// "staged" mbarrier.  An MMA warp waits on it, issues the
-// 3 W / 8 MMAs (one elected lane, the loop in warp-uniform control flow) into
-// one of two accumulators and commits them to that accumulator's mbarrier.
-// Four epilogue warps wait on it, read their 32 lanes of D, free the
-// accumulator (a third mbarrier) and store the outputs.  For x each line is a
-// row: a producer thread fetches its row's chunk with one bulk copy (TMA,
-// completing on the stage's mbarrier) and an epilogue thread writes its row of
-// outputs with one bulk store; unaligned or clamped pieces go through
-// coalesced per-element copies and a padded shared-memory transpose.
+// every chunk's positions).  NT-position chunks of their lines are copied into
+// shared memory several chunks ahead, in one stream that runs on across work
+// units: in the y / z forms by the producers themselves with cp.async
+// (16-byte copies when the boxes are 16-byte aligned); in the x form, where
+// each line is a row, by four copy warps, one per producer warp, with tensor
+// (TMA) or bulk copies completing on per-slice mbarriers, refilled once the
+// producer warp releases the slice.  The producers split a landed chunk, write
+// both rings and arrive on the tile's "staged" mbarrier.  An MMA warp waits on
+// it, issues the 3 W / 8 MMAs (one elected lane, the loop in warp-uniform
+// control flow) into one of two accumulators and commits them to that
+// accumulator's mbarrier.  Four epilogue warps wait on it, read their 32
+// lanes of D, free the accumulator (a third mbarrier) and store the outputs;
+// in the x form an epilogue thread writes its row of outputs by a tensor or
+// bulk store, and unaligned or clamped pieces go through coalesced
+// per-element copies and a padded shared-memory transpose.
 // Every wait is bounded; a CTA that gives up raises a flag that ends the other
 // roles' waits, drains its MMAs and releases the tensor memory.
 #include <cuda.h>  // CUtensorMap and its enums; the encoder is fetched from the driver at run time
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       if (XAXIS) {
         const uint32_t cb = smem_u32(&bar_xfull[k_issue % S][wq]);
         const int a = max(qs, qlo), b = min(qs + NT - 1, qhi);  // the chunk's part inside the box
-        if ((vec & 4) && inside) {  // two swizzled 32 x 32 boxes per warp, issued by one lane
+        if ((vec & 4) && inside) {  // two swizzled 32 x 32 boxes per slice, issued by one lane
           if (lane == 0) {
             mbar_arrive_tx(cb, NT * 32 * 4);
 #pragma unroll
