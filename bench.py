@@ -409,7 +409,7 @@ def _kernel_algorithmic(name: str, nvox: int, rs: int, rr: int, inside: float = 
 # DRAM bytes per output voxel of a kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launch / voxels of the
 # capture); valid only for the kernel version summarised in the named file.
-MEASURED_TRAFFIC = {"rho_x_tc": (45.2, "profiles/kernels_annulus256.md"),
+MEASURED_TRAFFIC = {"rho_x_tc": (45.1, "profiles/kernels_annulus256.md"),
                     "rho_y_tc": (44.8, "profiles/kernels_annulus256.md"),
                     "rho_z_tc_g16": (26.6, "profiles/kernels_annulus256.md"),
                     "grad_z_g16": (16.4, "profiles/kernels_annulus256.md"),
