@@ -68,10 +68,14 @@ constexpr int kTcLines = 128;  // = M: TMEM lane m holds line m
 // chunk's positions between two producer warps per lane quadrant (NP = 8: warp
 // w stages positions [(w / 4) NT / 2, + NT / 2) of the lines 32 (w % 4) ..),
 // which halves each producer thread's work per tile, and copy their own parts.
-template <bool XAXIS>
+#ifndef CT_TC_PCOPY
+#define CT_TC_PCOPY 1  // tuning: the products (first) pass with copy warps too (0: its producers copy)
+#endif
+template <bool XAXIS, int PROD = 0>
 struct TcRoles {
   static constexpr int NP = XAXIS ? 4 : 8;
-  static constexpr int THREADS = 32 * (NP + 5 + (XAXIS ? 4 : 0));
+  static constexpr bool COPY = XAXIS || (CT_TC_PCOPY && PROD != 0);  // copy warps NP+5 .. NP+8
+  static constexpr int THREADS = 32 * (NP + 5 + (COPY ? 4 : 0));
   static constexpr int MMA_WARP = NP + 4;
 };
 constexpr int kTcNB = 4;                       // mbarriers per hand-off, used by tiles g mod 4 in turn
@@ -80,6 +84,9 @@ constexpr int kTcNB = 4;                       // mbarriers per hand-off, used b
 #endif
 #ifndef CT_TC_XSTAGES
 #define CT_TC_XSTAGES 3  // tuning: x form, chunk stages in flight (with the copy warps 3 beat 2: 0.95 vs 1.04 ms)
+#endif
+#ifndef CT_TC_PSTAGES
+#define CT_TC_PSTAGES 5  // tuning: products pass from the FP16 gradient, chunk stages (at most what fits)
 #endif
 #ifndef CT_TC_YZSTAGES
 #define CT_TC_YZSTAGES 4  // tuning: y / z forms (plain and FP16 products), chunk stages in flight
@@ -118,6 +125,8 @@ struct TcGeom {
   static constexpr int TCOLS = 512;  // one CTA per SM holds all of it
   static_assert(DCOL + ND * NT <= TCOLS && WR % 8 == 0, "tensor memory");
   static constexpr int B_BYTES = NT * W * 4;
+  // FP16-gradient chunk stages that fit beside B (one 128-line x NT-position chunk of two FP16 components)
+  static constexpr int P2FIT = (232448 - 1024 - 2 * B_BYTES) / (NT * kTcLines * 4);
   static constexpr int XS = NT + 4;  // x-form chunk row: 16-byte aligned, conflict-free by line
   static constexpr int TE = NT + 4;  // x-form output row: 16-byte aligned, float4 writes conflict-free
   static constexpr int ROW_BYTES = kTcLines * 8;
@@ -132,7 +141,9 @@ struct TcGeom {
   }
   // chunks in flight (FP32 gradient pairs: two, the most that fit beside B)
   static constexpr int stages(bool xaxis, int prod = 0) {
-    return xaxis ? CT_TC_XSTAGES : (prod == 1 ? 2 : CT_TC_YZSTAGES);
+    return xaxis ? CT_TC_XSTAGES
+                 : (prod == 1 ? 2
+                              : (prod == 2 ? (CT_TC_PSTAGES < P2FIT ? CT_TC_PSTAGES : P2FIT) : CT_TC_YZSTAGES));
   }
   static_assert((2 * B_BYTES) % 1024 == 0 && NT * 32 * 4 <= WS && TE == XS, "x-form slices");
   static constexpr int need(bool xaxis, int prod = 0) {
@@ -369,7 +380,7 @@ struct GradT<2> {
 // in turn, so that the group's gradient lines are read from L2 after the
 // first component.
 template <int RR, bool XAXIS, int PROD>
-__global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
+__global__ void __launch_bounds__(TcRoles<XAXIS, PROD>::THREADS, 1)
     k_rho_tc(const float* __restrict__ in, Box ib, int dim_axis, float* __restrict__ out, Box ob, int axis, int seg,
              int vec, const __grid_constant__ Taps taps, const __grid_constant__ CUtensorMap tin,
              const __grid_constant__ CUtensorMap tout, const TcCtl ctl, const TcProd pr) {
@@ -388,15 +399,15 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
   float* sTe = reinterpret_cast<float*>(xs);
   const float** sSrc = reinterpret_cast<const float**>(xs + 4 * CT_TC_XEPI * G::WS);
   float** sDst = reinterpret_cast<float**>(xs + 4 * CT_TC_XEPI * G::WS + G::ROW_BYTES);
-  __shared__ __align__(8) uint64_t bar_xfull[4][4];    // x form: slice q of chunk stage s has landed
-  __shared__ __align__(8) uint64_t bar_xempty[4][4];   // x form: producer warp q has read slice q of stage s
+  __shared__ __align__(8) uint64_t bar_xfull[8][4];   // copy warps: slice q of chunk stage s has landed
+  __shared__ __align__(8) uint64_t bar_xempty[8][4];  // copy warps: the producers of slice q have read stage s
   __shared__ __align__(8) uint64_t bar_staged[kTcNB];  // the producers have staged tile g
   __shared__ __align__(8) uint64_t bar_mma[kTcNB];     // tile g's product is in D[g % ND]
   __shared__ __align__(8) uint64_t bar_dfree[kTcNB];   // the epilogue has read tile g's D
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  using RL = TcRoles<XAXIS>;
+  using RL = TcRoles<XAXIS, PROD>;
   const int role = w < RL::NP ? 0 : (w < RL::NP + 4 ? 1 : (w == RL::MMA_WARP ? 2 : 3));  // producer, epilogue,
                                                                                           // MMA, copy (x form)
   const int m = tid & (kTcLines - 1);            // line / TMEM lane (roles 0 and 1)
@@ -416,7 +427,8 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
     for (int a = 0; a < S; ++a)
       for (int q = 0; q < 4; ++q) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(smem_u32(&bar_xfull[a][q])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_xempty[a][q])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_xempty[a][q])),
+                     "r"(RL::NP / 4));  // the producer warps of lane quadrant q
       }
     for (int a = 0; a < kTcNB; ++a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_staged[a])), "n"(32 * RL::NP));
@@ -529,6 +541,72 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       __syncwarp();
     }
   };
+  // y / z forms: positions [plo, plo + NTP) of chunk rb (relative input position
+  // qs of its position 0; inside: no position needs clamping) for this thread's
+  // lines
+  auto stage_yz = [&](float* rb, int qs, bool inside, int plo) {
+    if (PROD) {
+      // the two gradient components of the unit's product (one for xx, yy, zz)
+      const GT* gbase = reinterpret_cast<const GT*>(in);
+      GT* sa = reinterpret_cast<GT*>(rb);
+      GT* sb = sa + NT * kTcLines;
+      const bool two = prod_a(IU.comp) != prod_b(IU.comp);
+      if ((vec & 1) && IU.wfull) {
+        // 16-byte copies of LPC consecutive lines, within the warp's own 32 lines:
+        // lane -> line group qd of the warp, positions pg + PPI i, each clamped
+        // to the box (a copy holds one position of its lines)
+        constexpr int LPC = 16 / (int)sizeof(GT), GPW = 32 / LPC, PPI = 32 / GPW;
+        const int qd = lane % GPW, pg = lane / GPW;
+        const GT* pa = gbase + IU.ga + (LPC * qd - lane);
+        const GT* pb = gbase + IU.gb + (LPC * qd - lane);
+#pragma unroll
+        for (int i = 0; i < NTP / PPI; ++i) {
+          const int pos = plo + pg + PPI * i;
+          const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
+          const int so = pos * kTcLines + 32 * wq + LPC * qd;
+          cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + q));
+          if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + q));
+        }
+      } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
+#pragma unroll 4
+        for (int j = plo; j < plo + NTP; ++j) {
+          const int64_t q = (int64_t)min(max(qs + j, qlo), qhi) * IU.istride;
+          if (PROD == 1) {  // FP32: asynchronous 4-byte copies
+            cp_async4(smem_u32(sa + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.ga + q));
+            if (two)
+              cp_async4(smem_u32(sb + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.gb + q));
+          } else {  // FP16: below the 4-byte copy size, loaded and stored here
+            sa[j * kTcLines + m] = gbase[IU.ga + q];
+            if (two) sb[j * kTcLines + m] = gbase[IU.gb + q];
+          }
+        }
+      }
+    } else if ((vec & 1) && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
+                                   // own 32 lines (the stage hand-off is warp-local):
+                                   // lane -> lines 32 wq + 4 (lane % 8).., positions
+                                   // lane / 8 + 4 i, each clamped to the box; a warp
+                                   // with lines past the box copies its own line below
+      const int qd = lane & 7, pg = lane >> 3;
+      const float* p = IU.src + (4 * qd - lane);
+#pragma unroll
+      for (int i = 0; i < NTP / 4; ++i) {
+        const int pos = plo + pg + 4 * i;
+        const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
+        cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + q);
+      }
+    } else if (!IU.lok) {
+      // a line past the box: its products are never stored and every line's
+      // row of the product is its own, so it stages nothing
+    } else if (inside) {
+      const float* p = IU.src + qs * IU.istride;
+#pragma unroll
+      for (int j = plo; j < plo + NTP; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
+    } else {
+#pragma unroll
+      for (int j = plo; j < plo + NTP; ++j)
+        cp_async4(smem_u32(rb + j * kTcLines + m), IU.src + min(max(qs + j, qlo), qhi) * IU.istride);
+    }
+  };
   uint32_t k_issue = 0;
   auto issue_next = [&]() {
     if (iu < n_units) {
@@ -563,66 +641,16 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
           // this thread's arrival once its copies have landed
           asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(cb) : "memory");
         }
-      } else if (PROD) {
-        // the two gradient components of the unit's product (one for xx, yy, zz)
-        const GT* gbase = reinterpret_cast<const GT*>(in);
-        GT* sa = reinterpret_cast<GT*>(rb);
-        GT* sb = sa + NT * kTcLines;
-        const bool two = prod_a(IU.comp) != prod_b(IU.comp);
-        if ((vec & 1) && IU.wfull) {
-          // 16-byte copies of LPC consecutive lines, within the warp's own 32 lines:
-          // lane -> line group qd of the warp, positions pg + PPI i, each clamped
-          // to the box (a copy holds one position of its lines)
-          constexpr int LPC = 16 / (int)sizeof(GT), GPW = 32 / LPC, PPI = 32 / GPW;
-          const int qd = lane % GPW, pg = lane / GPW;
-          const GT* pa = gbase + IU.ga + (LPC * qd - lane);
-          const GT* pb = gbase + IU.gb + (LPC * qd - lane);
-#pragma unroll
-          for (int i = 0; i < NTP / PPI; ++i) {
-            const int pos = p_lo + pg + PPI * i;
-            const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
-            const int so = pos * kTcLines + 32 * wq + LPC * qd;
-            cp_async16(smem_u32(sa + so), reinterpret_cast<const float*>(pa + q));
-            if (two) cp_async16(smem_u32(sb + so), reinterpret_cast<const float*>(pb + q));
-          }
-        } else if (IU.lok) {  // this thread's own line, position by position (clamped to the box)
-#pragma unroll 4
-          for (int j = p_lo; j < p_lo + NTP; ++j) {
-            const int64_t q = (int64_t)min(max(qs + j, qlo), qhi) * IU.istride;
-            if (PROD == 1) {  // FP32: asynchronous 4-byte copies
-              cp_async4(smem_u32(sa + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.ga + q));
-              if (two)
-                cp_async4(smem_u32(sb + j * kTcLines + m), reinterpret_cast<const float*>(gbase + IU.gb + q));
-            } else {  // FP16: below the 4-byte copy size, loaded and stored here
-              sa[j * kTcLines + m] = gbase[IU.ga + q];
-              if (two) sb[j * kTcLines + m] = gbase[IU.gb + q];
-            }
-          }
-        }
-      } else if ((vec & 1) && IU.wfull) {  // 16 bytes (4 lines) per copy, within the warp's
-                                     // own 32 lines (the stage hand-off is warp-local):
-                                     // lane -> lines 32 wq + 4 (lane % 8).., positions
-                                     // lane / 8 + 4 i, each clamped to the box; a warp
-                                     // with lines past the box copies its own line below
-        const int qd = lane & 7, pg = lane >> 3;
-        const float* p = IU.src + (4 * qd - lane);
-#pragma unroll
-        for (int i = 0; i < NTP / 4; ++i) {
-          const int pos = p_lo + pg + 4 * i;
-          const int64_t q = (int64_t)(inside ? qs + pos : min(max(qs + pos, qlo), qhi)) * IU.istride;
-          cp_async16(smem_u32(rb + pos * kTcLines + 32 * wq + 4 * qd), p + q);
-        }
-      } else if (!IU.lok) {
-        // a line past the box: its products are never stored and every line's
-        // row of the product is its own, so it stages nothing
-      } else if (inside) {
-        const float* p = IU.src + qs * IU.istride;
-#pragma unroll
-        for (int j = p_lo; j < p_lo + NTP; ++j) cp_async4(smem_u32(rb + j * kTcLines + m), p + j * IU.istride);
+      } else if (RL::COPY) {  // a copy warp of the products pass: both halves of its lines' positions
+        stage_yz(rb, qs, inside, 0);
+        stage_yz(rb, qs, inside, NTP);
+        const uint32_t cb = smem_u32(&bar_xfull[k_issue % S][wq]);
+        if (PROD == 2 && !((vec & 1) && IU.wfull))
+          mbar_arrive(cb);  // FP16 element copies are plain stores: a plain arrival releases them
+        else  // this thread's arrival once its copies have landed
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(cb) : "memory");
       } else {
-#pragma unroll
-        for (int j = p_lo; j < p_lo + NTP; ++j)
-          cp_async4(smem_u32(rb + j * kTcLines + m), IU.src + min(max(qs + j, qlo), qhi) * IU.istride);
+        stage_yz(rb, qs, inside, p_lo);
       }
       if (++ic == iC) enter(iu + gridDim.x);
     }
@@ -630,7 +658,7 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
     ++k_issue;
   };
   if (role == 0) {
-    if (!XAXIS) {
+    if (!RL::COPY) {
       enter(blockIdx.x);
 #pragma unroll 1
       for (int i = 0; i < S; ++i) issue_next();
@@ -648,14 +676,14 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       if (!G::BIG) gbase = 0;
       const int q0u = CU.p0 - G::RA - alo;  // relative input position of window position 0
       for (int c = 0; c < G::P + nt; ++c, ++k) {
-        if (!XAXIS) {
+        if (!RL::COPY) {
           cp_async_wait<S - 1>();  // chunk k has landed
           __syncwarp();            // and so have the other lanes' copies (each warp copies only its own lines)
         }
         // x form: the copy warp's copies of this warp's slice of chunk k have
         // landed (never waited for with the short limit: a copy warp that gives
         // up raises the abort flag)
-        if (XAXIS && !__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bar_xfull[k % S][wq]), (k / S) & 1u,
+        if (RL::COPY && !__all_sync(0xffffffffu, mbar_wait_or_abort(smem_u32(&bar_xfull[k % S][wq]), (k / S) & 1u,
                                                                  &abort_flag))) {
           abort_flag = 1;
           go = false;
@@ -699,12 +727,12 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
 #pragma unroll
           for (int j = 0; j < NTP; ++j) v[j] = rb[(p_lo + j) * kTcLines + m];
         }
-        if (XAXIS) {
-          // the copy warp refills the slice with bulk / tensor copies (the async
-          // proxy): this warp's reads are ordered before them by a proxy fence
-          // (without it a refill overtook the reads of a work unit's first
-          // chunk), then the warp releases the slice
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (RL::COPY) {
+          // the copy warp refills the slice (x: with bulk / tensor copies, the
+          // async proxy: this warp's reads are ordered before them by a proxy
+          // fence, without which a refill overtook the reads of a work unit's
+          // first chunk), then the warp releases the slice
+          if (XAXIS) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&bar_xempty[k % S][wq]));
         } else {
@@ -768,7 +796,7 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       }
       gbase += 2 * G::RA + NT * nt;
     }
-    if (!XAXIS) {
+    if (!RL::COPY) {
       cp_async_wait<0>();  // no cp.async copy is left in flight
       __syncwarp();
     }
@@ -805,9 +833,9 @@ __global__ void __launch_bounds__(TcRoles<XAXIS>::THREADS, 1)
       }
       gbase += 2 * G::RA + NT * nt;
     }
-  } else if (XAXIS && role == 3) {
-    // A copy warp (x form): slice wq of chunk k (its producer warp's 32 rows)
-    // into stage k mod S once that producer warp has read the slice's previous
+  } else if (RL::COPY && role == 3) {
+    // A copy warp: slice wq of chunk k (the lines of lane quadrant wq) into stage
+    // k mod S once the quadrant's producer warps have read the slice's previous
     // chunk there
     enter(blockIdx.x);
     while (iu < n_units) {
@@ -998,7 +1026,7 @@ struct TcLaunch {
       if (vin && ob.lo[1] == ib.lo[1] && ob.n[1] == ib.n[1] && rows_map(&tin, in, ib)) flags |= 4;
       if (vout && rows_map(&tout, out, ob)) flags |= 8;
     }
-    k_rho_tc<RR, XAXIS, PROD><<<grid, TcRoles<XAXIS>::THREADS, G::smem(XAXIS, PROD), st>>>(in, ib, dims[axis], out, ob,
+    k_rho_tc<RR, XAXIS, PROD><<<grid, TcRoles<XAXIS, PROD>::THREADS, G::smem(XAXIS, PROD), st>>>(in, ib, dims[axis], out, ob,
                                                                                            axis, seg,
                                                                               flags, taps, tin, tout, ctl, pr);
     return cudaGetLastError();
